@@ -1,0 +1,231 @@
+"""CPU oracle for the moving-grid hybrid LBM -- TEST INFRASTRUCTURE ONLY.
+
+Plain serial FP64 C (``hlbm_oracle.c``) behind a ctypes wrapper.  Only the
+tests, the smoke check and the benchmark's CPU-baseline / reference arm may
+import this package; the product path (``paper_2006_13631_gb300``) never does.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hlbm_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libhlbm_oracle.so")
+
+DISC, INTERP, UNUSED = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (serial, -ffp-contract=off)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hlbm_oracle.h"))):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("bc_x", C.c_int), ("bc_y", C.c_int),
+        ("rho0", C.c_double), ("rho_init", C.POINTER(C.c_double)),
+        ("u0x", C.c_double), ("u0y", C.c_double),
+        ("ux_init", C.POINTER(C.c_double)), ("uy_init", C.POINTER(C.c_double)), ("tau_s", C.c_double),
+        ("L", C.c_double), ("T", C.c_double), ("xc", C.c_double), ("yc", C.c_double),
+        ("delta_f", C.c_double),
+        ("n_nodes", C.c_int), ("n_tris", C.c_int),
+        ("xy", C.POINTER(C.c_double)), ("tri", C.POINTER(C.c_int32)), ("kind", C.POINTER(C.c_int8)),
+        ("n_sub", C.c_int), ("lumped", C.c_int), ("motion", C.c_int),
+        ("A", C.c_double), ("omega", C.c_double), ("vx", C.c_double), ("vy", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        L.orc_create.restype = P
+        L.orc_create.argtypes = [C.POINTER(_Params)]
+        L.orc_destroy.argtypes = [P]
+        L.orc_step.argtypes = [P, C.c_int64]
+        L.orc_status.argtypes = [P]
+        L.orc_time.argtypes = [P]
+        L.orc_time.restype = C.c_int64
+        for name in ("orc_struct_f", "orc_patch_f"):
+            getattr(L, name).argtypes = [P, dp]
+        for name in ("orc_struct_macro", "orc_patch_macro"):
+            getattr(L, name).argtypes = [P, dp, dp, dp]
+        L.orc_struct_class.argtypes = [P, C.POINTER(C.c_int8)]
+        L.orc_refill_record.argtypes = [P, ip, ip]
+        L.orc_force.argtypes = [P, dp, dp]
+        L.orc_gamma.argtypes = [P, C.c_double, C.c_double, dp, dp, dp]
+        L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+        L.orc_locate.argtypes = [P, C.c_double, C.c_double, dp]
+        L.orc_fv_nnz.argtypes = [P]
+        L.orc_fv_coeffs.argtypes = [P, ip, ip, dp, dp, dp, dp]
+        L.orc_n_wall_segments.argtypes = [P]
+        L.orc_sine_fit.argtypes = [dp, C.c_int64, C.c_int64, C.c_double, dp, dp, dp]
+        L.orc_fv_periodic.argtypes = [C.c_int, dp, C.c_int, ip, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_int, C.c_int, dp]
+        L.orc_lbgk.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp]
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def feq(rho, ux, uy):
+    out = np.zeros(9)
+    lib().orc_feq(rho, ux, uy, _dp(out))
+    return out
+
+
+def sine_fit(F, t0, t1, omega):
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    a, b, r = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_sine_fit(_dp(F), t0, t1, omega, C.byref(a), C.byref(b), C.byref(r))
+    return a.value, b.value, r.value
+
+
+def fv_periodic(xy, tri, period_x, period_y, tau_u, dt_u, n_iter, f9, lumped=0):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    f = np.ascontiguousarray(f9, dtype=np.float64).copy()
+    lib().orc_fv_periodic(xy.shape[0], _dp(xy), tri.shape[0], _ip(tri), period_x, period_y, tau_u, dt_u,
+                          lumped, n_iter, _dp(f))
+    return f
+
+
+def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
+    f = np.ascontiguousarray(f9, dtype=np.float64).copy()
+    _, ny, nx = f.shape
+    lib().orc_lbgk(nx, ny, bc_x, bc_y, tau_s, n_iter, _dp(f))
+    return f
+
+
+class Oracle:
+    """Serial FP64 MG-HLBM run for one workload (see ``inputs.Workload``)."""
+
+    def __init__(self, w, mesh=None, rho_init=None, u_init=None):
+        self.w = w
+        self.mesh = mesh if mesh is not None else w.mesh()
+        rho = rho_init if rho_init is not None else w.rho_init()
+        self._keep = [np.ascontiguousarray(rho, dtype=np.float64),
+                      np.ascontiguousarray(self.mesh.xy, dtype=np.float64),
+                      np.ascontiguousarray(self.mesh.tri, dtype=np.int32),
+                      np.ascontiguousarray(self.mesh.kind, dtype=np.int8)]
+        p = _Params()
+        p.nx, p.ny, p.bc_x, p.bc_y = w.nx, w.ny, w.bc_x, w.bc_y
+        p.rho0 = w.rho0
+        p.rho_init = _dp(self._keep[0])
+        p.u0x, p.u0y = w.u0x, w.u0y
+        if u_init is not None:
+            self._keep += [np.ascontiguousarray(u_init[0], dtype=np.float64),
+                           np.ascontiguousarray(u_init[1], dtype=np.float64)]
+            p.ux_init, p.uy_init = _dp(self._keep[-2]), _dp(self._keep[-1])
+        p.tau_s = w.tau_s
+        p.L, p.T, p.xc, p.yc, p.delta_f = w.L, w.T, w.xc, w.yc, w.delta_f
+        p.n_nodes, p.n_tris = self.mesh.n_nodes, self.mesh.n_tris
+        p.xy = _dp(self._keep[1])
+        p.tri = _ip(self._keep[2])
+        p.kind = self._keep[3].ctypes.data_as(C.POINTER(C.c_int8))
+        p.n_sub, p.lumped, p.motion = w.n_sub, w.lumped, w.motion
+        p.A, p.omega, p.vx, p.vy = w.A, w.omega, w.vx, w.vy
+        self._h = lib().orc_create(C.byref(p))
+        self.n = self.mesh.n_nodes
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    def step(self, nsteps=1):
+        return lib().orc_step(self._h, nsteps)
+
+    @property
+    def status(self):
+        return lib().orc_status(self._h)
+
+    @property
+    def time(self):
+        return lib().orc_time(self._h)
+
+    def struct_f(self):
+        out = np.empty((9, self.w.ny, self.w.nx))
+        lib().orc_struct_f(self._h, _dp(out))
+        return out
+
+    def struct_macro(self):
+        r, ux, uy = (np.empty((self.w.ny, self.w.nx)) for _ in range(3))
+        lib().orc_struct_macro(self._h, _dp(r), _dp(ux), _dp(uy))
+        return r, ux, uy
+
+    def struct_class(self):
+        out = np.empty((self.w.ny, self.w.nx), dtype=np.int8)
+        lib().orc_struct_class(self._h, out.ctypes.data_as(C.POINTER(C.c_int8)))
+        return out
+
+    def patch_f(self):
+        out = np.empty((self.n, 9))
+        lib().orc_patch_f(self._h, _dp(out))
+        return out
+
+    def patch_macro(self):
+        r, ux, uy = (np.empty(self.n) for _ in range(3))
+        lib().orc_patch_macro(self._h, _dp(r), _dp(ux), _dp(uy))
+        return r, ux, uy
+
+    def refill_record(self):
+        t, d = np.empty(self.n, np.int32), np.empty(self.n, np.int32)
+        lib().orc_refill_record(self._h, _ip(t), _ip(d))
+        return t, d
+
+    def force(self):
+        n = self.time + 1
+        fx, fy = np.empty(n), np.empty(n)
+        lib().orc_force(self._h, _dp(fx), _dp(fy))
+        return fx, fy
+
+    def gamma(self, discard=1.0, fit=3.0):
+        re, im, r = C.c_double(), C.c_double(), C.c_double()
+        rc = lib().orc_gamma(self._h, discard, fit, C.byref(re), C.byref(im), C.byref(r))
+        if rc != 0:
+            raise ValueError(f"orc_gamma failed ({rc})")
+        return re.value, im.value, r.value
+
+    def locate(self, qx, qy):
+        lam = np.zeros(3)
+        k = lib().orc_locate(self._h, qx, qy, _dp(lam))
+        return k, lam
+
+    def fv_coeffs(self):
+        nnz = lib().orc_fv_nnz(self._h)
+        rp = np.empty(self.n + 1, np.int32)
+        col = np.empty(nnz, np.int32)
+        gx, gy, cc = np.empty(nnz), np.empty(nnz), np.empty(nnz)
+        vol = np.empty(self.n)
+        lib().orc_fv_coeffs(self._h, _ip(rp), _ip(col), _dp(gx), _dp(gy), _dp(cc), _dp(vol))
+        return rp, col, gx, gy, cc, vol
+
+    @property
+    def n_wall_segments(self):
+        return lib().orc_n_wall_segments(self._h)

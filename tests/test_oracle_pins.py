@@ -1,0 +1,378 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms (lattice isotropy, shear-wave decay, linear exactness of the P1
+control-volume scheme), invariants (conservation, uniform states), brute
+force on small inputs, or statements of the paper (Sec. 3, Sec. 4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+CS2 = 1.0 / 3.0
+
+
+# --------------------------------------------------------------------------
+# Eq. local_eq: moments of the D2Q9 equilibrium
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (1.03, 0.05, -0.02), (0.97, -0.1, 0.07)])
+def test_equilibrium_moments(rho, ux, uy):
+    f = oracle.feq(rho, ux, uy)
+    assert f.sum() == pytest.approx(rho, rel=1e-14)
+    assert (f * CX).sum() == pytest.approx(rho * ux, abs=1e-15)
+    assert (f * CY).sum() == pytest.approx(rho * uy, abs=1e-15)
+    # second moments: rho cs^2 delta + rho u u (exact for the 2nd-order equilibrium)
+    assert (f * CX * CX).sum() == pytest.approx(rho * CS2 + rho * ux * ux, abs=1e-15)
+    assert (f * CY * CY).sum() == pytest.approx(rho * CS2 + rho * uy * uy, abs=1e-15)
+    assert (f * CX * CY).sum() == pytest.approx(rho * ux * uy, abs=1e-15)
+    # D2Q9 third moments: rho cs^2 u (the cubic Maxwellian term is absent)
+    assert (f * CX * CX * CY).sum() == pytest.approx(rho * CS2 * uy, abs=1e-15)
+    assert (f * CX * CY * CY).sum() == pytest.approx(rho * CS2 * ux, abs=1e-15)
+
+
+def test_lattice_weights_isotropy():
+    w = oracle.feq(1.0, 0.0, 0.0)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert (w * CX ** 2).sum() == pytest.approx(CS2, abs=1e-15)
+    assert (w * CX ** 4).sum() == pytest.approx(3 * CS2 ** 2, abs=1e-15)
+    assert (w * CX ** 2 * CY ** 2).sum() == pytest.approx(CS2 ** 2, abs=1e-15)
+
+
+# --------------------------------------------------------------------------
+# eq. LBE: structured LBGK with the Sec. 5 boundaries
+# --------------------------------------------------------------------------
+def _eq_field(rho, ux, uy):
+    ny, nx = rho.shape
+    f = np.empty((9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            f[:, y, x] = oracle.feq(rho[y, x], ux[y, x], uy[y, x])
+    return f
+
+
+def _macro(f):
+    rho = f.sum(0)
+    return rho, (f * CX[:, None, None]).sum(0) / rho, (f * CY[:, None, None]).sum(0) / rho
+
+
+def _amp(uy, x, k):
+    return 2.0 * (uy.mean(0) * np.sin(k * x)).mean()
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.9])
+def test_lbgk_shear_wave_viscosity_and_conservation(tau):
+    """Decaying shear wave u_y = U sin(kx) e^{-nu k^2 t}, nu = cs^2 (tau - 1/2) (Sec. 3)."""
+    nx, ny, U = 64, 4, 1e-4
+    k = 2 * math.pi / nx
+    x = np.arange(nx)
+    uy = np.tile(U * np.sin(k * x), (ny, 1))
+    f = _eq_field(np.ones((ny, nx)), np.zeros((ny, nx)), uy)
+    m0, px0, py0 = f.sum(), (f * CX[:, None, None]).sum(), (f * CY[:, None, None]).sum()
+    f1 = oracle.lbgk(f, inputs.BC_PERIODIC, inputs.BC_PERIODIC, tau, 100)
+    f2 = oracle.lbgk(f1, inputs.BC_PERIODIC, inputs.BC_PERIODIC, tau, 600)
+    a1 = _amp(_macro(f1)[2], x, k)
+    a2 = _amp(_macro(f2)[2], x, k)
+    nu = math.log(a1 / a2) / (k * k * 600)
+    assert nu == pytest.approx(CS2 * (tau - 0.5), rel=0.01)
+    assert f2.sum() == pytest.approx(m0, rel=1e-13)
+    assert abs((f2 * CX[:, None, None]).sum() - px0) < 1e-13
+    assert abs((f2 * CY[:, None, None]).sum() - py0) < 1e-13
+
+
+def test_lbgk_bounce_back_channel_mode():
+    """Half-way bounce-back walls at x = -1/2 and x = nx - 1/2: the slowest
+    mode u_y = U sin(pi (x + 1/2) / nx) decays at nu (pi / nx)^2."""
+    nx, ny, tau, U = 32, 4, 0.8, 1e-4
+    k = math.pi / nx
+    x = np.arange(nx) + 0.5
+    uy = np.tile(U * np.sin(k * x), (ny, 1))
+    f = _eq_field(np.ones((ny, nx)), np.zeros((ny, nx)), uy)
+    f1 = oracle.lbgk(f, inputs.BC_WALL, inputs.BC_PERIODIC, tau, 200)
+    f2 = oracle.lbgk(f1, inputs.BC_WALL, inputs.BC_PERIODIC, tau, 800)
+    a1 = (_macro(f1)[2].mean(0) * np.sin(k * x)).sum()
+    a2 = (_macro(f2)[2].mean(0) * np.sin(k * x)).sum()
+    nu = math.log(a1 / a2) / (k * k * 800)
+    assert nu == pytest.approx(CS2 * (tau - 0.5), rel=0.02)
+
+
+def test_outflow_keeps_uniform_stream_and_walls_keep_rest():
+    ny, nx = 12, 10
+    f = _eq_field(np.ones((ny, nx)), np.zeros((ny, nx)), np.full((ny, nx), 0.03))
+    g = oracle.lbgk(f, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, 0.7, 50)
+    r, ux, uy = _macro(g)
+    assert np.abs(uy - 0.03).max() < 1e-14 and np.abs(ux).max() < 1e-14 and np.abs(r - 1).max() < 1e-14
+    f = _eq_field(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    g = oracle.lbgk(f, inputs.BC_WALL, inputs.BC_OUTFLOW, 0.7, 50)
+    r, ux, uy = _macro(g)
+    assert np.abs(uy).max() < 1e-15 and np.abs(ux).max() < 1e-15 and np.abs(r - 1).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# eq. ulbe: FV coefficients on median-dual control volumes
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small_case():
+    w = inputs.workload("lamina-small-f64")
+    mesh = w.mesh()
+    return w, mesh, oracle.Oracle(w, mesh=mesh)
+
+
+def test_fv_coefficients_closed_forms(small_case):
+    w, mesh, o = small_case
+    rp, col, gx, gy, cc, vol = o.fv_coeffs()
+    xy, tri = mesh.xy, mesh.tri
+    n = mesh.n_nodes
+    p0, p1, p2 = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    A2 = (p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1]) - (p2[:, 0] - p0[:, 0]) * (p1[:, 1] - p0[:, 1])
+    area = 0.5 * np.abs(A2)
+    # V_P = sum of |T|/3 over incident triangles; total = mesh area
+    V = np.zeros(n)
+    np.add.at(V, tri.ravel(), np.repeat(area / 3.0, 3))
+    assert np.allclose(vol, V, rtol=1e-13)
+    # gradient theorem: g_Pk = -(1/V_P) sum_T (|T|/3) grad phi_k|_T
+    g_ref = {}
+    c_ref = {}
+    for t in range(tri.shape[0]):
+        v = tri[t]
+        P = xy[v]
+        for a in range(3):
+            b, c = (a + 1) % 3, (a + 2) % 3
+            grad = np.array([P[b, 1] - P[c, 1], P[c, 0] - P[b, 0]]) / A2[t]
+            for piv in range(3):
+                key = (v[piv], v[a])
+                g_ref[key] = g_ref.get(key, 0.0) - area[t] / 3.0 * grad
+                c_ref[key] = c_ref.get(key, 0.0) + area[t] * (11.0 / 54.0 if piv == a else 7.0 / 108.0)
+    for P in range(0, n, 7):
+        for e in range(rp[P], rp[P + 1]):
+            gk = g_ref[(P, col[e])] / V[P]
+            assert gx[e] == pytest.approx(gk[0], abs=1e-11)
+            assert gy[e] == pytest.approx(gk[1], abs=1e-11)
+            assert cc[e] == pytest.approx(c_ref[(P, col[e])] / V[P], abs=1e-12)
+    # constant and linear exactness, partition of unity
+    for P in range(n):
+        s = slice(rp[P], rp[P + 1])
+        xk, yk = xy[col[s], 0], xy[col[s], 1]
+        assert abs(gx[s].sum()) < 1e-10 and abs(gy[s].sum()) < 1e-10
+        assert np.allclose([(gx[s] * xk).sum(), (gx[s] * yk).sum(), (gy[s] * xk).sum(), (gy[s] * yk).sum()],
+                           [-1.0, 0.0, 0.0, -1.0], atol=1e-9)
+        assert cc[s].sum() == pytest.approx(1.0, abs=1e-13)
+        assert cc[rp[P]] == pytest.approx(11.0 / 18.0, abs=1e-13)
+
+
+def test_fv_collision_first_moment_is_cv_centroid(small_case):
+    """sum_k C_Pk x_k = centroid of CV(P) (shoelace over the median-dual pieces)."""
+    w, mesh, o = small_case
+    rp, col, gx, gy, cc, vol = o.fv_coeffs()
+    xy, tri = mesh.xy, mesh.tri
+    mom = np.zeros((mesh.n_nodes, 2))
+    ar = np.zeros(mesh.n_nodes)
+    for t in range(tri.shape[0]):
+        v = tri[t]
+        P = xy[v]
+        G = P.mean(0)
+        for a in range(3):
+            q = np.array([P[a], 0.5 * (P[a] + P[(a + 1) % 3]), G, 0.5 * (P[a] + P[(a + 2) % 3])])
+            x, y = q[:, 0], q[:, 1]
+            xn, yn = np.roll(x, -1), np.roll(y, -1)
+            cr = x * yn - xn * y
+            A = 0.5 * cr.sum()
+            ar[v[a]] += abs(A)
+            mom[v[a]] += np.sign(A) * np.array([((x + xn) * cr).sum(), ((y + yn) * cr).sum()]) / 6.0
+    for P in range(0, mesh.n_nodes, 5):
+        s = slice(rp[P], rp[P + 1])
+        c = np.array([(cc[s] * xy[col[s], 0]).sum(), (cc[s] * xy[col[s], 1]).sum()])
+        assert np.allclose(c, mom[P] / ar[P], atol=1e-11)
+
+
+def test_fv_periodic_shear_wave_viscosity_and_conservation():
+    """FV-LBM on a jittered periodic triangulation: nu = cs^2 tau_u (Sec. 3),
+    exact conservation of mass and momentum, and a uniform state is a fixed point."""
+    n, Lx = 32, 32.0
+    xy, tri = inputs.periodic_mesh(n, n, Lx, Lx, jitter=0.15, seed=3)
+    tau_u, dt_u, U = 0.3, 0.02, 1e-4
+    k = 2 * math.pi / Lx
+    f0 = np.array([oracle.feq(1.0, 0.0, U * math.sin(k * x)) for x in xy[:, 0]])
+    f1 = oracle.fv_periodic(xy, tri, Lx, Lx, tau_u, dt_u, 2500, f0)
+    f2 = oracle.fv_periodic(xy, tri, Lx, Lx, tau_u, dt_u, 5000, f1)
+
+    def amp(f):
+        rho = f.sum(1)
+        uy = (f * CY).sum(1) / rho
+        return 2 * (uy * np.sin(k * xy[:, 0])).mean()
+
+    nu = math.log(amp(f1) / amp(f2)) / (k * k * 5000 * dt_u)
+    assert nu == pytest.approx(CS2 * tau_u, rel=0.02)
+    # median-dual volumes of a periodic mesh: build them the plain way
+    p0, p1, p2 = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    d1, d2 = p1 - p0, p2 - p0
+    d1 -= Lx * np.round(d1 / Lx)
+    d2 -= Lx * np.round(d2 / Lx)
+    area = 0.5 * np.abs(d1[:, 0] * d2[:, 1] - d2[:, 0] * d1[:, 1])
+    V = np.zeros(len(xy))
+    np.add.at(V, tri.ravel(), np.repeat(area / 3.0, 3))
+    assert V.sum() == pytest.approx(Lx * Lx, rel=1e-12)
+    # the streaming term conserves each sum_P V_P f_i; the collision term
+    # conserves mass and momentum (sum_i f^neq = sum_i c_i f^neq = 0)
+    for f in (f1, f2):
+        assert (V[:, None] * f).sum() == pytest.approx((V[:, None] * f0).sum(), rel=1e-13)
+        assert abs((V[:, None] * f * CX).sum() - (V[:, None] * f0 * CX).sum()) < 1e-12
+        assert abs((V[:, None] * f * CY).sum() - (V[:, None] * f0 * CY).sum()) < 1e-12
+    fu = np.tile(oracle.feq(1.01, 0.02, -0.03), (len(xy), 1))
+    g = oracle.fv_periodic(xy, tri, Lx, Lx, tau_u, dt_u, 50, fu)
+    assert np.abs(g - fu).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Sec. 4: point location (type 3), brute force on a small mesh
+# --------------------------------------------------------------------------
+def test_point_location_matches_brute_force(small_case):
+    w, mesh, o = small_case
+    xy, tri = mesh.xy, mesh.tri
+    rng = np.random.default_rng(5)
+    pts = np.concatenate([
+        rng.uniform(xy.min(0) - 0.5, xy.max(0) + 0.5, size=(400, 2)),
+        xy[::3],                                             # mesh nodes (ties)
+        0.5 * (xy[tri[::4, 0]] + xy[tri[::4, 1]]),           # edge midpoints (ties)
+    ])
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    x1, y1, x2, y2 = b[:, 0] - a[:, 0], b[:, 1] - a[:, 1], c[:, 0] - a[:, 0], c[:, 1] - a[:, 1]
+    det = x1 * y2 - x2 * y1
+    for q in pts:
+        px, py = q[0] - a[:, 0], q[1] - a[:, 1]
+        lb = (px * y2 - x2 * py) / det
+        lc = (x1 * py - px * y1) / det
+        la = (1.0 - lb) - lc
+        mn = np.minimum(np.minimum(la, lb), lc)
+        ok = mn >= -1e-12
+        if not ok.any():
+            expect = -1
+        else:
+            best = mn[ok].max()
+            expect = int(np.flatnonzero(ok & (mn == best))[0])
+        k, lam = o.locate(q[0], q[1])
+        assert k == expect
+        if k >= 0:
+            assert np.array_equal(lam, [la[k], lb[k], lc[k]])
+
+
+# --------------------------------------------------------------------------
+# whole hybrid step: invariants and statements of Sec. 4
+# --------------------------------------------------------------------------
+def _translating_case(vx, vy, h1=0.2):
+    w = inputs.Workload("zero-disturbance", 64, 60, 12.0, 0.24, 30.3, 28.2, 0.7, 10, inputs.MOTION_UNIFORM,
+                        vx=vx, vy=vy, delta_f=1.8, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                        u0x=vx, u0y=vy,
+                        mesh_args=dict(n_L=24, n_T=1, n_layers=8, h1=h1, d_out=3.6))
+    return w
+
+
+def test_zero_disturbance_patch_translating_with_uniform_flow():
+    """A lamina and its patch translating with a uniform stream leave the
+    stream undisturbed: every interpolation reproduces constants (Sec. 4),
+    the FV streaming operator annihilates constants, and the wall velocity
+    equals the fluid velocity."""
+    w = _translating_case(0.02, 0.03)
+    o = oracle.Oracle(w)
+    o.step(120)  # the patch crosses several lattice cells in x and y
+    assert o.status == 0
+    r, ux, uy = o.struct_macro()
+    disc = o.struct_class() == oracle.DISC
+    assert np.abs(ux[disc] - 0.02).max() < 1e-12 and np.abs(uy[disc] - 0.03).max() < 1e-12
+    assert np.abs(r[disc] - 1.0).max() < 1e-12
+    r, ux, uy = o.patch_macro()
+    assert np.abs(ux - 0.02).max() < 1e-12 and np.abs(uy - 0.03).max() < 1e-12
+    assert np.abs(r - 1.0).max() < 1e-12
+    types, donors = o.refill_record()
+    assert set(np.unique(types)) <= {0, 1, 3} and (types == 1).any() and (types == 3).any()
+
+
+def test_type2_absent_when_spacing_exceeds_displacement_and_present_otherwise():
+    """Sec. 4: with the minimum node spacing above the per-step displacement
+    no node falls inside the body (type 2); a coarse step produces them."""
+    o = oracle.Oracle(_translating_case(0.0, 0.15, h1=0.2))
+    o.step(2)
+    types, _ = o.refill_record()
+    assert not (types == 2).any()
+    o = oracle.Oracle(_translating_case(0.0, 0.3, h1=0.1))
+    o.step(2)
+    types, _ = o.refill_record()
+    assert (types == 2).any()
+    assert o.status == 0
+
+
+def test_classification_statements(small_case):
+    """Sec. 4: interpolation nodes are unused nodes with a discretization
+    neighbour; every discretization node's lattice neighbours are computed."""
+    w = inputs.workload("lamina-small-f64")
+    o = oracle.Oracle(w)
+    o.step(3)
+    cls = o.struct_class()
+    ny, nx = cls.shape
+    for y in range(1, ny - 1):
+        for x in range(1, nx - 1):
+            nb = [cls[y + dy, x + dx] for dx, dy in zip(CX[1:], CY[1:])]
+            if cls[y, x] == oracle.DISC:
+                assert all(c != oracle.UNUSED for c in nb)
+            elif cls[y, x] == oracle.INTERP:
+                assert any(c == oracle.DISC for c in nb)
+            else:
+                assert all(c != oracle.DISC for c in nb)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1: hydrodynamic function
+# --------------------------------------------------------------------------
+def test_sine_fit_recovers_phasor():
+    om, F0, phi = 0.013, 2.5, -0.7
+    t = np.arange(3000)
+    F = F0 * np.sin(om * t + phi)
+    a, b, rms = oracle.sine_fit(F, 500, 2400, om)
+    assert a == pytest.approx(F0 * math.cos(phi), abs=1e-12)
+    assert b == pytest.approx(F0 * math.sin(phi), abs=1e-12)
+    assert rms < 1e-12
+
+
+def test_hybrid_disk_patch_reproduces_lbgk_shear_wave():
+    """A body-free disk patch inside a periodic LBGK lattice must carry a
+    decaying shear wave exactly as the plain LBGK does (same viscosity,
+    nu = cs^2 (tau_s - 1/2) = cs^2 tau_u, Sec. 3): the interface equations
+    (eq. postcollision2_s, the stress continuity of eq. continuity_stresses
+    and the outer-node feed) transfer f^neq with the right factors.  Wrong
+    factors give 30-250 times the error bound used here."""
+    nx = ny = 64
+    U, tau, nsteps = 1e-3, 0.8, 300
+    k = 2 * math.pi / nx
+    w = inputs.Workload("disk-shear", nx, ny, 0.0, 0.0, 32.3, 32.2, tau, 20, inputs.MOTION_STATIC, delta_f=3.0,
+                        bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                        mesh_args=dict(n_L=0, n_T=0, n_layers=12, h1=0.5, d_out=6.0))
+    mesh = w.mesh()
+    x = np.tile(np.arange(nx, dtype=float), (ny, 1))
+    uy0 = U * np.sin(k * x)
+    o = oracle.Oracle(w, mesh=mesh, rho_init=np.ones((ny, nx)), u_init=(np.zeros((ny, nx)), uy0))
+    o.step(nsteps)
+    assert o.status == 0
+    fr = oracle.lbgk(_eq_field(np.ones((ny, nx)), np.zeros((ny, nx)), uy0), inputs.BC_PERIODIC,
+                     inputs.BC_PERIODIC, tau, nsteps)
+    rr, uxr, uyr = _macro(fr)
+    amp = U * math.exp(-(tau - 0.5) / 3 * k * k * nsteps)
+    r, ux, uy = o.struct_macro()
+    d = o.struct_class() == oracle.DISC
+    assert np.abs(uy - uyr)[d].max() < 2e-3 * amp
+    assert np.abs(ux - uxr)[d].max() < 2e-3 * amp
+    pr, pux, puy = o.patch_macro()
+    px, py = mesh.xy[:, 0] + w.xc, mesh.xy[:, 1] + w.yc
+    ix, iy = np.floor(px).astype(int), np.floor(py).astype(int)
+    fx, fy = px - ix, py - iy
+
+    def bil(a):
+        return (a[iy, ix] * (1 - fx) * (1 - fy) + a[iy, ix + 1] * fx * (1 - fy)
+                + a[iy + 1, ix] * (1 - fx) * fy + a[iy + 1, ix + 1] * fx * fy)
+
+    assert np.abs(puy - bil(uyr)).max() < 3e-3 * amp
+    assert np.abs(pux - bil(uxr)).max() < 3e-3 * amp
