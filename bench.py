@@ -1,0 +1,299 @@
+"""Throughput of the moving-grid hybrid LBM step on GB300.
+
+One bench "step" is one lattice step of the whole hot path: relocation and
+refill of the patch, lattice classification, eq. 178 feed, stream-collide,
+n FV sub-steps with the outer-node feed, and the lamina force.
+
+Metric: MLUPS over both grids, (lattice discretization nodes + patch nodes)
+x steps / s / 1e6 (each grid counted once per lattice step); the variant that
+counts the patch n times (sub-steps) is reported as ``mlups_subiter``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...     # the CPU oracle, bounded sample
+Under torchrun every rank runs its own replica of the workload on its GPU
+(weak scaling; the instances share nothing).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (both grids)"
+UNIT = "MLUPS"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores, on a bounded sample of the
+    same workload (rank 0 only)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import inputs
+    import oracle
+
+    w = inputs.workload(args.workload)
+    mesh = w.mesh()
+    rho = w.rho_init()
+    o = oracle.Oracle(w, mesh=mesh, rho_init=rho)
+    warm = min(args.warmup, 1)
+    o.step(warm)
+    # bounded sample: as many of the K requested steps as fit in ~60 s of CPU work
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    k = max(1, min(args.steps - 1, int(60.0 / max(per, 1e-3)) - 1))
+    o.step(k)
+    t2 = time.perf_counter()
+    steps = k + 1
+    secs = t2 - t0
+    n_disc = int((o.struct_class() == oracle.DISC).sum())
+    units = (n_disc + mesh.n_nodes) * steps
+    value = units / secs / 1e6
+    sample = (f"{steps} of {args.steps} requested lattice steps of {w.name} after {warm} warm-up, "
+              f"serial FP64 oracle (one host thread)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": f"{w.nx}x{w.ny}", "patch_nodes": mesh.n_nodes,
+                       "n_sub": w.n_sub},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(workload):
+    import inputs
+    import oracle
+
+    w = inputs.workload(workload)
+    mesh = w.mesh()
+    o = oracle.Oracle(w, mesh=mesh)
+    t0 = time.perf_counter()
+    o.step(2)
+    secs = time.perf_counter() - t0
+    n_disc = int((o.struct_class() == oracle.DISC).sum())
+    return {"value": (n_disc + mesh.n_nodes) * 2 / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"2 lattice steps of {w.name} from the initial state, serial FP64 oracle"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2006_13631_gb300 import Solver, hlbm as H
+    from paper_2006_13631_gb300.build import build
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build()
+    w = inputs.workload(args.workload)
+    mesh = w.mesh()
+    rho = w.rho_init()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = Solver(w, mesh=mesh, rho_init=rho, stream=stream.cuda_stream)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        info = s.info()
+        n_disc, n_u = info["n_struct_disc"], info["n_nodes"]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.5)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.profile(True)
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        phases = s.profile_read()
+        s.profile(False)
+        status = s.status
+        _, fy = s.force()
+        finite = bool(np.isfinite(fy).all())
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units_per_rank = (n_disc + n_u) * args.steps
+    value = world * units_per_rank / (ms / 1e3) / 1e6
+    mlups_subiter = world * (n_disc + w.n_sub * n_u) * args.steps / (ms / 1e3) / 1e6
+
+    # roofline of the dominant phase (largest share of the timed region)
+    peak, peak_kind = _peaks()
+    bytes_per = 4 if w.dtype == "f32" else 8
+    dom = max(phases, key=lambda p: phases[p][0])
+    st_ms, st_n = phases["stream"]
+    stream_bytes = 18 * bytes_per * n_disc  # 9 populations read + 9 written per discretization node
+    stream_gbs = stream_bytes / (st_ms / st_n / 1e3) / 1e9 if st_n else None
+    fv_ms, fv_n = phases["fv"]
+    nnz = info["nnz"]
+    # per FV sub-step launch: the patch state read and written once, plus the
+    # CSR rows (column index and three coefficients per entry)
+    fv_bytes = 18 * bytes_per * n_u + nnz * (4 + 3 * bytes_per)
+    fv_gbs = fv_bytes / (fv_ms / fv_n / 1e3) / 1e9 if fv_n else None
+    traffic = None
+    tr_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_file):
+        try:
+            traffic = json.load(open(tr_file)).get(f"{w.name}:stream")
+        except Exception:
+            traffic = None
+    roof = {"bound": "hbm", "kernel": "stream_collide", "achieved": stream_gbs, "peak": peak, "unit": "GB/s",
+            "frac": stream_gbs / peak if stream_gbs else None, "traffic": traffic,
+            "peak_source": peak_kind, "dominant_phase": dom,
+            "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases},
+            "fv_substep_gbs": fv_gbs}
+    launches = sum(v[1] for v in phases.values())
+
+    # end to end through the public API from host buffers
+    e2e = None
+    if not args.no_e2e:
+        k_e2e = max(1, min(args.steps, 50))
+        rho_pinned = torch.from_numpy(rho).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            s2 = Solver(w, mesh=mesh, rho_init=rho_pinned.numpy(), stream=stream.cuda_stream)
+            for k in range(k_e2e):
+                H.hlbm_step(s2.h, 1)
+                H.hlbm_force(s2.h, k + 1, 1)
+            s2.close()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        h2d = rho.nbytes + mesh.xy.nbytes + mesh.tri.nbytes + mesh.kind.nbytes
+        e2e = {"value": world * (n_disc + n_u) * k_e2e / secs / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / k_e2e, "d2h_bytes_per_step": 16,
+               "note": f"{k_e2e} steps incl. creation from host arrays and a force read-back every step"}
+    s.close()
+    if rank != 0:
+        return 0
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.workload)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+            "config": {"workload": w.name, "lattice": f"{w.nx}x{w.ny}", "chord": w.L, "patch_nodes": n_u,
+                       "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)" % (9 * bytes_per * w.nx * w.ny / 1e6)},
+            "mlups_subiter": mlups_subiter, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lamina-4096-f32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/* hlbm.h -- C ABI of the GB300 moving-grid hybrid lattice Boltzmann solver.
+ *
+ * The solver advances the flow around a rigid lamina that moves through a
+ * viscous fluid, as in Di Ilio, Chiappini, Ubertini, Bella, Succi, "A
+ * moving-grid approach for fluid-structure interaction problems with hybrid
+ * lattice Boltzmann method":
+ *   - D2Q9 BGK stream-collide on a fixed Cartesian lattice (Sec. 3, eq. LBE,
+ *     eq. local_eq) with no-slip side walls and outflow top/bottom (Sec. 5);
+ *   - a cell-vertex finite-volume LB update on a triangular patch fitted to
+ *     the body, sub-cycled n times per lattice step (Sec. 3, eq. ulbe);
+ *   - the coupling of the two grids at interpolation nodes (eq.
+ *     postcollision2_s, eq. postcollision2_u);
+ *   - the per-step relocation of the patch and the refill of its nodes
+ *     (Sec. 4, types 1/2/3, eq. continuity_stresses);
+ *   - the force on the lamina and the complex hydrodynamic function
+ *     Theta (Sec. 2.1, eq. force_phasor).
+ *
+ * Conventions for every call:
+ *   - Lattice units: dx = dt = 1 on the Cartesian lattice, c_s^2 = 1/3.
+ *   - Every pointer argument is HOST memory unless stated otherwise.  Input
+ *     arrays are copied during the call; the caller keeps ownership.
+ *   - All device memory belongs to the solver.  It is obtained from the
+ *     allocator installed with hlbm_set_allocator (cudaMalloc otherwise) and
+ *     released by hlbm_destroy.
+ *   - Calls return HLBM_OK (0) or a negative HLBM_E* code; the message of
+ *     the last failure is available from hlbm_last_error.  Nothing aborts
+ *     the process.
+ *   - hlbm_step only enqueues work on the solver's stream and returns;
+ *     the hlbm_get_* / hlbm_force / hlbm_gamma / hlbm_status calls
+ *     synchronise that stream.
+ *   - A handle is used from one host thread at a time.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define HLBM_OK 0
+#define HLBM_EINVAL (-1)    /* invalid argument or configuration          */
+#define HLBM_ECUDA (-2)     /* a CUDA runtime call failed                 */
+#define HLBM_EUNSTABLE (-3) /* NaN/Inf in the force: the run diverged     */
+#define HLBM_EGEOM (-4)     /* a geometric precondition failed on device  */
+#define HLBM_ENOMEM (-5)    /* device allocation failed                   */
+
+/* boundary kinds of the Cartesian domain sides (Sec. 5) */
+#define HLBM_BC_WALL 0     /* half-way bounce-back no-slip wall          */
+#define HLBM_BC_OUTFLOW 1  /* zero-gradient outflow                      */
+#define HLBM_BC_PERIODIC 2
+
+/* storage and arithmetic precision of the populations */
+#define HLBM_F64 0
+#define HLBM_F32 1
+
+/* patch node kinds (Sec. 4) */
+#define HLBM_NODE_INTERIOR 0 /* discretization node                       */
+#define HLBM_NODE_OUTER 1    /* outer boundary = interpolation node        */
+#define HLBM_NODE_WALL 2     /* on the lamina surface                      */
+
+/* motion kinds (Sec. 2: y(t) = A sin(w t)) */
+#define HLBM_MOTION_STATIC 0
+#define HLBM_MOTION_HARMONIC 1 /* X = 0, Y = A sin(w t)                   */
+#define HLBM_MOTION_UNIFORM 2  /* X = vx t, Y = vy t                      */
+
+/* status bits reported by hlbm_status (device-side checks) */
+#define HLBM_ST_FILL_NOT_LOCATED 1u   /* eq. 178 node outside the patch     */
+#define HLBM_ST_DONOR_NOT_COMPUTED 2u /* bilinear donor not a computed node */
+#define HLBM_ST_NONFINITE 8u          /* NaN/Inf in the lamina force        */
+#define HLBM_ST_UNUSED_TO_DISC 16u    /* lattice node skipped a class       */
+
+/* Cartesian lattice: nx*ny nodes at integer positions (x, y), row-major.
+ * rho_init / ux_init / uy_init: optional host arrays [ny*nx] of the initial
+ * density and velocity (the state starts at equilibrium); NULL selects rho0
+ * and (u0x, u0y) everywhere. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t bc_x, bc_y; /* sides x = 0, nx-1 and y = 0, ny-1 */
+    int32_t dtype;      /* HLBM_F64 | HLBM_F32 */
+    double rho0;
+    double u0x, u0y;
+    const double* rho_init;
+    const double* ux_init;
+    const double* uy_init;
+} hlbm_grid_t;
+
+/* Body-fitted triangular patch around the lamina (Sec. 3, Sec. 4).
+ * xy: [n_nodes*2] node coordinates in the body frame (origin at the lamina
+ * centre); tri: [n_tris*3] node indices; kind: [n_nodes] HLBM_NODE_*.
+ * The lamina is the rectangle |x| <= L/2, |y| <= T/2 of the body frame,
+ * centred at (x_c, y_c) at t = 0.  Lattice nodes inside the rounded
+ * rectangle at offset delta_f (the fictitious curve) are unused.  n_sub FV
+ * sub-steps are taken per lattice step (dt_s = n_sub dt_u).  lumped = 1
+ * replaces the consistent collision matrix C_ik by the identity. */
+typedef struct {
+    int32_t n_nodes, n_tris;
+    const double* xy;
+    const int32_t* tri;
+    const int8_t* kind;
+    double lamina_L, lamina_T;
+    double x_c, y_c;
+    double delta_f;
+    int32_t n_sub;
+    int32_t lumped;
+} hlbm_patch_t;
+
+typedef struct {
+    int32_t kind; /* HLBM_MOTION_* */
+    double A, omega;
+    double vx, vy;
+} hlbm_motion_t;
+
+typedef struct hlbm hlbm_t;
+
+/* Device allocator hook used by every later hlbm_create.  alloc returns a
+ * device pointer of at least `bytes` usable on `stream` (NULL on failure);
+ * release frees it.  Passing NULLs restores cudaMalloc/cudaFree. */
+typedef void* (*hlbm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*hlbm_free_fn)(void* ptr, void* stream, void* ctx);
+int hlbm_set_allocator(hlbm_alloc_fn alloc, hlbm_free_fn release, void* ctx);
+
+/* Build a solver (Sec. 2 problem statement): copies the mesh, derives the FV
+ * matrices S_ik = c_i . g_Pk and C_ik of eq. ulbe on median-dual control
+ * volumes, the wall segments and the point-location bins, sets the initial
+ * equilibrium state and fills the patch from the lattice by the type-1
+ * rule of Sec. 4.  tau_s is the lattice relaxation time; the patch uses
+ * tau_u = tau_s - 1/2 (same viscosity, Sec. 3).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) on which all work is queued.
+ * Returns HLBM_EINVAL when the time step is unstable (dt_u >= 2 tau_u,
+ * Sec. 7), when the patch is too thin for the per-step displacement, or
+ * when the patch can come closer than 4 nodes to the lattice edge. */
+int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s,
+                const hlbm_motion_t* motion, void* cuda_stream, hlbm_t** out);
+
+/* Advance nsteps lattice steps (asynchronous).  Each step: move the patch
+ * to y(t) and refill it (Sec. 4), reclassify the lattice nodes, feed the
+ * lattice interpolation nodes from the patch (eq. postcollision2_s), one
+ * stream-collide of eq. LBE, n_sub FV sub-steps of eq. ulbe with the outer
+ * patch nodes fed from the lattice (eq. postcollision2_u), and the force on
+ * the lamina at the new time. */
+int hlbm_step(hlbm_t* h, int64_t nsteps);
+
+/* Copy the force history (per unit length, fluid on lamina) for times
+ * first .. first+count-1 into fx, fy.  Time 0 is the initial state. */
+int hlbm_force(hlbm_t* h, int64_t first, int64_t count, double* fx, double* fy);
+
+/* Hydrodynamic function Theta = F-hat / ((pi/4) rho0 w^2 L^2 A) from a
+ * least-squares fit F_y(t) = a sin(w t) + b cos(w t) over
+ * t in [discard_periods, discard_periods + fit_periods] periods (Sec. 2.1;
+ * the paper discards 1 period and fits 3).  re = a/N, im = b/N; rms is the
+ * fit residual in the same units.  HARMONIC motion only. */
+int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re, double* im,
+               double* rms);
+
+/* Macroscopic fields at the current time: lattice [ny*nx] (values at
+ * nodes that are not discretization nodes are unspecified) and patch
+ * [n_nodes].  Any pointer may be NULL. */
+int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double* rho_u,
+                    double* ux_u, double* uy_u);
+
+/* Node classes of the last step on the whole lattice [ny*nx]:
+ * 0 discretization, 1 interpolation, 2 unused (Sec. 4). */
+int hlbm_get_class(hlbm_t* h, int8_t* cls);
+
+/* Refill record of the last relocation, per patch node: type 0 (wall),
+ * 1, 2 or 3 (Sec. 4); donor = enclosing triangle (type 3), lattice cell
+ * iy*nx+ix of the bilinear stencil (type 1), else -1. */
+int hlbm_get_refill(hlbm_t* h, int32_t* type, int32_t* donor);
+
+/* Patch populations at the current time, [n_nodes*9] node-major. */
+int hlbm_get_patch_f(hlbm_t* h, double* f9);
+
+/* FV matrices as built on the device: CSR rows per node (pivot first),
+ * S_ik = c_i . (gx, gy), C_ik = cc.  Sizes from hlbm_info. */
+int hlbm_get_fv(hlbm_t* h, int32_t* row_ptr, int32_t* col, double* gx, double* gy, double* cc);
+
+typedef struct {
+    int64_t time;          /* current time (steps taken)                  */
+    int64_t n_struct;      /* nx*ny                                        */
+    int64_t n_struct_disc; /* discretization nodes in the last step       */
+    int32_t n_nodes, n_tris, nnz, n_outer, n_wall_segments;
+    int32_t box_w, box_h;  /* lattice window that follows the patch       */
+    int32_t launches_per_step;
+    int32_t dtype;
+} hlbm_info_t;
+int hlbm_info(hlbm_t* h, hlbm_info_t* info);
+
+/* Per-phase device time, measured with CUDA events recorded on the
+ * solver's stream around each phase of hlbm_step while profiling is on.
+ * hlbm_profile(h, 1) starts recording and clears the totals; (h, 0) stops.
+ * hlbm_profile_read fills ms[HLBM_N_PHASES] (summed milliseconds) and
+ * launches[HLBM_N_PHASES] (kernel launches) and synchronises the stream. */
+#define HLBM_PHASE_MOVE 0   /* refill, classification, eq. 178 feed      */
+#define HLBM_PHASE_STREAM 1 /* lattice stream-collide (eq. LBE)          */
+#define HLBM_PHASE_FV 2     /* outer-node feed and FV sub-steps          */
+#define HLBM_PHASE_FORCE 3  /* force on the lamina                       */
+#define HLBM_N_PHASES 4
+int hlbm_profile(hlbm_t* h, int enable);
+int hlbm_profile_read(hlbm_t* h, double* ms, int64_t* launches);
+
+/* Device status bits (HLBM_ST_*), accumulated since creation. */
+int hlbm_status(hlbm_t* h, uint32_t* bits);
+
+/* Message of the last failed call on h; with h == NULL, of the last failed
+ * hlbm_create on this thread. */
+const char* hlbm_last_error(const hlbm_t* h);
+void hlbm_destroy(hlbm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -345,14 +345,28 @@ def workload(name: str) -> Workload:
         KC = 2.0 * math.pi * eps
         A, om, tau = harmonic_params(L, KC, beta, vmax=0.02)
         n = int(5 * L)
-        tau_u = tau - 0.5
-        n_sub = max(50, int(math.ceil(1.0 / (1.6 * tau_u))))
-        w = Workload(name, n, n, L, L / 100.0, 0.5 * n + 0.3, 0.5 * n + 0.2, tau, n_sub, MOTION_HARMONIC,
+        w = Workload(name, n, n, L, L / 100.0, 0.5 * n + 0.3, 0.5 * n + 0.2, tau, 50, MOTION_HARMONIC,
                      A=A, omega=om, delta_f=2.0, dtype="f64",
-                     mesh_args=dict(n_L=int(2 * L), n_T=2, n_layers=14, h1=0.1, d_out=4.0))
+                     mesh_args=dict(n_L=int(2 * L), n_T=2, n_layers=14, h1=0.2, d_out=4.0))
+        w.n_sub = stable_substeps(w.mesh(), tau - 0.5, minimum=50)
         w.steps = int(math.floor(4 * w.period)) + 1
         return w
     raise KeyError(name)
+
+
+def min_edge(mesh: PatchMesh) -> float:
+    e = np.concatenate([mesh.tri[:, [0, 1]], mesh.tri[:, [1, 2]], mesh.tri[:, [2, 0]]])
+    return float(np.linalg.norm(mesh.xy[e[:, 0]] - mesh.xy[e[:, 1]], axis=1).min())
+
+
+def stable_substeps(mesh: PatchMesh, tau_u: float, minimum: int = 1) -> int:
+    """Sub-steps n with dt_u = 1/n below 2 tau_u (Sec. 7) and, with a factor 3
+    of margin, below the diffusive limit h^2 / (|c|^2 tau_u) of the explicit
+    central-flux FV update on the smallest edge h (|c|^2 = 2, diagonal
+    velocities)."""
+    h = min_edge(mesh)
+    n = max(minimum, int(math.ceil(1.0 / (1.9 * tau_u))), int(math.ceil(3.0 * 2.0 * tau_u / (h * h))))
+    return n
 
 
 def derived(w: Workload) -> dict:

@@ -69,6 +69,8 @@ def lib():
         for name in ("orc_struct_macro", "orc_patch_macro"):
             getattr(L, name).argtypes = [P, dp, dp, dp]
         L.orc_struct_class.argtypes = [P, C.POINTER(C.c_int8)]
+        L.orc_classify_at.argtypes = [P, C.c_int64, C.POINTER(C.c_int8)]
+        L.orc_relocate_at.argtypes = [P, C.c_int64, ip, ip]
         L.orc_refill_record.argtypes = [P, ip, ip]
         L.orc_force.argtypes = [P, dp, dp]
         L.orc_gamma.argtypes = [P, C.c_double, C.c_double, dp, dp, dp]
@@ -183,6 +185,16 @@ class Oracle:
         out = np.empty((self.w.ny, self.w.nx), dtype=np.int8)
         lib().orc_struct_class(self._h, out.ctypes.data_as(C.POINTER(C.c_int8)))
         return out
+
+    def classify_at(self, t):
+        out = np.empty((self.w.ny, self.w.nx), dtype=np.int8)
+        lib().orc_classify_at(self._h, t, out.ctypes.data_as(C.POINTER(C.c_int8)))
+        return out
+
+    def relocate_at(self, t):
+        ty, d = np.empty(self.n, np.int32), np.empty(self.n, np.int32)
+        lib().orc_relocate_at(self._h, t, _ip(ty), _ip(d))
+        return ty, d
 
     def patch_f(self):
         out = np.empty((self.n, 9))

@@ -966,6 +966,45 @@ int orc_step(orc_t* o, int64_t nsteps) {
     return o->status;
 }
 
+/* geometry only, for any time t >= 1 without advancing the run: the node
+ * classes of step t and the refill types and donors of the relocation
+ * t-1 -> t (Sec. 4) */
+void orc_classify_at(orc_t* o, int64_t t, int8_t* cls) {
+    double X, Y;
+    motion_pos(&o->p, t, &X, &Y);
+    classify(o, o->p.xc + X, o->p.yc + Y, cls);
+}
+
+void orc_relocate_at(const orc_t* o, int64_t t, int32_t* type, int32_t* donor) {
+    double X0, Y0, X1, Y1;
+    motion_pos(&o->p, t - 1, &X0, &Y0);
+    motion_pos(&o->p, t, &X1, &Y1);
+    double dX = X1 - X0, dY = Y1 - Y0;
+    double cx = o->p.xc + X1, cy = o->p.yc + Y1;
+    double a = 0.5 * o->p.L, b = 0.5 * o->p.T;
+    for (int P = 0; P < o->p.n_nodes; ++P) {
+        if (o->kind[P] == ORC_KIND_WALL) {
+            type[P] = 0;
+            donor[P] = -1;
+            continue;
+        }
+        double qx = o->xy[2 * P] + dX, qy = o->xy[2 * P + 1] + dY;
+        double lam[3];
+        int k = locate(o, qx, qy, lam);
+        if (k >= 0) {
+            type[P] = 3;
+            donor[P] = k;
+        } else if (fabs(qx) <= a && fabs(qy) <= b) {
+            type[P] = 2;
+            donor[P] = -1;
+        } else {
+            double wx = cx + o->xy[2 * P], wy = cy + o->xy[2 * P + 1];
+            type[P] = 1;
+            donor[P] = (int)floor(wy) * o->p.nx + (int)floor(wx);
+        }
+    }
+}
+
 int orc_status(const orc_t* o) { return o->status; }
 int64_t orc_time(const orc_t* o) { return o->t; }
 

@@ -75,6 +75,10 @@ void orc_force(const orc_t* o, double* fx, double* fy);
 int orc_gamma(const orc_t* o, double discard_periods, double fit_periods,
               double* re, double* im, double* rms);
 
+/* geometry only (no state change): classes of step t, refill record of t-1 -> t */
+void orc_classify_at(orc_t* o, int64_t t, int8_t* cls);
+void orc_relocate_at(const orc_t* o, int64_t t, int32_t* type, int32_t* donor);
+
 /* building blocks exposed for the pins */
 void orc_feq(double rho, double ux, double uy, double* feq9);
 int orc_locate(const orc_t* o, double qx, double qy, double* lam3);

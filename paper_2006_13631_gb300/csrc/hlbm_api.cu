@@ -1,0 +1,914 @@
+// Host side of the C ABI declared in include/hlbm.h: validation, mesh
+// topology (node-triangle incidence, FV rows, wall segments, point-location
+// bins), device memory, and the per-step launch sequence.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hlbm_dev.cuh"
+
+using namespace hk;
+
+namespace {
+
+hlbm_alloc_fn g_alloc = nullptr;
+hlbm_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+constexpr int kWindowMargin = 3;
+
+}  // namespace
+
+struct hlbm {
+    int dtype = HLBM_F32;
+    cudaStream_t stream = nullptr;
+    hlbm_alloc_fn alloc = nullptr;
+    hlbm_free_fn release = nullptr;
+    void* alloc_ctx = nullptr;
+    std::string err;
+    std::vector<void*> blocks;
+
+    hlbm_grid_t grid{};
+    hlbm_patch_t patch{};
+    hlbm_motion_t motion{};
+    double tau_s = 0.0;
+
+    // mesh (host copies)
+    std::vector<double> xy;
+    std::vector<int32_t> tri;
+    std::vector<int8_t> kind;
+    std::vector<int32_t> row_ptr, col, outer;
+    double mxmin = 0, mxmax = 0, mymin = 0, mymax = 0;
+    int nnz = 0, nseg = 0;
+
+    Dev<float> df{};
+    Dev<double> dd{};
+    void* fbuf[2] = {nullptr, nullptr};  // lattice populations
+    void* sbox[2] = {nullptr, nullptr};  // window states
+    int8_t* cls[2] = {nullptr, nullptr};
+    void* fu[2] = {nullptr, nullptr};    // patch populations
+    double* force = nullptr;
+    int64_t force_cap = 0;
+    unsigned* status = nullptr;
+    double* scratch = nullptr;           // 8 doubles for reductions
+
+    int64_t t = 0;
+    double Xprev = 0, Yprev = 0;
+    int pbx0 = 0, pby0 = 0;
+    int ci = 0;  // cls[ci]: latest class
+    int si = 0;  // sbox[si]: state at the current time
+    int ui = 0;  // fu[ui]: current patch state
+    int fi = 0;  // fbuf[fi]: post-collision populations read next
+
+    // per-phase profiling: event pairs recorded around each phase
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_marks;  // (phase, index of the start event)
+    size_t ev_used = 0;
+    double phase_ms[HLBM_N_PHASES] = {0, 0, 0, 0};
+    int64_t phase_launches[HLBM_N_PHASES] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int fail(hlbm* h, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(hlbm* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return code;
+}
+
+int cuda_check(hlbm* h, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return HLBM_OK;
+    return fail(h, HLBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* dev_alloc(hlbm* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (h->alloc) {
+        p = h->alloc(bytes, (void*)h->stream, h->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) h->blocks.push_back(p);
+    return p;
+}
+
+void dev_free(hlbm* h, void* p) {
+    if (!p) return;
+    auto it = std::find(h->blocks.begin(), h->blocks.end(), p);
+    if (it != h->blocks.end()) h->blocks.erase(it);
+    if (h->release)
+        h->release(p, (void*)h->stream, h->alloc_ctx);
+    else
+        cudaFree(p);
+}
+
+template <typename T>
+T* upload(hlbm* h, const T* src, size_t count, int* rc) {
+    T* p = (T*)dev_alloc(h, count * sizeof(T));
+    if (!p) {
+        *rc = fail(h, HLBM_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+        return nullptr;
+    }
+    if (count) {
+        cudaError_t e = cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) *rc = cuda_check(h, e, "cudaMemcpyAsync");
+    }
+    return p;
+}
+
+// lamina position at integer time t (Sec. 2: y(t) = A sin(w t))
+void motion_pos(const hlbm_motion_t& m, int64_t t, double* X, double* Y) {
+    double tt = (double)t;
+    if (m.kind == HLBM_MOTION_HARMONIC) {
+        *X = 0.0;
+        *Y = m.A * std::sin(m.omega * tt);
+    } else if (m.kind == HLBM_MOTION_UNIFORM) {
+        *X = m.vx * tt;
+        *Y = m.vy * tt;
+    } else {
+        *X = 0.0;
+        *Y = 0.0;
+    }
+}
+
+double rect_dist(double x, double y, double a, double b) {
+    double qx = std::max(std::fabs(x) - a, 0.0), qy = std::max(std::fabs(y) - b, 0.0);
+    return std::sqrt(qx * qx + qy * qy);
+}
+
+// window of lattice nodes that follows the patch: covers the mesh bounding
+// box at centre (cx, cy) widened by kWindowMargin nodes on every side
+void window_origin(const hlbm* h, double cx, double cy, int* bx0, int* by0) {
+    *bx0 = (int)std::floor(cx + h->mxmin) - kWindowMargin;
+    *by0 = (int)std::floor(cy + h->mymin) - kWindowMargin;
+}
+
+template <typename T>
+Dev<T>& dev_of(hlbm* h);
+template <>
+Dev<float>& dev_of<float>(hlbm* h) {
+    return h->df;
+}
+template <>
+Dev<double>& dev_of<double>(hlbm* h) {
+    return h->dd;
+}
+
+template <typename T>
+void bind(hlbm* h, Dev<T>& d) {
+    d.fA = (T*)h->fbuf[h->fi];
+    d.fB = (T*)h->fbuf[1 - h->fi];
+    d.fu_in = (const T*)h->fu[h->ui];
+    d.fu_out = (T*)h->fu[1 - h->ui];
+    d.force = h->force;
+    d.status = h->status;
+}
+
+// start of a profiled phase: returns the index of its start event, or -1
+int phase_begin(hlbm* h) {
+    if (!h->profiling) return -1;
+    while (h->ev_pool.size() < h->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        h->ev_pool.push_back(e);
+    }
+    int i = (int)h->ev_used;
+    h->ev_used += 2;
+    cudaEventRecord(h->ev_pool[i], h->stream);
+    return i;
+}
+
+void phase_end(hlbm* h, int phase, int i, int launches) {
+    if (i < 0) return;
+    cudaEventRecord(h->ev_pool[i + 1], h->stream);
+    h->ev_marks.push_back({phase, i});
+    h->phase_launches[phase] += launches;
+}
+
+// fold recorded event pairs into the totals (synchronises the stream)
+int phase_collect(hlbm* h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
+    for (auto& m : h->ev_marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[m.second], h->ev_pool[m.second + 1]) == cudaSuccess)
+            h->phase_ms[m.first] += ms;
+    }
+    h->ev_marks.clear();
+    h->ev_used = 0;
+    return HLBM_OK;
+}
+
+template <typename T>
+int step_impl(hlbm* h, int64_t nsteps) {
+    Dev<T>& d = dev_of<T>(h);
+    cudaStream_t s = h->stream;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const int64_t t = h->t;
+        // force history capacity
+        if (t + 2 > h->force_cap) {
+            int64_t cap = std::max<int64_t>(2 * h->force_cap, t + 4096);
+            double* nf = (double*)dev_alloc(h, (size_t)cap * 2 * sizeof(double));
+            if (!nf) return fail(h, HLBM_ENOMEM, "force history allocation failed");
+            cudaMemcpyAsync(nf, h->force, (size_t)h->force_cap * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            cudaStreamSynchronize(s);
+            dev_free(h, h->force);
+            h->force = nf;
+            h->force_cap = cap;
+        }
+        double X, Y;
+        motion_pos(h->motion, t, &X, &Y);
+        StepArgs a{};
+        a.t = t;
+        a.cx = h->patch.x_c + X;
+        a.cy = h->patch.y_c + Y;
+        a.dX = X - h->Xprev;
+        a.dY = Y - h->Yprev;
+        window_origin(h, a.cx, a.cy, &a.bx0, &a.by0);
+        a.pbx0 = h->pbx0;
+        a.pby0 = h->pby0;
+        a.first = (t == 0);
+        if (a.bx0 < 1 || a.by0 < 1 || a.bx0 + d.bw > d.nx - 1 || a.by0 + d.bh > d.ny - 1)
+            return fail(h, HLBM_EINVAL, "step %lld: the patch window [%d,%d)x[%d,%d) leaves the lattice",
+                        (long long)t, a.bx0, a.bx0 + d.bw, a.by0, a.by0 + d.bh);
+        if (std::fabs(a.dX) >= 1.0 || std::fabs(a.dY) >= 1.0)
+            return fail(h, HLBM_EINVAL, "step %lld: displacement (%g, %g) is not below one lattice spacing",
+                        (long long)t, a.dX, a.dY);
+        bind(h, d);
+        // 1. move the patch to y(t) and refill it (Sec. 4)
+        const int ncls = (t == 0) ? h->ci : 1 - h->ci;
+        d.cls_prev = h->cls[h->ci];
+        d.cls_cur = h->cls[ncls];
+        d.sbox_old = (const T*)h->sbox[h->si];
+        d.sbox_new = (T*)h->sbox[1 - h->si];
+        int ev = phase_begin(h);
+        if (t > 0) {
+            launch_refill<T>(d, a, s);
+            h->ui = 1 - h->ui;
+            bind(h, d);
+            // 2. classify the lattice nodes against the moved fictitious curve
+            launch_classify<T>(d, a, s);
+        }
+        // 3. interpolation nodes from the patch (eq. postcollision2_s)
+        launch_fill<T>(d, a, s);
+        phase_end(h, HLBM_PHASE_MOVE, ev, t > 0 ? 3 : 1);
+        // 4. stream-collide t -> t+1 (eq. LBE)
+        ev = phase_begin(h);
+        launch_stream_collide<T>(d, a, s);
+        phase_end(h, HLBM_PHASE_STREAM, ev, 1);
+        // 5. outer-node feed and n FV sub-steps (eq. ulbe, eq. postcollision2_u)
+        ev = phase_begin(h);
+        launch_feed<T>(d, a, s);
+        for (int m = 0; m < d.n_sub; ++m) {
+            launch_fv_substep<T>(d, a, m, s);
+            h->ui = 1 - h->ui;
+            bind(h, d);
+        }
+        phase_end(h, HLBM_PHASE_FV, ev, 1 + d.n_sub);
+        // 6. force on the lamina at t+1
+        ev = phase_begin(h);
+        launch_force<T>(d, t + 1, s);
+        phase_end(h, HLBM_PHASE_FORCE, ev, 1);
+        if (h->ev_used > 4096) {
+            int rc = phase_collect(h);
+            if (rc != HLBM_OK) return rc;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
+        h->fi = 1 - h->fi;
+        h->si = 1 - h->si;
+        h->ci = ncls;
+        h->pbx0 = a.bx0;
+        h->pby0 = a.by0;
+        h->Xprev = X;
+        h->Yprev = Y;
+        h->t = t + 1;
+    }
+    return HLBM_OK;
+}
+
+template <typename T>
+int create_impl(hlbm* h, const hlbm_grid_t* g) {
+    cudaStream_t s = h->stream;
+    Dev<T>& d = dev_of<T>(h);
+    int rc = HLBM_OK;
+    const hlbm_patch_t& p = h->patch;
+    const int n = p.n_nodes, nt = p.n_tris;
+    d.nx = g->nx;
+    d.ny = g->ny;
+    d.pitch = (g->nx + 31) / 32 * 32;
+    d.plane = (int64_t)d.pitch * g->ny;
+    d.bc_x = g->bc_x;
+    d.bc_y = g->bc_y;
+    d.rho0 = T(g->rho0);
+    d.tau_s = T(h->tau_s);
+    d.tau_u = T(h->tau_s - 0.5);
+    d.n_sub = p.n_sub;
+    d.dt_u = T(1.0 / p.n_sub);
+    d.k178 = T(2.0 * (h->tau_s - 1.0) / (2.0 * h->tau_s - 1.0));
+    d.kneq = T(1.0 - 1.0 / (2.0 * h->tau_s));
+    d.motion = h->motion.kind;
+    d.A = h->motion.A;
+    d.omega = h->motion.omega;
+    d.vx = h->motion.vx;
+    d.vy = h->motion.vy;
+    d.half_L = 0.5 * p.lamina_L;
+    d.half_T = 0.5 * p.lamina_T;
+    d.df2 = p.delta_f * p.delta_f;
+    d.n = n;
+    d.ntri = nt;
+
+    // --- topology: node -> triangles, FV rows (pivot first), wall segments
+    std::vector<int32_t> tstart(n + 1, 0), tlist(3 * (size_t)nt);
+    for (int k = 0; k < nt; ++k)
+        for (int j = 0; j < 3; ++j) tstart[h->tri[3 * k + j] + 1]++;
+    for (int i = 0; i < n; ++i) tstart[i + 1] += tstart[i];
+    {
+        std::vector<int32_t> fill(n, 0);
+        for (int k = 0; k < nt; ++k)
+            for (int j = 0; j < 3; ++j) {
+                int v = h->tri[3 * k + j];
+                tlist[tstart[v] + fill[v]++] = k;
+            }
+    }
+    h->row_ptr.assign(n + 1, 0);
+    h->col.clear();
+    int max_row = 0;
+    for (int P = 0; P < n; ++P) {
+        std::vector<int32_t> nb;
+        for (int e = tstart[P]; e < tstart[P + 1]; ++e)
+            for (int j = 0; j < 3; ++j) {
+                int v = h->tri[3 * tlist[e] + j];
+                if (v != P) nb.push_back(v);
+            }
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        h->col.push_back(P);
+        h->col.insert(h->col.end(), nb.begin(), nb.end());
+        h->row_ptr[P + 1] = (int32_t)h->col.size();
+        max_row = std::max(max_row, (int)nb.size() + 1);
+    }
+    if (max_row > 64) return fail(h, HLBM_EINVAL, "a patch node has %d neighbours (max 63)", max_row - 1);
+    h->nnz = (int)h->col.size();
+    d.nnz = h->nnz;
+    std::vector<int32_t> outer_of(n, -1);
+    h->outer.clear();
+    for (int P = 0; P < n; ++P)
+        if (h->kind[P] == HLBM_NODE_OUTER) {
+            outer_of[P] = (int32_t)h->outer.size();
+            h->outer.push_back(P);
+        }
+    d.n_outer = (int)h->outer.size();
+    // wall segments: boundary edges (one incident triangle) joining wall
+    // nodes, normal pointing away from the body (towards the third vertex)
+    std::vector<int32_t> sa, sb;
+    std::vector<double> sn;
+    for (int k = 0; k < nt; ++k)
+        for (int j = 0; j < 3; ++j) {
+            int a = h->tri[3 * k + j], b = h->tri[3 * k + (j + 1) % 3], c = h->tri[3 * k + (j + 2) % 3];
+            if (h->kind[a] != HLBM_NODE_WALL || h->kind[b] != HLBM_NODE_WALL) continue;
+            int count = 0;
+            for (int e = tstart[a]; e < tstart[a + 1]; ++e) {
+                const int32_t* v = &h->tri[3 * tlist[e]];
+                if (v[0] == b || v[1] == b || v[2] == b) ++count;
+            }
+            if (count != 1) continue;
+            double ex = h->xy[2 * b] - h->xy[2 * a], ey = h->xy[2 * b + 1] - h->xy[2 * a + 1];
+            double nx = ey, ny = -ex;
+            double tx = h->xy[2 * c] - h->xy[2 * a], ty = h->xy[2 * c + 1] - h->xy[2 * a + 1];
+            if (nx * tx + ny * ty < 0) {
+                nx = -nx;
+                ny = -ny;
+            }
+            sa.push_back(a);
+            sb.push_back(b);
+            sn.push_back(nx);
+            sn.push_back(ny);
+        }
+    h->nseg = (int)sa.size();
+    d.nseg = h->nseg;
+
+    // --- triangle geometry for barycentric tests, and point-location bins
+    std::vector<double> tg(8 * (size_t)nt);
+    double area_sum = 0.0;
+    for (int k = 0; k < nt; ++k) {
+        const int32_t* v = &h->tri[3 * k];
+        double ax = h->xy[2 * v[0]], ay = h->xy[2 * v[0] + 1];
+        double x1 = h->xy[2 * v[1]] - ax, y1 = h->xy[2 * v[1] + 1] - ay;
+        double x2 = h->xy[2 * v[2]] - ax, y2 = h->xy[2 * v[2] + 1] - ay;
+        double det = x1 * y2 - x2 * y1;
+        if (!(std::fabs(det) > 0.0)) return fail(h, HLBM_EINVAL, "triangle %d is degenerate", k);
+        double* o = &tg[8 * (size_t)k];
+        o[0] = ax;
+        o[1] = ay;
+        o[2] = x1;
+        o[3] = y1;
+        o[4] = x2;
+        o[5] = y2;
+        o[6] = det;
+        o[7] = 0.0;
+        area_sum += 0.5 * std::fabs(det);
+    }
+    double bh = 1.5 * std::sqrt(area_sum / nt);
+    double gx0 = h->mxmin - 1e-6, gy0 = h->mymin - 1e-6;
+    int gnx = (int)((h->mxmax + 1e-6 - gx0) / bh) + 1, gny = (int)((h->mymax + 1e-6 - gy0) / bh) + 1;
+    std::vector<int32_t> bcount((size_t)gnx * gny + 1, 0), bstart, bitems;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            bstart.assign((size_t)gnx * gny + 1, 0);
+            for (size_t b = 0; b < (size_t)gnx * gny; ++b) bstart[b + 1] = bstart[b] + bcount[b];
+            bitems.assign(bstart.back(), 0);
+            std::fill(bcount.begin(), bcount.end(), 0);
+        }
+        for (int k = 0; k < nt; ++k) {
+            const int32_t* v = &h->tri[3 * k];
+            double lx = 1e300, hx = -1e300, ly = 1e300, hy = -1e300;
+            for (int j = 0; j < 3; ++j) {
+                lx = std::min(lx, h->xy[2 * v[j]]);
+                hx = std::max(hx, h->xy[2 * v[j]]);
+                ly = std::min(ly, h->xy[2 * v[j] + 1]);
+                hy = std::max(hy, h->xy[2 * v[j] + 1]);
+            }
+            int i0 = std::max(0, (int)std::floor((lx - 1e-9 - gx0) / bh));
+            int i1 = std::min(gnx - 1, (int)std::floor((hx + 1e-9 - gx0) / bh));
+            int j0 = std::max(0, (int)std::floor((ly - 1e-9 - gy0) / bh));
+            int j1 = std::min(gny - 1, (int)std::floor((hy + 1e-9 - gy0) / bh));
+            for (int bj = j0; bj <= j1; ++bj)
+                for (int bi = i0; bi <= i1; ++bi) {
+                    size_t b = (size_t)bj * gnx + bi;
+                    if (pass == 0)
+                        bcount[b]++;
+                    else
+                        bitems[bstart[b] + bcount[b]++] = k;
+                }
+        }
+    }
+    d.gbx0 = gx0;
+    d.gby0 = gy0;
+    d.gbh = bh;
+    d.gnbx = gnx;
+    d.gnby = gny;
+
+    // --- window size
+    d.bw = (int)std::ceil(h->mxmax - h->mxmin) + 2 * kWindowMargin + 2;
+    d.bh = (int)std::ceil(h->mymax - h->mymin) + 2 * kWindowMargin + 2;
+    d.bplane = (int64_t)d.bw * d.bh;
+
+    // --- device memory
+    size_t fbytes = (size_t)9 * d.plane * sizeof(T);
+    for (int b = 0; b < 2; ++b) {
+        h->fbuf[b] = dev_alloc(h, fbytes);
+        h->sbox[b] = dev_alloc(h, (size_t)9 * d.bplane * sizeof(T));
+        h->cls[b] = (int8_t*)dev_alloc(h, (size_t)d.bplane);
+        h->fu[b] = dev_alloc(h, (size_t)9 * n * sizeof(T));
+        if (!h->fbuf[b] || !h->sbox[b] || !h->cls[b] || !h->fu[b])
+            return fail(h, HLBM_ENOMEM, "device allocation failed (lattice %zu bytes per buffer)", fbytes);
+    }
+    d.xy = upload(h, h->xy.data(), h->xy.size(), &rc);
+    d.kind = upload(h, h->kind.data(), h->kind.size(), &rc);
+    d.tri = upload(h, h->tri.data(), h->tri.size(), &rc);
+    d.trigeo = upload(h, tg.data(), tg.size(), &rc);
+    d.bstart = upload(h, bstart.data(), bstart.size(), &rc);
+    d.bitems = upload(h, bitems.data(), bitems.size(), &rc);
+    d.row_ptr = upload(h, h->row_ptr.data(), h->row_ptr.size(), &rc);
+    d.col = upload(h, h->col.data(), h->col.size(), &rc);
+    d.outer = upload(h, h->outer.data(), h->outer.size(), &rc);
+    d.outer_of = upload(h, outer_of.data(), outer_of.size(), &rc);
+    d.seg_a = upload(h, sa.data(), sa.size(), &rc);
+    d.seg_b = upload(h, sb.data(), sb.size(), &rc);
+    d.seg_n = upload(h, sn.data(), sn.size(), &rc);
+    int32_t* d_tstart = upload(h, tstart.data(), tstart.size(), &rc);
+    int32_t* d_tlist = upload(h, tlist.data(), tlist.size(), &rc);
+    T* gxv = (T*)dev_alloc(h, (size_t)h->nnz * sizeof(T));
+    T* gyv = (T*)dev_alloc(h, (size_t)h->nnz * sizeof(T));
+    T* ccv = (T*)dev_alloc(h, (size_t)h->nnz * sizeof(T));
+    d.snap = (T*)dev_alloc(h, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
+    d.rtype = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
+    d.rdonor = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
+    h->status = (unsigned*)dev_alloc(h, 64);
+    h->scratch = (double*)dev_alloc(h, 16 * sizeof(double));
+    h->force_cap = 4096;
+    h->force = (double*)dev_alloc(h, (size_t)h->force_cap * 2 * sizeof(double));
+    if (rc != HLBM_OK) return rc;
+    if (!gxv || !gyv || !ccv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force)
+        return fail(h, HLBM_ENOMEM, "device allocation failed");
+    d.gx = gxv;
+    d.gy = gyv;
+    d.cc = ccv;
+    cudaMemsetAsync(h->status, 0, 64, s);
+    cudaMemsetAsync(d.rtype, 0, (size_t)n * sizeof(int32_t), s);
+    cudaMemsetAsync(d.rdonor, 0xff, (size_t)n * sizeof(int32_t), s);
+    cudaMemsetAsync(h->force, 0, (size_t)h->force_cap * 2 * sizeof(double), s);
+    for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->fbuf[b], 0, fbytes, s);
+    h->fi = h->si = h->ui = h->ci = 0;
+    bind(h, d);
+    launch_fv_coeffs<T>(d, d_tstart, d_tlist, p.lumped, gxv, gyv, ccv, s);
+
+    // --- initial state: equilibrium at the initial density and velocity
+    const size_t N = (size_t)g->nx * g->ny;
+    double* drho = g->rho_init ? upload(h, g->rho_init, N, &rc) : nullptr;
+    double* dux = g->ux_init ? upload(h, g->ux_init, N, &rc) : nullptr;
+    double* duy = g->uy_init ? upload(h, g->uy_init, N, &rc) : nullptr;
+    if (rc != HLBM_OK) return rc;
+    launch_init_struct<T>(d, drho, dux, duy, g->u0x, g->u0y, s);
+    double X0, Y0;
+    motion_pos(h->motion, 0, &X0, &Y0);
+    StepArgs a{};
+    a.t = 0;
+    a.cx = p.x_c + X0;
+    a.cy = p.y_c + Y0;
+    window_origin(h, a.cx, a.cy, &a.bx0, &a.by0);
+    if (a.bx0 < 1 || a.by0 < 1 || a.bx0 + d.bw > d.nx - 1 || a.by0 + d.bh > d.ny - 1)
+        return fail(h, HLBM_EINVAL, "the patch window does not fit in the lattice");
+    a.pbx0 = a.bx0;
+    a.pby0 = a.by0;
+    a.first = 1;
+    d.sbox_new = (T*)h->sbox[0];
+    launch_init_box<T>(d, a.bx0, a.by0, drho, dux, duy, g->u0x, g->u0y, s);
+    d.cls_cur = h->cls[0];
+    launch_classify<T>(d, a, s);
+    d.sbox_old = (const T*)h->sbox[0];
+    launch_patch_init<T>(d, a, s);
+    h->ui = 1;
+    bind(h, d);
+    launch_force<T>(d, 0, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(h, e, "initialisation");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(h, e, "initialisation");
+    dev_free(h, drho);
+    dev_free(h, dux);
+    dev_free(h, duy);
+    dev_free(h, d_tstart);
+    dev_free(h, d_tlist);
+    h->t = 0;
+    h->Xprev = X0;
+    h->Yprev = Y0;
+    h->pbx0 = a.bx0;
+    h->pby0 = a.by0;
+    h->ci = 0;
+    h->si = 0;
+    return HLBM_OK;
+}
+
+int sync_status(hlbm* h, unsigned* bits) {
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->status, sizeof v, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "status readback");
+    *bits = v;
+    return HLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlbm_set_allocator(hlbm_alloc_fn alloc, hlbm_free_fn release, void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return HLBM_EINVAL;
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return HLBM_OK;
+}
+
+namespace {
+thread_local std::string g_create_err;
+}
+
+int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s, const hlbm_motion_t* motion,
+                void* cuda_stream, hlbm_t** out) {
+    std::string& create_err = g_create_err;
+    if (!out) return HLBM_EINVAL;
+    *out = nullptr;
+    if (!grid || !patch || !motion) return HLBM_EINVAL;
+    hlbm* h = new hlbm();
+    h->alloc = g_alloc;
+    h->release = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->grid = *grid;
+    h->patch = *patch;
+    h->motion = *motion;
+    h->tau_s = tau_s;
+    h->dtype = grid->dtype;
+    int rc = HLBM_OK;
+    const hlbm_patch_t& p = *patch;
+    // --- validation (Sec. 3: nu = cs^2 (tau_s - 1/2) = cs^2 tau_u; Sec. 7: dt < 2 tau)
+    if (grid->nx < 8 || grid->ny < 8)
+        rc = fail(h, HLBM_EINVAL, "lattice %dx%d is too small", grid->nx, grid->ny);
+    else if (grid->dtype != HLBM_F32 && grid->dtype != HLBM_F64)
+        rc = fail(h, HLBM_EINVAL, "unknown dtype %d", grid->dtype);
+    else if (grid->bc_x < 0 || grid->bc_x > 2 || grid->bc_y < 0 || grid->bc_y > 2)
+        rc = fail(h, HLBM_EINVAL, "unknown boundary kind");
+    else if (!(tau_s > 0.5))
+        rc = fail(h, HLBM_EINVAL, "tau_s = %g must exceed 1/2", tau_s);
+    else if (p.n_sub < 1 || !(1.0 / p.n_sub < 2.0 * (tau_s - 0.5)))
+        rc = fail(h, HLBM_EINVAL, "unstable FV sub-step: dt_u = 1/%d must be below 2 tau_u = %g", p.n_sub,
+                  2.0 * (tau_s - 0.5));
+    else if (std::fabs(2.0 * tau_s - 1.0) < 1e-12)
+        rc = fail(h, HLBM_EINVAL, "tau_s = 1/2 makes eq. 178 singular");
+    else if (p.n_nodes < 3 || p.n_tris < 1 || !p.xy || !p.tri || !p.kind)
+        rc = fail(h, HLBM_EINVAL, "empty patch mesh");
+    else if (motion->kind < 0 || motion->kind > 2)
+        rc = fail(h, HLBM_EINVAL, "unknown motion kind %d", motion->kind);
+    else if (!(p.delta_f > 1.5))
+        rc = fail(h, HLBM_EINVAL, "delta_f = %g must exceed 1.5 (interpolation nodes outside the body)",
+                  p.delta_f);
+    if (rc == HLBM_OK) {
+        h->xy.assign(p.xy, p.xy + 2 * (size_t)p.n_nodes);
+        h->tri.assign(p.tri, p.tri + 3 * (size_t)p.n_tris);
+        h->kind.assign(p.kind, p.kind + p.n_nodes);
+        for (size_t k = 0; k < h->tri.size() && rc == HLBM_OK; ++k)
+            if (h->tri[k] < 0 || h->tri[k] >= p.n_nodes) rc = fail(h, HLBM_EINVAL, "triangle index out of range");
+        for (int i = 0; i < p.n_nodes && rc == HLBM_OK; ++i)
+            if (h->kind[i] < 0 || h->kind[i] > 2) rc = fail(h, HLBM_EINVAL, "node %d has kind %d", i, h->kind[i]);
+    }
+    if (rc == HLBM_OK) {
+        h->mxmin = h->mymin = 1e300;
+        h->mxmax = h->mymax = -1e300;
+        double dmin_outer = 1e300;
+        for (int i = 0; i < p.n_nodes; ++i) {
+            double x = h->xy[2 * i], y = h->xy[2 * i + 1];
+            h->mxmin = std::min(h->mxmin, x);
+            h->mxmax = std::max(h->mxmax, x);
+            h->mymin = std::min(h->mymin, y);
+            h->mymax = std::max(h->mymax, y);
+            if (h->kind[i] == HLBM_NODE_OUTER)
+                dmin_outer = std::min(dmin_outer, rect_dist(x, y, 0.5 * p.lamina_L, 0.5 * p.lamina_T));
+        }
+        double dmax = 0.0;
+        if (motion->kind == HLBM_MOTION_HARMONIC) dmax = std::fabs(motion->A * motion->omega);
+        if (motion->kind == HLBM_MOTION_UNIFORM) dmax = std::hypot(motion->vx, motion->vy);
+        // outer nodes' bilinear donors (within sqrt 2 < 1.5 of the node) must
+        // be discretization nodes at t and t+1
+        if (dmin_outer < 1e299 && !(dmin_outer > p.delta_f + 1.5 + dmax))
+            rc = fail(h, HLBM_EINVAL,
+                      "outer patch boundary at distance %g from the lamina; needs > delta_f + 1.5 + %g", dmin_outer,
+                      dmax);
+        if (dmax >= 1.0) rc = fail(h, HLBM_EINVAL, "lamina moves %g >= 1 lattice spacing per step", dmax);
+        if (motion->kind == HLBM_MOTION_HARMONIC) {
+            int bw = (int)std::ceil(h->mxmax - h->mxmin) + 2 * kWindowMargin + 2;
+            int bh = (int)std::ceil(h->mymax - h->mymin) + 2 * kWindowMargin + 2;
+            for (int sgn = -1; sgn <= 1 && rc == HLBM_OK; sgn += 2) {
+                int bx0, by0;
+                window_origin(h, p.x_c, p.y_c + sgn * std::fabs(motion->A), &bx0, &by0);
+                if (bx0 < 1 || by0 < 1 || bx0 + bw > grid->nx - 1 || by0 + bh > grid->ny - 1)
+                    rc = fail(h, HLBM_EINVAL, "the oscillating patch comes within %d nodes of the lattice edge",
+                              kWindowMargin);
+            }
+        }
+    }
+    if (rc == HLBM_OK) rc = (grid->dtype == HLBM_F32) ? create_impl<float>(h, grid) : create_impl<double>(h, grid);
+    if (rc != HLBM_OK) {
+        create_err = h->err;
+        cudaStreamSynchronize(h->stream);
+        for (void* b : std::vector<void*>(h->blocks)) dev_free(h, b);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return HLBM_OK;
+}
+
+int hlbm_step(hlbm_t* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return HLBM_EINVAL;
+    return h->dtype == HLBM_F32 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
+}
+
+int hlbm_status(hlbm_t* h, uint32_t* bits) {
+    if (!h || !bits) return HLBM_EINVAL;
+    unsigned v;
+    int rc = sync_status(h, &v);
+    *bits = v;
+    return rc;
+}
+
+int hlbm_force(hlbm_t* h, int64_t first, int64_t count, double* fx, double* fy) {
+    if (!h || first < 0 || count < 0 || first + count > h->t + 1) return HLBM_EINVAL;
+    std::vector<double> buf(2 * (size_t)count);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), h->force + 2 * first, 2 * (size_t)count * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "force readback");
+    for (int64_t k = 0; k < count; ++k) {
+        if (fx) fx[k] = buf[2 * k];
+        if (fy) fy[k] = buf[2 * k + 1];
+    }
+    unsigned st;
+    int rc = sync_status(h, &st);
+    if (rc != HLBM_OK) return rc;
+    if (st & HLBM_ST_NONFINITE) return fail(h, HLBM_EUNSTABLE, "the force became NaN/Inf: the run diverged");
+    return HLBM_OK;
+}
+
+int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re, double* im, double* rms) {
+    if (!h || !re || !im) return HLBM_EINVAL;
+    if (h->motion.kind != HLBM_MOTION_HARMONIC || !(h->motion.omega > 0) || h->motion.A == 0.0)
+        return fail(h, HLBM_EINVAL, "the hydrodynamic function needs harmonic motion");
+    const double PI = 3.14159265358979323846;
+    double Tp = 2.0 * PI / h->motion.omega;
+    int64_t t0 = (int64_t)std::ceil(discard_periods * Tp);
+    int64_t t1 = (int64_t)std::floor((discard_periods + fit_periods) * Tp);
+    if (t1 > h->t || t1 <= t0)
+        return fail(h, HLBM_EINVAL, "fit window [%lld, %lld] is not inside the %lld steps taken", (long long)t0,
+                    (long long)t1, (long long)h->t);
+    launch_gamma_sums(h->force, t0, t1, h->motion.omega, h->scratch, h->stream);
+    double sums[5];
+    cudaError_t e = cudaMemcpyAsync(sums, h->scratch, sizeof sums, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "fit readback");
+    double det = sums[0] * sums[2] - sums[1] * sums[1];
+    double a = (sums[3] * sums[2] - sums[4] * sums[1]) / det;
+    double b = (sums[4] * sums[0] - sums[3] * sums[1]) / det;
+    launch_gamma_resid(h->force, t0, t1, h->motion.omega, a, b, h->scratch + 8, h->stream);
+    double r2 = 0;
+    e = cudaMemcpyAsync(&r2, h->scratch + 8, sizeof r2, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "fit readback");
+    double N = 0.25 * PI * h->grid.rho0 * h->motion.omega * h->motion.omega * h->patch.lamina_L *
+               h->patch.lamina_L * h->motion.A;
+    *re = a / N;
+    *im = b / N;
+    if (rms) *rms = std::sqrt(r2 / (double)(t1 - t0 + 1)) / N;
+    unsigned st;
+    int rc = sync_status(h, &st);
+    if (rc != HLBM_OK) return rc;
+    if (st & HLBM_ST_NONFINITE) return fail(h, HLBM_EUNSTABLE, "the force became NaN/Inf: the run diverged");
+    return HLBM_OK;
+}
+
+int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double* rho_u, double* ux_u,
+                    double* uy_u) {
+    if (!h) return HLBM_EINVAL;
+    int rc = HLBM_OK;
+    const size_t N = (size_t)h->grid.nx * h->grid.ny, n = h->patch.n_nodes;
+    double* buf = (double*)dev_alloc(h, (3 * N + 3 * n) * sizeof(double));
+    if (!buf) return fail(h, HLBM_ENOMEM, "readback buffer");
+    if (h->dtype == HLBM_F32) {
+        bind(h, h->df);
+        launch_struct_macro<float>(h->df, buf, buf + N, buf + 2 * N, h->stream);
+        launch_patch_macro<float>(h->df, buf + 3 * N, buf + 3 * N + n, buf + 3 * N + 2 * n, nullptr, h->stream);
+    } else {
+        bind(h, h->dd);
+        launch_struct_macro<double>(h->dd, buf, buf + N, buf + 2 * N, h->stream);
+        launch_patch_macro<double>(h->dd, buf + 3 * N, buf + 3 * N + n, buf + 3 * N + 2 * n, nullptr, h->stream);
+    }
+    double* dst[6] = {rho_s, ux_s, uy_s, rho_u, ux_u, uy_u};
+    size_t off[6] = {0, N, 2 * N, 3 * N, 3 * N + n, 3 * N + 2 * n};
+    size_t len[6] = {N, N, N, n, n, n};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        if (dst[k]) e = cudaMemcpyAsync(dst[k], buf + off[k], len[k] * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_check(h, e, "field readback");
+    dev_free(h, buf);
+    return rc;
+}
+
+int hlbm_get_patch_f(hlbm_t* h, double* f9) {
+    if (!h || !f9) return HLBM_EINVAL;
+    const size_t n = h->patch.n_nodes;
+    double* buf = (double*)dev_alloc(h, 9 * n * sizeof(double));
+    if (!buf) return fail(h, HLBM_ENOMEM, "readback buffer");
+    if (h->dtype == HLBM_F32) {
+        bind(h, h->df);
+        launch_patch_macro<float>(h->df, nullptr, nullptr, nullptr, buf, h->stream);
+    } else {
+        bind(h, h->dd);
+        launch_patch_macro<double>(h->dd, nullptr, nullptr, nullptr, buf, h->stream);
+    }
+    cudaError_t e = cudaMemcpyAsync(f9, buf, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, buf);
+    return e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "patch readback");
+}
+
+int hlbm_get_class(hlbm_t* h, int8_t* cls) {
+    if (!h || !cls) return HLBM_EINVAL;
+    const int bw = h->dtype == HLBM_F32 ? h->df.bw : h->dd.bw;
+    const int bh = h->dtype == HLBM_F32 ? h->df.bh : h->dd.bh;
+    std::vector<int8_t> win((size_t)bw * bh);
+    cudaError_t e = cudaMemcpyAsync(win.data(), h->cls[h->ci], win.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "class readback");
+    const int nx = h->grid.nx, ny = h->grid.ny;
+    std::memset(cls, CLS_DISC, (size_t)nx * ny);
+    for (int j = 0; j < bh; ++j)
+        for (int i = 0; i < bw; ++i) {
+            int x = h->pbx0 + i, y = h->pby0 + j;
+            if (x >= 0 && y >= 0 && x < nx && y < ny) cls[(size_t)y * nx + x] = win[(size_t)j * bw + i];
+        }
+    return HLBM_OK;
+}
+
+int hlbm_get_refill(hlbm_t* h, int32_t* type, int32_t* donor) {
+    if (!h) return HLBM_EINVAL;
+    const size_t n = h->patch.n_nodes;
+    int32_t* rt = h->dtype == HLBM_F32 ? h->df.rtype : h->dd.rtype;
+    int32_t* rd = h->dtype == HLBM_F32 ? h->df.rdonor : h->dd.rdonor;
+    cudaError_t e = cudaSuccess;
+    if (type) e = cudaMemcpyAsync(type, rt, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (donor && e == cudaSuccess) e = cudaMemcpyAsync(donor, rd, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "refill readback");
+}
+
+int hlbm_get_fv(hlbm_t* h, int32_t* row_ptr, int32_t* col, double* gx, double* gy, double* cc) {
+    if (!h) return HLBM_EINVAL;
+    if (row_ptr) std::memcpy(row_ptr, h->row_ptr.data(), h->row_ptr.size() * sizeof(int32_t));
+    if (col) std::memcpy(col, h->col.data(), h->col.size() * sizeof(int32_t));
+    const size_t nnz = h->nnz;
+    std::vector<double> tmp(nnz);
+    double* outs[3] = {gx, gy, cc};
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        cudaError_t e;
+        if (h->dtype == HLBM_F32) {
+            const float* src[3] = {h->df.gx, h->df.gy, h->df.cc};
+            std::vector<float> f(nnz);
+            e = cudaMemcpyAsync(f.data(), src[k], nnz * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            for (size_t i = 0; i < nnz; ++i) outs[k][i] = f[i];
+        } else {
+            const double* src[3] = {h->dd.gx, h->dd.gy, h->dd.cc};
+            e = cudaMemcpyAsync(outs[k], src[k], nnz * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        }
+        if (e != cudaSuccess) return cuda_check(h, e, "FV readback");
+    }
+    return HLBM_OK;
+}
+
+int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
+    if (!h || !info) return HLBM_EINVAL;
+    const int bw = h->dtype == HLBM_F32 ? h->df.bw : h->dd.bw;
+    const int bh = h->dtype == HLBM_F32 ? h->df.bh : h->dd.bh;
+    std::vector<int8_t> win((size_t)bw * bh);
+    cudaError_t e = cudaMemcpyAsync(win.data(), h->cls[h->ci], win.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "class readback");
+    int64_t nondisc = 0;
+    for (int8_t c : win) nondisc += (c != CLS_DISC);
+    info->time = h->t;
+    info->n_struct = (int64_t)h->grid.nx * h->grid.ny;
+    info->n_struct_disc = info->n_struct - nondisc;
+    info->n_nodes = h->patch.n_nodes;
+    info->n_tris = h->patch.n_tris;
+    info->nnz = h->nnz;
+    info->n_outer = (int32_t)h->outer.size();
+    info->n_wall_segments = h->nseg;
+    info->box_w = bw;
+    info->box_h = bh;
+    // refill, classify, fill, stream-collide, feed, n_sub FV, force
+    info->launches_per_step = 6 + h->patch.n_sub;
+    info->dtype = h->dtype;
+    return HLBM_OK;
+}
+
+int hlbm_profile(hlbm_t* h, int enable) {
+    if (!h) return HLBM_EINVAL;
+    int rc = phase_collect(h);
+    if (rc != HLBM_OK) return rc;
+    h->profiling = enable != 0;
+    if (enable)
+        for (int k = 0; k < HLBM_N_PHASES; ++k) {
+            h->phase_ms[k] = 0.0;
+            h->phase_launches[k] = 0;
+        }
+    return HLBM_OK;
+}
+
+int hlbm_profile_read(hlbm_t* h, double* ms, int64_t* launches) {
+    if (!h) return HLBM_EINVAL;
+    int rc = phase_collect(h);
+    if (rc != HLBM_OK) return rc;
+    for (int k = 0; k < HLBM_N_PHASES; ++k) {
+        if (ms) ms[k] = h->phase_ms[k];
+        if (launches) launches[k] = h->phase_launches[k];
+    }
+    return HLBM_OK;
+}
+
+const char* hlbm_last_error(const hlbm_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+void hlbm_destroy(hlbm_t* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (void* b : std::vector<void*>(h->blocks)) dev_free(h, b);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// Device-side definitions shared by the solver's translation units.
+//
+// Populations are stored as deviations from the rest equilibrium,
+// f'_i = f_i - w_i rho0, in the storage type T (float or double); the
+// arithmetic runs in T as well.  Geometric decisions (node classes, donor
+// triangles and cells) are taken in FP64 with explicitly rounded operations
+// (__dadd_rn, __dmul_rn, ...) so that they never depend on FMA contraction.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hlbm.h"
+
+namespace hk {
+
+// ---------------------------------------------------------------- D2Q9
+// Sec. 3: D2Q9 lattice, c_s^2 = 1/3.
+__host__ __device__ __forceinline__ constexpr int cx_of(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cy_of(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp_of(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+template <typename T>
+__host__ __device__ __forceinline__ constexpr T w_of(int i) {
+    return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+
+enum : int8_t { CLS_DISC = 0, CLS_INTERP = 1, CLS_UNUSED = 2 };
+
+// Moments of a deviation set: rho = rho0 + sum f', j = sum f' c.
+template <typename T>
+__device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& rho, T& ux, T& uy) {
+    T r = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        r += f[i];
+        jx += T(cx_of(i)) * f[i];
+        jy += T(cy_of(i)) * f[i];
+    }
+    rho = rho0 + r;
+    T inv = T(1) / rho;
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
+// Eq. local_eq minus w_i rho0:
+// f_i^eq - w_i rho0 = w_i (rho - rho0) + w_i rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)
+template <typename T>
+__device__ __forceinline__ T feq_dev(int i, T rho, T rho0, T ux, T uy) {
+    T cu = T(cx_of(i)) * ux + T(cy_of(i)) * uy;
+    T usq = ux * ux + uy * uy;
+    return w_of<T>(i) * ((rho - rho0) + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+}
+
+// ---------------------------------------------------------------- layout
+struct StepArgs {
+    int64_t t;      // time at the start of the step
+    double cx, cy;  // lamina centre at y(t)
+    double dX, dY;  // displacement of the patch from t-1 to t
+    int bx0, by0;   // window of this step (class and new state)
+    int pbx0, pby0; // window of the previous step (previous class and state)
+    int first;      // 1 at t == 0
+};
+
+template <typename T>
+struct Dev {
+    // lattice
+    int nx, ny, pitch;
+    int64_t plane; // pitch * ny
+    int bc_x, bc_y;
+    T* fA;         // post-collision populations read by this step [9][plane]
+    T* fB;         // written by this step
+    // lattice window that follows the patch
+    int bw, bh;
+    int64_t bplane; // bw * bh
+    int8_t* cls_cur;
+    const int8_t* cls_prev;
+    T* sbox_new;        // pre-collision state at t+1 in the window [9][bplane]
+    const T* sbox_old;  // pre-collision state at t in the previous window
+    // lamina / fictitious curve
+    double half_L, half_T, df2;
+    // patch mesh
+    int n, ntri, nnz, n_outer, nseg;
+    const double* xy;      // [n][2]
+    const int8_t* kind;    // [n]
+    const int32_t* tri;    // [ntri][3]
+    const double* trigeo;  // [ntri][8]: ax ay x1 y1 x2 y2 det pad
+    const int32_t* bstart; // point-location bins (CSR)
+    const int32_t* bitems;
+    double gbx0, gby0, gbh;
+    int gnbx, gnby;
+    const int32_t* row_ptr; // FV rows, pivot first
+    const int32_t* col;
+    const T* gx;
+    const T* gy;
+    const T* cc;
+    const int32_t* outer;  // outer node ids [n_outer]
+    const int32_t* outer_of; // node -> outer index, -1 elsewhere
+    const int32_t* seg_a;  // wall segments
+    const int32_t* seg_b;
+    const double* seg_n;   // [nseg][2] body-outward normal times length
+    // patch state [9][n] (SoA), ping-pong
+    const T* fu_in;
+    T* fu_out;
+    T* snap;               // outer-node feed [2][12][n_outer]
+    int32_t* rtype;
+    int32_t* rdonor;
+    double* force;         // [cap][2]
+    unsigned* status;
+    // physics
+    T rho0, tau_s, tau_u, dt_u, k178, kneq;
+    int n_sub;
+    int motion;
+    double A, omega, vx, vy;
+};
+
+// ---------------------------------------------------------------- geometry
+// Barycentric coordinates of q in triangle k (precomputed ax ay x1 y1 x2 y2 det).
+__device__ __forceinline__ void bary_rn(const double* g, double qx, double qy, double& la,
+                                        double& lb, double& lc) {
+    double px = __dsub_rn(qx, g[0]);
+    double py = __dsub_rn(qy, g[1]);
+    double x1 = g[2], y1 = g[3], x2 = g[4], y2 = g[5], det = g[6];
+    lb = __ddiv_rn(__dsub_rn(__dmul_rn(px, y2), __dmul_rn(x2, py)), det);
+    lc = __ddiv_rn(__dsub_rn(__dmul_rn(x1, py), __dmul_rn(px, y1)), det);
+    la = __dsub_rn(__dsub_rn(1.0, lb), lc);
+}
+
+// Triangle of the body-frame mesh containing q: the candidate with the
+// largest smallest barycentric coordinate (>= -1e-12), ties to the lowest
+// index; -1 if none.
+template <typename T>
+__device__ __forceinline__ int locate_dev(const Dev<T>& d, double qx, double qy, double lam[3]) {
+    int bi = (int)floor(__ddiv_rn(__dsub_rn(qx, d.gbx0), d.gbh));
+    int bj = (int)floor(__ddiv_rn(__dsub_rn(qy, d.gby0), d.gbh));
+    if (bi < 0 || bj < 0 || bi >= d.gnbx || bj >= d.gnby) return -1;
+    int b = bj * d.gnbx + bi;
+    int best = -1;
+    double best_min = -1.0e300;
+    for (int e = d.bstart[b]; e < d.bstart[b + 1]; ++e) {
+        int k = d.bitems[e];
+        double la, lb, lc;
+        bary_rn(d.trigeo + 8 * (int64_t)k, qx, qy, la, lb, lc);
+        double mn = la < lb ? la : lb;
+        if (lc < mn) mn = lc;
+        if (mn >= -1e-12 && mn > best_min) {
+            best = k;
+            best_min = mn;
+            lam[0] = la;
+            lam[1] = lb;
+            lam[2] = lc;
+        }
+    }
+    return best;
+}
+
+// Inside the fictitious curve: squared distance to the lamina rectangle
+// below delta_f^2 (Sec. 4).
+template <typename T>
+__device__ __forceinline__ bool inside_curve(const Dev<T>& d, int x, int y, double cx, double cy) {
+    double qx = __dsub_rn(fabs(__dsub_rn((double)x, cx)), d.half_L);
+    double qy = __dsub_rn(fabs(__dsub_rn((double)y, cy)), d.half_T);
+    if (qx < 0.0) qx = 0.0;
+    if (qy < 0.0) qy = 0.0;
+    return __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)) < d.df2;
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T> void launch_init_struct(const Dev<T>& d, const double* rho, const double* ux,
+                                              const double* uy, double u0x, double u0y,
+                                              cudaStream_t s);
+template <typename T> void launch_init_box(const Dev<T>& d, int bx0, int by0, const double* rho,
+                                           const double* ux, const double* uy, double u0x,
+                                           double u0y, cudaStream_t s);
+template <typename T> void launch_classify(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> void launch_fill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
+                                               cudaStream_t s);
+template <typename T> void launch_fv_coeffs(const Dev<T>& d, const int32_t* tstart,
+                                            const int32_t* tlist, int lumped, T* gx, T* gy, T* cc,
+                                            cudaStream_t s);
+template <typename T> void launch_patch_init(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> void launch_refill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> void launch_fv_substep(const Dev<T>& d, const StepArgs& a, int m, cudaStream_t s);
+template <typename T> void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s);
+template <typename T> void launch_patch_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
+                                              double* f9, cudaStream_t s);
+void launch_gamma_sums(const double* force, int64_t t0, int64_t t1, double omega, double* out,
+                       cudaStream_t s);
+void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omega, double a,
+                        double b, double* out, cudaStream_t s);
+
+}  // namespace hk

@@ -1,0 +1,255 @@
+"""Python binding of the C ABI (include/hlbm.h).
+
+The functions below carry the C names and only marshal arguments; every
+step of the solver runs in the CUDA library.  PyTorch supplies device memory
+(its caching allocator is installed as the library's allocator) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+
+_callbacks = None
+
+
+class HLBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hlbm error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, h=None):
+    if rc != N.HLBM_OK:
+        lib = N.load()
+        msg = lib.hlbm_last_error(h).decode() if lib.hlbm_last_error(h) else ""
+        raise HLBMError(rc, msg)
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _callbacks
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:  # allocation failure is reported to the library as NULL
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _callbacks = (N.ALLOC_FN(_alloc), N.FREE_FN(_free))
+    _check(N.load().hlbm_set_allocator(_callbacks[0], _callbacks[1], None))
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
+    """grid: nx, ny, bc_x, bc_y, dtype ('f32'|'f64'), rho0, u0x, u0y, rho_init, ux_init, uy_init
+    patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped
+    motion: kind, A, omega, vx, vy.  Returns an opaque handle (keeps the host copies alive
+    for the duration of the call only)."""
+    lib = N.load()
+    keep = []
+
+    def arr(x, dt):
+        if x is None:
+            return None
+        a = np.ascontiguousarray(x, dtype=dt)
+        keep.append(a)
+        return a
+
+    g = N.hlbm_grid_t()
+    g.nx, g.ny = int(grid["nx"]), int(grid["ny"])
+    g.bc_x, g.bc_y = int(grid.get("bc_x", N.HLBM_BC_WALL)), int(grid.get("bc_y", N.HLBM_BC_OUTFLOW))
+    g.dtype = N.HLBM_F32 if grid.get("dtype", "f32") in ("f32", N.HLBM_F32) else N.HLBM_F64
+    g.rho0 = float(grid.get("rho0", 1.0))
+    g.u0x, g.u0y = float(grid.get("u0x", 0.0)), float(grid.get("u0y", 0.0))
+    g.rho_init = _dp(arr(grid.get("rho_init"), np.float64))
+    g.ux_init = _dp(arr(grid.get("ux_init"), np.float64))
+    g.uy_init = _dp(arr(grid.get("uy_init"), np.float64))
+    p = N.hlbm_patch_t()
+    xy, tri, kind = arr(patch["xy"], np.float64), arr(patch["tri"], np.int32), arr(patch["kind"], np.int8)
+    p.n_nodes, p.n_tris = xy.shape[0], tri.shape[0]
+    p.xy = _dp(xy)
+    p.tri = tri.ctypes.data_as(C.POINTER(C.c_int32))
+    p.kind = kind.ctypes.data_as(C.POINTER(C.c_int8))
+    p.lamina_L, p.lamina_T = float(patch["lamina_L"]), float(patch["lamina_T"])
+    p.x_c, p.y_c = float(patch["x_c"]), float(patch["y_c"])
+    p.delta_f = float(patch["delta_f"])
+    p.n_sub, p.lumped = int(patch["n_sub"]), int(patch.get("lumped", 0))
+    m = N.hlbm_motion_t()
+    m.kind = int(motion.get("kind", N.HLBM_MOTION_STATIC))
+    m.A, m.omega = float(motion.get("A", 0.0)), float(motion.get("omega", 0.0))
+    m.vx, m.vy = float(motion.get("vx", 0.0)), float(motion.get("vy", 0.0))
+    h = C.c_void_p()
+    _check(lib.hlbm_create(C.byref(g), C.byref(p), float(tau_s), C.byref(m), C.c_void_p(cuda_stream or None),
+                           C.byref(h)))
+    return h
+
+
+def hlbm_step(h, nsteps: int):
+    _check(N.load().hlbm_step(h, int(nsteps)), h)
+
+
+def hlbm_force(h, first: int, count: int):
+    fx, fy = np.empty(count), np.empty(count)
+    _check(N.load().hlbm_force(h, int(first), int(count), _dp(fx), _dp(fy)), h)
+    return fx, fy
+
+
+def hlbm_gamma(h, discard_periods: float = 1.0, fit_periods: float = 3.0):
+    re, im, rms = C.c_double(), C.c_double(), C.c_double()
+    _check(N.load().hlbm_gamma(h, discard_periods, fit_periods, C.byref(re), C.byref(im), C.byref(rms)), h)
+    return re.value, im.value, rms.value
+
+
+def hlbm_info(h):
+    info = N.hlbm_info_t()
+    _check(N.load().hlbm_info(h, C.byref(info)), h)
+    return {k: getattr(info, k) for k, _ in N.hlbm_info_t._fields_}
+
+
+def hlbm_get_fields(h, nx: int, ny: int, n_nodes: int):
+    out = [np.empty((ny, nx)) for _ in range(3)] + [np.empty(n_nodes) for _ in range(3)]
+    _check(N.load().hlbm_get_fields(h, *[_dp(o) for o in out]), h)
+    return out
+
+
+def hlbm_get_class(h, nx: int, ny: int):
+    out = np.empty((ny, nx), dtype=np.int8)
+    _check(N.load().hlbm_get_class(h, out.ctypes.data_as(C.POINTER(C.c_int8))), h)
+    return out
+
+
+def hlbm_get_refill(h, n_nodes: int):
+    t, d = np.empty(n_nodes, np.int32), np.empty(n_nodes, np.int32)
+    _check(N.load().hlbm_get_refill(h, t.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    d.ctypes.data_as(C.POINTER(C.c_int32))), h)
+    return t, d
+
+
+def hlbm_get_patch_f(h, n_nodes: int):
+    out = np.empty((n_nodes, 9))
+    _check(N.load().hlbm_get_patch_f(h, _dp(out)), h)
+    return out
+
+
+def hlbm_get_fv(h, n_nodes: int, nnz: int):
+    rp, col = np.empty(n_nodes + 1, np.int32), np.empty(nnz, np.int32)
+    gx, gy, cc = np.empty(nnz), np.empty(nnz), np.empty(nnz)
+    _check(N.load().hlbm_get_fv(h, rp.ctypes.data_as(C.POINTER(C.c_int32)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+                                _dp(gx), _dp(gy), _dp(cc)), h)
+    return rp, col, gx, gy, cc
+
+
+def hlbm_status(h) -> int:
+    v = C.c_uint32()
+    _check(N.load().hlbm_status(h, C.byref(v)), h)
+    return v.value
+
+
+def hlbm_profile(h, enable: bool):
+    _check(N.load().hlbm_profile(h, 1 if enable else 0), h)
+
+
+def hlbm_profile_read(h):
+    ms = np.zeros(len(N.PHASES))
+    launches = np.zeros(len(N.PHASES), dtype=np.int64)
+    _check(N.load().hlbm_profile_read(h, _dp(ms), launches.ctypes.data_as(C.POINTER(C.c_int64))), h)
+    return {p: (float(ms[k]), int(launches[k])) for k, p in enumerate(N.PHASES)}
+
+
+def hlbm_destroy(h):
+    if h:
+        N.load().hlbm_destroy(h)
+
+
+class Solver:
+    """Convenience owner of one hlbm handle built from a workload description
+    (an object with the attributes of ``inputs.Workload``)."""
+
+    def __init__(self, w, mesh=None, rho_init=None, u_init=None, stream: int | None = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        if _callbacks is None:
+            use_torch_allocator()
+        self.w = w
+        self.mesh = mesh if mesh is not None else w.mesh()
+        rho = rho_init if rho_init is not None else w.rho_init()
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        grid = dict(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, dtype=w.dtype, rho0=w.rho0, u0x=w.u0x,
+                    u0y=w.u0y, rho_init=rho,
+                    ux_init=None if u_init is None else u_init[0], uy_init=None if u_init is None else u_init[1])
+        patch = dict(xy=self.mesh.xy, tri=self.mesh.tri, kind=self.mesh.kind, lamina_L=w.L, lamina_T=w.T,
+                     x_c=w.xc, y_c=w.yc, delta_f=w.delta_f, n_sub=w.n_sub, lumped=w.lumped)
+        motion = dict(kind=w.motion, A=w.A, omega=w.omega, vx=w.vx, vy=w.vy)
+        self.h = hlbm_create(grid, patch, w.tau_s, motion, self.stream)
+        self.n = self.mesh.n_nodes
+
+    def close(self):
+        if getattr(self, "h", None):
+            hlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps: int = 1):
+        hlbm_step(self.h, nsteps)
+
+    def info(self):
+        return hlbm_info(self.h)
+
+    @property
+    def time(self):
+        return self.info()["time"]
+
+    def force(self):
+        t = self.time
+        return hlbm_force(self.h, 0, t + 1)
+
+    def gamma(self, discard=1.0, fit=3.0):
+        return hlbm_gamma(self.h, discard, fit)
+
+    def fields(self):
+        return hlbm_get_fields(self.h, self.w.nx, self.w.ny, self.n)
+
+    def struct_macro(self):
+        return tuple(self.fields()[:3])
+
+    def patch_macro(self):
+        return tuple(self.fields()[3:])
+
+    def struct_class(self):
+        return hlbm_get_class(self.h, self.w.nx, self.w.ny)
+
+    def refill_record(self):
+        return hlbm_get_refill(self.h, self.n)
+
+    def patch_f(self):
+        return hlbm_get_patch_f(self.h, self.n)
+
+    def fv_coeffs(self):
+        return hlbm_get_fv(self.h, self.n, self.info()["nnz"])
+
+    @property
+    def status(self):
+        return hlbm_status(self.h)
+
+    def profile(self, enable: bool = True):
+        hlbm_profile(self.h, enable)
+
+    def profile_read(self):
+        return hlbm_profile_read(self.h)

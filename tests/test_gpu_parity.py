@@ -1,0 +1,183 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+Bars: node classes and refill donors bit-exact; FP64 fields within 1e-10
+relative L2; FP32 fields within 1e-5 relative L2 over 200 steps; the
+hydrodynamic function within 0.5 %.  Sizes span several thread blocks and
+ragged lattice edges (203 x 157), plus the full 4096^2 workload on sampled
+outputs and properties.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_13631_gb300.build import build
+
+    build()
+
+
+def rel_l2(a, b, mask=None):
+    if mask is not None:
+        a, b = a[mask], b[mask]
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def vel_rel_l2(ux, uy, vx, vy, mask=None):
+    if mask is not None:
+        ux, uy, vx, vy = ux[mask], uy[mask], vx[mask], vy[mask]
+    return float(np.sqrt((((ux - vx) ** 2 + (uy - vy) ** 2).sum()) / ((vx ** 2 + vy ** 2).sum())))
+
+
+def pair(name, **over):
+    from paper_2006_13631_gb300 import Solver
+
+    w = inputs.workload(name) if isinstance(name, str) else name
+    for k, v in over.items():
+        setattr(w, k, v)
+    mesh = w.mesh()
+    rho = w.rho_init()
+    return w, Solver(w, mesh=mesh, rho_init=rho), oracle.Oracle(w, mesh=mesh, rho_init=rho)
+
+
+def compare_geometry(s, o):
+    assert np.array_equal(s.struct_class(), o.struct_class())
+    tg, dg = s.refill_record()
+    to, do = o.refill_record()
+    assert np.array_equal(tg, to)
+    assert np.array_equal(dg, do)
+
+
+def compare_fields(s, o, tol_u, tol_rho):
+    cls = o.struct_class()
+    disc = cls == oracle.DISC
+    rs, uxs, uys, ru, uxu, uyu = s.fields()
+    ro, uxo, uyo = o.struct_macro()
+    pr, pux, puy = o.patch_macro()
+    e = dict(struct_u=vel_rel_l2(uxs, uys, uxo, uyo, disc), struct_rho=rel_l2(rs, ro, disc),
+             patch_u=vel_rel_l2(uxu, uyu, pux, puy), patch_rho=rel_l2(ru, pr))
+    assert e["struct_u"] < tol_u and e["patch_u"] < tol_u, e
+    assert e["struct_rho"] < tol_rho and e["patch_rho"] < tol_rho, e
+    return e
+
+
+def test_fv_matrices_match_oracle():
+    w, s, o = pair("lamina-small-f64")
+    rp, col, gx, gy, cc = s.fv_coeffs()
+    rpo, colo, gxo, gyo, cco, vol = o.fv_coeffs()
+    assert np.array_equal(rp, rpo) and np.array_equal(col, colo)
+    scale = np.abs(gxo).max()
+    assert np.abs(gx - gxo).max() < 1e-12 * scale and np.abs(gy - gyo).max() < 1e-12 * scale
+    assert np.abs(cc - cco).max() < 1e-13
+
+
+def test_initial_state_matches_oracle():
+    w, s, o = pair("lamina-small-f64")
+    assert np.array_equal(s.struct_class(), o.struct_class())
+    assert np.abs(s.patch_f() - o.patch_f()).max() < 1e-14
+    fxs, fys = s.force()
+    fxo, fyo = o.force()
+    assert abs(fys[0] - fyo[0]) < 1e-12 and abs(fxs[0] - fxo[0]) < 1e-12
+
+
+def test_parity_fp64_small_ragged_lattice():
+    w, s, o = pair("lamina-small-f64")
+    for chunk in (1, 4, 25, 30):
+        s.step(chunk)
+        o.step(chunk)
+        compare_geometry(s, o)
+        compare_fields(s, o, 1e-10, 1e-12)
+    assert s.status == 0 and o.status == 0
+    fxs, fys = s.force()
+    fxo, fyo = o.force()
+    assert np.abs(fys - fyo).max() < 1e-9 * np.abs(fyo).max()
+
+
+def test_parity_fp32_200_steps():
+    w, s, o = pair("lamina-small-f32")
+    for chunk in (10, 40, 50, 100):
+        s.step(chunk)
+        o.step(chunk)
+        compare_geometry(s, o)
+    e = compare_fields(s, o, 1e-5, 1e-5)
+    print("fp32 200-step errors", e)
+    assert s.status == 0
+
+
+def test_parity_lamina_256_fp64_four_periods_and_gamma():
+    """256^2, chord 20, beta 500, KC 0.25, tau 0.6, FP64: 4 periods, Theta."""
+    w, s, o = pair("lamina-256-f64")
+    s.step(w.steps)
+    o.step(w.steps)
+    compare_geometry(s, o)
+    compare_fields(s, o, 1e-9, 1e-11)
+    re_g, im_g, _ = s.gamma(1.0, 3.0)
+    re_o, im_o, _ = o.gamma(1.0, 3.0)
+    assert abs(re_g - re_o) < 5e-3 * abs(re_o) and abs(im_g - im_o) < 5e-3 * abs(im_o)
+    assert abs(re_g - re_o) < 1e-8 and abs(im_g - im_o) < 1e-8
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_zero_disturbance_translating_patch(dtype, tol):
+    w = inputs.Workload("zero-disturbance", 64, 60, 12.0, 0.24, 30.3, 28.2, 0.7, 10, inputs.MOTION_UNIFORM,
+                        vx=0.02, vy=0.03, delta_f=1.8, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                        u0x=0.02, u0y=0.03, dtype=dtype,
+                        mesh_args=dict(n_L=24, n_T=1, n_layers=8, h1=0.2, d_out=3.6))
+    from paper_2006_13631_gb300 import Solver
+
+    s = Solver(w)
+    s.step(120)
+    assert s.status == 0
+    rs, uxs, uys, ru, uxu, uyu = s.fields()
+    disc = s.struct_class() == 0
+    assert np.abs(uxs[disc] - 0.02).max() < tol and np.abs(uys[disc] - 0.03).max() < tol
+    assert np.abs(uxu - 0.02).max() < tol and np.abs(uyu - 0.03).max() < tol
+    assert np.abs(rs[disc] - 1).max() < tol and np.abs(ru - 1).max() < tol
+
+
+def test_disk_patch_shear_wave_matches_oracle():
+    nx = ny = 64
+    w = inputs.Workload("disk-shear", nx, ny, 0.0, 0.0, 32.3, 32.2, 0.8, 20, inputs.MOTION_STATIC, delta_f=3.0,
+                        bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC, dtype="f32",
+                        mesh_args=dict(n_L=0, n_T=0, n_layers=12, h1=0.5, d_out=6.0))
+    mesh = w.mesh()
+    uy0 = 1e-3 * np.sin(2 * math.pi / nx * np.tile(np.arange(nx, dtype=float), (ny, 1)))
+    u0 = (np.zeros((ny, nx)), uy0)
+    from paper_2006_13631_gb300 import Solver
+
+    s = Solver(w, mesh=mesh, rho_init=np.ones((ny, nx)), u_init=u0)
+    o = oracle.Oracle(w, mesh=mesh, rho_init=np.ones((ny, nx)), u_init=u0)
+    s.step(300)
+    o.step(300)
+    compare_fields(s, o, 1e-5, 1e-6)
+
+
+def test_full_size_4096_first_steps_and_sampled_geometry():
+    """4096^2, chord 128, ~200k-node patch, FP32 -- the benchmark's launch
+    configuration: two full steps against the oracle, then geometry
+    (classes, refill types and donors) bit-exact at later sampled steps."""
+    w, s, o = pair("lamina-4096-f32")
+    s.step(2)
+    o.step(2)
+    compare_geometry(s, o)
+    e = compare_fields(s, o, 1e-5, 1e-5)
+    print("4096^2 two-step errors", e)
+    target = 400
+    s.step(target - 2)
+    assert s.status == 0
+    assert np.array_equal(s.struct_class(), o.classify_at(target - 1))
+    tg, dg = s.refill_record()
+    to, do = o.relocate_at(target - 1)
+    assert np.array_equal(tg, to) and np.array_equal(dg, do)
+    fx, fy = s.force()
+    assert np.isfinite(fy).all()
