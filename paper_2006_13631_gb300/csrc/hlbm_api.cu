@@ -279,7 +279,7 @@ int step_impl(hlbm* h, int64_t nsteps) {
         // 6. force on the lamina at t+1
         ev = phase_begin(h);
         launch_force<T>(d, t + 1, s);
-        phase_end(h, HLBM_PHASE_FORCE, ev, 1);
+        phase_end(h, HLBM_PHASE_FORCE, ev, d.nseg > 0 ? 2 : 1);
         if (h->ev_used > 4096) {
             int rc = phase_collect(h);
             if (rc != HLBM_OK) return rc;
@@ -496,12 +496,16 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.snap = (T*)dev_alloc(h, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
     d.rtype = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
     d.rdonor = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
+    d.tstart = d_tstart;
+    d.tlist = d_tlist;
+    d.fcontrib = (double*)dev_alloc(h, (size_t)2 * std::max(h->nseg, 1) * sizeof(double));
     h->status = (unsigned*)dev_alloc(h, 64);
     h->scratch = (double*)dev_alloc(h, 16 * sizeof(double));
     h->force_cap = 4096;
     h->force = (double*)dev_alloc(h, (size_t)h->force_cap * 2 * sizeof(double));
     if (rc != HLBM_OK) return rc;
-    if (!gxv || !gyv || !ccv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force)
+    if (!gxv || !gyv || !ccv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force ||
+        !d.fcontrib)
         return fail(h, HLBM_ENOMEM, "device allocation failed");
     d.gx = gxv;
     d.gy = gyv;
@@ -550,8 +554,6 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     dev_free(h, drho);
     dev_free(h, dux);
     dev_free(h, duy);
-    dev_free(h, d_tstart);
-    dev_free(h, d_tlist);
     h->t = 0;
     h->Xprev = X0;
     h->Yprev = Y0;
@@ -871,8 +873,8 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->n_wall_segments = h->nseg;
     info->box_w = bw;
     info->box_h = bh;
-    // refill, classify, fill, stream-collide, feed, n_sub FV, force
-    info->launches_per_step = 6 + h->patch.n_sub;
+    // refill, classify, fill, stream-collide, feed, n_sub FV, force (2)
+    info->launches_per_step = 7 + h->patch.n_sub;
     info->dtype = h->dtype;
     return HLBM_OK;
 }

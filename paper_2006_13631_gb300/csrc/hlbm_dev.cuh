@@ -31,9 +31,11 @@ __host__ __device__ __forceinline__ constexpr T w_of(int i) {
 
 enum : int8_t { CLS_DISC = 0, CLS_INTERP = 1, CLS_UNUSED = 2 };
 
-// Moments of a deviation set: rho = rho0 + sum f', j = sum f' c.
+// Moments of a deviation set: drho = sum f' (= rho - rho0, kept as its own
+// number so that small density changes are not rounded against rho0),
+// rho = rho0 + drho, u = (sum f' c) / rho.
 template <typename T>
-__device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& rho, T& ux, T& uy) {
+__device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& drho, T& rho, T& ux, T& uy) {
     T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -41,6 +43,7 @@ __device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& rho, T& 
         jx += T(cx_of(i)) * f[i];
         jy += T(cy_of(i)) * f[i];
     }
+    drho = r;
     rho = rho0 + r;
     T inv = T(1) / rho;
     ux = jx * inv;
@@ -48,12 +51,12 @@ __device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& rho, T& 
 }
 
 // Eq. local_eq minus w_i rho0:
-// f_i^eq - w_i rho0 = w_i (rho - rho0) + w_i rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)
+// f_i^eq - w_i rho0 = w_i (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2))
 template <typename T>
-__device__ __forceinline__ T feq_dev(int i, T rho, T rho0, T ux, T uy) {
+__device__ __forceinline__ T feq_dev(int i, T drho, T rho, T ux, T uy) {
     T cu = T(cx_of(i)) * ux + T(cy_of(i)) * uy;
     T usq = ux * ux + uy * uy;
-    return w_of<T>(i) * ((rho - rho0) + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+    return w_of<T>(i) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
 }
 
 // ---------------------------------------------------------------- layout
@@ -93,7 +96,10 @@ struct Dev {
     const int32_t* bitems;
     double gbx0, gby0, gbh;
     int gnbx, gnby;
+    const int32_t* tstart;  // node -> incident triangles (CSR)
+    const int32_t* tlist;
     const int32_t* row_ptr; // FV rows, pivot first
+    double* fcontrib;       // per-segment force contributions [nseg][2]
     const int32_t* col;
     const T* gx;
     const T* gy;
@@ -158,6 +164,31 @@ __device__ __forceinline__ int locate_dev(const Dev<T>& d, double qx, double qy,
     return best;
 }
 
+// locate_dev for the relocated position q of patch node P: the triangles
+// around P are tried first.  When q lies inside one of them with every
+// barycentric coordinate above 1e-6 (numerators checked against det with
+// margin), that triangle is the only candidate the full search could
+// accept (triangles do not overlap), so it is returned with the same
+// coordinates the full search computes; otherwise the full search runs.
+template <typename T>
+__device__ __forceinline__ int locate_from_node(const Dev<T>& d, int P, double qx, double qy, double lam[3]) {
+    for (int e = d.tstart[P]; e < d.tstart[P + 1]; ++e) {
+        int k = d.tlist[e];
+        const double* g = d.trigeo + 8 * (int64_t)k;
+        double px = __dsub_rn(qx, g[0]), py = __dsub_rn(qy, g[1]);
+        double nb = __dsub_rn(__dmul_rn(px, g[5]), __dmul_rn(g[4], py));
+        double nc = __dsub_rn(__dmul_rn(g[2], py), __dmul_rn(px, g[3]));
+        double det = g[6];
+        double s = det > 0.0 ? 1.0 : -1.0;
+        double lim = 2e-6 * fabs(det);
+        if (s * nb > lim && s * nc > lim && s * (det - nb - nc) > lim) {
+            bary_rn(g, qx, qy, lam[0], lam[1], lam[2]);
+            return k;
+        }
+    }
+    return locate_dev(d, qx, qy, lam);
+}
+
 // Inside the fictitious curve: squared distance to the lamina rectangle
 // below delta_f^2 (Sec. 4).
 template <typename T>
@@ -188,7 +219,7 @@ template <typename T> void launch_patch_init(const Dev<T>& d, const StepArgs& a,
 template <typename T> void launch_refill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_fv_substep(const Dev<T>& d, const StepArgs& a, int m, cudaStream_t s);
-template <typename T> void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s);
+template <typename T> void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s);  // 2 launches
 template <typename T> void launch_patch_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                               double* f9, cudaStream_t s);
 void launch_gamma_sums(const double* force, int64_t t0, int64_t t1, double omega, double* out,

@@ -84,20 +84,21 @@ __device__ __forceinline__ void bilinear_state(const Dev<T>& d, const T* box, in
         T f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = box[i * d.bplane + b];
-        T r, ux, uy;
-        moments_dev(f, d.rho0, r, ux, uy);
-        st[0] += w4[q] * r;
+        T dr, r, ux, uy;
+        moments_dev(f, d.rho0, dr, r, ux, uy);
+        st[0] += w4[q] * dr;
         st[1] += w4[q] * ux;
         st[2] += w4[q] * uy;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st[3 + i] += w4[q] * (f[i] - feq_dev<T>(i, r, d.rho0, ux, uy));
+        for (int i = 0; i < 9; ++i) st[3 + i] += w4[q] * (f[i] - feq_dev<T>(i, dr, r, ux, uy));
     }
 }
 
-// eq. continuity_stresses: f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq,s
+// eq. continuity_stresses: f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq,s;
+// st = (drho, ux, uy, f^neq[9])
 template <typename T>
 __device__ __forceinline__ T f_from_state(const Dev<T>& d, const T st[12], int i) {
-    return feq_dev<T>(i, st[0], d.rho0, st[1], st[2]) + d.kneq * st[3 + i];
+    return feq_dev<T>(i, st[0], d.rho0 + st[0], st[1], st[2]) + d.kneq * st[3 + i];
 }
 
 // initial patch: every node by the type-1 rule from the initial lattice state
@@ -137,7 +138,7 @@ __global__ void k_refill(Dev<T> d, StepArgs a) {
     }
     double qx = __dadd_rn(d.xy[2 * P], a.dX), qy = __dadd_rn(d.xy[2 * P + 1], a.dY);
     double lam[3];
-    int k = locate_dev(d, qx, qy, lam);
+    int k = locate_from_node(d, P, qx, qy, lam);
     if (k >= 0) {
         const int32_t* v = d.tri + 3 * k;
         T l0 = T(lam[0]), l1 = T(lam[1]), l2 = T(lam[2]);
@@ -227,13 +228,13 @@ __global__ void __launch_bounds__(128) k_fv_substep(Dev<T> d, StepArgs a, int m)
         T f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * n + k];
-        T r, ux, uy;
-        moments_dev(f, d.rho0, r, ux, uy);
+        T dr, r, ux, uy;
+        moments_dev(f, d.rho0, dr, r, ux, uy);
         T gxe = d.gx[e], gye = d.gy[e], ce = d.cc[e] * inv_tau;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             T S = T(cx_of(i)) * gxe + T(cy_of(i)) * gye;
-            acc[i] += S * f[i] - ce * (f[i] - feq_dev<T>(i, r, d.rho0, ux, uy));
+            acc[i] += S * f[i] - ce * (f[i] - feq_dev<T>(i, dr, r, ux, uy));
         }
     }
     T fn[9];
@@ -248,10 +249,10 @@ __global__ void __launch_bounds__(128) k_fv_substep(Dev<T> d, StepArgs a, int m)
             U = T(d.vx);
             V = T(d.vy);
         }
-        T r, ux, uy;
-        moments_dev(fn, d.rho0, r, ux, uy);
+        T dr, r, ux, uy;
+        moments_dev(fn, d.rho0, dr, r, ux, uy);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, r, d.rho0, U, V) - feq_dev<T>(i, r, d.rho0, ux, uy);
+        for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, dr, r, U, V) - feq_dev<T>(i, dr, r, ux, uy);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) d.fu_out[i * n + P] = fn[i];
@@ -273,33 +274,42 @@ __device__ void wall_stress(const Dev<T>& d, int P, double s[3]) {
     T f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * (int64_t)d.n + P];
-    T r, ux, uy;
-    moments_dev(f, d.rho0, r, ux, uy);
+    T dr, r, ux, uy;
+    moments_dev(f, d.rho0, dr, r, ux, uy);
     double pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        double fneq = double(f[i] - feq_dev<T>(i, r, d.rho0, ux, uy));
+        double fneq = double(f[i] - feq_dev<T>(i, dr, r, ux, uy));
         pxx += fneq * (cx_of(i) * cx_of(i));
         pxy += fneq * (cx_of(i) * cy_of(i));
         pyy += fneq * (cy_of(i) * cy_of(i));
     }
-    double p = (double(r) - double(d.rho0)) / 3.0;
+    double p = double(dr) / 3.0;
     s[0] = -p - pxx;
     s[1] = -pxy;
     s[2] = -p - pyy;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_force(Dev<T> d, int64_t t_out) {
+__global__ void __launch_bounds__(128) k_force_segments(Dev<T> d) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.nseg) return;
+    double sa[3], sb[3];
+    wall_stress(d, d.seg_a[k], sa);
+    wall_stress(d, d.seg_b[k], sb);
+    double nx = d.seg_n[2 * k], ny = d.seg_n[2 * k + 1];
+    d.fcontrib[2 * k] = 0.5 * ((sa[0] + sb[0]) * nx + (sa[1] + sb[1]) * ny);
+    d.fcontrib[2 * k + 1] = 0.5 * ((sa[1] + sb[1]) * nx + (sa[2] + sb[2]) * ny);
+}
+
+// fixed-order sum of the segment contributions (independent of scheduling)
+__global__ void __launch_bounds__(512) k_force_sum(const double* contrib, int nseg, double* force, int64_t t_out,
+                                                  unsigned* status) {
     __shared__ double sx[512], sy[512];
     double fx = 0.0, fy = 0.0;
-    for (int k = threadIdx.x; k < d.nseg; k += blockDim.x) {
-        double sa[3], sb[3];
-        wall_stress(d, d.seg_a[k], sa);
-        wall_stress(d, d.seg_b[k], sb);
-        double nx = d.seg_n[2 * k], ny = d.seg_n[2 * k + 1];
-        fx += 0.5 * ((sa[0] + sb[0]) * nx + (sa[1] + sb[1]) * ny);
-        fy += 0.5 * ((sa[1] + sb[1]) * nx + (sa[2] + sb[2]) * ny);
+    for (int k = threadIdx.x; k < nseg; k += blockDim.x) {
+        fx += contrib[2 * k];
+        fy += contrib[2 * k + 1];
     }
     sx[threadIdx.x] = fx;
     sy[threadIdx.x] = fy;
@@ -312,15 +322,16 @@ __global__ void __launch_bounds__(512) k_force(Dev<T> d, int64_t t_out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        d.force[2 * t_out] = sx[0];
-        d.force[2 * t_out + 1] = sy[0];
-        if (!isfinite(sx[0]) || !isfinite(sy[0])) atomicOr(d.status, HLBM_ST_NONFINITE);
+        force[2 * t_out] = sx[0];
+        force[2 * t_out + 1] = sy[0];
+        if (!isfinite(sx[0]) || !isfinite(sy[0])) atomicOr(status, HLBM_ST_NONFINITE);
     }
 }
 
 template <typename T>
 void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s) {
-    k_force<T><<<1, 512, 0, s>>>(d, t_out);
+    if (d.nseg > 0) k_force_segments<T><<<(d.nseg + 127) / 128, 128, 0, s>>>(d);
+    k_force_sum<<<1, 512, 0, s>>>(d.fcontrib, d.nseg, d.force, t_out, d.status);
 }
 
 // ---------------------------------------------------------- readback
@@ -331,9 +342,9 @@ __global__ void k_patch_macro(Dev<T> d, double* rho, double* ux, double* uy, dou
     T f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * (int64_t)d.n + P];
-    T r, vx, vy;
-    moments_dev(f, d.rho0, r, vx, vy);
-    if (rho) rho[P] = double(r);
+    T dr, r, vx, vy;
+    moments_dev(f, d.rho0, dr, r, vx, vy);
+    if (rho) rho[P] = double(d.rho0) + double(dr);
     if (ux) ux[P] = double(vx);
     if (uy) uy[P] = double(vy);
     if (f9) {

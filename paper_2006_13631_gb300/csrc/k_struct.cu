@@ -13,13 +13,14 @@ __global__ void k_init_struct(Dev<T> d, const double* rho, const double* ux, con
     int y = blockIdx.y;
     if (x >= d.nx) return;
     int64_t g = (int64_t)y * d.nx + x;
-    T r = rho ? T(rho[g]) : d.rho0;
+    double r = rho ? rho[g] : double(d.rho0);
+    T dr = T(r - double(d.rho0)), rr = T(r);
     T vx = ux ? T(ux[g]) : T(u0x);
     T vy = uy ? T(uy[g]) : T(u0y);
     int64_t s = (int64_t)y * d.pitch + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        T v = feq_dev<T>(i, r, d.rho0, vx, vy);
+        T v = feq_dev<T>(i, dr, rr, vx, vy);
         d.fA[i * d.plane + s] = v;
         d.fB[i * d.plane + s] = v;
     }
@@ -40,11 +41,12 @@ __global__ void k_init_box(Dev<T> d, int bx0, int by0, const double* rho, const 
     if (b >= d.bplane) return;
     int x = bx0 + (int)(b % d.bw), y = by0 + (int)(b / d.bw);
     int64_t g = (int64_t)y * d.nx + x;
-    T r = rho ? T(rho[g]) : d.rho0;
+    double r = rho ? rho[g] : double(d.rho0);
+    T dr = T(r - double(d.rho0)), rr = T(r);
     T vx = ux ? T(ux[g]) : T(u0x);
     T vy = uy ? T(uy[g]) : T(u0y);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d.sbox_new[i * d.bplane + b] = feq_dev<T>(i, r, d.rho0, vx, vy);
+    for (int i = 0; i < 9; ++i) d.sbox_new[i * d.bplane + b] = feq_dev<T>(i, dr, rr, vx, vy);
 }
 
 template <typename T>
@@ -122,18 +124,19 @@ __global__ void k_fill(Dev<T> d, StepArgs a) {
         T f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * (int64_t)d.n + v];
-        T r, ux, uy;
-        moments_dev(f, d.rho0, r, ux, uy);
+        T dr, r, ux, uy;
+        moments_dev(f, d.rho0, dr, r, ux, uy);
         T l = T(lam[j]);
-        st[0] += l * r;
+        st[0] += l * dr;
         st[1] += l * ux;
         st[2] += l * uy;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st[3 + i] += l * (f[i] - feq_dev<T>(i, r, d.rho0, ux, uy));
+        for (int i = 0; i < 9; ++i) st[3 + i] += l * (f[i] - feq_dev<T>(i, dr, r, ux, uy));
     }
+    const T rr = d.rho0 + st[0];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        d.fA[i * d.plane + s] = feq_dev<T>(i, st[0], d.rho0, st[1], st[2]) + d.k178 * st[3 + i];
+        d.fA[i * d.plane + s] = feq_dev<T>(i, st[0], rr, st[1], st[2]) + d.k178 * st[3 + i];
 }
 
 template <typename T>
@@ -186,12 +189,12 @@ __global__ void __launch_bounds__(256) k_stream_collide(Dev<T> d, StepArgs a) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = pull_edge(d, x, y, i);
     }
-    T r, ux, uy;
-    moments_dev(f, d.rho0, r, ux, uy);
+    T dr, r, ux, uy;
+    moments_dev(f, d.rho0, dr, r, ux, uy);
     T omega = T(1) / d.tau_s;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        T fe = feq_dev<T>(i, r, d.rho0, ux, uy);
+        T fe = feq_dev<T>(i, dr, r, ux, uy);
         d.fB[i * d.plane + s] = f[i] - omega * (f[i] - fe);
     }
     if (inbox) {
@@ -216,10 +219,10 @@ __global__ void k_struct_macro(Dev<T> d, double* rho, double* ux, double* uy) {
     T f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = d.fA[i * d.plane + s];
-    T r, vx, vy;
-    moments_dev(f, d.rho0, r, vx, vy);
+    T dr, r, vx, vy;
+    moments_dev(f, d.rho0, dr, r, vx, vy);
     int64_t g = (int64_t)y * d.nx + x;
-    rho[g] = double(r);
+    rho[g] = double(d.rho0) + double(dr);
     ux[g] = double(vx);
     uy[g] = double(vy);
 }
