@@ -71,6 +71,7 @@ extern "C" {
 #define HLBM_ST_DONOR_NOT_COMPUTED 2u /* bilinear donor not a computed node */
 #define HLBM_ST_NONFINITE 8u          /* NaN/Inf in the lamina force        */
 #define HLBM_ST_UNUSED_TO_DISC 16u    /* lattice node skipped a class       */
+#define HLBM_ST_SYNC_TIMEOUT 32u      /* FV tiles waited too long: aborted  */
 
 /* Cartesian lattice: nx*ny nodes at integer positions (x, y), row-major.
  * rho_init / ux_init / uy_init: optional host arrays [ny*nx] of the initial

@@ -42,6 +42,9 @@ struct hlbm {
     std::vector<int32_t> tri;
     std::vector<int8_t> kind;
     std::vector<int32_t> row_ptr, col, outer;
+    std::vector<int32_t> perm;  // internal node -> caller's node (Morton order)
+    int n_tiles = 0;
+    bool use_smem = false;      // shared-memory FV kernel (else global-memory kernel)
     double mxmin = 0, mxmax = 0, mymin = 0, mymax = 0;
     int nnz = 0, nseg = 0;
 
@@ -270,12 +273,11 @@ int step_impl(hlbm* h, int64_t nsteps) {
         // 5. outer-node feed and n FV sub-steps (eq. ulbe, eq. postcollision2_u)
         ev = phase_begin(h);
         launch_feed<T>(d, a, s);
-        for (int m = 0; m < d.n_sub; ++m) {
-            launch_fv_substep<T>(d, a, m, s);
-            h->ui = 1 - h->ui;
-            bind(h, d);
-        }
-        phase_end(h, HLBM_PHASE_FV, ev, 1 + d.n_sub);
+        cudaError_t fe = h->use_smem ? launch_fv_smem<T>(d, a, s) : launch_fv_persistent<T>(d, a, s);
+        if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
+        if (d.n_sub & 1) h->ui = 1 - h->ui;
+        bind(h, d);
+        phase_end(h, HLBM_PHASE_FV, ev, 2);
         // 6. force on the lamina at t+1
         ev = phase_begin(h);
         launch_force<T>(d, t + 1, s);
@@ -314,6 +316,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.rho0 = T(g->rho0);
     d.tau_s = T(h->tau_s);
     d.tau_u = T(h->tau_s - 0.5);
+    d.inv_tau_u = T(1.0 / (h->tau_s - 0.5));
     d.n_sub = p.n_sub;
     d.dt_u = T(1.0 / p.n_sub);
     d.k178 = T(2.0 * (h->tau_s - 1.0) / (2.0 * h->tau_s - 1.0));
@@ -328,6 +331,45 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.df2 = p.delta_f * p.delta_f;
     d.n = n;
     d.ntri = nt;
+
+    // --- renumber the nodes along a Morton curve of their positions so that
+    // contiguous node ranges (the FV tiles) are compact; triangles keep the
+    // caller's order (donor ties resolve to the lowest triangle index)
+    {
+        double hq = 0.0;
+        for (int k = 0; k < nt; ++k) {
+            const int32_t* v = &h->tri[3 * k];
+            hq += 0.5 * std::fabs((h->xy[2 * v[1]] - h->xy[2 * v[0]]) * (h->xy[2 * v[2] + 1] - h->xy[2 * v[0] + 1]) -
+                                  (h->xy[2 * v[2]] - h->xy[2 * v[0]]) * (h->xy[2 * v[1] + 1] - h->xy[2 * v[0] + 1]));
+        }
+        hq = std::sqrt(hq / std::max(n, 1));
+        double span = std::max(h->mxmax - h->mxmin, h->mymax - h->mymin);
+        if (span / hq > 65000.0) hq = span / 65000.0;
+        std::vector<std::pair<uint64_t, int32_t>> key(n);
+        for (int i = 0; i < n; ++i) {
+            uint32_t ix = (uint32_t)((h->xy[2 * i] - h->mxmin) / hq), iy = (uint32_t)((h->xy[2 * i + 1] - h->mymin) / hq);
+            uint64_t k = 0;
+            for (int b = 0; b < 16; ++b) k |= (uint64_t)((ix >> b) & 1u) << (2 * b) | (uint64_t)((iy >> b) & 1u) << (2 * b + 1);
+            key[i] = {k, i};
+        }
+        std::sort(key.begin(), key.end());
+        h->perm.resize(n);
+        std::vector<int32_t> inv(n);
+        for (int p = 0; p < n; ++p) {
+            h->perm[p] = key[p].second;
+            inv[key[p].second] = p;
+        }
+        std::vector<double> xy2(2 * (size_t)n);
+        std::vector<int8_t> kind2(n);
+        for (int p = 0; p < n; ++p) {
+            xy2[2 * p] = h->xy[2 * h->perm[p]];
+            xy2[2 * p + 1] = h->xy[2 * h->perm[p] + 1];
+            kind2[p] = h->kind[h->perm[p]];
+        }
+        for (auto& v : h->tri) v = inv[v];
+        h->xy.swap(xy2);
+        h->kind.swap(kind2);
+    }
 
     // --- topology: node -> triangles, FV rows (pivot first), wall segments
     std::vector<int32_t> tstart(n + 1, 0), tlist(3 * (size_t)nt);
@@ -362,6 +404,60 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     if (max_row > 64) return fail(h, HLBM_EINVAL, "a patch node has %d neighbours (max 63)", max_row - 1);
     h->nnz = (int)h->col.size();
     d.nnz = h->nnz;
+    // FV tiles: equal ranges of the Morton-ordered nodes.  The shared-memory
+    // kernel runs one block per SM; when a tile and its halo do not fit in
+    // shared memory, the global-memory kernel runs with as many tiles as it
+    // has co-resident blocks.  Neighbour tiles own a column of a tile's rows.
+    int sms = 0, devi = 0;
+    cudaGetDevice(&devi);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devi);
+    std::vector<int32_t> tile_start, owner(n), tile_nb_ptr, tile_nb, halo_ptr, halo_ids;
+    int tile_cap = 0, halo_cap = 0;
+    auto make_tiles = [&](int nt_) {
+        tile_start.assign(nt_ + 1, 0);
+        for (int k = 0; k <= nt_; ++k) tile_start[k] = (int32_t)((int64_t)k * n / nt_);
+        for (int k = 0; k < nt_; ++k)
+            for (int p = tile_start[k]; p < tile_start[k + 1]; ++p) owner[p] = k;
+        tile_nb_ptr.assign(nt_ + 1, 0);
+        tile_nb.clear();
+        halo_ptr.assign(nt_ + 1, 0);
+        halo_ids.clear();
+        tile_cap = halo_cap = 0;
+        for (int k = 0; k < nt_; ++k) {
+            std::vector<int32_t> nb, hl;
+            for (int p = tile_start[k]; p < tile_start[k + 1]; ++p)
+                for (int e = h->row_ptr[p]; e < h->row_ptr[p + 1]; ++e)
+                    if (owner[h->col[e]] != k) {
+                        nb.push_back(owner[h->col[e]]);
+                        hl.push_back(h->col[e]);
+                    }
+            std::sort(nb.begin(), nb.end());
+            nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+            std::sort(hl.begin(), hl.end());
+            hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
+            tile_nb.insert(tile_nb.end(), nb.begin(), nb.end());
+            tile_nb_ptr[k + 1] = (int32_t)tile_nb.size();
+            halo_ids.insert(halo_ids.end(), hl.begin(), hl.end());
+            halo_ptr[k + 1] = (int32_t)halo_ids.size();
+            tile_cap = std::max(tile_cap, tile_start[k + 1] - tile_start[k]);
+            halo_cap = std::max(halo_cap, (int)hl.size());
+        }
+    };
+    int n_tiles = std::max(1, std::min(sms, (n + 63) / 64));
+    make_tiles(n_tiles);
+    size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0), p.n_sub);
+    h->use_smem = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536 &&
+                  fv_smem_tile_capacity<T>(smem) >= n_tiles;
+    if (!h->use_smem) {
+        int cap = fv_tile_capacity<T>();
+        if (cap < 1) return fail(h, HLBM_ECUDA, "the FV kernel cannot be resident on this device");
+        n_tiles = std::max(1, std::min(cap, (n + 63) / 64));
+        make_tiles(n_tiles);
+    }
+    d.tile_cap = tile_cap;
+    d.halo_cap = std::max(halo_cap, 1);
+    h->n_tiles = n_tiles;
+    d.n_tiles = n_tiles;
     std::vector<int32_t> outer_of(n, -1);
     h->outer.clear();
     for (int P = 0; P < n; ++P)
@@ -471,7 +567,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         h->fbuf[b] = dev_alloc(h, fbytes);
         h->sbox[b] = dev_alloc(h, (size_t)9 * d.bplane * sizeof(T));
         h->cls[b] = (int8_t*)dev_alloc(h, (size_t)d.bplane);
-        h->fu[b] = dev_alloc(h, (size_t)9 * n * sizeof(T));
+        h->fu[b] = dev_alloc(h, (size_t)kRec * n * sizeof(T));
         if (!h->fbuf[b] || !h->sbox[b] || !h->cls[b] || !h->fu[b])
             return fail(h, HLBM_ENOMEM, "device allocation failed (lattice %zu bytes per buffer)", fbytes);
     }
@@ -490,9 +586,66 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.seg_n = upload(h, sn.data(), sn.size(), &rc);
     int32_t* d_tstart = upload(h, tstart.data(), tstart.size(), &rc);
     int32_t* d_tlist = upload(h, tlist.data(), tlist.size(), &rc);
-    T* gxv = (T*)dev_alloc(h, (size_t)h->nnz * sizeof(T));
-    T* gyv = (T*)dev_alloc(h, (size_t)h->nnz * sizeof(T));
-    T* ccv = (T*)dev_alloc(h, (size_t)h->nnz * sizeof(T));
+    Coef<T>* coefv = (Coef<T>*)dev_alloc(h, (size_t)h->nnz * sizeof(Coef<T>));
+    d.tile_start = upload(h, tile_start.data(), tile_start.size(), &rc);
+    d.tile_nb_ptr = upload(h, tile_nb_ptr.data(), tile_nb_ptr.size(), &rc);
+    d.tile_nb = upload(h, tile_nb.data(), tile_nb.size(), &rc);
+    d.progress = (unsigned long long*)dev_alloc(h, (size_t)n_tiles * sizeof(unsigned long long));
+    d.halo_ptr = upload(h, halo_ptr.data(), halo_ptr.size(), &rc);
+    d.halo_ids = upload(h, halo_ids.data(), halo_ids.size(), &rc);
+    // ELL layout (tile-local columns) and the nodes other tiles read
+    int ell_w = 0;
+    for (int p = 0; p < n; ++p) ell_w = std::max(ell_w, h->row_ptr[p + 1] - h->row_ptr[p]);
+    d.ell_width = ell_w;
+    std::vector<int32_t> ell_src((size_t)ell_w * n, -1), ell_col((size_t)ell_w * n, 0);
+    std::vector<int8_t> send(n, 0);
+    for (int32_t x : halo_ids) send[x] = 1;
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k], tn = tile_start[k + 1] - p0;
+        const int32_t* hb = halo_ids.data() + halo_ptr[k];
+        const int hn = halo_ptr[k + 1] - halo_ptr[k];
+        for (int r = 0; r < tn; ++r) {
+            const int p = p0 + r;
+            for (int j = 0; j < ell_w; ++j) {
+                size_t idx = (size_t)ell_w * p0 + (size_t)j * tn + r;
+                int e = h->row_ptr[p] + j;
+                if (e < h->row_ptr[p + 1]) {
+                    int c = h->col[e];
+                    ell_src[idx] = e;
+                    if (c >= p0 && c < p0 + tn)
+                        ell_col[idx] = c - p0;
+                    else
+                        ell_col[idx] = d.tile_cap + (int)(std::lower_bound(hb, hb + hn, c) - hb);
+                } else {
+                    ell_col[idx] = r;
+                }
+            }
+        }
+    }
+    // per tile: nodes whose rows read only the tile first (tile-local index)
+    std::vector<uint16_t> tile_order(std::max(n, 1), 0);
+    std::vector<int32_t> tile_interior(n_tiles, 0);
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k], p1 = tile_start[k + 1];
+        std::vector<uint16_t> in, bd;
+        for (int q = p0; q < p1; ++q) {
+            bool interior = true;
+            for (int e = h->row_ptr[q]; e < h->row_ptr[q + 1]; ++e)
+                if (h->col[e] < p0 || h->col[e] >= p1) interior = false;
+            (interior ? in : bd).push_back((uint16_t)(q - p0));
+        }
+        tile_interior[k] = (int32_t)in.size();
+        std::copy(in.begin(), in.end(), tile_order.begin() + p0);
+        std::copy(bd.begin(), bd.end(), tile_order.begin() + p0 + in.size());
+    }
+    d.tile_order = upload(h, tile_order.data(), tile_order.size(), &rc);
+    d.tile_interior = upload(h, tile_interior.data(), tile_interior.size(), &rc);
+    d.send = upload(h, send.data(), send.size(), &rc);
+    int32_t* d_ell_src = upload(h, ell_src.data(), ell_src.size(), &rc);
+    int32_t* d_ell_col = upload(h, ell_col.data(), ell_col.size(), &rc);
+    Coef<T>* ellv = (Coef<T>*)dev_alloc(h, std::max<size_t>(ell_src.size(), 1) * sizeof(Coef<T>));
+    d.ell = ellv;
+    d.abort_flag = (unsigned*)dev_alloc(h, 16);
     d.snap = (T*)dev_alloc(h, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
     d.rtype = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
     d.rdonor = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
@@ -504,12 +657,12 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     h->force_cap = 4096;
     h->force = (double*)dev_alloc(h, (size_t)h->force_cap * 2 * sizeof(double));
     if (rc != HLBM_OK) return rc;
-    if (!gxv || !gyv || !ccv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force ||
-        !d.fcontrib)
+    if (!coefv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force || !d.fcontrib ||
+        !d.progress || !d.abort_flag)
         return fail(h, HLBM_ENOMEM, "device allocation failed");
-    d.gx = gxv;
-    d.gy = gyv;
-    d.cc = ccv;
+    d.coef = coefv;
+    cudaMemsetAsync(d.progress, 0, (size_t)n_tiles * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.abort_flag, 0, 16, s);
     cudaMemsetAsync(h->status, 0, 64, s);
     cudaMemsetAsync(d.rtype, 0, (size_t)n * sizeof(int32_t), s);
     cudaMemsetAsync(d.rdonor, 0xff, (size_t)n * sizeof(int32_t), s);
@@ -517,7 +670,9 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->fbuf[b], 0, fbytes, s);
     h->fi = h->si = h->ui = h->ci = 0;
     bind(h, d);
-    launch_fv_coeffs<T>(d, d_tstart, d_tlist, p.lumped, gxv, gyv, ccv, s);
+    launch_fv_coeffs<T>(d, p.lumped, coefv, s);
+    if (!ellv) return fail(h, HLBM_ENOMEM, "device allocation failed");
+    launch_build_ell<T>(coefv, d_ell_src, d_ell_col, ellv, (int64_t)ell_src.size(), s);
 
     // --- initial state: equilibrium at the initial density and velocity
     const size_t N = (size_t)g->nx * g->ny;
@@ -554,6 +709,8 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     dev_free(h, drho);
     dev_free(h, dux);
     dev_free(h, duy);
+    dev_free(h, d_ell_src);
+    dev_free(h, d_ell_col);
     h->t = 0;
     h->Xprev = X0;
     h->Yprev = Y0;
@@ -570,6 +727,43 @@ int sync_status(hlbm* h, unsigned* bits) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "status readback");
     *bits = v;
+    return HLBM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+int get_fv_impl(hlbm_t* h, const Coef<T>* dcoef, int32_t* row_ptr, int32_t* col, double* gx, double* gy,
+                double* cc) {
+    const int n = h->patch.n_nodes;
+    std::vector<Coef<T>> c(h->nnz);
+    cudaError_t e = cudaMemcpyAsync(c.data(), dcoef, c.size() * sizeof(Coef<T>), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "FV readback");
+    std::vector<int32_t> inv(n);
+    for (int p = 0; p < n; ++p) inv[h->perm[p]] = p;
+    // rows in the caller's numbering: pivot first, then ascending columns
+    int pos = 0;
+    if (row_ptr) row_ptr[0] = 0;
+    for (int P = 0; P < n; ++P) {
+        int p = inv[P];
+        std::vector<std::pair<int32_t, int>> ent;
+        for (int e2 = h->row_ptr[p]; e2 < h->row_ptr[p + 1]; ++e2) {
+            int user = h->perm[c[e2].col];
+            ent.push_back({user == P ? -1 : user, e2});
+        }
+        std::sort(ent.begin(), ent.end());
+        for (auto& x : ent) {
+            if (col) col[pos] = x.first < 0 ? P : x.first;
+            if (gx) gx[pos] = double(c[x.second].gx);
+            if (gy) gy[pos] = double(c[x.second].gy);
+            if (cc) cc[pos] = double(c[x.second].c);
+            ++pos;
+        }
+        if (row_ptr) row_ptr[P + 1] = pos;
+    }
     return HLBM_OK;
 }
 
@@ -767,14 +961,19 @@ int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double
         launch_struct_macro<double>(h->dd, buf, buf + N, buf + 2 * N, h->stream);
         launch_patch_macro<double>(h->dd, buf + 3 * N, buf + 3 * N + n, buf + 3 * N + 2 * n, nullptr, h->stream);
     }
-    double* dst[6] = {rho_s, ux_s, uy_s, rho_u, ux_u, uy_u};
-    size_t off[6] = {0, N, 2 * N, 3 * N, 3 * N + n, 3 * N + 2 * n};
-    size_t len[6] = {N, N, N, n, n, n};
+    double* dst[3] = {rho_s, ux_s, uy_s};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
-        if (dst[k]) e = cudaMemcpyAsync(dst[k], buf + off[k], len[k] * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (dst[k]) e = cudaMemcpyAsync(dst[k], buf + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<double> patch(3 * n);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(patch.data(), buf + 3 * N, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) rc = cuda_check(h, e, "field readback");
+    double* pdst[3] = {rho_u, ux_u, uy_u};
+    for (int k = 0; k < 3 && rc == HLBM_OK; ++k)
+        if (pdst[k])
+            for (size_t p = 0; p < n; ++p) pdst[k][h->perm[p]] = patch[k * n + p];
     dev_free(h, buf);
     return rc;
 }
@@ -791,10 +990,14 @@ int hlbm_get_patch_f(hlbm_t* h, double* f9) {
         bind(h, h->dd);
         launch_patch_macro<double>(h->dd, nullptr, nullptr, nullptr, buf, h->stream);
     }
-    cudaError_t e = cudaMemcpyAsync(f9, buf, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<double> tmp(9 * n);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), buf, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     dev_free(h, buf);
-    return e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "patch readback");
+    if (e != cudaSuccess) return cuda_check(h, e, "patch readback");
+    for (size_t p = 0; p < n; ++p)
+        for (int i = 0; i < 9; ++i) f9[9 * (size_t)h->perm[p] + i] = tmp[9 * p + i];
+    return HLBM_OK;
 }
 
 int hlbm_get_class(hlbm_t* h, int8_t* cls) {
@@ -820,37 +1023,22 @@ int hlbm_get_refill(hlbm_t* h, int32_t* type, int32_t* donor) {
     const size_t n = h->patch.n_nodes;
     int32_t* rt = h->dtype == HLBM_F32 ? h->df.rtype : h->dd.rtype;
     int32_t* rd = h->dtype == HLBM_F32 ? h->df.rdonor : h->dd.rdonor;
-    cudaError_t e = cudaSuccess;
-    if (type) e = cudaMemcpyAsync(type, rt, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
-    if (donor && e == cudaSuccess) e = cudaMemcpyAsync(donor, rd, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<int32_t> t(n), d(n);
+    cudaError_t e = cudaMemcpyAsync(t.data(), rt, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.data(), rd, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    return e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "refill readback");
+    if (e != cudaSuccess) return cuda_check(h, e, "refill readback");
+    for (size_t p = 0; p < n; ++p) {
+        if (type) type[h->perm[p]] = t[p];
+        if (donor) donor[h->perm[p]] = d[p];
+    }
+    return HLBM_OK;
 }
 
 int hlbm_get_fv(hlbm_t* h, int32_t* row_ptr, int32_t* col, double* gx, double* gy, double* cc) {
     if (!h) return HLBM_EINVAL;
-    if (row_ptr) std::memcpy(row_ptr, h->row_ptr.data(), h->row_ptr.size() * sizeof(int32_t));
-    if (col) std::memcpy(col, h->col.data(), h->col.size() * sizeof(int32_t));
-    const size_t nnz = h->nnz;
-    std::vector<double> tmp(nnz);
-    double* outs[3] = {gx, gy, cc};
-    for (int k = 0; k < 3; ++k) {
-        if (!outs[k]) continue;
-        cudaError_t e;
-        if (h->dtype == HLBM_F32) {
-            const float* src[3] = {h->df.gx, h->df.gy, h->df.cc};
-            std::vector<float> f(nnz);
-            e = cudaMemcpyAsync(f.data(), src[k], nnz * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-            for (size_t i = 0; i < nnz; ++i) outs[k][i] = f[i];
-        } else {
-            const double* src[3] = {h->dd.gx, h->dd.gy, h->dd.cc};
-            e = cudaMemcpyAsync(outs[k], src[k], nnz * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        }
-        if (e != cudaSuccess) return cuda_check(h, e, "FV readback");
-    }
-    return HLBM_OK;
+    return h->dtype == HLBM_F32 ? get_fv_impl<float>(h, h->df.coef, row_ptr, col, gx, gy, cc)
+                                : get_fv_impl<double>(h, h->dd.coef, row_ptr, col, gx, gy, cc);
 }
 
 int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
@@ -873,8 +1061,8 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->n_wall_segments = h->nseg;
     info->box_w = bw;
     info->box_h = bh;
-    // refill, classify, fill, stream-collide, feed, n_sub FV, force (2)
-    info->launches_per_step = 7 + h->patch.n_sub;
+    // refill, classify, fill, stream-collide, feed, FV sub-steps, force (2)
+    info->launches_per_step = 8;
     info->dtype = h->dtype;
     return HLBM_OK;
 }

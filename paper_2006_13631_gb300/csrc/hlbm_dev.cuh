@@ -31,6 +31,22 @@ __host__ __device__ __forceinline__ constexpr T w_of(int i) {
 
 enum : int8_t { CLS_DISC = 0, CLS_INTERP = 1, CLS_UNUSED = 2 };
 
+// patch node record: f'[9], q[6], pad
+constexpr int kRec = 16;
+
+// FV matrix entry of row P: column k, g_Pk and C_Pk (S_ik = c_i . g_Pk)
+template <typename T>
+struct alignas(4 * sizeof(T)) Coef {
+    int32_t col;
+    T gx, gy, c;
+};
+template <>
+struct alignas(32) Coef<double> {
+    int32_t col;
+    int32_t pad;
+    double gx, gy, c;
+};
+
 // Moments of a deviation set: drho = sum f' (= rho - rho0, kept as its own
 // number so that small density changes are not rounded against rho0),
 // rho = rho0 + drho, u = (sum f' c) / rho.
@@ -101,15 +117,31 @@ struct Dev {
     const int32_t* row_ptr; // FV rows, pivot first
     double* fcontrib;       // per-segment force contributions [nseg][2]
     const int32_t* col;
-    const T* gx;
-    const T* gy;
-    const T* cc;
+    const Coef<T>* coef;    // per CSR entry: column, g_Pk (x, y), C_Pk
+    // persistent FV kernel: node tiles, neighbour tiles, progress counters
+    int n_tiles;
+    const int32_t* tile_start;
+    const int32_t* tile_nb_ptr;
+    const int32_t* tile_nb;
+    unsigned long long* progress;
+    unsigned* abort_flag;
+    // shared-memory tiles: halo node lists, ELL matrices with tile-local
+    // columns (own nodes first, then halo), and the nodes other tiles read
+    int ell_width;            // entries per row (rows padded)
+    int tile_cap, halo_cap;   // largest tile and halo
+    const int32_t* halo_ptr;  // [n_tiles + 1]
+    const int32_t* halo_ids;  // global node ids
+    const Coef<T>* ell;       // tile k: entry (row r, slot j) at ell_width*p0 + j*(p1-p0) + r
+    const int8_t* send;       // [n] 1 if some other tile reads the node
+    const uint16_t* tile_order; // per tile: local node order, nodes reading no halo first
+    const int32_t* tile_interior; // per tile: number of nodes reading no halo
     const int32_t* outer;  // outer node ids [n_outer]
     const int32_t* outer_of; // node -> outer index, -1 elsewhere
     const int32_t* seg_a;  // wall segments
     const int32_t* seg_b;
     const double* seg_n;   // [nseg][2] body-outward normal times length
-    // patch state [9][n] (SoA), ping-pong
+    // patch state, ping-pong, one record of kRec values per node:
+    // f'[0..8] and the moment terms q[0..5] of the equilibrium (see q_of)
     const T* fu_in;
     T* fu_out;
     T* snap;               // outer-node feed [2][12][n_outer]
@@ -118,7 +150,7 @@ struct Dev {
     double* force;         // [cap][2]
     unsigned* status;
     // physics
-    T rho0, tau_s, tau_u, dt_u, k178, kneq;
+    T rho0, tau_s, tau_u, inv_tau_u, dt_u, k178, kneq;
     int n_sub;
     int motion;
     double A, omega, vx, vy;
@@ -164,28 +196,41 @@ __device__ __forceinline__ int locate_dev(const Dev<T>& d, double qx, double qy,
     return best;
 }
 
-// locate_dev for the relocated position q of patch node P: the triangles
-// around P are tried first.  When q lies inside one of them with every
-// barycentric coordinate above 1e-6 (numerators checked against det with
-// margin), that triangle is the only candidate the full search could
-// accept (triangles do not overlap), so it is returned with the same
-// coordinates the full search computes; otherwise the full search runs.
+// locate_dev for the relocated position q of patch node P.  The triangles
+// around P (its star) are searched first with the same rule as locate_dev.
+// If the best of them holds q with P's own coordinate above 1e-6, q lies
+// inside the star away from its outer boundary, where no triangle outside
+// the star can come within the 1e-12 tolerance (triangles do not overlap);
+// that triangle is then the answer of the full search as well, with the
+// same coordinates.  Otherwise the full search runs.
 template <typename T>
 __device__ __forceinline__ int locate_from_node(const Dev<T>& d, int P, double qx, double qy, double lam[3]) {
+    int best = -1, best_slot = 0;
+    double best_min = -1.0e300;
     for (int e = d.tstart[P]; e < d.tstart[P + 1]; ++e) {
         int k = d.tlist[e];
         const double* g = d.trigeo + 8 * (int64_t)k;
+        // cheap reject on the numerators before the divisions
         double px = __dsub_rn(qx, g[0]), py = __dsub_rn(qy, g[1]);
         double nb = __dsub_rn(__dmul_rn(px, g[5]), __dmul_rn(g[4], py));
         double nc = __dsub_rn(__dmul_rn(g[2], py), __dmul_rn(px, g[3]));
-        double det = g[6];
-        double s = det > 0.0 ? 1.0 : -1.0;
-        double lim = 2e-6 * fabs(det);
-        if (s * nb > lim && s * nc > lim && s * (det - nb - nc) > lim) {
-            bary_rn(g, qx, qy, lam[0], lam[1], lam[2]);
-            return k;
+        double det = g[6], s = det > 0.0 ? 1.0 : -1.0, lim = -1e-9 * fabs(det);
+        if (s * nb < lim || s * nc < lim || s * (det - nb - nc) < lim) continue;
+        double la, lb, lc;
+        bary_rn(g, qx, qy, la, lb, lc);
+        double mn = la < lb ? la : lb;
+        if (lc < mn) mn = lc;
+        if (mn >= -1e-12 && mn > best_min) {
+            best = k;
+            best_min = mn;
+            lam[0] = la;
+            lam[1] = lb;
+            lam[2] = lc;
+            const int32_t* v = d.tri + 3 * k;
+            best_slot = v[0] == P ? 0 : (v[1] == P ? 1 : 2);
         }
     }
+    if (best >= 0 && lam[best_slot] > 1e-6) return best;
     return locate_dev(d, qx, qy, lam);
 }
 
@@ -212,13 +257,18 @@ template <typename T> void launch_fill(const Dev<T>& d, const StepArgs& a, cudaS
 template <typename T> void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                                cudaStream_t s);
-template <typename T> void launch_fv_coeffs(const Dev<T>& d, const int32_t* tstart,
-                                            const int32_t* tlist, int lumped, T* gx, T* gy, T* cc,
-                                            cudaStream_t s);
+template <typename T> void launch_fv_coeffs(const Dev<T>& d, int lumped, Coef<T>* coef, cudaStream_t s);
 template <typename T> void launch_patch_init(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_refill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
-template <typename T> void launch_fv_substep(const Dev<T>& d, const StepArgs& a, int m, cudaStream_t s);
+template <typename T> int fv_tile_capacity();
+template <typename T> cudaError_t launch_fv_persistent(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T> size_t fv_smem_bytes(int tile_cap, int halo_cap, int roff, int n_sub);
+template <typename T> int fv_tile_max();  // nodes per tile of the shared-memory FV kernel
+template <typename T> void launch_build_ell(const Coef<T>* coef, const int32_t* src, const int32_t* col, Coef<T>* ell,
+                                            int64_t count, cudaStream_t s);
+template <typename T> int fv_smem_tile_capacity(size_t smem);
+template <typename T> cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s);  // 2 launches
 template <typename T> void launch_patch_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                               double* f9, cudaStream_t s);

@@ -1,11 +1,74 @@
 // Patch kernels: FV matrices of eq. ulbe, the refill procedure of Sec. 4,
-// the outer-node feed of eq. postcollision2_u, the FV sub-step, the force on
-// the lamina and the reductions of the hydrodynamic-function fit (Sec. 2.1).
+// the outer-node feed of eq. postcollision2_u, the n FV sub-steps of one
+// lattice step (one persistent cooperative kernel), the force on the lamina
+// and the reductions of the hydrodynamic-function fit (Sec. 2.1).
+//
+// Patch state: one record of kRec values per node, f'[0..8] (deviation from
+// w_i rho0) followed by the quadratic equilibrium terms z[0..2] (z_of).
 #include "hlbm_dev.cuh"
 
 namespace hk {
 
 constexpr int kMaxRow = 64;
+constexpr int kMaxSub = 1024;
+
+// Patch record: f'[0..8] and the quadratic equilibrium terms
+// z = (jx^2 / rho, jx jy / rho, jy^2 / rho) at [9..11].  With j = sum_i c_i f'_i
+// and drho = sum_i f'_i,
+//   f_i^eq - w_i rho0 = w_i (drho - 1.5 (z0 + z2) + 3 c_i.j + 4.5 (cx^2 z0 + 2 cx cy z1 + cy^2 z2)),
+// linear in (drho, j, z).  For sum_k C_Pk f^eq(P_k) the drho and j parts
+// are sums of Cf_i = sum_k C_Pk f'_k,i, so only z has to be carried.
+template <typename T>
+__device__ __forceinline__ void z_of(const T (&f)[9], T rho0, T (&z)[3]) {
+    T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        dr += f[i];
+        jx += T(cx_of(i)) * f[i];
+        jy += T(cy_of(i)) * f[i];
+    }
+    T inv = T(1) / (rho0 + dr);
+    z[0] = jx * jx * inv;
+    z[1] = jx * jy * inv;
+    z[2] = jy * jy * inv;
+}
+
+// sum_k C_Pk (f^eq_k,i - w_i rho0) from Cf_i and Z = sum_k C_Pk z_k
+template <typename T>
+__device__ __forceinline__ void ceq_of(const T (&Cf)[9], const T (&Z)[3], T (&ceq)[9]) {
+    T dr = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        dr += Cf[i];
+        jx += T(cx_of(i)) * Cf[i];
+        jy += T(cy_of(i)) * Cf[i];
+    }
+    const T q0 = dr - T(1.5) * (Z[0] + Z[2]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T cx = T(cx_of(i)), cy = T(cy_of(i));
+        ceq[i] = w_of<T>(i) * (q0 + T(3) * (cx * jx + cy * jy) +
+                               T(4.5) * (cx * cx * Z[0] + T(2) * cx * cy * Z[1] + cy * cy * Z[2]));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_f(const T* rec, T (&f)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = rec[i];
+}
+
+template <typename T>
+__device__ __forceinline__ void store_rec(T* rec, const T (&f)[9], T rho0) {
+    T z[3];
+    z_of(f, rho0, z);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rec[i] = f[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rec[9 + j] = z[j];
+#pragma unroll
+    for (int j = 12; j < kRec; ++j) rec[j] = T(0);
+}
 
 // ------------------------------------------------------ FV matrices
 // Cell-vertex FV on median-dual control volumes with f linear on each
@@ -15,23 +78,23 @@ constexpr int kMaxRow = 64;
 //   C_Pk = (1/V_P) sum_{T ni P,k} |T| (11/54 if k = P else 7/108)
 //          (integral of phi_k over CV(P)), or the identity when lumped.
 template <typename T>
-__global__ void k_fv_coeffs(Dev<T> d, const int32_t* tstart, const int32_t* tlist, int lumped, T* gx_out,
-                            T* gy_out, T* cc_out) {
+__global__ void k_fv_coeffs(Dev<T> d, int lumped, Coef<T>* coef) {
     int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= d.n) return;
     int r0 = d.row_ptr[P], r1 = d.row_ptr[P + 1];
     double gx[kMaxRow], gy[kMaxRow], cc[kMaxRow];
     for (int e = 0; e < r1 - r0; ++e) gx[e] = gy[e] = cc[e] = 0.0;
     double V = 0.0;
-    for (int e = tstart[P]; e < tstart[P + 1]; ++e) {
-        const int32_t* v = d.tri + 3 * tlist[e];
-        double x0 = d.xy[2 * v[0]], y0 = d.xy[2 * v[0] + 1];
-        double x1 = d.xy[2 * v[1]], y1 = d.xy[2 * v[1] + 1];
-        double x2 = d.xy[2 * v[2]], y2 = d.xy[2 * v[2] + 1];
-        double A2 = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+    for (int e = d.tstart[P]; e < d.tstart[P + 1]; ++e) {
+        const int32_t* v = d.tri + 3 * d.tlist[e];
+        double X[3], Y[3];
+        for (int j = 0; j < 3; ++j) {
+            X[j] = d.xy[2 * v[j]];
+            Y[j] = d.xy[2 * v[j] + 1];
+        }
+        double A2 = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]);
         double area = 0.5 * fabs(A2);
         V += area / 3.0;
-        double X[3] = {x0, x1, x2}, Y[3] = {y0, y1, y2};
         for (int a = 0; a < 3; ++a) {
             int b = (a + 1) % 3, c = (a + 2) % 3;
             double grx = (Y[b] - Y[c]) / A2, gry = (X[c] - X[b]) / A2;
@@ -45,16 +108,18 @@ __global__ void k_fv_coeffs(Dev<T> d, const int32_t* tstart, const int32_t* tlis
         }
     }
     for (int e = 0; e < r1 - r0; ++e) {
-        gx_out[r0 + e] = T(gx[e] / V);
-        gy_out[r0 + e] = T(gy[e] / V);
-        cc_out[r0 + e] = lumped ? T(d.col[r0 + e] == P ? 1 : 0) : T(cc[e] / V);
+        Coef<T> c;
+        c.col = d.col[r0 + e];
+        c.gx = T(gx[e] / V);
+        c.gy = T(gy[e] / V);
+        c.c = lumped ? T(c.col == P ? 1 : 0) : T(cc[e] / V);
+        coef[r0 + e] = c;
     }
 }
 
 template <typename T>
-void launch_fv_coeffs(const Dev<T>& d, const int32_t* tstart, const int32_t* tlist, int lumped, T* gx, T* gy,
-                      T* cc, cudaStream_t s) {
-    k_fv_coeffs<T><<<(d.n + 127) / 128, 128, 0, s>>>(d, tstart, tlist, lumped, gx, gy, cc);
+void launch_fv_coeffs(const Dev<T>& d, int lumped, Coef<T>* coef, cudaStream_t s) {
+    k_fv_coeffs<T><<<(d.n + 127) / 128, 128, 0, s>>>(d, lumped, coef);
 }
 
 // ------------------------------------------------ bilinear from lattice
@@ -62,6 +127,7 @@ void launch_fv_coeffs(const Dev<T>& d, const int32_t* tstart, const int32_t* tli
 // the four lattice nodes of the cell enclosing (wx, wy).  The lattice state
 // is read from a window (origin ox, oy) of pre-collision populations; with
 // cls given, the four donors must be discretization nodes.
+// st = (drho, ux, uy, f^neq[9]).
 template <typename T>
 __device__ __forceinline__ void bilinear_state(const Dev<T>& d, const T* box, int ox, int oy, const int8_t* cls,
                                                double wx, double wy, T st[12], int& cell) {
@@ -94,11 +160,12 @@ __device__ __forceinline__ void bilinear_state(const Dev<T>& d, const T* box, in
     }
 }
 
-// eq. continuity_stresses: f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq,s;
-// st = (drho, ux, uy, f^neq[9])
+// eq. continuity_stresses: f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq,s
 template <typename T>
-__device__ __forceinline__ T f_from_state(const Dev<T>& d, const T st[12], int i) {
-    return feq_dev<T>(i, st[0], d.rho0 + st[0], st[1], st[2]) + d.kneq * st[3 + i];
+__device__ __forceinline__ void f_from_state(const Dev<T>& d, const T st[12], T (&f)[9]) {
+    const T r = d.rho0 + st[0];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = feq_dev<T>(i, st[0], r, st[1], st[2]) + d.kneq * st[3 + i];
 }
 
 // initial patch: every node by the type-1 rule from the initial lattice state
@@ -106,12 +173,12 @@ template <typename T>
 __global__ void k_patch_init(Dev<T> d, StepArgs a) {
     int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= d.n) return;
-    T st[12];
+    T st[12], f[9];
     int cell;
     bilinear_state(d, d.sbox_old, a.pbx0, a.pby0, (const int8_t*)nullptr, __dadd_rn(a.cx, d.xy[2 * P]),
                    __dadd_rn(a.cy, d.xy[2 * P + 1]), st, cell);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) d.fu_out[i * (int64_t)d.n + P] = f_from_state(d, st, i);
+    f_from_state(d, st, f);
+    store_rec(d.fu_out + (int64_t)kRec * P, f, d.rho0);
 }
 
 template <typename T>
@@ -128,10 +195,11 @@ template <typename T>
 __global__ void k_refill(Dev<T> d, StepArgs a) {
     int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= d.n) return;
-    const int64_t n = d.n;
+    const T* in = d.fu_in;
+    T* out = d.fu_out + (int64_t)kRec * P;
     if (d.kind[P] == HLBM_NODE_WALL) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d.fu_out[i * n + P] = d.fu_in[i * n + P];
+        for (int j = 0; j < kRec; ++j) out[j] = in[(int64_t)kRec * P + j];
         d.rtype[P] = 0;
         d.rdonor[P] = -1;
         return;
@@ -139,17 +207,17 @@ __global__ void k_refill(Dev<T> d, StepArgs a) {
     double qx = __dadd_rn(d.xy[2 * P], a.dX), qy = __dadd_rn(d.xy[2 * P + 1], a.dY);
     double lam[3];
     int k = locate_from_node(d, P, qx, qy, lam);
+    T f[9];
     if (k >= 0) {
         const int32_t* v = d.tri + 3 * k;
         T l0 = T(lam[0]), l1 = T(lam[1]), l2 = T(lam[2]);
+        const T *a0 = in + (int64_t)kRec * v[0], *a1 = in + (int64_t)kRec * v[1], *a2 = in + (int64_t)kRec * v[2];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            d.fu_out[i * n + P] = l0 * d.fu_in[i * n + v[0]] + l1 * d.fu_in[i * n + v[1]] + l2 * d.fu_in[i * n + v[2]];
+        for (int i = 0; i < 9; ++i) f[i] = l0 * a0[i] + l1 * a1[i] + l2 * a2[i];
         d.rtype[P] = 3;
         d.rdonor[P] = k;
     } else if (fabs(qx) <= d.half_L && fabs(qy) <= d.half_T) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d.fu_out[i * n + P] = d.fu_in[i * n + P];
+        load_f(in + (int64_t)kRec * P, f);
         d.rtype[P] = 2;
         d.rdonor[P] = -1;
     } else {
@@ -157,11 +225,11 @@ __global__ void k_refill(Dev<T> d, StepArgs a) {
         int cell;
         bilinear_state(d, d.sbox_old, a.pbx0, a.pby0, d.cls_prev, __dadd_rn(a.cx, d.xy[2 * P]),
                        __dadd_rn(a.cy, d.xy[2 * P + 1]), st, cell);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d.fu_out[i * n + P] = f_from_state(d, st, i);
+        f_from_state(d, st, f);
         d.rtype[P] = 1;
         d.rdonor[P] = cell;
     }
+    store_rec(out, f, d.rho0);
 }
 
 template <typename T>
@@ -195,52 +263,103 @@ void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
     if (d.n_outer) k_feed<T><<<(d.n_outer + 127) / 128, 128, 0, s>>>(d, a);
 }
 
-// ----------------------------------------------------------- FV step
-// One explicit step of eq. ulbe on interior and wall nodes:
-//   f_P += dt_u sum_k [ (c_i . g_Pk) f_k - (C_Pk / tau_u) (f_k - f_k^eq) ]
-// (deviations drop out of the streaming sum because sum_k g_Pk = 0);
-// wall nodes then take the lamina velocity: f += f^eq(rho, U) - f^eq(rho, u).
+// ----------------------------------------------------------- FV steps
+// n explicit steps of eq. ulbe on interior and wall nodes,
+//   f_P += dt_u sum_k [ (c_i . g_Pk) f_k - (C_Pk / tau_u) (f_k - f_k^eq) ],
+// evaluated as dt_u [ c_ix Gx_i + c_iy Gy_i - (Cf_i - f^eq_i(Q)) / tau_u ]
+// with Gx_i = sum_k gx_Pk f'_k,i, Cf_i = sum_k C_Pk f'_k,i, Q = sum_k C_Pk q_k
+// (the deviations drop out of the streaming sum because sum_k g_Pk = 0).
+// Wall nodes then take the lamina velocity: f += f^eq(rho, U) - f^eq(rho, u).
 // Outer nodes take the lattice state, linear in time at theta = (m+1)/n:
-//   f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq  (eq. postcollision2_u).
+//   f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq   (eq. postcollision2_u).
 template <typename T>
-__global__ void __launch_bounds__(128) k_fv_substep(Dev<T> d, StepArgs a, int m) {
-    int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= d.n) return;
-    const int64_t n = d.n;
-    int8_t kind = d.kind[P];
+__device__ __forceinline__ void fv_node(const Dev<T>& d, const T* __restrict__ in, T* __restrict__ out, int P,
+                                        int m, T U, T V) {
+    const int8_t kind = d.kind[P];
+    T fn[9];
     if (kind == HLBM_NODE_OUTER) {
-        int o = d.outer_of[P];
+        const int o = d.outer_of[P];
         const int64_t no = d.n_outer;
-        T th = T(m + 1) / T(d.n_sub);
+        const T th = T(m + 1) / T(d.n_sub);
         T st[12];
 #pragma unroll
         for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * d.snap[j * no + o] + th * d.snap[(12 + j) * no + o];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d.fu_out[i * n + P] = f_from_state(d, st, i);
+        f_from_state(d, st, fn);
+        store_rec(out + (int64_t)kRec * P, fn, d.rho0);
         return;
     }
-    T acc[9];
+    T Gx[9], Gy[9], Cf[9], Z[3], fP[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) acc[i] = T(0);
-    T inv_tau = T(1) / d.tau_u;
-    for (int e = d.row_ptr[P]; e < d.row_ptr[P + 1]; ++e) {
-        int k = d.col[e];
+    for (int i = 0; i < 9; ++i) Gx[i] = Gy[i] = Cf[i] = fP[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Z[j] = T(0);
+    const int r0 = d.row_ptr[P], r1 = d.row_ptr[P + 1];
+    for (int e = r0; e < r1; ++e) {
+        const Coef<T> c = d.coef[e];
+        const T* rec = in + (int64_t)kRec * c.col;
         T f[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * n + k];
-        T dr, r, ux, uy;
-        moments_dev(f, d.rho0, dr, r, ux, uy);
-        T gxe = d.gx[e], gye = d.gy[e], ce = d.cc[e] * inv_tau;
+        for (int i = 0; i < 9; ++i) f[i] = rec[i];
+        if (e == r0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fP[i] = f[i];
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            T S = T(cx_of(i)) * gxe + T(cy_of(i)) * gye;
-            acc[i] += S * f[i] - ce * (f[i] - feq_dev<T>(i, dr, r, ux, uy));
+            if (cx_of(i) != 0) Gx[i] += c.gx * f[i];
+            if (cy_of(i) != 0) Gy[i] += c.gy * f[i];
+            Cf[i] += c.c * f[i];
         }
-    }
-    T fn[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fn[i] = d.fu_in[i * n + P] + d.dt_u * acc[i];
+        for (int j = 0; j < 3; ++j) Z[j] += c.c * rec[9 + j];
+    }
+    T ceq[9];
+    ceq_of(Cf, Z, ceq);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        T s = -(Cf[i] - ceq[i]) * d.inv_tau_u;
+        if (cx_of(i) != 0) s += T(cx_of(i)) * Gx[i];
+        if (cy_of(i) != 0) s += T(cy_of(i)) * Gy[i];
+        fn[i] = fP[i] + d.dt_u * s;
+    }
     if (kind == HLBM_NODE_WALL) {
+        T dr, r, ux, uy;
+        moments_dev(fn, d.rho0, dr, r, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, dr, r, U, V) - feq_dev<T>(i, dr, r, ux, uy);
+    }
+    store_rec(out + (int64_t)kRec * P, fn, d.rho0);
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr int kFvThreads = 256;
+constexpr long kMaxSpins = 1L << 23;  // with 128 ns sleeps: about a second
+
+// All n sub-steps of one lattice step in one cooperative launch.  Block b
+// owns the node tile [tile_start[b], tile_start[b+1]) (nodes are numbered
+// along a Morton curve, so tiles are compact).  Before sub-step m a block
+// waits only for the tiles that own columns of its rows to finish sub-step
+// m-1 (monotone progress counters, acquire/release); that also guarantees
+// they are done reading the buffer it is about to overwrite.  Sub-step m
+// reads record buffer m%2 and writes buffer (m+1)%2.  Every wait is
+// bounded: on timeout the block raises HLBM_ST_SYNC_TIMEOUT and the abort
+// flag, and every block returns.
+template <typename T>
+__global__ void __launch_bounds__(kFvThreads) k_fv_steps(Dev<T> d, StepArgs a, const T* buf0, T* buf1) {
+    __shared__ T Us[kMaxSub], Vs[kMaxSub];
+    __shared__ int abort_sh;
+    const int tile = blockIdx.x;
+    const int p0 = d.tile_start[tile], p1 = d.tile_start[tile + 1];
+    for (int m = threadIdx.x; m < d.n_sub; m += blockDim.x) {
         double time = double(a.t) + double(m + 1) / double(d.n_sub);
         T U = T(0), V = T(0);
         if (d.motion == HLBM_MOTION_HARMONIC) {
@@ -249,31 +368,456 @@ __global__ void __launch_bounds__(128) k_fv_substep(Dev<T> d, StepArgs a, int m)
             U = T(d.vx);
             V = T(d.vy);
         }
-        T dr, r, ux, uy;
-        moments_dev(fn, d.rho0, dr, r, ux, uy);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, dr, r, U, V) - feq_dev<T>(i, dr, r, ux, uy);
+        Us[m] = U;
+        Vs[m] = V;
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) d.fu_out[i * n + P] = fn[i];
+    if (threadIdx.x == 0) abort_sh = 0;
+    const unsigned long long base = (unsigned long long)a.t * (unsigned long long)d.n_sub;
+    const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
+    __syncthreads();
+    for (int m = 0; m < d.n_sub; ++m) {
+        if (m > 0 && threadIdx.x < 32) {
+            bool ok = true;
+            for (int e = nb0 + (int)threadIdx.x; e < nb1 && ok; e += 32) {
+                const unsigned long long* pc = d.progress + d.tile_nb[e];
+                long spins = 0;
+                while (ld_acquire(pc) < base + m) {
+                    if (*(volatile unsigned*)d.abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    if (++spins > kMaxSpins) {
+                        atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
+                        atomicExch(d.abort_flag, 1u);
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            __threadfence();
+            ok = __all_sync(0xffffffffu, ok);
+            if (threadIdx.x == 0 && !ok) abort_sh = 1;
+        }
+        __syncthreads();
+        if (abort_sh) return;
+        const T* in = (m & 1) ? (const T*)buf1 : buf0;
+        T* out = (m & 1) ? (T*)buf0 : buf1;
+        for (int P = p0 + threadIdx.x; P < p1; P += blockDim.x) fv_node(d, in, out, P, m, Us[m], Vs[m]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(d.progress + tile, base + m + 1);
+        }
+    }
 }
 
 template <typename T>
-void launch_fv_substep(const Dev<T>& d, const StepArgs& a, int m, cudaStream_t s) {
-    k_fv_substep<T><<<(d.n + 127) / 128, 128, 0, s>>>(d, a, m);
+int fv_tile_capacity() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_steps<T>, kFvThreads, 0);
+    return sms * per;
+}
+
+template <typename T>
+cudaError_t launch_fv_persistent(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
+    if (d.n_sub > kMaxSub) return cudaErrorInvalidValue;
+    Dev<T> dd = d;
+    StepArgs aa = a;
+    const T* b0 = d.fu_in;
+    T* b1 = d.fu_out;
+    void* args[] = {&dd, &aa, &b0, &b1};
+    return cudaLaunchCooperativeKernel((const void*)k_fv_steps<T>, dim3(d.n_tiles), dim3(kFvThreads), args, 0, s);
+}
+
+// Shared-memory variant of k_fv_steps: one block per SM and everything its
+// inner loop reads in shared memory.  Block b holds, for its tile of nodes:
+//   - the records (f', z; 12 values) of its own nodes, updated in place:
+//     the new values of a thread's nodes wait in registers until every read
+//     of the old ones is done,
+//   - the records of its halo (the nodes of other tiles its rows read),
+//     reloaded each sub-step,
+//   - the off-diagonal FV entries in ELL form (tile-local column, g_Pk,
+//     C_Pk) and per node C_PP; the pivot g_PP is minus the sum of the
+//     off-diagonal g_Pk (the rows of g sum to zero),
+//   - node kinds, which nodes other tiles read, and a node order with the
+//     nodes that read no halo first.
+// A sub-step first updates the nodes that read no halo, then waits for the
+// neighbour tiles, loads the halo and updates the rest, so the exchange
+// overlaps the first part.  Only nodes read by other tiles are written to
+// global memory each sub-step, into record buffer (m+1)%2; the final state
+// of every node goes to buffer n%2.
+constexpr int kSmemThreads = 512;
+constexpr int kSR = 12;  // values per record in shared memory
+// own nodes per thread: tile_n <= kSlots<T> * kSmemThreads
+template <typename T>
+constexpr int kSlots = sizeof(T) == 4 ? 3 : 1;
+
+template <typename T>
+int fv_tile_max() {
+    return kSlots<T> * kSmemThreads;
+}
+
+struct TileSmem {
+    size_t own, halo, ecol, ecoef, cpp, order, kind, send, hid, uv, total;
+};
+
+template <typename T>
+__host__ __device__ inline TileSmem tile_smem_layout(int cap, int hcap, int roff, int n_sub) {
+    auto up = [](size_t x) { return (x + 15) / 16 * 16; };
+    TileSmem L;
+    size_t o = 0;
+    L.own = o;
+    o = up(o + sizeof(T) * kSR * (size_t)cap);
+    L.halo = o;
+    o = up(o + sizeof(T) * kSR * (size_t)hcap);
+    L.ecoef = o;
+    o = up(o + sizeof(T) * 3 * (size_t)roff * cap);
+    L.cpp = o;
+    o = up(o + sizeof(T) * (size_t)cap);
+    L.uv = o;
+    o = up(o + sizeof(T) * 2 * (size_t)n_sub);
+    L.hid = o;
+    o = up(o + sizeof(int32_t) * (size_t)hcap);
+    L.ecol = o;
+    o = up(o + sizeof(uint16_t) * (size_t)roff * cap);
+    L.order = o;
+    o = up(o + sizeof(uint16_t) * (size_t)cap);
+    L.kind = o;
+    o = up(o + (size_t)cap);
+    L.send = o;
+    o = up(o + (size_t)cap);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+size_t fv_smem_bytes(int tile_cap, int halo_cap, int roff, int n_sub) {
+    return tile_smem_layout<T>(tile_cap, halo_cap, roff, n_sub).total;
+}
+
+// 16-byte (float) or 2 x 16-byte (double) vector load and store
+template <typename T>
+struct Vec4 {
+    T x, y, z, w;
+};
+template <typename T>
+__device__ __forceinline__ Vec4<T> ld4(const T* p) {
+    Vec4<T> v;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(p);
+        v.x = a4.x, v.y = a4.y, v.z = a4.z, v.w = a4.w;
+    } else {
+        const double2 a2 = *reinterpret_cast<const double2*>(p);
+        const double2 b2 = *reinterpret_cast<const double2*>(p + 2);
+        v.x = a2.x, v.y = a2.y, v.z = b2.x, v.w = b2.y;
+    }
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, T x, T y, T z, T w) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x, y, z, w);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(x, y);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(z, w);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void read_rec12(const T* r, T (&f)[9], T (&z)[3]) {
+    const Vec4<T> a = ld4(r), b = ld4(r + 4), c = ld4(r + 8);
+    f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w;
+    f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+    f[8] = c.x, z[0] = c.y, z[1] = c.z, z[2] = c.w;
+}
+
+template <typename T>
+__device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r,
+                                             T (&fn)[9]) {
+    const int cap = d.tile_cap, roff = d.ell_width - 1;
+    const T* own = reinterpret_cast<const T*>(sm + L.own);
+    const T* halo = reinterpret_cast<const T*>(sm + L.halo) - (size_t)kSR * cap;
+    const T* ec = reinterpret_cast<const T*>(sm + L.ecoef);
+    const uint16_t* ecol = reinterpret_cast<const uint16_t*>(sm + L.ecol);
+    T Gx[9], Gy[9], Cf[9], Z[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Gx[i] = Gy[i] = Cf[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Z[j] = T(0);
+    T gpx = T(0), gpy = T(0);
+    for (int j = 0; j < roff; ++j) {
+        const int e = j * cap + r;
+        const int col = ecol[e];
+        const T gx = ec[e], gy = ec[(roff + j) * cap + r], c = ec[(2 * roff + j) * cap + r];
+        gpx -= gx;
+        gpy -= gy;
+        T f[9], z[3];
+        read_rec12((col < cap ? own : halo) + (size_t)kSR * col, f, z);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (cx_of(i) != 0) Gx[i] += gx * f[i];
+            if (cy_of(i) != 0) Gy[i] += gy * f[i];
+            Cf[i] += c * f[i];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Z[k] += c * z[k];
+    }
+    T fP[9], zP[3];
+    read_rec12(own + (size_t)kSR * r, fP, zP);
+    const T cP = reinterpret_cast<const T*>(sm + L.cpp)[r];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (cx_of(i) != 0) Gx[i] += gpx * fP[i];
+        if (cy_of(i) != 0) Gy[i] += gpy * fP[i];
+        Cf[i] += cP * fP[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Z[k] += cP * zP[k];
+    T ceq[9];
+    ceq_of(Cf, Z, ceq);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        T s = -(Cf[i] - ceq[i]) * d.inv_tau_u;
+        if (cx_of(i) != 0) s += T(cx_of(i)) * Gx[i];
+        if (cy_of(i) != 0) s += T(cy_of(i)) * Gy[i];
+        fn[i] = fP[i] + d.dt_u * s;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r,
+                                               int p0, int m, T (&fn)[9]) {
+    const int8_t kind = reinterpret_cast<const int8_t*>(sm + L.kind)[r];
+    if (kind == HLBM_NODE_OUTER) {
+        const int o = d.outer_of[p0 + r];
+        const int64_t no = d.n_outer;
+        const T th = T(m + 1) / T(d.n_sub);
+        T st[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * d.snap[j * no + o] + th * d.snap[(12 + j) * no + o];
+        f_from_state(d, st, fn);
+        return;
+    }
+    fv_node_tile(d, sm, L, r, fn);
+    if (kind == HLBM_NODE_WALL) {
+        const T* uv = reinterpret_cast<const T*>(sm + L.uv);
+        T dr, rr, ux, uy;
+        moments_dev(fn, d.rho0, dr, rr, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            fn[i] += feq_dev<T>(i, dr, rr, uv[m], uv[d.n_sub + m]) - feq_dev<T>(i, dr, rr, ux, uy);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs a, T* g0, T* g1) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int abort_sh;
+    const int cap = d.tile_cap, hcap = d.halo_cap, roff = d.ell_width - 1;
+    const TileSmem L = tile_smem_layout<T>(cap, hcap, roff, d.n_sub);
+    T* own = reinterpret_cast<T*>(sm + L.own);
+    T* halo = reinterpret_cast<T*>(sm + L.halo);
+    T* uv = reinterpret_cast<T*>(sm + L.uv);
+    int32_t* hid = reinterpret_cast<int32_t*>(sm + L.hid);
+    const uint16_t* order = reinterpret_cast<const uint16_t*>(sm + L.order);
+    const int8_t* send = reinterpret_cast<const int8_t*>(sm + L.send);
+    const int tile = blockIdx.x;
+    const int p0 = d.tile_start[tile], p1 = d.tile_start[tile + 1], tile_n = p1 - p0;
+    const int h0 = d.halo_ptr[tile], halo_n = d.halo_ptr[tile + 1] - h0;
+    const int n_int = d.tile_interior[tile];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // ---- tile set-up: wall velocity per sub-step, own records (buffer 0),
+    // matrices, kinds, send flags, node order, halo ids
+    for (int m = tid; m < d.n_sub; m += nt) {
+        double time = double(a.t) + double(m + 1) / double(d.n_sub);
+        T U = T(0), V = T(0);
+        if (d.motion == HLBM_MOTION_HARMONIC) {
+            V = T(d.A * d.omega * cos(d.omega * time));
+        } else if (d.motion == HLBM_MOTION_UNIFORM) {
+            U = T(d.vx);
+            V = T(d.vy);
+        }
+        uv[m] = U;
+        uv[d.n_sub + m] = V;
+    }
+    for (int x = tid; x < 3 * tile_n; x += nt) {
+        const int r = x / 3, c = x - 3 * r;
+        const Vec4<T> v = ld4(g0 + (int64_t)kRec * (p0 + r) + 4 * c);
+        st4(own + (size_t)kSR * r + 4 * c, v.x, v.y, v.z, v.w);
+    }
+    {
+        const Coef<T>* ell = d.ell + (int64_t)d.ell_width * p0;
+        T* ec = reinterpret_cast<T*>(sm + L.ecoef);
+        uint16_t* ecol = reinterpret_cast<uint16_t*>(sm + L.ecol);
+        T* cpp = reinterpret_cast<T*>(sm + L.cpp);
+        for (int x = tid; x < d.ell_width * tile_n; x += nt) {
+            const int j = x / tile_n, r = x - j * tile_n;
+            const Coef<T> c = ell[x];
+            if (j == 0) {
+                cpp[r] = c.c;
+            } else {
+                const int e = (j - 1) * cap + r;
+                ecol[e] = (uint16_t)c.col;
+                ec[e] = c.gx;
+                ec[(roff + j - 1) * cap + r] = c.gy;
+                ec[(2 * roff + j - 1) * cap + r] = c.c;
+            }
+        }
+        int8_t* kd = reinterpret_cast<int8_t*>(sm + L.kind);
+        int8_t* sd = reinterpret_cast<int8_t*>(sm + L.send);
+        uint16_t* od = reinterpret_cast<uint16_t*>(sm + L.order);
+        for (int r = tid; r < tile_n; r += nt) {
+            kd[r] = d.kind[p0 + r];
+            sd[r] = d.send[p0 + r];
+            od[r] = d.tile_order[p0 + r];
+        }
+        for (int h = tid; h < halo_n; h += nt) hid[h] = d.halo_ids[h0 + h];
+    }
+    if (tid == 0) abort_sh = 0;
+    __syncthreads();
+    const unsigned long long base = (unsigned long long)a.t * (unsigned long long)d.n_sub;
+    const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
+    for (int m = 0; m < d.n_sub; ++m) {
+        T fn[kSlots<T>][9];
+        // nodes that read no halo
+#pragma unroll
+        for (int s = 0; s < kSlots<T>; ++s) {
+            const int x = tid + s * nt;
+            if (x < n_int) fv_update_slot(d, sm, L, order[x], p0, m, fn[s]);
+        }
+        // wait for the neighbour tiles to publish state m, then load the halo
+        if (m > 0 && tid < 32) {
+            bool ok = true;
+            for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
+                const unsigned long long* pc = d.progress + d.tile_nb[e];
+                long spins = 0;
+                while (ld_acquire(pc) < base + m) {
+                    if (*(volatile unsigned*)d.abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    if (++spins > kMaxSpins) {
+                        atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
+                        atomicExch(d.abort_flag, 1u);
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+            ok = __all_sync(0xffffffffu, ok);
+            if (tid == 0 && !ok) abort_sh = 1;
+        }
+        __syncthreads();
+        if (abort_sh) return;
+        {
+            const T* gin = (m & 1) ? g1 : g0;
+            for (int x = tid; x < 3 * halo_n; x += nt) {
+                const int h = x / 3, c = x - 3 * h;
+                const Vec4<T> v = ld4(gin + (int64_t)kRec * hid[h] + 4 * c);
+                st4(halo + (size_t)kSR * h + 4 * c, v.x, v.y, v.z, v.w);
+            }
+        }
+        __syncthreads();
+        // nodes that read the halo
+#pragma unroll
+        for (int s = 0; s < kSlots<T>; ++s) {
+            const int x = tid + s * nt;
+            if (x >= n_int && x < tile_n) fv_update_slot(d, sm, L, order[x], p0, m, fn[s]);
+        }
+        __syncthreads();
+        // publish state m+1
+        T* gout = (m & 1) ? g0 : g1;
+        const bool last = (m == d.n_sub - 1);
+#pragma unroll
+        for (int s = 0; s < kSlots<T>; ++s) {
+            const int x = tid + s * nt;
+            if (x < tile_n) {
+                const int r = order[x];
+                T z[3];
+                z_of(fn[s], d.rho0, z);
+                T* o = own + (size_t)kSR * r;
+                st4(o, fn[s][0], fn[s][1], fn[s][2], fn[s][3]);
+                st4(o + 4, fn[s][4], fn[s][5], fn[s][6], fn[s][7]);
+                st4(o + 8, fn[s][8], z[0], z[1], z[2]);
+                if (last || send[r]) {
+                    T* rec = gout + (int64_t)kRec * (p0 + r);
+                    st4(rec, fn[s][0], fn[s][1], fn[s][2], fn[s][3]);
+                    st4(rec + 4, fn[s][4], fn[s][5], fn[s][6], fn[s][7]);
+                    st4(rec + 8, fn[s][8], z[0], z[1], z[2]);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release(d.progress + tile, base + m + 1);
+        }
+    }
+}
+
+// ELL copy of the FV matrices for the shared-memory kernel: entry i takes
+// CSR entry src[i] with tile-local column col[i] (src -1: padding, zero)
+template <typename T>
+__global__ void k_build_ell(const Coef<T>* coef, const int32_t* src, const int32_t* col, Coef<T>* ell, int64_t count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    Coef<T> c;
+    c.col = col[i];
+    c.gx = c.gy = c.c = T(0);
+    if (src[i] >= 0) {
+        const Coef<T> s = coef[src[i]];
+        c.gx = s.gx;
+        c.gy = s.gy;
+        c.c = s.c;
+    }
+    ell[i] = c;
+}
+
+template <typename T>
+void launch_build_ell(const Coef<T>* coef, const int32_t* src, const int32_t* col, Coef<T>* ell, int64_t count,
+                      cudaStream_t s) {
+    k_build_ell<T><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(coef, src, col, ell, count);
+}
+
+template <typename T>
+int fv_smem_tile_capacity(size_t smem) {
+    if (smem == 0) return 0;
+    int dev = 0, sms = 0, per = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)maxsm) return 0;
+    if (cudaFuncSetAttribute(k_fv_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tiles<T>, kSmemThreads, smem);
+    return sms * per;
+}
+
+template <typename T>
+cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
+    if (d.n_sub > kMaxSub) return cudaErrorInvalidValue;
+    Dev<T> dd = d;
+    StepArgs aa = a;
+    T* b0 = (T*)d.fu_in;
+    T* b1 = d.fu_out;
+    void* args[] = {&dd, &aa, &b0, &b1};
+    size_t smem = fv_smem_bytes<T>(d.tile_cap, d.halo_cap, d.ell_width - 1, d.n_sub);
+    return cudaLaunchCooperativeKernel((const void*)k_fv_tiles<T>, dim3(d.n_tiles), dim3(kSmemThreads), args, smem, s);
 }
 
 // ------------------------------------------------------------- force
 // Stress at wall nodes, sigma = -(rho - rho0) c_s^2 I - sum_i f^neq_i c_i c_i,
 // integrated by the trapezoid rule over the wall segments with the body's
 // outward normal (force of the fluid on the lamina, per unit length).
-// One block, fixed-order tree reduction: the result does not depend on
-// scheduling.
 template <typename T>
 __device__ void wall_stress(const Dev<T>& d, int P, double s[3]) {
     T f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * (int64_t)d.n + P];
+    load_f(d.fu_in + (int64_t)kRec * P, f);
     T dr, r, ux, uy;
     moments_dev(f, d.rho0, dr, r, ux, uy);
     double pxx = 0, pxy = 0, pyy = 0;
@@ -340,8 +884,7 @@ __global__ void k_patch_macro(Dev<T> d, double* rho, double* ux, double* uy, dou
     int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= d.n) return;
     T f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * (int64_t)d.n + P];
+    load_f(d.fu_in + (int64_t)kRec * P, f);
     T dr, r, vx, vy;
     moments_dev(f, d.rho0, dr, r, vx, vy);
     if (rho) rho[P] = double(d.rho0) + double(dr);
@@ -413,12 +956,18 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
 }
 
 #define HLBM_INST(T)                                                                                        \
-    template void launch_fv_coeffs<T>(const Dev<T>&, const int32_t*, const int32_t*, int, T*, T*, T*,         \
-                                      cudaStream_t);                                                        \
+    template void launch_fv_coeffs<T>(const Dev<T>&, int, Coef<T>*, cudaStream_t);                          \
     template void launch_patch_init<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                         \
     template void launch_refill<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                             \
     template void launch_feed<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                               \
-    template void launch_fv_substep<T>(const Dev<T>&, const StepArgs&, int, cudaStream_t);                   \
+    template int fv_tile_capacity<T>();                                                                       \
+    template cudaError_t launch_fv_persistent<T>(const Dev<T>&, const StepArgs&, cudaStream_t);               \
+    template size_t fv_smem_bytes<T>(int, int, int, int);                                                     \
+    template int fv_tile_max<T>();                                                                            \
+    template void launch_build_ell<T>(const Coef<T>*, const int32_t*, const int32_t*, Coef<T>*, int64_t,       \
+                                      cudaStream_t);                                                          \
+    template int fv_smem_tile_capacity<T>(size_t);                                                            \
+    template cudaError_t launch_fv_smem<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \
     template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);
 HLBM_INST(float)

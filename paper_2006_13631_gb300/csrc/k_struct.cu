@@ -123,7 +123,7 @@ __global__ void k_fill(Dev<T> d, StepArgs a) {
         int v = d.tri[3 * k + j];
         T f[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = d.fu_in[i * (int64_t)d.n + v];
+        for (int i = 0; i < 9; ++i) f[i] = d.fu_in[(int64_t)kRec * v + i];
         T dr, r, ux, uy;
         moments_dev(f, d.rho0, dr, r, ux, uy);
         T l = T(lam[j]);
