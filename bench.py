@@ -159,6 +159,51 @@ def cpu_baseline(workload):
             "sample": f"2 lattice steps of {w.name} from the initial state, serial FP64 oracle"}
 
 
+def _stream_source_hash():
+    """Hash of the source that defines the stream-collide kernel's traffic."""
+    import hashlib
+
+    def section(path, start, end):
+        s = open(path).read()
+        return s[s.index(start):s.index(end)]
+
+    csrc = os.path.join(ROOT, "paper_2006_13631_gb300", "csrc")
+    src = (section(os.path.join(csrc, "k_struct.cu"), "// ------------------------------------------------------ stream-collide",
+                   "// ------------------------------------------------------------- readback") +
+           section(os.path.join(csrc, "hlbm_dev.cuh"), "// ---------------------------------------------------------------- D2Q9",
+                   "// ---------------------------------------------------------------- layout"))
+    return hashlib.sha256(src.encode()).hexdigest()
+
+
+def stream_traffic(workload):
+    """DRAM bytes per stream-collide launch from the committed ncu summary, or
+    None if there is none for this workload or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", f"stream_collide_{workload}.md")
+    try:
+        text = open(path).read()
+        vals = dict(line.split(":", 1) for line in text.splitlines()
+                    if line.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+        if vals["source_sha256"].strip() != _stream_source_hash():
+            return None
+        return int(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def combine_ranks(ms: float, units: float, dist=None, device=None):
+    """Whole-job figures over the ranks: the slowest rank's time and the
+    units all ranks processed (each rank runs its own replica)."""
+    if dist is None:
+        return ms, units
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -206,13 +251,10 @@ def run_ours(args):
         status = s.status
         _, fy = s.force()
         finite = bool(np.isfinite(fy).all())
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    units_per_rank = (n_disc + n_u) * args.steps
-    value = world * units_per_rank / (ms / 1e3) / 1e6
-    mlups_subiter = world * (n_disc + w.n_sub * n_u) * args.steps / (ms / 1e3) / 1e6
+    ms, units = combine_ranks(ms, float((n_disc + n_u) * args.steps), dist, "cuda")
+    value = units / (ms / 1e3) / 1e6
+    _, units_sub = combine_ranks(ms, float((n_disc + w.n_sub * n_u) * args.steps), dist, "cuda")
+    mlups_subiter = units_sub / (ms / 1e3) / 1e6
 
     # roofline of the dominant phase (largest share of the timed region)
     peak, peak_kind = _peaks()
@@ -227,13 +269,7 @@ def run_ours(args):
     # CSR rows (column index and three coefficients per entry)
     fv_bytes = 18 * bytes_per * n_u + nnz * (4 + 3 * bytes_per)
     fv_gbs = fv_bytes / (fv_ms / fv_n / 1e3) / 1e9 if fv_n else None
-    traffic = None
-    tr_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_file):
-        try:
-            traffic = json.load(open(tr_file)).get(f"{w.name}:stream")
-        except Exception:
-            traffic = None
+    traffic = stream_traffic(w.name)
     roof = {"bound": "hbm", "kernel": "stream_collide", "achieved": stream_gbs, "peak": peak, "unit": "GB/s",
             "frac": stream_gbs / peak if stream_gbs else None, "traffic": traffic,
             "peak_source": peak_kind, "dominant_phase": dom,
