@@ -205,6 +205,31 @@ int hlbm_profile_read(hlbm_t* h, double* ms, int64_t* launches);
 /* Device status bits (HLBM_ST_*), accumulated since creation. */
 int hlbm_status(hlbm_t* h, uint32_t* bits);
 
+/* Least-squares fit F(t) = a sin(w t) + b cos(w t) over t = t0..t1 of the
+ * samples F(t) = samples[t * stride] (DEVICE memory, caller-owned, at least
+ * t1 * stride + 1 doubles), the fit hlbm_gamma performs, for callers that
+ * must not allocate device memory: code recording a CUDA graph by stream
+ * capture, code running under a fixed device-memory budget or inside a
+ * framework that owns all allocations, and loops that cannot take the
+ * device-wide synchronisation of cudaMalloc / cudaFree.  The paper has no
+ * counterpart; it is an interface of this library.  (A solver's force
+ * history interleaves F_x and F_y: pass its F_y column with stride 2.)
+ *
+ * Allocates nothing: its intermediate sums live in a file-scope device
+ * array of 257 x 8 doubles that every GPU loading the library holds until
+ * the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so make the first call on each
+ * device before any stream capture.  Calls share the array: every value a
+ * call reads is written earlier in the same call, but calls that overlap
+ * on the GPU (other streams or host threads) race and must be serialised
+ * by the caller.  Work is queued on cuda_stream (a cudaStream_t, NULL =
+ * legacy default stream), which is synchronised before a, b and rms (host
+ * pointers; rms may be NULL) are written.  Returns HLBM_EINVAL for more
+ * than 2^26 samples, t1 <= t0, t0 < 0, stride < 1 or omega <= 0, and
+ * HLBM_ECUDA when a CUDA call fails. */
+int hlbm_fit_static(const double* samples, int64_t stride, int64_t t0, int64_t t1, double omega,
+                    void* cuda_stream, double* a, double* b, double* rms);
+
 /* Message of the last failed call on h; with h == NULL, of the last failed
  * hlbm_create on this thread. */
 const char* hlbm_last_error(const hlbm_t* h);

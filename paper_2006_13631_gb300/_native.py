@@ -64,6 +64,8 @@ SIGNATURES = {
     "hlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "hlbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hlbm_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
+    "hlbm_fit_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_void_p, _dp, _dp,
+                                  _dp]),
     "hlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "hlbm_destroy": (None, [C.c_void_p]),
 }

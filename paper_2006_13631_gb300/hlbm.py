@@ -166,6 +166,17 @@ def hlbm_profile_read(h):
     return {p: (float(ms[k]), int(launches[k])) for k, p in enumerate(N.PHASES)}
 
 
+def hlbm_fit_static(samples_ptr: int, stride: int, t0: int, t1: int, omega: float, cuda_stream: int = 0):
+    """Sine fit of device samples without any device allocation (see include/hlbm.h).
+    samples_ptr: device address of the samples.  Returns (a, b, rms)."""
+    a, b, rms = C.c_double(), C.c_double(), C.c_double()
+    rc = N.load().hlbm_fit_static(C.c_void_p(samples_ptr), int(stride), int(t0), int(t1), float(omega),
+                                  C.c_void_p(cuda_stream or None), C.byref(a), C.byref(b), C.byref(rms))
+    if rc != N.HLBM_OK:
+        raise HLBMError(rc, "hlbm_fit_static failed")
+    return a.value, b.value, rms.value
+
+
 def hlbm_destroy(h):
     if h:
         N.load().hlbm_destroy(h)
