@@ -497,6 +497,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
 
     // --- triangle geometry for barycentric tests, and point-location bins
     std::vector<double> tg(8 * (size_t)nt);
+    std::vector<float> tgrad(6 * (size_t)nt);
     double area_sum = 0.0;
     for (int k = 0; k < nt; ++k) {
         const int32_t* v = &h->tri[3 * k];
@@ -514,6 +515,14 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         o[5] = y2;
         o[6] = det;
         o[7] = 0.0;
+        // gradients of the barycentric coordinates (a, b, c) of triangle k
+        float* gr = &tgrad[6 * (size_t)k];
+        gr[2] = (float)(y2 / det);
+        gr[3] = (float)(-x2 / det);
+        gr[4] = (float)(-y1 / det);
+        gr[5] = (float)(x1 / det);
+        gr[0] = (float)(-(y2 - y1) / det);
+        gr[1] = (float)((x2 - x1) / det);
         area_sum += 0.5 * std::fabs(det);
     }
     double bh = 1.5 * std::sqrt(area_sum / nt);
@@ -575,6 +584,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.kind = upload(h, h->kind.data(), h->kind.size(), &rc);
     d.tri = upload(h, h->tri.data(), h->tri.size(), &rc);
     d.trigeo = upload(h, tg.data(), tg.size(), &rc);
+    d.trigrad = upload(h, tgrad.data(), tgrad.size(), &rc);
     d.bstart = upload(h, bstart.data(), bstart.size(), &rc);
     d.bitems = upload(h, bitems.data(), bitems.size(), &rc);
     d.row_ptr = upload(h, h->row_ptr.data(), h->row_ptr.size(), &rc);

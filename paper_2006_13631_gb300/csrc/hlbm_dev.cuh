@@ -108,6 +108,7 @@ struct Dev {
     const int8_t* kind;    // [n]
     const int32_t* tri;    // [ntri][3]
     const double* trigeo;  // [ntri][8]: ax ay x1 y1 x2 y2 det pad
+    const float* trigrad;  // [ntri][6]: gradients of the three barycentric coordinates
     const int32_t* bstart; // point-location bins (CSR)
     const int32_t* bitems;
     double gbx0, gby0, gbh;
@@ -207,17 +208,22 @@ template <typename T>
 __device__ __forceinline__ int locate_from_node(const Dev<T>& d, int P, double qx, double qy, double lam[3]) {
     int best = -1, best_slot = 0;
     double best_min = -1.0e300;
+    // q = x_P + (dx, dy): an FP32 estimate of the coordinates, lambda_j =
+    // [j == P] + grad lambda_j . (dx, dy), discards triangles clearly not
+    // holding q (estimate below -1e-5, far beyond its ~1e-7 error); the
+    // others take the exact FP64 test
+    const float dx = float(__dsub_rn(qx, d.xy[2 * P])), dy = float(__dsub_rn(qy, d.xy[2 * P + 1]));
     for (int e = d.tstart[P]; e < d.tstart[P + 1]; ++e) {
         int k = d.tlist[e];
-        const double* g = d.trigeo + 8 * (int64_t)k;
-        // cheap reject on the numerators before the divisions
-        double px = __dsub_rn(qx, g[0]), py = __dsub_rn(qy, g[1]);
-        double nb = __dsub_rn(__dmul_rn(px, g[5]), __dmul_rn(g[4], py));
-        double nc = __dsub_rn(__dmul_rn(g[2], py), __dmul_rn(px, g[3]));
-        double det = g[6], s = det > 0.0 ? 1.0 : -1.0, lim = -1e-9 * fabs(det);
-        if (s * nb < lim || s * nc < lim || s * (det - nb - nc) < lim) continue;
+        const int32_t* v = d.tri + 3 * k;
+        const int slot = v[0] == P ? 0 : (v[1] == P ? 1 : 2);
+        const float* gr = d.trigrad + 6 * (int64_t)k;
+        float l0 = fmaf(gr[0], dx, gr[1] * dy) + (slot == 0 ? 1.0f : 0.0f);
+        float l1 = fmaf(gr[2], dx, gr[3] * dy) + (slot == 1 ? 1.0f : 0.0f);
+        float l2 = fmaf(gr[4], dx, gr[5] * dy) + (slot == 2 ? 1.0f : 0.0f);
+        if (fminf(l0, fminf(l1, l2)) < -1e-5f) continue;
         double la, lb, lc;
-        bary_rn(g, qx, qy, la, lb, lc);
+        bary_rn(d.trigeo + 8 * (int64_t)k, qx, qy, la, lb, lc);
         double mn = la < lb ? la : lb;
         if (lc < mn) mn = lc;
         if (mn >= -1e-12 && mn > best_min) {
@@ -226,8 +232,7 @@ __device__ __forceinline__ int locate_from_node(const Dev<T>& d, int P, double q
             lam[0] = la;
             lam[1] = lb;
             lam[2] = lc;
-            const int32_t* v = d.tri + 3 * k;
-            best_slot = v[0] == P ? 0 : (v[1] == P ? 1 : 2);
+            best_slot = slot;
         }
     }
     if (best >= 0 && lam[best_slot] > 1e-6) return best;
