@@ -297,6 +297,32 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d / k_e2e, "d2h_bytes_per_step": 16,
                "note": f"{k_e2e} steps incl. creation from host arrays and a force read-back every step"}
     s.close()
+    # the same workload with the lattice populations stored as FP16 / BF16
+    # deviations (FP32 arithmetic), each against the FP32 path above
+    reduced = {}
+    if not args.no_reduced:
+        k_red = max(10, min(args.steps, 100))
+        for st in ("f16", "bf16"):
+            w.dtype = st
+            with torch.cuda.stream(stream):
+                s3 = Solver(w, mesh=mesh, rho_init=rho, stream=stream.cuda_stream)
+                s3.step(args.warmup)
+                torch.cuda.synchronize()
+                s3.profile(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s3.step(k_red)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ph = s3.profile_read()
+                ms3 = e0.elapsed_time(e1)
+                sms, sn = ph["stream"]
+                gbs = 18 * 2 * n_disc / (sms / sn / 1e3) / 1e9 if sn else None
+                reduced[st] = {"value": (n_disc + n_u) * k_red / (ms3 / 1e3) / 1e6, "unit": UNIT, "steps": k_red,
+                               "ms_per_step": ms3 / k_red, "speedup_vs_f32": (ms / args.steps) / (ms3 / k_red),
+                               "stream_gbs": gbs, "stream_frac": gbs / peak if gbs else None}
+                s3.close()
+        w.dtype = "f32"
     if rank != 0:
         return 0
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.workload)
@@ -307,6 +333,7 @@ def run_ours(args):
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)" % (9 * bytes_per * w.nx * w.ny / 1e6)},
             "mlups_subiter": mlups_subiter, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "reduced_storage": reduced or None,
             "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}
     print(json.dumps(line), flush=True)
     if dist:
@@ -323,6 +350,7 @@ def main():
     ap.add_argument("--workload", default="lamina-4096-f32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-reduced", action="store_true", help="skip the FP16/BF16 lattice-storage runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

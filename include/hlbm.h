@@ -53,8 +53,11 @@ extern "C" {
 #define HLBM_BC_PERIODIC 2
 
 /* storage and arithmetic precision of the populations */
-#define HLBM_F64 0
-#define HLBM_F32 1
+#define HLBM_F64 0  /* FP64 storage and arithmetic                               */
+#define HLBM_F32 1  /* FP32 storage and arithmetic                               */
+#define HLBM_F16 2  /* lattice populations stored as FP16 (scaled by 2^10)       */
+                    /* deviations; FP32 arithmetic and patch; FP64 force and fit */
+#define HLBM_BF16 3 /* as HLBM_F16 with BF16 lattice storage (no scaling)        */
 
 /* patch node kinds (Sec. 4) */
 #define HLBM_NODE_INTERIOR 0 /* discretization node                       */
@@ -80,7 +83,7 @@ extern "C" {
 typedef struct {
     int32_t nx, ny;
     int32_t bc_x, bc_y; /* sides x = 0, nx-1 and y = 0, ny-1 */
-    int32_t dtype;      /* HLBM_F64 | HLBM_F32 */
+    int32_t dtype;      /* HLBM_F64 | HLBM_F32 | HLBM_F16 | HLBM_BF16 */
     double rho0;
     double u0x, u0y;
     const double* rho_init;

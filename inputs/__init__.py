@@ -337,6 +337,17 @@ def workload(name: str) -> Workload:
         w = workload("lamina-small-f32")
         w.name, w.dtype = name, "f64"
         return w
+    if name.startswith("lamina-1024-"):
+        # the physics of the 256^2 FP64 workload (tau 0.6, beta 500, KC 0.25) at
+        # 1024^2 with chord 32, thickness chord/50, 4 periods; the suffix names
+        # the population storage (f64, f32, f16, bf16)
+        dtype = name.split("-")[-1]
+        A, om, tau = harmonic_params(32.0, 0.25, 500.0, tau=0.6)
+        w = Workload(name, 1024, 1024, 32.0, 0.64, 512.3, 512.2, tau, 50, MOTION_HARMONIC, A=A, omega=om,
+                     delta_f=2.0, dtype=dtype,
+                     mesh_args=dict(n_L=64, n_T=2, n_layers=15, h1=0.25, d_out=4.0))
+        w.steps = int(round(4 * w.period))
+        return w
     if name.startswith("validation-"):
         # paper point (beta, eps) at chord L, domain 5L x 5L (Sec. 5)
         # name: validation-<beta>-<eps>-<L>

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhlbm.so")
 
 HLBM_OK, HLBM_EINVAL, HLBM_ECUDA, HLBM_EUNSTABLE, HLBM_EGEOM, HLBM_ENOMEM = 0, -1, -2, -3, -4, -5
 HLBM_BC_WALL, HLBM_BC_OUTFLOW, HLBM_BC_PERIODIC = 0, 1, 2
-HLBM_F64, HLBM_F32 = 0, 1
+HLBM_F64, HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2, 3
 HLBM_NODE_INTERIOR, HLBM_NODE_OUTER, HLBM_NODE_WALL = 0, 1, 2
 HLBM_MOTION_STATIC, HLBM_MOTION_HARMONIC, HLBM_MOTION_UNIFORM = 0, 1, 2
 HLBM_ST_FILL_NOT_LOCATED, HLBM_ST_DONOR_NOT_COMPUTED, HLBM_ST_NONFINITE, HLBM_ST_UNUSED_TO_DISC = 1, 2, 8, 16

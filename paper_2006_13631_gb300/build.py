@@ -12,7 +12,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhlbm.so")
 SOURCES = ["k_struct.cu", "k_patch.cu", "hlbm_api.cu", "fit_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
+FLAGS = ["-std=c++20", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]
 
 

@@ -309,6 +309,10 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     const int n = p.n_nodes, nt = p.n_tris;
     d.nx = g->nx;
     d.ny = g->ny;
+    d.store = (g->dtype == HLBM_F16 || g->dtype == HLBM_BF16) ? g->dtype : 0;
+    d.fscale = g->dtype == HLBM_F16 ? 1024.0f : 1.0f;
+    d.finv = 1.0f / d.fscale;
+    const size_t lat_elem = g->dtype == HLBM_F16 || g->dtype == HLBM_BF16 ? 2 : sizeof(T);
     d.pitch = (g->nx + 31) / 32 * 32;
     d.plane = (int64_t)d.pitch * g->ny;
     d.bc_x = g->bc_x;
@@ -571,7 +575,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.bplane = (int64_t)d.bw * d.bh;
 
     // --- device memory
-    size_t fbytes = (size_t)9 * d.plane * sizeof(T);
+    size_t fbytes = (size_t)9 * d.plane * lat_elem;
     for (int b = 0; b < 2; ++b) {
         h->fbuf[b] = dev_alloc(h, fbytes);
         h->sbox[b] = dev_alloc(h, (size_t)9 * d.bplane * sizeof(T));
@@ -814,7 +818,7 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
     // --- validation (Sec. 3: nu = cs^2 (tau_s - 1/2) = cs^2 tau_u; Sec. 7: dt < 2 tau)
     if (grid->nx < 8 || grid->ny < 8)
         rc = fail(h, HLBM_EINVAL, "lattice %dx%d is too small", grid->nx, grid->ny);
-    else if (grid->dtype != HLBM_F32 && grid->dtype != HLBM_F64)
+    else if (grid->dtype < HLBM_F64 || grid->dtype > HLBM_BF16)
         rc = fail(h, HLBM_EINVAL, "unknown dtype %d", grid->dtype);
     else if (grid->bc_x < 0 || grid->bc_x > 2 || grid->bc_y < 0 || grid->bc_y > 2)
         rc = fail(h, HLBM_EINVAL, "unknown boundary kind");
@@ -876,7 +880,7 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
             }
         }
     }
-    if (rc == HLBM_OK) rc = (grid->dtype == HLBM_F32) ? create_impl<float>(h, grid) : create_impl<double>(h, grid);
+    if (rc == HLBM_OK) rc = (grid->dtype == HLBM_F64) ? create_impl<double>(h, grid) : create_impl<float>(h, grid);
     if (rc != HLBM_OK) {
         create_err = h->err;
         cudaStreamSynchronize(h->stream);
@@ -890,7 +894,7 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
 
 int hlbm_step(hlbm_t* h, int64_t nsteps) {
     if (!h || nsteps < 0) return HLBM_EINVAL;
-    return h->dtype == HLBM_F32 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
+    return h->dtype != HLBM_F64 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
 }
 
 int hlbm_status(hlbm_t* h, uint32_t* bits) {
@@ -962,7 +966,7 @@ int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double
     const size_t N = (size_t)h->grid.nx * h->grid.ny, n = h->patch.n_nodes;
     double* buf = (double*)dev_alloc(h, (3 * N + 3 * n) * sizeof(double));
     if (!buf) return fail(h, HLBM_ENOMEM, "readback buffer");
-    if (h->dtype == HLBM_F32) {
+    if (h->dtype != HLBM_F64) {
         bind(h, h->df);
         launch_struct_macro<float>(h->df, buf, buf + N, buf + 2 * N, h->stream);
         launch_patch_macro<float>(h->df, buf + 3 * N, buf + 3 * N + n, buf + 3 * N + 2 * n, nullptr, h->stream);
@@ -993,7 +997,7 @@ int hlbm_get_patch_f(hlbm_t* h, double* f9) {
     const size_t n = h->patch.n_nodes;
     double* buf = (double*)dev_alloc(h, 9 * n * sizeof(double));
     if (!buf) return fail(h, HLBM_ENOMEM, "readback buffer");
-    if (h->dtype == HLBM_F32) {
+    if (h->dtype != HLBM_F64) {
         bind(h, h->df);
         launch_patch_macro<float>(h->df, nullptr, nullptr, nullptr, buf, h->stream);
     } else {
@@ -1012,8 +1016,8 @@ int hlbm_get_patch_f(hlbm_t* h, double* f9) {
 
 int hlbm_get_class(hlbm_t* h, int8_t* cls) {
     if (!h || !cls) return HLBM_EINVAL;
-    const int bw = h->dtype == HLBM_F32 ? h->df.bw : h->dd.bw;
-    const int bh = h->dtype == HLBM_F32 ? h->df.bh : h->dd.bh;
+    const int bw = h->dtype != HLBM_F64 ? h->df.bw : h->dd.bw;
+    const int bh = h->dtype != HLBM_F64 ? h->df.bh : h->dd.bh;
     std::vector<int8_t> win((size_t)bw * bh);
     cudaError_t e = cudaMemcpyAsync(win.data(), h->cls[h->ci], win.size(), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1031,8 +1035,8 @@ int hlbm_get_class(hlbm_t* h, int8_t* cls) {
 int hlbm_get_refill(hlbm_t* h, int32_t* type, int32_t* donor) {
     if (!h) return HLBM_EINVAL;
     const size_t n = h->patch.n_nodes;
-    int32_t* rt = h->dtype == HLBM_F32 ? h->df.rtype : h->dd.rtype;
-    int32_t* rd = h->dtype == HLBM_F32 ? h->df.rdonor : h->dd.rdonor;
+    int32_t* rt = h->dtype != HLBM_F64 ? h->df.rtype : h->dd.rtype;
+    int32_t* rd = h->dtype != HLBM_F64 ? h->df.rdonor : h->dd.rdonor;
     std::vector<int32_t> t(n), d(n);
     cudaError_t e = cudaMemcpyAsync(t.data(), rt, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.data(), rd, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
@@ -1047,14 +1051,14 @@ int hlbm_get_refill(hlbm_t* h, int32_t* type, int32_t* donor) {
 
 int hlbm_get_fv(hlbm_t* h, int32_t* row_ptr, int32_t* col, double* gx, double* gy, double* cc) {
     if (!h) return HLBM_EINVAL;
-    return h->dtype == HLBM_F32 ? get_fv_impl<float>(h, h->df.coef, row_ptr, col, gx, gy, cc)
+    return h->dtype != HLBM_F64 ? get_fv_impl<float>(h, h->df.coef, row_ptr, col, gx, gy, cc)
                                 : get_fv_impl<double>(h, h->dd.coef, row_ptr, col, gx, gy, cc);
 }
 
 int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     if (!h || !info) return HLBM_EINVAL;
-    const int bw = h->dtype == HLBM_F32 ? h->df.bw : h->dd.bw;
-    const int bh = h->dtype == HLBM_F32 ? h->df.bh : h->dd.bh;
+    const int bw = h->dtype != HLBM_F64 ? h->df.bw : h->dd.bw;
+    const int bh = h->dtype != HLBM_F64 ? h->df.bh : h->dd.bh;
     std::vector<int8_t> win((size_t)bw * bh);
     cudaError_t e = cudaMemcpyAsync(win.data(), h->cls[h->ci], win.size(), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -93,6 +93,8 @@ struct Dev {
     int bc_x, bc_y;
     T* fA;         // post-collision populations read by this step [9][plane]
     T* fB;         // written by this step
+    int store;     // lattice storage: 0 as T, HLBM_F16 or HLBM_BF16 (pointers then hold that type)
+    float fscale, finv;  // FP16 storage holds fscale * f'
     // lattice window that follows the patch
     int bw, bh;
     int64_t bplane; // bw * bh

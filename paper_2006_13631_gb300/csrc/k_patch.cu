@@ -627,8 +627,12 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
     const int tile = blockIdx.x;
     const int p0 = d.tile_start[tile], p1 = d.tile_start[tile + 1], tile_n = p1 - p0;
     const int h0 = d.halo_ptr[tile], halo_n = d.halo_ptr[tile + 1] - h0;
-    const int n_int = d.tile_interior[tile];
     const int tid = threadIdx.x, nt = blockDim.x;
+    // nodes updated before the halo arrives: the interior ones, but only as
+    // many as fill whole rounds of the block, so that the rest (boundary
+    // nodes and the remainder) take exactly one more round
+    const int rounds = (tile_n + nt - 1) / nt;
+    const int n_int = min(d.tile_interior[tile], (rounds - 1) * nt);
     // ---- tile set-up: wall velocity per sub-step, own records (buffer 0),
     // matrices, kinds, send flags, node order, halo ids
     for (int m = tid; m < d.n_sub; m += nt) {

@@ -1,12 +1,52 @@
 // Cartesian-lattice kernels: initial state, node classification (Sec. 4),
 // the eq. postcollision2_s feed of interpolation nodes, and the fused pull
 // stream-collide of eq. LBE with the Sec. 5 boundaries.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "hlbm_dev.cuh"
 
 namespace hk {
 
+// Lattice storage.  S = T stores f' as is; __half stores fscale * f' (a
+// power of two, so the scaling is exact), __nv_bfloat16 stores f'.  The
+// arithmetic always runs in T.
+template <typename T, typename S>
+struct Store {
+    static __device__ __forceinline__ T ld(const S* p, int64_t i, float) { return p[i]; }
+    static __device__ __forceinline__ void st(S* p, int64_t i, T v, float) { p[i] = v; }
+};
+template <>
+struct Store<float, __half> {
+    static __device__ __forceinline__ float ld(const __half* p, int64_t i, float inv) {
+        return __half2float(p[i]) * inv;
+    }
+    static __device__ __forceinline__ void st(__half* p, int64_t i, float v, float scale) {
+        p[i] = __float2half_rn(v * scale);
+    }
+};
+template <>
+struct Store<float, __nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i, float) {
+        return __bfloat162float(p[i]);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float v, float) {
+        p[i] = __float2bfloat16_rn(v);
+    }
+};
+
+// call f.template operator()<S>() with the lattice storage type of d
+template <typename T, typename F>
+void with_store(const Dev<T>& d, F&& f) {
+    if constexpr (sizeof(T) == 4) {
+        if (d.store == HLBM_F16) return f.template operator()<__half>();
+        if (d.store == HLBM_BF16) return f.template operator()<__nv_bfloat16>();
+    }
+    f.template operator()<T>();
+}
+
 // ------------------------------------------------------------------ init
-template <typename T>
+template <typename T, typename S>
 __global__ void k_init_struct(Dev<T> d, const double* rho, const double* ux, const double* uy, double u0x,
                               double u0y) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -18,11 +58,13 @@ __global__ void k_init_struct(Dev<T> d, const double* rho, const double* ux, con
     T vx = ux ? T(ux[g]) : T(u0x);
     T vy = uy ? T(uy[g]) : T(u0y);
     int64_t s = (int64_t)y * d.pitch + x;
+    S* A = reinterpret_cast<S*>(d.fA);
+    S* B = reinterpret_cast<S*>(d.fB);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         T v = feq_dev<T>(i, dr, rr, vx, vy);
-        d.fA[i * d.plane + s] = v;
-        d.fB[i * d.plane + s] = v;
+        Store<T, S>::st(A, i * d.plane + s, v, d.fscale);
+        Store<T, S>::st(B, i * d.plane + s, v, d.fscale);
     }
 }
 
@@ -30,7 +72,7 @@ template <typename T>
 void launch_init_struct(const Dev<T>& d, const double* rho, const double* ux, const double* uy, double u0x,
                         double u0y, cudaStream_t s) {
     dim3 grid((d.nx + 255) / 256, d.ny);
-    k_init_struct<T><<<grid, 256, 0, s>>>(d, rho, ux, uy, u0x, u0y);
+    with_store(d, [&]<typename S>() { k_init_struct<T, S><<<grid, 256, 0, s>>>(d, rho, ux, uy, u0x, u0y); });
 }
 
 // pre-collision state at t = 0 inside a window: the initial equilibrium
@@ -91,8 +133,9 @@ void launch_classify(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 // that just became discretization nodes) from the patch at time t:
 // f~ = f^eq,u + 2(tau_s - 1)/(2 tau_s - 1) f^neq,u, with rho, u and f^neq
 // barycentric over the enclosing patch triangle.
-template <typename T>
+template <typename T, typename S>
 __global__ void k_fill(Dev<T> d, StepArgs a) {
+    S* A = reinterpret_cast<S*>(d.fA);
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= d.bplane) return;
     int8_t c = d.cls_cur[b];
@@ -113,7 +156,7 @@ __global__ void k_fill(Dev<T> d, StepArgs a) {
     if (k < 0) {
         atomicOr(d.status, HLBM_ST_FILL_NOT_LOCATED);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d.fA[i * d.plane + s] = T(0);
+        for (int i = 0; i < 9; ++i) Store<T, S>::st(A, i * d.plane + s, T(0), d.fscale);
         return;
     }
     T st[12];
@@ -136,26 +179,26 @@ __global__ void k_fill(Dev<T> d, StepArgs a) {
     const T rr = d.rho0 + st[0];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        d.fA[i * d.plane + s] = feq_dev<T>(i, st[0], rr, st[1], st[2]) + d.k178 * st[3 + i];
+        Store<T, S>::st(A, i * d.plane + s, feq_dev<T>(i, st[0], rr, st[1], st[2]) + d.k178 * st[3 + i], d.fscale);
 }
 
 template <typename T>
 void launch_fill(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
-    k_fill<T><<<(unsigned)((d.bplane + 127) / 128), 128, 0, s>>>(d, a);
+    with_store(d, [&]<typename S>() { k_fill<T, S><<<(unsigned)((d.bplane + 127) / 128), 128, 0, s>>>(d, a); });
 }
 
 // ------------------------------------------------------ stream-collide
 // Pull form of eq. LBE: f_i(x, t+1) = f~_i(x - c_i, t), then BGK relaxation
 // with tau_s.  Boundaries (Sec. 5): half-way bounce-back walls (taking
 // precedence at corners), zero-gradient outflow, or periodic wrap.
-template <typename T>
-__device__ __forceinline__ T pull_edge(const Dev<T>& d, int x, int y, int i) {
+template <typename T, typename S>
+__device__ __forceinline__ T pull_edge(const Dev<T>& d, const S* A, int x, int y, int i) {
     int sx = x - cx_of(i), sy = y - cy_of(i);
     if (sx < 0 || sx >= d.nx) {
         if (d.bc_x == HLBM_BC_PERIODIC)
             sx = (sx + d.nx) % d.nx;
         else if (d.bc_x == HLBM_BC_WALL)
-            return d.fA[opp_of(i) * d.plane + (int64_t)y * d.pitch + x];
+            return Store<T, S>::ld(A, opp_of(i) * d.plane + (int64_t)y * d.pitch + x, d.finv);
         else
             sx = x;
     }
@@ -163,62 +206,179 @@ __device__ __forceinline__ T pull_edge(const Dev<T>& d, int x, int y, int i) {
         if (d.bc_y == HLBM_BC_PERIODIC)
             sy = (sy + d.ny) % d.ny;
         else if (d.bc_y == HLBM_BC_WALL)
-            return d.fA[opp_of(i) * d.plane + (int64_t)y * d.pitch + x];
+            return Store<T, S>::ld(A, opp_of(i) * d.plane + (int64_t)y * d.pitch + x, d.finv);
         else
             sy = y;
     }
-    return d.fA[i * d.plane + (int64_t)sy * d.pitch + sx];
+    return Store<T, S>::ld(A, i * d.plane + (int64_t)sy * d.pitch + sx, d.finv);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_stream_collide(Dev<T> d, StepArgs a) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
-    if (x >= d.nx) return;
+// One lattice node: pull (or take the given pulled values), BGK, store.
+template <typename T, typename S>
+__device__ __forceinline__ void collide_store(const Dev<T>& d, const StepArgs& a, int x, int y, T (&f)[9]) {
     unsigned rx = (unsigned)(x - a.bx0), ry = (unsigned)(y - a.by0);
     bool inbox = rx < (unsigned)d.bw && ry < (unsigned)d.bh;
     int64_t b = (int64_t)ry * d.bw + rx;
     if (inbox && d.cls_cur[b] != CLS_DISC) return;
     int64_t s = (int64_t)y * d.pitch + x;
-    T f[9];
-    if (x > 0 && y > 0 && x < d.nx - 1 && y < d.ny - 1) {
-        const T* __restrict__ A = d.fA;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = __ldg(A + i * d.plane + s - cy_of(i) * d.pitch - cx_of(i));
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = pull_edge(d, x, y, i);
-    }
+    S* __restrict__ B = reinterpret_cast<S*>(d.fB);
     T dr, r, ux, uy;
     moments_dev(f, d.rho0, dr, r, ux, uy);
-    T omega = T(1) / d.tau_s;
+    const T omega = T(1) / d.tau_s;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        T fe = feq_dev<T>(i, dr, r, ux, uy);
-        d.fB[i * d.plane + s] = f[i] - omega * (f[i] - fe);
-    }
+    for (int i = 0; i < 9; ++i)
+        Store<T, S>::st(B, i * d.plane + s, f[i] - omega * (f[i] - feq_dev<T>(i, dr, r, ux, uy)), d.fscale);
     if (inbox) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) d.sbox_new[i * d.bplane + b] = f[i];
     }
 }
 
+// a vector of consecutive storage elements: 4 nodes (2 for FP64), i.e.
+// 16 bytes for FP32 / FP64 and 8 bytes for FP16 / BF16
+template <typename S>
+struct alignas(sizeof(S) == 8 ? 16 : 4 * sizeof(S)) Pack {
+    static constexpr int N = sizeof(S) == 8 ? 2 : 4;
+    S v[N];
+};
+
+template <typename S>
+__device__ __forceinline__ S shfl_up1(S v) {
+    if constexpr (sizeof(S) == 2) {
+        unsigned short u;
+        memcpy(&u, &v, 2);
+        u = (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)u, 1);
+        memcpy(&v, &u, 2);
+        return v;
+    } else {
+        return __shfl_up_sync(0xffffffffu, v, 1);
+    }
+}
+template <typename S>
+__device__ __forceinline__ S shfl_down1(S v) {
+    if constexpr (sizeof(S) == 2) {
+        unsigned short u;
+        memcpy(&u, &v, 2);
+        u = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)u, 1);
+        memcpy(&v, &u, 2);
+        return v;
+    } else {
+        return __shfl_down_sync(0xffffffffu, v, 1);
+    }
+}
+
+// Pull form of eq. LBE: f_i(x, t+1) = f~_i(x - c_i, t), then BGK relaxation
+// with tau_s.  Each thread owns V consecutive nodes of a row (Pack<S>) and
+// reads each population as one vector load from row y - c_iy;
+// the x - c_ix shift comes from the neighbouring lane (warp shuffle), and
+// the first and last lane of a warp load the one element beyond their
+// vector.  Nodes on the lattice edge take the scalar path with the Sec. 5
+// boundaries (half-way bounce-back walls taking precedence at corners,
+// zero-gradient outflow, or periodic wrap).  Every lane runs the vector
+// loads and shuffles (rows and columns clamped into the buffer); only the
+// nodes of lanes whose whole vector is interior use their results.
+template <typename T, typename S>
+__global__ void __launch_bounds__(128) k_stream_collide(Dev<T> d, StepArgs a) {
+    constexpr int V = Pack<S>::N;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const int y = blockIdx.y;
+    const S* __restrict__ A = reinterpret_cast<const S*>(d.fA);
+    const bool interior = x0 >= 1 && x0 + V <= d.nx - 1 && y >= 1 && y <= d.ny - 2;
+    T f[V][9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sy = y - cy_of(i);
+        sy = sy < 0 ? 0 : (sy >= d.ny ? d.ny - 1 : sy);
+        const int64_t row = i * d.plane + (int64_t)sy * d.pitch;
+        const int xv = x0 < d.pitch ? x0 : d.pitch - V;
+        const Pack<S> p = *reinterpret_cast<const Pack<S>*>(A + row + xv);
+        if (cx_of(i) == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) f[k][i] = Store<T, S>::ld(p.v, k, d.finv);
+        } else if (cx_of(i) == 1) {
+            // node x0 + k takes the element at x0 + k - 1
+            S left = shfl_up1(p.v[V - 1]);
+            if (lane == 0) left = A[row + (xv > 0 ? xv - 1 : 0)];
+            f[0][i] = Store<T, S>::ld(&left, 0, d.finv);
+#pragma unroll
+            for (int k = 1; k < V; ++k) f[k][i] = Store<T, S>::ld(p.v, k - 1, d.finv);
+        } else {
+            // node x0 + k takes the element at x0 + k + 1
+            S right = shfl_down1(p.v[0]);
+            if (lane == 31) right = A[row + (xv + V < d.pitch ? xv + V : d.pitch - 1)];
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) f[k][i] = Store<T, S>::ld(p.v, k + 1, d.finv);
+            f[V - 1][i] = Store<T, S>::ld(&right, 0, d.finv);
+        }
+    }
+    if (interior) {
+        // BGK for all V nodes, one 16-byte store per population.  Values
+        // written at nodes that are not discretization nodes are never read:
+        // interpolation and newly uncovered nodes are overwritten by eq. 178
+        // before the next pull, unused nodes are never pulled from.
+        S* __restrict__ B = reinterpret_cast<S*>(d.fB);
+        const T omega = T(1) / d.tau_s;
+        Pack<S> out[9];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            T dr, r, ux, uy;
+            moments_dev(f[k], d.rho0, dr, r, ux, uy);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                Store<T, S>::st(out[i].v, k, f[k][i] - omega * (f[k][i] - feq_dev<T>(i, dr, r, ux, uy)), d.fscale);
+        }
+        const int64_t s0 = (int64_t)y * d.pitch + x0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) *reinterpret_cast<Pack<S>*>(B + i * d.plane + s0) = out[i];
+        // the pre-collision state of discretization nodes in the window
+        const unsigned ry = (unsigned)(y - a.by0);
+        if (ry < (unsigned)d.bh) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const unsigned rx = (unsigned)(x0 + k - a.bx0);
+                if (rx < (unsigned)d.bw) {
+                    const int64_t b = (int64_t)ry * d.bw + rx;
+                    if (d.cls_cur[b] == CLS_DISC) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) d.sbox_new[i * d.bplane + b] = f[k][i];
+                    }
+                }
+            }
+        }
+    } else {
+        for (int k = 0; k < V; ++k) {
+            const int x = x0 + k;
+            if (x >= d.nx) break;
+            T g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = pull_edge<T, S>(d, A, x, y, i);
+            collide_store<T, S>(d, a, x, y, g);
+        }
+    }
+}
+
 template <typename T>
 void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
-    dim3 grid((d.nx + 255) / 256, d.ny);
-    k_stream_collide<T><<<grid, 256, 0, s>>>(d, a);
+    with_store(d, [&]<typename S>() {
+        constexpr int V = Pack<S>::N;
+        const int threads_x = (d.nx + V - 1) / V;
+        dim3 grid((threads_x + 127) / 128, d.ny);
+        k_stream_collide<T, S><<<grid, 128, 0, s>>>(d, a);
+    });
 }
 
 // ------------------------------------------------------------- readback
-template <typename T>
+template <typename T, typename S>
 __global__ void k_struct_macro(Dev<T> d, double* rho, double* ux, double* uy) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     if (x >= d.nx) return;
     int64_t s = (int64_t)y * d.pitch + x;
+    const S* A = reinterpret_cast<const S*>(d.fA);
     T f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = d.fA[i * d.plane + s];
+    for (int i = 0; i < 9; ++i) f[i] = Store<T, S>::ld(A, i * d.plane + s, d.finv);
     T dr, r, vx, vy;
     moments_dev(f, d.rho0, dr, r, vx, vy);
     int64_t g = (int64_t)y * d.nx + x;
@@ -230,7 +390,7 @@ __global__ void k_struct_macro(Dev<T> d, double* rho, double* ux, double* uy) {
 template <typename T>
 void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy, cudaStream_t s) {
     dim3 grid((d.nx + 255) / 256, d.ny);
-    k_struct_macro<T><<<grid, 256, 0, s>>>(d, rho, ux, uy);
+    with_store(d, [&]<typename S>() { k_struct_macro<T, S><<<grid, 256, 0, s>>>(d, rho, ux, uy); });
 }
 
 #define HLBM_INST(T)                                                                                     \

@@ -51,7 +51,7 @@ def _dp(a):
 
 
 def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
-    """grid: nx, ny, bc_x, bc_y, dtype ('f32'|'f64'), rho0, u0x, u0y, rho_init, ux_init, uy_init
+    """grid: nx, ny, bc_x, bc_y, dtype ('f64'|'f32'|'f16'|'bf16'), rho0, u0x, u0y, rho_init, ux_init, uy_init
     patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped
     motion: kind, A, omega, vx, vy.  Returns an opaque handle (keeps the host copies alive
     for the duration of the call only)."""
@@ -68,7 +68,8 @@ def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream
     g = N.hlbm_grid_t()
     g.nx, g.ny = int(grid["nx"]), int(grid["ny"])
     g.bc_x, g.bc_y = int(grid.get("bc_x", N.HLBM_BC_WALL)), int(grid.get("bc_y", N.HLBM_BC_OUTFLOW))
-    g.dtype = N.HLBM_F32 if grid.get("dtype", "f32") in ("f32", N.HLBM_F32) else N.HLBM_F64
+    dt = grid.get("dtype", "f32")
+    g.dtype = {"f64": N.HLBM_F64, "f32": N.HLBM_F32, "f16": N.HLBM_F16, "bf16": N.HLBM_BF16}.get(dt, dt)
     g.rho0 = float(grid.get("rho0", 1.0))
     g.u0x, g.u0y = float(grid.get("u0x", 0.0)), float(grid.get("u0y", 0.0))
     g.rho_init = _dp(arr(grid.get("rho_init"), np.float64))
