@@ -159,35 +159,56 @@ def cpu_baseline(workload):
             "sample": f"2 lattice steps of {w.name} from the initial state, serial FP64 oracle"}
 
 
-def _stream_source_hash():
-    """Hash of the source that defines the stream-collide kernel's traffic."""
+# the source sections whose arithmetic and memory access define each
+# profiled kernel's DRAM traffic (file, first marker, end marker)
+_KERNEL_SOURCES = {
+    "stream_collide": [("k_struct.cu", "// ------------------------------------------------------ stream-collide",
+                        "// ------------------------------------------------------------- readback"),
+                       ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
+                        "// ---------------------------------------------------------------- layout")],
+    "fv_tiles": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
+                  "// ------------------------------------------------------------- force"),
+                 ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
+                  "// ---------------------------------------------------------------- layout")],
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the source sections that define a kernel's traffic."""
     import hashlib
 
-    def section(path, start, end):
-        s = open(path).read()
-        return s[s.index(start):s.index(end)]
-
     csrc = os.path.join(ROOT, "paper_2006_13631_gb300", "csrc")
-    src = (section(os.path.join(csrc, "k_struct.cu"), "// ------------------------------------------------------ stream-collide",
-                   "// ------------------------------------------------------------- readback") +
-           section(os.path.join(csrc, "hlbm_dev.cuh"), "// ---------------------------------------------------------------- D2Q9",
-                   "// ---------------------------------------------------------------- layout"))
+    src = ""
+    for name, start, end in _KERNEL_SOURCES[kernel]:
+        text = open(os.path.join(csrc, name)).read()
+        src += text[text.index(start):text.index(end)]
     return hashlib.sha256(src.encode()).hexdigest()
 
 
-def stream_traffic(workload):
-    """DRAM bytes per stream-collide launch from the committed ncu summary, or
-    None if there is none for this workload or the kernel changed since."""
-    path = os.path.join(ROOT, "profiles", f"stream_collide_{workload}.md")
+def kernel_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary
+    profiles/<kernel>_<workload>.md, or None if there is none or the kernel's
+    source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         text = open(path).read()
         vals = dict(line.split(":", 1) for line in text.splitlines()
                     if line.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
-        if vals["source_sha256"].strip() != _stream_source_hash():
+        if vals["source_sha256"].strip() != kernel_source_hash(kernel):
             return None
         return int(vals["traffic_bytes_per_launch"])
     except Exception:
         return None
+
+
+# FP32 peak of plain (non-tensor) arithmetic: 152 SMs x 128 FP32 lanes x
+# 2 FLOP per FMA x 2.07 GHz maximum SM clock
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_ALU_TFLOPS = FP32_ALU_TFLOPS / 64
+# algorithmic FLOP of one FV sub-step per CSR entry (row P, column k): for each
+# of the 9 directions a multiply-add of the streaming term S_ik f_k and one of
+# the collision term C_Pk (f - f^eq)_k
+FV_FLOP_PER_ENTRY = 9 * 4
 
 
 def combine_ranks(ms: float, units: float, dist=None, device=None):
@@ -256,25 +277,28 @@ def run_ours(args):
     _, units_sub = combine_ranks(ms, float((n_disc + w.n_sub * n_u) * args.steps), dist, "cuda")
     mlups_subiter = units_sub / (ms / 1e3) / 1e6
 
-    # roofline of the dominant phase (largest share of the timed region)
+    # roofline of the dominant kernel (the FV sub-steps: plain FP32
+    # arithmetic on shared-memory tiles) and of the HBM-bound stream-collide
     peak, peak_kind = _peaks()
     bytes_per = 4 if w.dtype == "f32" else 8
     dom = max(phases, key=lambda p: phases[p][0])
     st_ms, st_n = phases["stream"]
     stream_bytes = 18 * bytes_per * n_disc  # 9 populations read + 9 written per discretization node
     stream_gbs = stream_bytes / (st_ms / st_n / 1e3) / 1e9 if st_n else None
-    fv_ms, fv_n = phases["fv"]
+    fv_ms, _ = phases["fv"]
     nnz = info["nnz"]
-    # per FV sub-step launch: the patch state read and written once, plus the
-    # CSR rows (column index and three coefficients per entry)
-    fv_bytes = 18 * bytes_per * n_u + nnz * (4 + 3 * bytes_per)
-    fv_gbs = fv_bytes / (fv_ms / fv_n / 1e3) / 1e9 if fv_n else None
-    traffic = stream_traffic(w.name)
-    roof = {"bound": "hbm", "kernel": "stream_collide", "achieved": stream_gbs, "peak": peak, "unit": "GB/s",
-            "frac": stream_gbs / peak if stream_gbs else None, "traffic": traffic,
-            "peak_source": peak_kind, "dominant_phase": dom,
-            "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases},
-            "fv_substep_gbs": fv_gbs}
+    fv_flop = FV_FLOP_PER_ENTRY * nnz * w.n_sub  # per launch (one lattice step)
+    fv_tflops = fv_flop / (fv_ms / args.steps / 1e3) / 1e12 if fv_ms else None
+    alu_peak = FP32_ALU_TFLOPS if w.dtype == "f32" else FP64_ALU_TFLOPS
+    roof = {"bound": "alu", "kernel": "k_fv_tiles", "achieved": fv_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": fv_tflops / alu_peak if fv_tflops else None, "traffic": kernel_traffic("fv_tiles", w.name),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+            "flop_per_launch": fv_flop, "ms_per_launch": fv_ms / args.steps, "dominant_phase": dom,
+            "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases}}
+    roof_stream = {"bound": "hbm", "kernel": "k_stream_collide", "achieved": stream_gbs, "peak": peak, "unit": "GB/s",
+                   "frac": stream_gbs / peak if stream_gbs else None,
+                   "traffic": kernel_traffic("stream_collide", w.name), "peak_source": peak_kind,
+                   "bytes_per_launch": stream_bytes, "ms_per_launch": st_ms / st_n if st_n else None}
     launches = sum(v[1] for v in phases.values())
 
     # end to end through the public API from host buffers
@@ -323,6 +347,7 @@ def run_ours(args):
                                "stream_gbs": gbs, "stream_frac": gbs / peak if gbs else None}
                 s3.close()
         w.dtype = "f32"
+    sweep = None if args.no_sweep else run_sweep(stream, args)
     if rank != 0:
         return 0
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.workload)
@@ -332,13 +357,63 @@ def run_ours(args):
             "config": {"workload": w.name, "lattice": f"{w.nx}x{w.ny}", "chord": w.L, "patch_nodes": n_u,
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)" % (9 * bytes_per * w.nx * w.ny / 1e6)},
-            "mlups_subiter": mlups_subiter, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "reduced_storage": reduced or None,
+            "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "cpu_baseline": cpu, "e2e": e2e,
+            "reduced_storage": reduced or None, "sweep": sweep,
             "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_sweep(stream, args):
+    """The 64-instance KC/beta study stepped as one batch (hlbm_sweep_*),
+    FV tiles chosen per instance by the tuner; against the same instances
+    stepped one after another on one stream."""
+    import torch
+
+    import inputs
+    from paper_2006_13631_gb300 import Solver, Sweep
+
+    ws = inputs.sweep_workloads()
+    with torch.cuda.stream(stream):
+        solvers = [Solver(w, stream=stream.cuda_stream) for w in ws]
+        infos = [s.info() for s in solvers]
+        lat = sum(i["n_struct_disc"] for i in infos)
+        pat = sum(i["n_nodes"] for i in infos)
+        sub = sum(w.n_sub * i["n_nodes"] for w, i in zip(ws, infos))
+        sw = Sweep(solvers, stream=stream.cuda_stream)
+        picks = sw.tune(trial_steps=1)
+        sw.step(args.warmup)
+        k = max(1, args.sweep_steps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sw.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fv = sw.fv_time(1)
+        # the same instances one after another, each a plain hlbm_step
+        k_serial = max(1, min(k, 3))
+        e0.record(stream)
+        for s in solvers:
+            s.step(k_serial)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_serial = e0.elapsed_time(e1) / k_serial
+        bad = sum(1 for s in solvers if s.status != 0)
+        sw.close()
+        for s in solvers:
+            s.close()
+    hist = {str(c): picks.count(c) for c in sorted(set(picks))}
+    return {"instances": len(ws), "value": (lat + pat) * k / (ms / 1e3) / 1e6, "unit": UNIT, "steps": k,
+            "ms_per_step": ms / k, "mlups_subiter": (lat + sub) * k / (ms / 1e3) / 1e6,
+            "serial_ms_per_step": ms_serial, "speedup_vs_serial": ms_serial / (ms / k),
+            "fv_ms_per_step": float(fv.sum()), "lattice_nodes": lat, "patch_nodes": pat,
+            "fv_node_substeps_per_step": sub, "n_sub_range": [min(w.n_sub for w in ws), max(w.n_sub for w in ws)],
+            "throughput_only": sum(1 for w in ws if w.throughput_only), "tile_nodes_chosen": hist,
+            "instances_with_status": bad}
 
 
 def main():
@@ -351,6 +426,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16/BF16 lattice-storage runs")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 64-instance KC/beta sweep")
+    ap.add_argument("--sweep-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -46,6 +46,7 @@ extern "C" {
 #define HLBM_EUNSTABLE (-3) /* NaN/Inf in the force: the run diverged     */
 #define HLBM_EGEOM (-4)     /* a geometric precondition failed on device  */
 #define HLBM_ENOMEM (-5)    /* device allocation failed                   */
+#define HLBM_EIO (-6)       /* a checkpoint file could not be read/written */
 
 /* boundary kinds of the Cartesian domain sides (Sec. 5) */
 #define HLBM_BC_WALL 0     /* half-way bounce-back no-slip wall          */
@@ -208,6 +209,31 @@ int hlbm_profile_read(hlbm_t* h, double* ms, int64_t* launches);
 /* Device status bits (HLBM_ST_*), accumulated since creation. */
 int hlbm_status(hlbm_t* h, uint32_t* bits);
 
+/* ---- batched sweep: independent solvers stepped together ----------------
+ * The paper runs a parametric study over (beta, eps) (Sec. 2, Sec. 6);
+ * a sweep steps many solvers with one call.  Each lattice step, every
+ * instance issues its lattice part (relocation, classification, eq. 178
+ * feed, stream-collide) on a stream of its own; the FV sub-steps of the
+ * instances follow one another on a single stream, each starting as soon
+ * as its instance's lattice part is done; each instance then issues its
+ * force.  The solvers stay owned by the caller (destroy them after the
+ * sweep) and keep their own force history, fields and status; their own
+ * streams are ordered after the sweep's work when a sweep call returns.
+ * All work starts after, and cuda_stream waits for, the sweep's calls. */
+typedef struct hlbm_sweep hlbm_sweep_t;
+int hlbm_sweep_create(int32_t n, hlbm_t* const* solvers, void* cuda_stream, hlbm_sweep_t** out);
+int hlbm_sweep_step(hlbm_sweep_t* w, int64_t nsteps);
+/* Tile-size autotuner for the FV kernels: for each candidate size (256,
+ * 512, 1024, 1536 nodes per tile) every instance is re-tiled and
+ * trial_steps sweep steps are timed per instance; each instance keeps the
+ * fastest.  The trial steps advance the solvers like hlbm_sweep_step.
+ * tile_nodes (may be NULL) receives the chosen size per instance. */
+int hlbm_sweep_tune(hlbm_sweep_t* w, int32_t trial_steps, int32_t* tile_nodes);
+/* nsteps sweep steps with the FV time of each instance summed into fv_ms[n]. */
+int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms);
+const char* hlbm_sweep_last_error(const hlbm_sweep_t* w);
+void hlbm_sweep_destroy(hlbm_sweep_t* w);
+
 /* Least-squares fit F(t) = a sin(w t) + b cos(w t) over t = t0..t1 of the
  * samples F(t) = samples[t * stride] (DEVICE memory, caller-owned, at least
  * t1 * stride + 1 doubles), the fit hlbm_gamma performs, for callers that
@@ -232,6 +258,27 @@ int hlbm_status(hlbm_t* h, uint32_t* bits);
  * HLBM_ECUDA when a CUDA call fails. */
 int hlbm_fit_static(const double* samples, int64_t stride, int64_t t0, int64_t t1, double omega,
                     void* cuda_stream, double* a, double* b, double* rms);
+
+/* Checkpoint and restart.  hlbm_save writes the solver's dynamic state at
+ * its current step t to the file `path` (a host path; the file is replaced):
+ * both lattice population buffers, the window classes and states, both
+ * patch record buffers, the latest refill record, the force history
+ * 0..t, the status word, and the step counters.  It synchronises the
+ * solver's stream first.  hlbm_load restores such a file into a solver
+ * created from the same inputs (lattice, boundaries, dtype, patch mesh,
+ * physics and motion, checked against the file's header and a hash of the
+ * mesh); stepping on from there gives bit for bit the fields, refill
+ * records and forces the saved solver would have given.  Geometry, FV
+ * matrices and tile tables are not stored: hlbm_create rebuilds them.
+ * The file is in the host's byte order and holds, after a fixed header,
+ * about 18 * nx * ny * sizeof(population) bytes.
+ * Returns HLBM_EIO when the file cannot be opened, written or read, is
+ * not a checkpoint or is not complete; HLBM_EINVAL when it belongs to other
+ * inputs; HLBM_ENOMEM when the longer force history cannot be allocated --
+ * in these cases before anything of the solver is changed; HLBM_ECUDA on a
+ * failed copy, which leaves the solver's state undefined. */
+int hlbm_save(hlbm_t* h, const char* path);
+int hlbm_load(hlbm_t* h, const char* path);
 
 /* Message of the last failed call on h; with h == NULL, of the last failed
  * hlbm_create on this thread. */

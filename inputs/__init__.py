@@ -413,3 +413,35 @@ def periodic_mesh(nx: int, ny: int, Lx: float, Ly: float, jitter: float = 0.15, 
             else:
                 tris += [(a, b, d), (b, c, d)]
     return xy, np.asarray(tris, dtype=np.int32)
+
+
+def sweep_workloads(vmax: float = 0.025):
+    """The parametric KC/beta study as 64 independent instances: KC at 8
+    log-spaced values in [0.1, 5], beta at 8 log-spaced values in [100, 5000]
+    (the paper's study spans beta 20-300 and eps 0.02-0.1, Sec. 2).  Chord
+    L = 16 * 2^round(2 log(beta/100) / log 50) in {16, 32, 64}, lattice 32 L,
+    thickness L/50, tau from beta at peak speed vmax.  The patch has about
+    10k (L 16) to 100k (L 64) nodes, log-interpolated in L; the number of FV
+    sub-steps is the smallest stable one (Sec. 7 and the diffusive limit).
+    Instances with tau < 0.505 or Re > 2000 are flagged throughput-only."""
+    out = []
+    for i in range(8):
+        kc = 0.1 * 50.0 ** (i / 7.0)
+        for j in range(8):
+            beta = 100.0 * 50.0 ** (j / 7.0)
+            L = 16.0 * 2 ** round(2.0 * math.log(beta / 100.0) / math.log(50.0))
+            A, om, tau = harmonic_params(L, kc, beta, vmax=vmax)
+            n = int(32 * L)
+            target = 10000.0 * (L / 16.0) ** (math.log(10.0) / math.log(4.0))
+            s = math.sqrt(8.0 * L / target)  # node spacing giving about `target` nodes
+            layers = max(6, int(round(4.0 / s)) + 1)
+            w = Workload(f"sweep-kc{kc:.3g}-beta{beta:.4g}", n, n, L, L / 50.0, 0.5 * n + 0.3, 0.5 * n + 0.2, tau, 8,
+                         MOTION_HARMONIC, A=A, omega=om, delta_f=2.0, dtype="f32",
+                         mesh_args=dict(n_L=max(8, int(round(L / s))), n_T=max(2, int(round(L / 50.0 / s))),
+                                        n_layers=layers, h1=4.0 / (layers - 1), d_out=4.0))
+            w.n_sub = stable_substeps(w.mesh(), tau - 0.5, minimum=8)
+            w.steps = 1000
+            re = 2.0 * math.pi * beta * A / L
+            w.throughput_only = tau < 0.505 or re > 2000.0
+            out.append(w)
+    return out

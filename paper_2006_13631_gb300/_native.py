@@ -7,7 +7,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhlbm.so")
 
-HLBM_OK, HLBM_EINVAL, HLBM_ECUDA, HLBM_EUNSTABLE, HLBM_EGEOM, HLBM_ENOMEM = 0, -1, -2, -3, -4, -5
+HLBM_OK, HLBM_EINVAL, HLBM_ECUDA, HLBM_EUNSTABLE, HLBM_EGEOM, HLBM_ENOMEM, HLBM_EIO = 0, -1, -2, -3, -4, -5, -6
 HLBM_BC_WALL, HLBM_BC_OUTFLOW, HLBM_BC_PERIODIC = 0, 1, 2
 HLBM_F64, HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2, 3
 HLBM_NODE_INTERIOR, HLBM_NODE_OUTER, HLBM_NODE_WALL = 0, 1, 2
@@ -66,6 +66,14 @@ SIGNATURES = {
     "hlbm_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "hlbm_fit_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_void_p, _dp, _dp,
                                   _dp]),
+    "hlbm_sweep_create": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "hlbm_sweep_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "hlbm_sweep_tune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "hlbm_sweep_fv_time": (C.c_int, [C.c_void_p, C.c_int64, _dp]),
+    "hlbm_sweep_last_error": (C.c_char_p, [C.c_void_p]),
+    "hlbm_sweep_destroy": (None, [C.c_void_p]),
+    "hlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "hlbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "hlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "hlbm_destroy": (None, [C.c_void_p]),
 }

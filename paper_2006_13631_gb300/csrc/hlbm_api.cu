@@ -44,6 +44,7 @@ struct hlbm {
     std::vector<int32_t> row_ptr, col, outer;
     std::vector<int32_t> perm;  // internal node -> caller's node (Morton order)
     int n_tiles = 0;
+    std::vector<void*> tile_blocks;  // device tables of the current FV tiling
     bool use_smem = false;      // shared-memory FV kernel (else global-memory kernel)
     double mxmin = 0, mxmax = 0, mymin = 0, mymax = 0;
     int nnz = 0, nseg = 0;
@@ -179,7 +180,7 @@ void bind(hlbm* h, Dev<T>& d) {
 }
 
 // start of a profiled phase: returns the index of its start event, or -1
-int phase_begin(hlbm* h) {
+int phase_begin(hlbm* h, cudaStream_t s) {
     if (!h->profiling) return -1;
     while (h->ev_pool.size() < h->ev_used + 2) {
         cudaEvent_t e;
@@ -188,13 +189,13 @@ int phase_begin(hlbm* h) {
     }
     int i = (int)h->ev_used;
     h->ev_used += 2;
-    cudaEventRecord(h->ev_pool[i], h->stream);
+    cudaEventRecord(h->ev_pool[i], s);
     return i;
 }
 
-void phase_end(hlbm* h, int phase, int i, int launches) {
+void phase_end(hlbm* h, int phase, int i, int launches, cudaStream_t s) {
     if (i < 0) return;
-    cudaEventRecord(h->ev_pool[i + 1], h->stream);
+    cudaEventRecord(h->ev_pool[i + 1], s);
     h->ev_marks.push_back({phase, i});
     h->phase_launches[phase] += launches;
 }
@@ -213,91 +214,272 @@ int phase_collect(hlbm* h) {
     return HLBM_OK;
 }
 
+// One lattice step is issued in three parts so that a sweep can interleave
+// independent solvers: the lattice part (relocation, classification,
+// eq. 178 feed, stream-collide, outer-node feed), the FV sub-steps, and the
+// force plus the host bookkeeping.  A plain step issues them back to back.
+struct PendingStep {
+    StepArgs a;
+    int ncls;
+    double X, Y;
+};
+
+template <typename T>
+int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
+    Dev<T>& d = dev_of<T>(h);
+    const int64_t t = h->t;
+    // force history capacity
+    if (t + 2 > h->force_cap) {
+        int64_t cap = std::max<int64_t>(2 * h->force_cap, t + 4096);
+        double* nf = (double*)dev_alloc(h, (size_t)cap * 2 * sizeof(double));
+        if (!nf) return fail(h, HLBM_ENOMEM, "force history allocation failed");
+        cudaMemcpyAsync(nf, h->force, (size_t)h->force_cap * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+        dev_free(h, h->force);
+        h->force = nf;
+        h->force_cap = cap;
+    }
+    double X, Y;
+    motion_pos(h->motion, t, &X, &Y);
+    StepArgs a{};
+    a.t = t;
+    a.cx = h->patch.x_c + X;
+    a.cy = h->patch.y_c + Y;
+    a.dX = X - h->Xprev;
+    a.dY = Y - h->Yprev;
+    window_origin(h, a.cx, a.cy, &a.bx0, &a.by0);
+    a.pbx0 = h->pbx0;
+    a.pby0 = h->pby0;
+    a.first = (t == 0);
+    if (a.bx0 < 1 || a.by0 < 1 || a.bx0 + d.bw > d.nx - 1 || a.by0 + d.bh > d.ny - 1)
+        return fail(h, HLBM_EINVAL, "step %lld: the patch window [%d,%d)x[%d,%d) leaves the lattice",
+                    (long long)t, a.bx0, a.bx0 + d.bw, a.by0, a.by0 + d.bh);
+    if (std::fabs(a.dX) >= 1.0 || std::fabs(a.dY) >= 1.0)
+        return fail(h, HLBM_EINVAL, "step %lld: displacement (%g, %g) is not below one lattice spacing",
+                    (long long)t, a.dX, a.dY);
+    bind(h, d);
+    // 1. move the patch to y(t) and refill it (Sec. 4)
+    const int ncls = (t == 0) ? h->ci : 1 - h->ci;
+    d.cls_prev = h->cls[h->ci];
+    d.cls_cur = h->cls[ncls];
+    d.sbox_old = (const T*)h->sbox[h->si];
+    d.sbox_new = (T*)h->sbox[1 - h->si];
+    int ev = phase_begin(h, s);
+    if (t > 0) {
+        launch_refill<T>(d, a, s);
+        h->ui = 1 - h->ui;
+        bind(h, d);
+        // 2. classify the lattice nodes against the moved fictitious curve
+        launch_classify<T>(d, a, s);
+    }
+    // 3. interpolation nodes from the patch (eq. postcollision2_s)
+    launch_fill<T>(d, a, s);
+    phase_end(h, HLBM_PHASE_MOVE, ev, t > 0 ? 3 : 1, s);
+    // 4. stream-collide t -> t+1 (eq. LBE)
+    ev = phase_begin(h, s);
+    launch_stream_collide<T>(d, a, s);
+    phase_end(h, HLBM_PHASE_STREAM, ev, 1, s);
+    // 5a. the outer nodes' feed from the lattice at t and t+1
+    launch_feed<T>(d, a, s);
+    ps.a = a;
+    ps.ncls = ncls;
+    ps.X = X;
+    ps.Y = Y;
+    return HLBM_OK;
+}
+
+template <typename T>
+int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+    Dev<T>& d = dev_of<T>(h);
+    // 5b. n FV sub-steps (eq. ulbe, eq. postcollision2_u)
+    int ev = phase_begin(h, s);
+    if (ev0) cudaEventRecord(ev0, s);
+    cudaError_t fe = h->use_smem ? launch_fv_smem<T>(d, ps.a, s) : launch_fv_persistent<T>(d, ps.a, s);
+    if (ev1) cudaEventRecord(ev1, s);
+    if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
+    if (d.n_sub & 1) h->ui = 1 - h->ui;
+    bind(h, d);
+    phase_end(h, HLBM_PHASE_FV, ev, 2, s);
+    return HLBM_OK;
+}
+
+template <typename T>
+int step_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
+    Dev<T>& d = dev_of<T>(h);
+    // 6. force on the lamina at t+1
+    int ev = phase_begin(h, s);
+    launch_force<T>(d, ps.a.t + 1, s);
+    phase_end(h, HLBM_PHASE_FORCE, ev, d.nseg > 0 ? 2 : 1, s);
+    if (h->ev_used > 4096) {
+        int rc = phase_collect(h);
+        if (rc != HLBM_OK) return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
+    h->fi = 1 - h->fi;
+    h->si = 1 - h->si;
+    h->ci = ps.ncls;
+    h->pbx0 = ps.a.bx0;
+    h->pby0 = ps.a.by0;
+    h->Xprev = ps.X;
+    h->Yprev = ps.Y;
+    h->t = ps.a.t + 1;
+    return HLBM_OK;
+}
+
 template <typename T>
 int step_impl(hlbm* h, int64_t nsteps) {
-    Dev<T>& d = dev_of<T>(h);
-    cudaStream_t s = h->stream;
     for (int64_t k = 0; k < nsteps; ++k) {
-        const int64_t t = h->t;
-        // force history capacity
-        if (t + 2 > h->force_cap) {
-            int64_t cap = std::max<int64_t>(2 * h->force_cap, t + 4096);
-            double* nf = (double*)dev_alloc(h, (size_t)cap * 2 * sizeof(double));
-            if (!nf) return fail(h, HLBM_ENOMEM, "force history allocation failed");
-            cudaMemcpyAsync(nf, h->force, (size_t)h->force_cap * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-            cudaStreamSynchronize(s);
-            dev_free(h, h->force);
-            h->force = nf;
-            h->force_cap = cap;
-        }
-        double X, Y;
-        motion_pos(h->motion, t, &X, &Y);
-        StepArgs a{};
-        a.t = t;
-        a.cx = h->patch.x_c + X;
-        a.cy = h->patch.y_c + Y;
-        a.dX = X - h->Xprev;
-        a.dY = Y - h->Yprev;
-        window_origin(h, a.cx, a.cy, &a.bx0, &a.by0);
-        a.pbx0 = h->pbx0;
-        a.pby0 = h->pby0;
-        a.first = (t == 0);
-        if (a.bx0 < 1 || a.by0 < 1 || a.bx0 + d.bw > d.nx - 1 || a.by0 + d.bh > d.ny - 1)
-            return fail(h, HLBM_EINVAL, "step %lld: the patch window [%d,%d)x[%d,%d) leaves the lattice",
-                        (long long)t, a.bx0, a.bx0 + d.bw, a.by0, a.by0 + d.bh);
-        if (std::fabs(a.dX) >= 1.0 || std::fabs(a.dY) >= 1.0)
-            return fail(h, HLBM_EINVAL, "step %lld: displacement (%g, %g) is not below one lattice spacing",
-                        (long long)t, a.dX, a.dY);
-        bind(h, d);
-        // 1. move the patch to y(t) and refill it (Sec. 4)
-        const int ncls = (t == 0) ? h->ci : 1 - h->ci;
-        d.cls_prev = h->cls[h->ci];
-        d.cls_cur = h->cls[ncls];
-        d.sbox_old = (const T*)h->sbox[h->si];
-        d.sbox_new = (T*)h->sbox[1 - h->si];
-        int ev = phase_begin(h);
-        if (t > 0) {
-            launch_refill<T>(d, a, s);
-            h->ui = 1 - h->ui;
-            bind(h, d);
-            // 2. classify the lattice nodes against the moved fictitious curve
-            launch_classify<T>(d, a, s);
-        }
-        // 3. interpolation nodes from the patch (eq. postcollision2_s)
-        launch_fill<T>(d, a, s);
-        phase_end(h, HLBM_PHASE_MOVE, ev, t > 0 ? 3 : 1);
-        // 4. stream-collide t -> t+1 (eq. LBE)
-        ev = phase_begin(h);
-        launch_stream_collide<T>(d, a, s);
-        phase_end(h, HLBM_PHASE_STREAM, ev, 1);
-        // 5. outer-node feed and n FV sub-steps (eq. ulbe, eq. postcollision2_u)
-        ev = phase_begin(h);
-        launch_feed<T>(d, a, s);
-        cudaError_t fe = h->use_smem ? launch_fv_smem<T>(d, a, s) : launch_fv_persistent<T>(d, a, s);
-        if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
-        if (d.n_sub & 1) h->ui = 1 - h->ui;
-        bind(h, d);
-        phase_end(h, HLBM_PHASE_FV, ev, 2);
-        // 6. force on the lamina at t+1
-        ev = phase_begin(h);
-        launch_force<T>(d, t + 1, s);
-        phase_end(h, HLBM_PHASE_FORCE, ev, d.nseg > 0 ? 2 : 1);
-        if (h->ev_used > 4096) {
-            int rc = phase_collect(h);
-            if (rc != HLBM_OK) return rc;
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_check(h, e, "kernel launch");
-        h->fi = 1 - h->fi;
-        h->si = 1 - h->si;
-        h->ci = ncls;
-        h->pbx0 = a.bx0;
-        h->pby0 = a.by0;
-        h->Xprev = X;
-        h->Yprev = Y;
-        h->t = t + 1;
+        PendingStep ps{};
+        int rc = step_lattice<T>(h, h->stream, ps);
+        if (rc == HLBM_OK) rc = step_fv<T>(h, h->stream, ps);
+        if (rc == HLBM_OK) rc = step_finish<T>(h, h->stream, ps);
+        if (rc != HLBM_OK) return rc;
     }
     return HLBM_OK;
+}
+
+// FV tiles: equal ranges of the Morton-ordered nodes.  The shared-memory
+// kernel runs one block per tile, all co-resident; when a tile and its halo
+// do not fit in shared memory the global-memory kernel runs instead, with
+// as many tiles as it has co-resident blocks.  Neighbour tiles own a column
+// of a tile's rows.  n_tiles_req <= 0 picks one tile per SM (at least 64
+// nodes each).  Builds the tile tables, halo lists, ELL matrices with
+// tile-local columns, node orders and send flags; previous tables are
+// released.  Needs the FV matrices (d.coef).
+template <typename T>
+int build_tiles(hlbm* h, int n_tiles_req) {
+    Dev<T>& d = dev_of<T>(h);
+    cudaStream_t s = h->stream;
+    const int n = h->patch.n_nodes;
+    int rc = HLBM_OK;
+    int sms = 0, devi = 0;
+    cudaGetDevice(&devi);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devi);
+    int max_row = 0;
+    for (int q = 0; q < n; ++q) max_row = std::max(max_row, h->row_ptr[q + 1] - h->row_ptr[q]);
+    std::vector<int32_t> tile_start, owner(n), tile_nb_ptr, tile_nb, halo_ptr, halo_ids;
+    int tile_cap = 0, halo_cap = 0;
+    auto make_tiles = [&](int nt_) {
+        tile_start.assign(nt_ + 1, 0);
+        for (int k = 0; k <= nt_; ++k) tile_start[k] = (int32_t)((int64_t)k * n / nt_);
+        for (int k = 0; k < nt_; ++k)
+            for (int q = tile_start[k]; q < tile_start[k + 1]; ++q) owner[q] = k;
+        tile_nb_ptr.assign(nt_ + 1, 0);
+        tile_nb.clear();
+        halo_ptr.assign(nt_ + 1, 0);
+        halo_ids.clear();
+        tile_cap = halo_cap = 0;
+        for (int k = 0; k < nt_; ++k) {
+            std::vector<int32_t> nb, hl;
+            for (int q = tile_start[k]; q < tile_start[k + 1]; ++q)
+                for (int e = h->row_ptr[q]; e < h->row_ptr[q + 1]; ++e)
+                    if (owner[h->col[e]] != k) {
+                        nb.push_back(owner[h->col[e]]);
+                        hl.push_back(h->col[e]);
+                    }
+            std::sort(nb.begin(), nb.end());
+            nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+            std::sort(hl.begin(), hl.end());
+            hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
+            tile_nb.insert(tile_nb.end(), nb.begin(), nb.end());
+            tile_nb_ptr[k + 1] = (int32_t)tile_nb.size();
+            halo_ids.insert(halo_ids.end(), hl.begin(), hl.end());
+            halo_ptr[k + 1] = (int32_t)halo_ids.size();
+            tile_cap = std::max(tile_cap, tile_start[k + 1] - tile_start[k]);
+            halo_cap = std::max(halo_cap, (int)hl.size());
+        }
+    };
+    int n_tiles = n_tiles_req > 0 ? std::min(n_tiles_req, n) : std::max(1, std::min(sms, (n + 63) / 64));
+    make_tiles(n_tiles);
+    size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0), h->patch.n_sub);
+    h->use_smem = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536 &&
+                  fv_smem_tile_capacity<T>(smem) >= n_tiles;
+    if (!h->use_smem) {
+        int cap = fv_tile_capacity<T>();
+        if (cap < 1) return fail(h, HLBM_ECUDA, "the FV kernel cannot be resident on this device");
+        n_tiles = std::max(1, std::min(cap, n_tiles_req > 0 ? n_tiles_req : (n + 63) / 64));
+        make_tiles(n_tiles);
+    }
+    // release the previous tables once the stream has finished with them
+    cudaStreamSynchronize(s);
+    for (void* old : h->tile_blocks) dev_free(h, old);
+    h->tile_blocks.clear();
+    auto track = [&](void* ptr) {
+        if (ptr) h->tile_blocks.push_back(ptr);
+        return ptr;
+    };
+    d.tile_cap = tile_cap;
+    d.halo_cap = std::max(halo_cap, 1);
+    h->n_tiles = n_tiles;
+    d.n_tiles = n_tiles;
+    d.tile_start = (int32_t*)track(upload(h, tile_start.data(), tile_start.size(), &rc));
+    d.tile_nb_ptr = (int32_t*)track(upload(h, tile_nb_ptr.data(), tile_nb_ptr.size(), &rc));
+    d.tile_nb = (int32_t*)track(upload(h, tile_nb.data(), tile_nb.size(), &rc));
+    // the FV kernel counts sub-steps from t * n_sub (t: the solver's step), so a
+    // table rebuilt after some steps starts its counters there
+    std::vector<unsigned long long> progress0(n_tiles, (unsigned long long)h->t * (unsigned long long)h->patch.n_sub);
+    d.progress = (unsigned long long*)track(upload(h, progress0.data(), progress0.size(), &rc));
+    d.halo_ptr = (int32_t*)track(upload(h, halo_ptr.data(), halo_ptr.size(), &rc));
+    d.halo_ids = (int32_t*)track(upload(h, halo_ids.data(), halo_ids.size(), &rc));
+    // ELL layout (tile-local columns) and the nodes other tiles read
+    const int ell_w = max_row;
+    d.ell_width = ell_w;
+    std::vector<int32_t> ell_src((size_t)ell_w * n, -1), ell_col((size_t)ell_w * n, 0);
+    std::vector<int8_t> send(n, 0);
+    for (int32_t x : halo_ids) send[x] = 1;
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k], tn = tile_start[k + 1] - p0;
+        const int32_t* hb = halo_ids.data() + halo_ptr[k];
+        const int hn = halo_ptr[k + 1] - halo_ptr[k];
+        for (int r = 0; r < tn; ++r) {
+            const int q = p0 + r;
+            for (int j = 0; j < ell_w; ++j) {
+                size_t idx = (size_t)ell_w * p0 + (size_t)j * tn + r;
+                int e = h->row_ptr[q] + j;
+                if (e < h->row_ptr[q + 1]) {
+                    int c = h->col[e];
+                    ell_src[idx] = e;
+                    if (c >= p0 && c < p0 + tn)
+                        ell_col[idx] = c - p0;
+                    else
+                        ell_col[idx] = d.tile_cap + (int)(std::lower_bound(hb, hb + hn, c) - hb);
+                } else {
+                    ell_col[idx] = r;
+                }
+            }
+        }
+    }
+    // per tile: nodes whose rows read only the tile first (tile-local index)
+    std::vector<uint16_t> tile_order(std::max(n, 1), 0);
+    std::vector<int32_t> tile_interior(n_tiles, 0);
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k], p1 = tile_start[k + 1];
+        std::vector<uint16_t> in, bd;
+        for (int q = p0; q < p1; ++q) {
+            bool interior = true;
+            for (int e = h->row_ptr[q]; e < h->row_ptr[q + 1]; ++e)
+                if (h->col[e] < p0 || h->col[e] >= p1) interior = false;
+            (interior ? in : bd).push_back((uint16_t)(q - p0));
+        }
+        tile_interior[k] = (int32_t)in.size();
+        std::copy(in.begin(), in.end(), tile_order.begin() + p0);
+        std::copy(bd.begin(), bd.end(), tile_order.begin() + p0 + in.size());
+    }
+    d.tile_order = (uint16_t*)track(upload(h, tile_order.data(), tile_order.size(), &rc));
+    d.tile_interior = (int32_t*)track(upload(h, tile_interior.data(), tile_interior.size(), &rc));
+    d.send = (int8_t*)track(upload(h, send.data(), send.size(), &rc));
+    int32_t* d_ell_src = upload(h, ell_src.data(), ell_src.size(), &rc);
+    int32_t* d_ell_col = upload(h, ell_col.data(), ell_col.size(), &rc);
+    Coef<T>* ellv = (Coef<T>*)track(dev_alloc(h, std::max<size_t>(ell_src.size(), 1) * sizeof(Coef<T>)));
+    if (rc != HLBM_OK) return rc;
+    if (!ellv || !d.progress || !d_ell_src || !d_ell_col) return fail(h, HLBM_ENOMEM, "device allocation failed");
+    d.ell = ellv;
+    launch_build_ell<T>(d.coef, d_ell_src, d_ell_col, ellv, (int64_t)ell_src.size(), s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    dev_free(h, d_ell_src);
+    dev_free(h, d_ell_col);
+    return e2 == cudaSuccess ? HLBM_OK : cuda_check(h, e2, "tile tables");
 }
 
 template <typename T>
@@ -408,60 +590,6 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     if (max_row > 64) return fail(h, HLBM_EINVAL, "a patch node has %d neighbours (max 63)", max_row - 1);
     h->nnz = (int)h->col.size();
     d.nnz = h->nnz;
-    // FV tiles: equal ranges of the Morton-ordered nodes.  The shared-memory
-    // kernel runs one block per SM; when a tile and its halo do not fit in
-    // shared memory, the global-memory kernel runs with as many tiles as it
-    // has co-resident blocks.  Neighbour tiles own a column of a tile's rows.
-    int sms = 0, devi = 0;
-    cudaGetDevice(&devi);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devi);
-    std::vector<int32_t> tile_start, owner(n), tile_nb_ptr, tile_nb, halo_ptr, halo_ids;
-    int tile_cap = 0, halo_cap = 0;
-    auto make_tiles = [&](int nt_) {
-        tile_start.assign(nt_ + 1, 0);
-        for (int k = 0; k <= nt_; ++k) tile_start[k] = (int32_t)((int64_t)k * n / nt_);
-        for (int k = 0; k < nt_; ++k)
-            for (int p = tile_start[k]; p < tile_start[k + 1]; ++p) owner[p] = k;
-        tile_nb_ptr.assign(nt_ + 1, 0);
-        tile_nb.clear();
-        halo_ptr.assign(nt_ + 1, 0);
-        halo_ids.clear();
-        tile_cap = halo_cap = 0;
-        for (int k = 0; k < nt_; ++k) {
-            std::vector<int32_t> nb, hl;
-            for (int p = tile_start[k]; p < tile_start[k + 1]; ++p)
-                for (int e = h->row_ptr[p]; e < h->row_ptr[p + 1]; ++e)
-                    if (owner[h->col[e]] != k) {
-                        nb.push_back(owner[h->col[e]]);
-                        hl.push_back(h->col[e]);
-                    }
-            std::sort(nb.begin(), nb.end());
-            nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-            std::sort(hl.begin(), hl.end());
-            hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
-            tile_nb.insert(tile_nb.end(), nb.begin(), nb.end());
-            tile_nb_ptr[k + 1] = (int32_t)tile_nb.size();
-            halo_ids.insert(halo_ids.end(), hl.begin(), hl.end());
-            halo_ptr[k + 1] = (int32_t)halo_ids.size();
-            tile_cap = std::max(tile_cap, tile_start[k + 1] - tile_start[k]);
-            halo_cap = std::max(halo_cap, (int)hl.size());
-        }
-    };
-    int n_tiles = std::max(1, std::min(sms, (n + 63) / 64));
-    make_tiles(n_tiles);
-    size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0), p.n_sub);
-    h->use_smem = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536 &&
-                  fv_smem_tile_capacity<T>(smem) >= n_tiles;
-    if (!h->use_smem) {
-        int cap = fv_tile_capacity<T>();
-        if (cap < 1) return fail(h, HLBM_ECUDA, "the FV kernel cannot be resident on this device");
-        n_tiles = std::max(1, std::min(cap, (n + 63) / 64));
-        make_tiles(n_tiles);
-    }
-    d.tile_cap = tile_cap;
-    d.halo_cap = std::max(halo_cap, 1);
-    h->n_tiles = n_tiles;
-    d.n_tiles = n_tiles;
     std::vector<int32_t> outer_of(n, -1);
     h->outer.clear();
     for (int P = 0; P < n; ++P)
@@ -601,64 +729,6 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     int32_t* d_tstart = upload(h, tstart.data(), tstart.size(), &rc);
     int32_t* d_tlist = upload(h, tlist.data(), tlist.size(), &rc);
     Coef<T>* coefv = (Coef<T>*)dev_alloc(h, (size_t)h->nnz * sizeof(Coef<T>));
-    d.tile_start = upload(h, tile_start.data(), tile_start.size(), &rc);
-    d.tile_nb_ptr = upload(h, tile_nb_ptr.data(), tile_nb_ptr.size(), &rc);
-    d.tile_nb = upload(h, tile_nb.data(), tile_nb.size(), &rc);
-    d.progress = (unsigned long long*)dev_alloc(h, (size_t)n_tiles * sizeof(unsigned long long));
-    d.halo_ptr = upload(h, halo_ptr.data(), halo_ptr.size(), &rc);
-    d.halo_ids = upload(h, halo_ids.data(), halo_ids.size(), &rc);
-    // ELL layout (tile-local columns) and the nodes other tiles read
-    int ell_w = 0;
-    for (int p = 0; p < n; ++p) ell_w = std::max(ell_w, h->row_ptr[p + 1] - h->row_ptr[p]);
-    d.ell_width = ell_w;
-    std::vector<int32_t> ell_src((size_t)ell_w * n, -1), ell_col((size_t)ell_w * n, 0);
-    std::vector<int8_t> send(n, 0);
-    for (int32_t x : halo_ids) send[x] = 1;
-    for (int k = 0; k < n_tiles; ++k) {
-        const int p0 = tile_start[k], tn = tile_start[k + 1] - p0;
-        const int32_t* hb = halo_ids.data() + halo_ptr[k];
-        const int hn = halo_ptr[k + 1] - halo_ptr[k];
-        for (int r = 0; r < tn; ++r) {
-            const int p = p0 + r;
-            for (int j = 0; j < ell_w; ++j) {
-                size_t idx = (size_t)ell_w * p0 + (size_t)j * tn + r;
-                int e = h->row_ptr[p] + j;
-                if (e < h->row_ptr[p + 1]) {
-                    int c = h->col[e];
-                    ell_src[idx] = e;
-                    if (c >= p0 && c < p0 + tn)
-                        ell_col[idx] = c - p0;
-                    else
-                        ell_col[idx] = d.tile_cap + (int)(std::lower_bound(hb, hb + hn, c) - hb);
-                } else {
-                    ell_col[idx] = r;
-                }
-            }
-        }
-    }
-    // per tile: nodes whose rows read only the tile first (tile-local index)
-    std::vector<uint16_t> tile_order(std::max(n, 1), 0);
-    std::vector<int32_t> tile_interior(n_tiles, 0);
-    for (int k = 0; k < n_tiles; ++k) {
-        const int p0 = tile_start[k], p1 = tile_start[k + 1];
-        std::vector<uint16_t> in, bd;
-        for (int q = p0; q < p1; ++q) {
-            bool interior = true;
-            for (int e = h->row_ptr[q]; e < h->row_ptr[q + 1]; ++e)
-                if (h->col[e] < p0 || h->col[e] >= p1) interior = false;
-            (interior ? in : bd).push_back((uint16_t)(q - p0));
-        }
-        tile_interior[k] = (int32_t)in.size();
-        std::copy(in.begin(), in.end(), tile_order.begin() + p0);
-        std::copy(bd.begin(), bd.end(), tile_order.begin() + p0 + in.size());
-    }
-    d.tile_order = upload(h, tile_order.data(), tile_order.size(), &rc);
-    d.tile_interior = upload(h, tile_interior.data(), tile_interior.size(), &rc);
-    d.send = upload(h, send.data(), send.size(), &rc);
-    int32_t* d_ell_src = upload(h, ell_src.data(), ell_src.size(), &rc);
-    int32_t* d_ell_col = upload(h, ell_col.data(), ell_col.size(), &rc);
-    Coef<T>* ellv = (Coef<T>*)dev_alloc(h, std::max<size_t>(ell_src.size(), 1) * sizeof(Coef<T>));
-    d.ell = ellv;
     d.abort_flag = (unsigned*)dev_alloc(h, 16);
     d.snap = (T*)dev_alloc(h, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
     d.rtype = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
@@ -672,10 +742,9 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     h->force = (double*)dev_alloc(h, (size_t)h->force_cap * 2 * sizeof(double));
     if (rc != HLBM_OK) return rc;
     if (!coefv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force || !d.fcontrib ||
-        !d.progress || !d.abort_flag)
+        !d.abort_flag)
         return fail(h, HLBM_ENOMEM, "device allocation failed");
     d.coef = coefv;
-    cudaMemsetAsync(d.progress, 0, (size_t)n_tiles * sizeof(unsigned long long), s);
     cudaMemsetAsync(d.abort_flag, 0, 16, s);
     cudaMemsetAsync(h->status, 0, 64, s);
     cudaMemsetAsync(d.rtype, 0, (size_t)n * sizeof(int32_t), s);
@@ -685,8 +754,8 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     h->fi = h->si = h->ui = h->ci = 0;
     bind(h, d);
     launch_fv_coeffs<T>(d, p.lumped, coefv, s);
-    if (!ellv) return fail(h, HLBM_ENOMEM, "device allocation failed");
-    launch_build_ell<T>(coefv, d_ell_src, d_ell_col, ellv, (int64_t)ell_src.size(), s);
+    rc = build_tiles<T>(h, 0);
+    if (rc != HLBM_OK) return rc;
 
     // --- initial state: equilibrium at the initial density and velocity
     const size_t N = (size_t)g->nx * g->ny;
@@ -723,8 +792,6 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     dev_free(h, drho);
     dev_free(h, dux);
     dev_free(h, duy);
-    dev_free(h, d_ell_src);
-    dev_free(h, d_ell_col);
     h->t = 0;
     h->Xprev = X0;
     h->Yprev = Y0;
@@ -741,6 +808,227 @@ int sync_status(hlbm* h, unsigned* bits) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "status readback");
     *bits = v;
+    return HLBM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// ---- checkpoint file: a fixed header, then the dynamic device state -------
+// The header records what the state depends on (sizes, physics, a hash of
+// the mesh) so that a file is only restored into a solver created from the
+// same inputs; everything derived from the inputs at creation (geometry,
+// FV matrices, tiles) is rebuilt by hlbm_create, not stored.
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t dtype, nx, ny, n_nodes, n_tris, n_sub, bw, bh, bc_x, bc_y, motion, lumped;
+    double tau_s, rho0, A, omega, vx, vy, lamina_L, lamina_T, x_c, y_c, delta_f;
+    uint64_t mesh_hash;
+    int64_t t;
+    double Xprev, Yprev;
+    int32_t pbx0, pby0, ci, si, ui, fi;
+    uint32_t status, pad;
+};
+constexpr char kCkptMagic[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
+
+uint64_t fnv1a(uint64_t hsh, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        hsh ^= b[i];
+        hsh *= 1099511628211ull;
+    }
+    return hsh;
+}
+
+uint64_t mesh_hash(const hlbm* h) {
+    uint64_t v = 1469598103934665603ull;
+    v = fnv1a(v, h->xy.data(), h->xy.size() * sizeof(double));
+    v = fnv1a(v, h->tri.data(), h->tri.size() * sizeof(int32_t));
+    v = fnv1a(v, h->kind.data(), h->kind.size());
+    return v;
+}
+
+template <typename T>
+CkptHeader ckpt_header(hlbm* h) {
+    Dev<T>& d = dev_of<T>(h);
+    CkptHeader c{};
+    std::memcpy(c.magic, kCkptMagic, 8);
+    c.version = 1;
+    c.dtype = h->dtype;
+    c.nx = d.nx;
+    c.ny = d.ny;
+    c.n_nodes = h->patch.n_nodes;
+    c.n_tris = h->patch.n_tris;
+    c.n_sub = h->patch.n_sub;
+    c.bw = d.bw;
+    c.bh = d.bh;
+    c.bc_x = h->grid.bc_x;
+    c.bc_y = h->grid.bc_y;
+    c.motion = h->motion.kind;
+    c.lumped = h->patch.lumped;
+    c.tau_s = h->tau_s;
+    c.rho0 = h->grid.rho0;
+    c.A = h->motion.A;
+    c.omega = h->motion.omega;
+    c.vx = h->motion.vx;
+    c.vy = h->motion.vy;
+    c.lamina_L = h->patch.lamina_L;
+    c.lamina_T = h->patch.lamina_T;
+    c.x_c = h->patch.x_c;
+    c.y_c = h->patch.y_c;
+    c.delta_f = h->patch.delta_f;
+    c.mesh_hash = mesh_hash(h);
+    c.t = h->t;
+    c.Xprev = h->Xprev;
+    c.Yprev = h->Yprev;
+    c.pbx0 = h->pbx0;
+    c.pby0 = h->pby0;
+    c.ci = h->ci;
+    c.si = h->si;
+    c.ui = h->ui;
+    c.fi = h->fi;
+    return c;
+}
+
+// the device buffers of the state, in file order
+template <typename T>
+std::vector<std::pair<void*, size_t>> ckpt_sections(hlbm* h, int64_t t) {
+    Dev<T>& d = dev_of<T>(h);
+    const size_t lat = (d.store ? 2 : sizeof(T)) * 9 * (size_t)d.plane;
+    const size_t box = sizeof(T) * 9 * (size_t)d.bplane;
+    const size_t rec = sizeof(T) * kRec * (size_t)d.n;
+    return {{h->fbuf[0], lat},
+            {h->fbuf[1], lat},
+            {h->sbox[0], box},
+            {h->sbox[1], box},
+            {h->cls[0], (size_t)d.bplane},
+            {h->cls[1], (size_t)d.bplane},
+            {h->fu[0], rec},
+            {h->fu[1], rec},
+            {d.rtype, sizeof(int32_t) * (size_t)d.n},
+            {d.rdonor, sizeof(int32_t) * (size_t)d.n},
+            {h->force, 2 * sizeof(double) * (size_t)(t + 1)}};
+}
+
+constexpr size_t kCkptChunk = size_t(64) << 20;
+
+template <typename T>
+int save_impl(hlbm* h, const char* path) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "checkpoint sync");
+    CkptHeader c = ckpt_header<T>(h);
+    unsigned st = 0;
+    int rc = sync_status(h, &st);
+    if (rc != HLBM_OK) return rc;
+    c.status = st;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(h, HLBM_EIO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&c, sizeof c, 1, fp) == 1;
+    std::vector<unsigned char> buf;
+    for (auto& sec : ckpt_sections<T>(h, h->t)) {
+        for (size_t off = 0; ok && off < sec.second; off += kCkptChunk) {
+            const size_t n = std::min(kCkptChunk, sec.second - off);
+            buf.resize(n);
+            e = cudaMemcpyAsync(buf.data(), (const char*)sec.first + off, n, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) {
+                std::fclose(fp);
+                return cuda_check(h, e, "checkpoint read-back");
+            }
+            ok = std::fwrite(buf.data(), 1, n, fp) == n;
+        }
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? HLBM_OK : fail(h, HLBM_EIO, "writing %s failed", path);
+}
+
+template <typename T>
+int load_impl(hlbm* h, const char* path) {
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(h, HLBM_EIO, "cannot open %s", path);
+    CkptHeader c{};
+    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 1) {
+        std::fclose(fp);
+        return fail(h, HLBM_EIO, "%s is not a solver checkpoint", path);
+    }
+    const CkptHeader m = ckpt_header<T>(h);
+    const bool same = c.dtype == m.dtype && c.nx == m.nx && c.ny == m.ny && c.n_nodes == m.n_nodes &&
+                      c.n_tris == m.n_tris && c.n_sub == m.n_sub && c.bw == m.bw && c.bh == m.bh &&
+                      c.bc_x == m.bc_x && c.bc_y == m.bc_y && c.motion == m.motion && c.lumped == m.lumped &&
+                      c.tau_s == m.tau_s && c.rho0 == m.rho0 && c.A == m.A && c.omega == m.omega &&
+                      c.vx == m.vx && c.vy == m.vy && c.lamina_L == m.lamina_L && c.lamina_T == m.lamina_T &&
+                      c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash;
+    if (!same || c.t < 0 || ((c.ci | c.si | c.ui | c.fi) & ~1)) {
+        std::fclose(fp);
+        return fail(h, HLBM_EINVAL, "%s was written by a solver with other inputs", path);
+    }
+    // the whole file must be there before anything is overwritten
+    size_t want = sizeof c;
+    for (auto& sec : ckpt_sections<T>(h, c.t)) want += sec.second;
+    long have = -1;
+    if (std::fseek(fp, 0, SEEK_END) == 0) have = std::ftell(fp);
+    if (have < 0 || (size_t)have != want || std::fseek(fp, (long)sizeof c, SEEK_SET) != 0) {
+        std::fclose(fp);
+        return fail(h, HLBM_EIO, "%s holds %ld bytes, a checkpoint of this solver at step %lld holds %zu", path,
+                    have, (long long)c.t, want);
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        std::fclose(fp);
+        return cuda_check(h, e, "checkpoint sync");
+    }
+    // room for the force history up to t
+    if (c.t + 2 > h->force_cap) {
+        const int64_t cap = c.t + 4096;
+        double* nf = (double*)dev_alloc(h, (size_t)cap * 2 * sizeof(double));
+        if (!nf) {
+            std::fclose(fp);
+            return fail(h, HLBM_ENOMEM, "force history allocation failed");
+        }
+        cudaMemsetAsync(nf, 0, (size_t)cap * 2 * sizeof(double), h->stream);
+        dev_free(h, h->force);
+        h->force = nf;
+        h->force_cap = cap;
+    }
+    bool ok = true;
+    std::vector<unsigned char> buf;
+    for (auto& sec : ckpt_sections<T>(h, c.t)) {
+        for (size_t off = 0; ok && off < sec.second; off += kCkptChunk) {
+            const size_t n = std::min(kCkptChunk, sec.second - off);
+            buf.resize(n);
+            ok = std::fread(buf.data(), 1, n, fp) == n;
+            if (!ok) break;
+            e = cudaMemcpyAsync((char*)sec.first + off, buf.data(), n, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) {
+                std::fclose(fp);
+                return cuda_check(h, e, "checkpoint upload");
+            }
+        }
+    }
+    std::fclose(fp);
+    if (!ok) return fail(h, HLBM_EIO, "%s is truncated", path);
+    h->t = c.t;
+    h->Xprev = c.Xprev;
+    h->Yprev = c.Yprev;
+    h->pbx0 = c.pbx0;
+    h->pby0 = c.pby0;
+    h->ci = c.ci;
+    h->si = c.si;
+    h->ui = c.ui;
+    h->fi = c.fi;
+    Dev<T>& d = dev_of<T>(h);
+    e = cudaMemcpyAsync(h->status, &c.status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
+    // the FV kernel counts sub-steps from t * n_sub
+    std::vector<unsigned long long> prog(d.n_tiles, (unsigned long long)c.t * (unsigned long long)c.n_sub);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.progress, prog.data(), prog.size() * sizeof(unsigned long long),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "checkpoint state");
+    bind(h, d);
     return HLBM_OK;
 }
 
@@ -777,6 +1065,79 @@ int get_fv_impl(hlbm_t* h, const Coef<T>* dcoef, int32_t* row_ptr, int32_t* col,
             ++pos;
         }
         if (row_ptr) row_ptr[P + 1] = pos;
+    }
+    return HLBM_OK;
+}
+
+}  // namespace
+
+struct hlbm_sweep {
+    std::vector<hlbm*> inst;
+    std::vector<cudaStream_t> streams;  // one per instance
+    std::vector<cudaEvent_t> ev_lat, ev_fv, ev_done, fv_t0, fv_t1;
+    cudaStream_t main = nullptr;        // the caller's stream
+    cudaStream_t fv = nullptr;          // FV launches of all instances, one after another
+    cudaEvent_t ev_main = nullptr;
+    std::vector<double> fv_ms;          // FV time of each instance, summed since the last reset
+    std::vector<int32_t> tile_nodes;    // target nodes per FV tile chosen by the tuner (0: default)
+    std::string err;
+};
+
+namespace {
+
+int inst_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
+    return h->dtype != HLBM_F64 ? step_lattice<float>(h, s, ps) : step_lattice<double>(h, s, ps);
+}
+int inst_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t e0, cudaEvent_t e1) {
+    return h->dtype != HLBM_F64 ? step_fv<float>(h, s, ps, e0, e1) : step_fv<double>(h, s, ps, e0, e1);
+}
+int inst_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
+    return h->dtype != HLBM_F64 ? step_finish<float>(h, s, ps) : step_finish<double>(h, s, ps);
+}
+int inst_retile(hlbm* h, int tiles) {
+    return h->dtype != HLBM_F64 ? build_tiles<float>(h, tiles) : build_tiles<double>(h, tiles);
+}
+
+// One step of every instance.  Instance i issues its lattice part on its
+// own stream; the FV sub-steps of all instances run one after another on a
+// single stream (each is a cooperative launch that wants the whole GPU, so
+// two of them never compete for residency), each as soon as its instance's
+// lattice part is done, while other instances' lattice parts run beside
+// it; instance i then issues its force on its own stream.
+int sweep_one_step(hlbm_sweep* w, bool time_fv) {
+    const size_t n = w->inst.size();
+    std::vector<PendingStep> ps(n);
+    for (size_t i = 0; i < n; ++i) {
+        int rc = inst_lattice(w->inst[i], w->streams[i], ps[i]);
+        if (rc != HLBM_OK) {
+            w->err = "instance " + std::to_string(i) + ": " + w->inst[i]->err;
+            return rc;
+        }
+        cudaEventRecord(w->ev_lat[i], w->streams[i]);
+    }
+    for (size_t i = 0; i < n; ++i) {
+        cudaStreamWaitEvent(w->fv, w->ev_lat[i], 0);
+        int rc = inst_fv(w->inst[i], w->fv, ps[i], time_fv ? w->fv_t0[i] : nullptr, time_fv ? w->fv_t1[i] : nullptr);
+        if (rc != HLBM_OK) {
+            w->err = "instance " + std::to_string(i) + ": " + w->inst[i]->err;
+            return rc;
+        }
+        cudaEventRecord(w->ev_fv[i], w->fv);
+    }
+    for (size_t i = 0; i < n; ++i) {
+        cudaStreamWaitEvent(w->streams[i], w->ev_fv[i], 0);
+        int rc = inst_finish(w->inst[i], w->streams[i], ps[i]);
+        if (rc != HLBM_OK) {
+            w->err = "instance " + std::to_string(i) + ": " + w->inst[i]->err;
+            return rc;
+        }
+    }
+    if (time_fv) {
+        for (size_t i = 0; i < n; ++i) {
+            cudaEventSynchronize(w->fv_t1[i]);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, w->fv_t0[i], w->fv_t1[i]) == cudaSuccess) w->fv_ms[i] += ms;
+        }
     }
     return HLBM_OK;
 }
@@ -1103,6 +1464,148 @@ int hlbm_profile_read(hlbm_t* h, double* ms, int64_t* launches) {
         if (launches) launches[k] = h->phase_launches[k];
     }
     return HLBM_OK;
+}
+
+int hlbm_sweep_create(int32_t n, hlbm_t* const* solvers, void* cuda_stream, hlbm_sweep_t** out) {
+    if (!out || n < 1 || !solvers) return HLBM_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!solvers[i]) return HLBM_EINVAL;
+    hlbm_sweep* w = new hlbm_sweep();
+    w->main = (cudaStream_t)cuda_stream;
+    w->inst.assign(solvers, solvers + n);
+    w->streams.resize(n);
+    w->ev_lat.resize(n);
+    w->ev_fv.resize(n);
+    w->ev_done.resize(n);
+    w->fv_t0.resize(n);
+    w->fv_t1.resize(n);
+    w->fv_ms.assign(n, 0.0);
+    w->tile_nodes.assign(n, 0);
+    bool ok = cudaStreamCreateWithFlags(&w->fv, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&w->ev_main, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < n && ok; ++i) {
+        ok = cudaStreamCreateWithFlags(&w->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&w->ev_lat[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&w->ev_fv[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&w->ev_done[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&w->fv_t0[i]) == cudaSuccess && cudaEventCreate(&w->fv_t1[i]) == cudaSuccess;
+    }
+    if (!ok) {
+        hlbm_sweep_destroy(w);
+        return HLBM_ECUDA;
+    }
+    *out = w;
+    return HLBM_OK;
+}
+
+// every stream of the sweep waits for the work already queued on `from`,
+// and instance i's stream also for the work queued on that solver's own stream
+static void sweep_fork(hlbm_sweep* w, cudaStream_t from) {
+    cudaEventRecord(w->ev_main, from);
+    cudaStreamWaitEvent(w->fv, w->ev_main, 0);
+    for (size_t i = 0; i < w->inst.size(); ++i) {
+        cudaStreamWaitEvent(w->streams[i], w->ev_main, 0);
+        if (w->inst[i]->stream != from) {
+            cudaEventRecord(w->ev_done[i], w->inst[i]->stream);
+            cudaStreamWaitEvent(w->streams[i], w->ev_done[i], 0);
+        }
+    }
+}
+
+// `to` and every instance's own stream wait for all the sweep's work
+static void sweep_join(hlbm_sweep* w, cudaStream_t to) {
+    for (size_t i = 0; i < w->inst.size(); ++i) {
+        cudaEventRecord(w->ev_done[i], w->streams[i]);
+        cudaStreamWaitEvent(to, w->ev_done[i], 0);
+        if (w->inst[i]->stream != to) cudaStreamWaitEvent(w->inst[i]->stream, w->ev_done[i], 0);
+    }
+    cudaEventRecord(w->ev_main, w->fv);
+    cudaStreamWaitEvent(to, w->ev_main, 0);
+}
+
+int hlbm_sweep_step(hlbm_sweep_t* w, int64_t nsteps) {
+    if (!w || nsteps < 0) return HLBM_EINVAL;
+    sweep_fork(w, w->main);
+    int rc = HLBM_OK;
+    for (int64_t k = 0; k < nsteps && rc == HLBM_OK; ++k) rc = sweep_one_step(w, false);
+    sweep_join(w, w->main);
+    return rc;
+}
+
+int hlbm_sweep_tune(hlbm_sweep_t* w, int32_t trial_steps, int32_t* tile_nodes) {
+    if (!w || trial_steps < 1) return HLBM_EINVAL;
+    const int candidates[] = {256, 512, 1024, 1536};
+    const size_t n = w->inst.size();
+    std::vector<double> best(n, 1e300);
+    std::vector<int32_t> pick(n, 0);
+    int rc = HLBM_OK;
+    for (int c : candidates) {
+        for (size_t i = 0; i < n && rc == HLBM_OK; ++i) {
+            const int nodes = w->inst[i]->patch.n_nodes;
+            rc = inst_retile(w->inst[i], (nodes + c - 1) / c);
+        }
+        if (rc != HLBM_OK) break;
+        std::fill(w->fv_ms.begin(), w->fv_ms.end(), 0.0);
+        sweep_fork(w, w->main);
+        for (int32_t k = 0; k < trial_steps && rc == HLBM_OK; ++k) rc = sweep_one_step(w, true);
+        sweep_join(w, w->main);
+        for (size_t i = 0; i < n; ++i)
+            if (w->fv_ms[i] < best[i]) {
+                best[i] = w->fv_ms[i];
+                pick[i] = c;
+            }
+    }
+    for (size_t i = 0; i < n && rc == HLBM_OK; ++i) {
+        const int nodes = w->inst[i]->patch.n_nodes;
+        rc = inst_retile(w->inst[i], (nodes + pick[i] - 1) / pick[i]);
+        w->tile_nodes[i] = pick[i];
+        if (tile_nodes) tile_nodes[i] = pick[i];
+    }
+    cudaStreamSynchronize(w->main);
+    return rc;
+}
+
+int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms) {
+    if (!w || nsteps < 1 || !fv_ms) return HLBM_EINVAL;
+    std::fill(w->fv_ms.begin(), w->fv_ms.end(), 0.0);
+    sweep_fork(w, w->main);
+    int rc = HLBM_OK;
+    for (int64_t k = 0; k < nsteps && rc == HLBM_OK; ++k) rc = sweep_one_step(w, true);
+    sweep_join(w, w->main);
+    for (size_t i = 0; i < w->inst.size(); ++i) fv_ms[i] = w->fv_ms[i];
+    return rc;
+}
+
+const char* hlbm_sweep_last_error(const hlbm_sweep_t* w) { return w ? w->err.c_str() : "null sweep"; }
+
+void hlbm_sweep_destroy(hlbm_sweep_t* w) {
+    if (!w) return;
+    if (w->main) cudaStreamSynchronize(w->main);
+    for (cudaStream_t s : w->streams)
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    if (w->fv) {
+        cudaStreamSynchronize(w->fv);
+        cudaStreamDestroy(w->fv);
+    }
+    for (auto* v : {&w->ev_lat, &w->ev_fv, &w->ev_done, &w->fv_t0, &w->fv_t1})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+    if (w->ev_main) cudaEventDestroy(w->ev_main);
+    delete w;
+}
+
+int hlbm_save(hlbm_t* h, const char* path) {
+    if (!h || !path) return HLBM_EINVAL;
+    return h->dtype != HLBM_F64 ? save_impl<float>(h, path) : save_impl<double>(h, path);
+}
+
+int hlbm_load(hlbm_t* h, const char* path) {
+    if (!h || !path) return HLBM_EINVAL;
+    return h->dtype != HLBM_F64 ? load_impl<float>(h, path) : load_impl<double>(h, path);
 }
 
 const char* hlbm_last_error(const hlbm_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }

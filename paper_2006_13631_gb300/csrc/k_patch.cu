@@ -10,7 +10,6 @@
 namespace hk {
 
 constexpr int kMaxRow = 64;
-constexpr int kMaxSub = 1024;
 
 // Patch record: f'[0..8] and the quadratic equilibrium terms
 // z = (jx^2 / rho, jx jy / rho, jy^2 / rho) at [9..11].  With j = sum_i c_i f'_i
@@ -272,62 +271,113 @@ void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 // Wall nodes then take the lamina velocity: f += f^eq(rho, U) - f^eq(rho, u).
 // Outer nodes take the lattice state, linear in time at theta = (m+1)/n:
 //   f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq   (eq. postcollision2_u).
+// The FV update of one node (eq. ulbe), shared by both FV kernels so that
+// the result of a node does not depend on the kernel or the tiling: the
+// off-diagonal entries k != P in row order, then the pivot with
+// g_PP = -sum_k g_Pk (exact zero row sum).
+template <typename T>
+struct FvAcc {
+    T Gx[9], Gy[9], Cf[9], Z[3];
+    T gpx, gpy;
+};
+
+template <typename T>
+__device__ __forceinline__ void fv_acc_init(FvAcc<T>& a) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.Gx[i] = a.Gy[i] = a.Cf[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a.Z[j] = T(0);
+    a.gpx = a.gpy = T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void fv_acc_entry(FvAcc<T>& a, T gx, T gy, T c, const T (&f)[9], const T (&z)[3]) {
+    a.gpx -= gx;
+    a.gpy -= gy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (cx_of(i) != 0) a.Gx[i] += gx * f[i];
+        if (cy_of(i) != 0) a.Gy[i] += gy * f[i];
+        a.Cf[i] += c * f[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.Z[k] += c * z[k];
+}
+
+template <typename T>
+__device__ __forceinline__ void fv_acc_finish(const Dev<T>& d, FvAcc<T>& a, T cP, const T (&fP)[9], const T (&zP)[3],
+                                              T (&fn)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (cx_of(i) != 0) a.Gx[i] += a.gpx * fP[i];
+        if (cy_of(i) != 0) a.Gy[i] += a.gpy * fP[i];
+        a.Cf[i] += cP * fP[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.Z[k] += cP * zP[k];
+    T ceq[9];
+    ceq_of(a.Cf, a.Z, ceq);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        T s = -(a.Cf[i] - ceq[i]) * d.inv_tau_u;
+        if (cx_of(i) != 0) s += T(cx_of(i)) * a.Gx[i];
+        if (cy_of(i) != 0) s += T(cy_of(i)) * a.Gy[i];
+        fn[i] = fP[i] + d.dt_u * s;
+    }
+}
+
+// wall nodes: impose the lamina velocity, keep the non-equilibrium part
+template <typename T>
+__device__ __forceinline__ void fv_wall(const Dev<T>& d, T U, T V, T (&fn)[9]) {
+    T dr, rr, ux, uy;
+    moments_dev(fn, d.rho0, dr, rr, ux, uy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, dr, rr, U, V) - feq_dev<T>(i, dr, rr, ux, uy);
+}
+
+// outer nodes: the lattice state interpolated linearly in time (eq. 182, Dirichlet reading)
+template <typename T>
+__device__ __forceinline__ void fv_outer(const Dev<T>& d, int P, int m, T (&fn)[9]) {
+    const int o = d.outer_of[P];
+    const int64_t no = d.n_outer;
+    const T th = T(m + 1) / T(d.n_sub);
+    T st[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * d.snap[j * no + o] + th * d.snap[(12 + j) * no + o];
+    f_from_state(d, st, fn);
+}
+
 template <typename T>
 __device__ __forceinline__ void fv_node(const Dev<T>& d, const T* __restrict__ in, T* __restrict__ out, int P,
                                         int m, T U, T V) {
     const int8_t kind = d.kind[P];
     T fn[9];
     if (kind == HLBM_NODE_OUTER) {
-        const int o = d.outer_of[P];
-        const int64_t no = d.n_outer;
-        const T th = T(m + 1) / T(d.n_sub);
-        T st[12];
-#pragma unroll
-        for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * d.snap[j * no + o] + th * d.snap[(12 + j) * no + o];
-        f_from_state(d, st, fn);
+        fv_outer(d, P, m, fn);
         store_rec(out + (int64_t)kRec * P, fn, d.rho0);
         return;
     }
-    T Gx[9], Gy[9], Cf[9], Z[3], fP[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Gx[i] = Gy[i] = Cf[i] = fP[i] = T(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Z[j] = T(0);
+    FvAcc<T> acc;
+    fv_acc_init(acc);
     const int r0 = d.row_ptr[P], r1 = d.row_ptr[P + 1];
-    for (int e = r0; e < r1; ++e) {
+    for (int e = r0 + 1; e < r1; ++e) {
         const Coef<T> c = d.coef[e];
+        T f[9], z[3];
         const T* rec = in + (int64_t)kRec * c.col;
-        T f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = rec[i];
-        if (e == r0) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) fP[i] = f[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if (cx_of(i) != 0) Gx[i] += c.gx * f[i];
-            if (cy_of(i) != 0) Gy[i] += c.gy * f[i];
-            Cf[i] += c.c * f[i];
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Z[j] += c.c * rec[9 + j];
+        for (int j = 0; j < 3; ++j) z[j] = rec[9 + j];
+        fv_acc_entry(acc, c.gx, c.gy, c.c, f, z);
     }
-    T ceq[9];
-    ceq_of(Cf, Z, ceq);
+    T fP[9], zP[3];
+    const T* own = in + (int64_t)kRec * P;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        T s = -(Cf[i] - ceq[i]) * d.inv_tau_u;
-        if (cx_of(i) != 0) s += T(cx_of(i)) * Gx[i];
-        if (cy_of(i) != 0) s += T(cy_of(i)) * Gy[i];
-        fn[i] = fP[i] + d.dt_u * s;
-    }
-    if (kind == HLBM_NODE_WALL) {
-        T dr, r, ux, uy;
-        moments_dev(fn, d.rho0, dr, r, ux, uy);
+    for (int i = 0; i < 9; ++i) fP[i] = own[i];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, dr, r, U, V) - feq_dev<T>(i, dr, r, ux, uy);
-    }
+    for (int j = 0; j < 3; ++j) zP[j] = own[9 + j];
+    fv_acc_finish(d, acc, d.coef[r0].c, fP, zP, fn);
+    if (kind == HLBM_NODE_WALL) fv_wall(d, U, V, fn);
     store_rec(out + (int64_t)kRec * P, fn, d.rho0);
 }
 
@@ -344,6 +394,21 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
 constexpr int kFvThreads = 256;
 constexpr long kMaxSpins = 1L << 23;  // with 128 ns sleeps: about a second
 
+// Lamina velocity at the end of sub-step m, t + (m+1)/n (the wall nodes'
+// Dirichlet value, eq. 182).
+template <typename T>
+__device__ __forceinline__ void wall_velocity(const Dev<T>& d, const StepArgs& a, int m, T& U, T& V) {
+    const double time = double(a.t) + double(m + 1) / double(d.n_sub);
+    U = T(0);
+    V = T(0);
+    if (d.motion == HLBM_MOTION_HARMONIC) {
+        V = T(d.A * d.omega * cos(d.omega * time));
+    } else if (d.motion == HLBM_MOTION_UNIFORM) {
+        U = T(d.vx);
+        V = T(d.vy);
+    }
+}
+
 // All n sub-steps of one lattice step in one cooperative launch.  Block b
 // owns the node tile [tile_start[b], tile_start[b+1]) (nodes are numbered
 // along a Morton curve, so tiles are compact).  Before sub-step m a block
@@ -355,22 +420,9 @@ constexpr long kMaxSpins = 1L << 23;  // with 128 ns sleeps: about a second
 // flag, and every block returns.
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv_steps(Dev<T> d, StepArgs a, const T* buf0, T* buf1) {
-    __shared__ T Us[kMaxSub], Vs[kMaxSub];
     __shared__ int abort_sh;
     const int tile = blockIdx.x;
     const int p0 = d.tile_start[tile], p1 = d.tile_start[tile + 1];
-    for (int m = threadIdx.x; m < d.n_sub; m += blockDim.x) {
-        double time = double(a.t) + double(m + 1) / double(d.n_sub);
-        T U = T(0), V = T(0);
-        if (d.motion == HLBM_MOTION_HARMONIC) {
-            V = T(d.A * d.omega * cos(d.omega * time));
-        } else if (d.motion == HLBM_MOTION_UNIFORM) {
-            U = T(d.vx);
-            V = T(d.vy);
-        }
-        Us[m] = U;
-        Vs[m] = V;
-    }
     if (threadIdx.x == 0) abort_sh = 0;
     const unsigned long long base = (unsigned long long)a.t * (unsigned long long)d.n_sub;
     const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
@@ -403,7 +455,9 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_steps(Dev<T> d, StepArgs a, c
         if (abort_sh) return;
         const T* in = (m & 1) ? (const T*)buf1 : buf0;
         T* out = (m & 1) ? (T*)buf0 : buf1;
-        for (int P = p0 + threadIdx.x; P < p1; P += blockDim.x) fv_node(d, in, out, P, m, Us[m], Vs[m]);
+        T U, V;
+        wall_velocity(d, a, m, U, V);
+        for (int P = p0 + threadIdx.x; P < p1; P += blockDim.x) fv_node(d, in, out, P, m, U, V);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -423,7 +477,6 @@ int fv_tile_capacity() {
 
 template <typename T>
 cudaError_t launch_fv_persistent(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
-    if (d.n_sub > kMaxSub) return cudaErrorInvalidValue;
     Dev<T> dd = d;
     StepArgs aa = a;
     const T* b0 = d.fu_in;
@@ -542,49 +595,18 @@ __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned cha
     const T* halo = reinterpret_cast<const T*>(sm + L.halo) - (size_t)kSR * cap;
     const T* ec = reinterpret_cast<const T*>(sm + L.ecoef);
     const uint16_t* ecol = reinterpret_cast<const uint16_t*>(sm + L.ecol);
-    T Gx[9], Gy[9], Cf[9], Z[3];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Gx[i] = Gy[i] = Cf[i] = T(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Z[j] = T(0);
-    T gpx = T(0), gpy = T(0);
+    FvAcc<T> acc;
+    fv_acc_init(acc);
     for (int j = 0; j < roff; ++j) {
         const int e = j * cap + r;
         const int col = ecol[e];
-        const T gx = ec[e], gy = ec[(roff + j) * cap + r], c = ec[(2 * roff + j) * cap + r];
-        gpx -= gx;
-        gpy -= gy;
         T f[9], z[3];
         read_rec12((col < cap ? own : halo) + (size_t)kSR * col, f, z);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if (cx_of(i) != 0) Gx[i] += gx * f[i];
-            if (cy_of(i) != 0) Gy[i] += gy * f[i];
-            Cf[i] += c * f[i];
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Z[k] += c * z[k];
+        fv_acc_entry(acc, ec[e], ec[(roff + j) * cap + r], ec[(2 * roff + j) * cap + r], f, z);
     }
     T fP[9], zP[3];
     read_rec12(own + (size_t)kSR * r, fP, zP);
-    const T cP = reinterpret_cast<const T*>(sm + L.cpp)[r];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if (cx_of(i) != 0) Gx[i] += gpx * fP[i];
-        if (cy_of(i) != 0) Gy[i] += gpy * fP[i];
-        Cf[i] += cP * fP[i];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Z[k] += cP * zP[k];
-    T ceq[9];
-    ceq_of(Cf, Z, ceq);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        T s = -(Cf[i] - ceq[i]) * d.inv_tau_u;
-        if (cx_of(i) != 0) s += T(cx_of(i)) * Gx[i];
-        if (cy_of(i) != 0) s += T(cy_of(i)) * Gy[i];
-        fn[i] = fP[i] + d.dt_u * s;
-    }
+    fv_acc_finish(d, acc, reinterpret_cast<const T*>(sm + L.cpp)[r], fP, zP, fn);
 }
 
 template <typename T>
@@ -592,23 +614,13 @@ __device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned c
                                                int p0, int m, T (&fn)[9]) {
     const int8_t kind = reinterpret_cast<const int8_t*>(sm + L.kind)[r];
     if (kind == HLBM_NODE_OUTER) {
-        const int o = d.outer_of[p0 + r];
-        const int64_t no = d.n_outer;
-        const T th = T(m + 1) / T(d.n_sub);
-        T st[12];
-#pragma unroll
-        for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * d.snap[j * no + o] + th * d.snap[(12 + j) * no + o];
-        f_from_state(d, st, fn);
+        fv_outer(d, p0 + r, m, fn);
         return;
     }
     fv_node_tile(d, sm, L, r, fn);
     if (kind == HLBM_NODE_WALL) {
         const T* uv = reinterpret_cast<const T*>(sm + L.uv);
-        T dr, rr, ux, uy;
-        moments_dev(fn, d.rho0, dr, rr, ux, uy);
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-            fn[i] += feq_dev<T>(i, dr, rr, uv[m], uv[d.n_sub + m]) - feq_dev<T>(i, dr, rr, ux, uy);
+        fv_wall(d, uv[m], uv[d.n_sub + m], fn);
     }
 }
 
@@ -635,18 +647,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
     const int n_int = min(d.tile_interior[tile], (rounds - 1) * nt);
     // ---- tile set-up: wall velocity per sub-step, own records (buffer 0),
     // matrices, kinds, send flags, node order, halo ids
-    for (int m = tid; m < d.n_sub; m += nt) {
-        double time = double(a.t) + double(m + 1) / double(d.n_sub);
-        T U = T(0), V = T(0);
-        if (d.motion == HLBM_MOTION_HARMONIC) {
-            V = T(d.A * d.omega * cos(d.omega * time));
-        } else if (d.motion == HLBM_MOTION_UNIFORM) {
-            U = T(d.vx);
-            V = T(d.vy);
-        }
-        uv[m] = U;
-        uv[d.n_sub + m] = V;
-    }
+    for (int m = tid; m < d.n_sub; m += nt) wall_velocity(d, a, m, uv[m], uv[d.n_sub + m]);
     for (int x = tid; x < 3 * tile_n; x += nt) {
         const int r = x / 3, c = x - 3 * r;
         const Vec4<T> v = ld4(g0 + (int64_t)kRec * (p0 + r) + 4 * c);
@@ -795,16 +796,26 @@ int fv_smem_tile_capacity(size_t smem) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem > (size_t)maxsm) return 0;
-    if (cudaFuncSetAttribute(k_fv_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    // the opt-in maximum less the kernel's static shared memory, so that
+    // solvers with different tile sizes can all launch; residency follows
+    // from the bytes each launch asks for
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_fv_tiles<T>) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
+    const int limit = maxsm - (int)fa.sharedSizeBytes;
+    if (smem > (size_t)limit) return 0;
+    if (cudaFuncSetAttribute(k_fv_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tiles<T>, kSmemThreads, smem);
     return sms * per;
 }
 
 template <typename T>
 cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
-    if (d.n_sub > kMaxSub) return cudaErrorInvalidValue;
     Dev<T> dd = d;
     StepArgs aa = a;
     T* b0 = (T*)d.fu_in;

@@ -7,6 +7,7 @@ step of the solver runs in the CUDA library.  PyTorch supplies device memory
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -183,6 +184,14 @@ def hlbm_destroy(h):
         N.load().hlbm_destroy(h)
 
 
+def hlbm_save(h, path: str):
+    _check(N.load().hlbm_save(h, os.fsencode(path)), h)
+
+
+def hlbm_load(h, path: str):
+    _check(N.load().hlbm_load(h, os.fsencode(path)), h)
+
+
 class Solver:
     """Convenience owner of one hlbm handle built from a workload description
     (an object with the attributes of ``inputs.Workload``)."""
@@ -220,6 +229,12 @@ class Solver:
 
     def step(self, nsteps: int = 1):
         hlbm_step(self.h, nsteps)
+
+    def save(self, path: str):
+        hlbm_save(self.h, path)
+
+    def load(self, path: str):
+        hlbm_load(self.h, path)
 
     def info(self):
         return hlbm_info(self.h)
@@ -265,3 +280,48 @@ class Solver:
 
     def profile_read(self):
         return hlbm_profile_read(self.h)
+
+
+class Sweep:
+    """Independent solvers stepped together (hlbm_sweep_*): each instance's
+    lattice part on its own stream, the FV sub-steps one instance after
+    another on a shared stream.  The solvers stay owned by the caller."""
+
+    def __init__(self, solvers, stream: int | None = None):
+        import torch
+
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        arr = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        self.h = C.c_void_p()
+        rc = N.load().hlbm_sweep_create(len(self.solvers), arr, C.c_void_p(self.stream or None), C.byref(self.h))
+        if rc != N.HLBM_OK:
+            raise HLBMError(rc, "hlbm_sweep_create failed")
+
+    def _check(self, rc):
+        if rc != N.HLBM_OK:
+            raise HLBMError(rc, N.load().hlbm_sweep_last_error(self.h).decode())
+
+    def step(self, nsteps: int = 1):
+        self._check(N.load().hlbm_sweep_step(self.h, int(nsteps)))
+
+    def tune(self, trial_steps: int = 2):
+        out = (C.c_int32 * len(self.solvers))()
+        self._check(N.load().hlbm_sweep_tune(self.h, int(trial_steps), out))
+        return list(out)
+
+    def fv_time(self, nsteps: int = 1):
+        out = np.zeros(len(self.solvers))
+        self._check(N.load().hlbm_sweep_fv_time(self.h, int(nsteps), _dp(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.load().hlbm_sweep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
