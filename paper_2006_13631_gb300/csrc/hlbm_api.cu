@@ -392,7 +392,18 @@ int build_tiles(hlbm* h, int n_tiles_req) {
     };
     int n_tiles = n_tiles_req > 0 ? std::min(n_tiles_req, n) : std::max(1, std::min(sms, (n + 63) / 64));
     make_tiles(n_tiles);
-    size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0), h->patch.n_sub);
+    // outer nodes per tile (their feed is staged in shared memory)
+    auto outer_cap = [&]() {
+        int cap = 0;
+        for (size_t k = 0; k + 1 < tile_start.size(); ++k) {
+            int c = 0;
+            for (int q = tile_start[k]; q < tile_start[k + 1]; ++q) c += h->kind[q] == HLBM_NODE_OUTER;
+            cap = std::max(cap, c);
+        }
+        return cap;
+    };
+    size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0), h->patch.n_sub,
+                                   outer_cap());
     h->use_smem = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536 &&
                   fv_smem_tile_capacity<T>(smem) >= n_tiles;
     if (!h->use_smem) {
@@ -422,36 +433,11 @@ int build_tiles(hlbm* h, int n_tiles_req) {
     d.progress = (unsigned long long*)track(upload(h, progress0.data(), progress0.size(), &rc));
     d.halo_ptr = (int32_t*)track(upload(h, halo_ptr.data(), halo_ptr.size(), &rc));
     d.halo_ids = (int32_t*)track(upload(h, halo_ids.data(), halo_ids.size(), &rc));
-    // ELL layout (tile-local columns) and the nodes other tiles read
-    const int ell_w = max_row;
-    d.ell_width = ell_w;
-    std::vector<int32_t> ell_src((size_t)ell_w * n, -1), ell_col((size_t)ell_w * n, 0);
-    std::vector<int8_t> send(n, 0);
-    for (int32_t x : halo_ids) send[x] = 1;
-    for (int k = 0; k < n_tiles; ++k) {
-        const int p0 = tile_start[k], tn = tile_start[k + 1] - p0;
-        const int32_t* hb = halo_ids.data() + halo_ptr[k];
-        const int hn = halo_ptr[k + 1] - halo_ptr[k];
-        for (int r = 0; r < tn; ++r) {
-            const int q = p0 + r;
-            for (int j = 0; j < ell_w; ++j) {
-                size_t idx = (size_t)ell_w * p0 + (size_t)j * tn + r;
-                int e = h->row_ptr[q] + j;
-                if (e < h->row_ptr[q + 1]) {
-                    int c = h->col[e];
-                    ell_src[idx] = e;
-                    if (c >= p0 && c < p0 + tn)
-                        ell_col[idx] = c - p0;
-                    else
-                        ell_col[idx] = d.tile_cap + (int)(std::lower_bound(hb, hb + hn, c) - hb);
-                } else {
-                    ell_col[idx] = r;
-                }
-            }
-        }
-    }
-    // per tile: nodes whose rows read only the tile first (tile-local index)
-    std::vector<uint16_t> tile_order(std::max(n, 1), 0);
+    // per tile: the processing order of its nodes, those whose rows read only
+    // the tile first.  The shared-memory kernel keeps a tile's nodes in this
+    // order ("slots"), so the threads of a warp read consecutive slots.
+    std::vector<uint16_t> tile_order(std::max(n, 1), 0);  // slot -> tile-local index
+    std::vector<int32_t> slot_of(std::max(n, 1), 0);      // node -> slot in its tile
     std::vector<int32_t> tile_interior(n_tiles, 0);
     for (int k = 0; k < n_tiles; ++k) {
         const int p0 = tile_start[k], p1 = tile_start[k + 1];
@@ -465,7 +451,52 @@ int build_tiles(hlbm* h, int n_tiles_req) {
         tile_interior[k] = (int32_t)in.size();
         std::copy(in.begin(), in.end(), tile_order.begin() + p0);
         std::copy(bd.begin(), bd.end(), tile_order.begin() + p0 + in.size());
+        for (int sl = 0; sl < p1 - p0; ++sl) slot_of[p0 + tile_order[p0 + sl]] = sl;
     }
+    // ELL layout by slot (columns: slots of the tile, then halo entries) and
+    // the nodes other tiles read
+    const int ell_w = max_row;
+    d.ell_width = ell_w;
+    std::vector<int32_t> ell_src((size_t)ell_w * n, -1), ell_col((size_t)ell_w * n, 0);
+    std::vector<int8_t> send(n, 0);
+    for (int32_t x : halo_ids) send[x] = 1;
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k], tn = tile_start[k + 1] - p0;
+        const int32_t* hb = halo_ids.data() + halo_ptr[k];
+        const int hn = halo_ptr[k + 1] - halo_ptr[k];
+        for (int sl = 0; sl < tn; ++sl) {
+            const int q = p0 + tile_order[p0 + sl];
+            for (int j = 0; j < ell_w; ++j) {
+                size_t idx = (size_t)ell_w * p0 + (size_t)j * tn + sl;
+                int e = h->row_ptr[q] + j;
+                if (e < h->row_ptr[q + 1]) {
+                    int c = h->col[e];
+                    ell_src[idx] = e;
+                    if (c >= p0 && c < p0 + tn)
+                        ell_col[idx] = slot_of[c];
+                    else
+                        ell_col[idx] = d.tile_cap + (int)(std::lower_bound(hb, hb + hn, c) - hb);
+                } else {
+                    ell_col[idx] = sl;
+                }
+            }
+        }
+    }
+    // per tile: the slots of its outer nodes
+    std::vector<int32_t> tile_outer_ptr(n_tiles + 1, 0);
+    std::vector<uint16_t> tile_outer_r;
+    int ocap = 0;
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k];
+        for (int sl = 0; sl < tile_start[k + 1] - p0; ++sl)
+            if (h->kind[p0 + tile_order[p0 + sl]] == HLBM_NODE_OUTER) tile_outer_r.push_back((uint16_t)sl);
+        tile_outer_ptr[k + 1] = (int32_t)tile_outer_r.size();
+        ocap = std::max(ocap, tile_outer_ptr[k + 1] - tile_outer_ptr[k]);
+    }
+    if (tile_outer_r.empty()) tile_outer_r.push_back(0);
+    d.tile_ocap = ocap;
+    d.tile_outer_ptr = (int32_t*)track(upload(h, tile_outer_ptr.data(), tile_outer_ptr.size(), &rc));
+    d.tile_outer_r = (uint16_t*)track(upload(h, tile_outer_r.data(), tile_outer_r.size(), &rc));
     d.tile_order = (uint16_t*)track(upload(h, tile_order.data(), tile_order.size(), &rc));
     d.tile_interior = (int32_t*)track(upload(h, tile_interior.data(), tile_interior.size(), &rc));
     d.send = (int8_t*)track(upload(h, send.data(), send.size(), &rc));
@@ -582,6 +613,24 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
             }
         std::sort(nb.begin(), nb.end());
         nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        // neighbours counter-clockwise from the +x direction: nodes that are
+        // consecutive in the Morton order then read their j-th neighbours in
+        // about the same direction, i.e. at nearby, mostly distinct
+        // shared-memory banks (exact comparisons, no libm)
+        const double px = h->xy[2 * P], py = h->xy[2 * P + 1];
+        auto half = [&](int v) {
+            const double vx = h->xy[2 * v] - px, vy = h->xy[2 * v + 1] - py;
+            return (vy < 0.0 || (vy == 0.0 && vx < 0.0)) ? 1 : 0;
+        };
+        std::sort(nb.begin(), nb.end(), [&](int a, int b) {
+            const int ha = half(a), hb = half(b);
+            if (ha != hb) return ha < hb;
+            const double ax = h->xy[2 * a] - px, ay = h->xy[2 * a + 1] - py;
+            const double bx = h->xy[2 * b] - px, by = h->xy[2 * b + 1] - py;
+            const double cr = ax * by - ay * bx;
+            if (cr != 0.0) return cr > 0.0;
+            return a < b;
+        });
         h->col.push_back(P);
         h->col.insert(h->col.end(), nb.begin(), nb.end());
         h->row_ptr[P + 1] = (int32_t)h->col.size();

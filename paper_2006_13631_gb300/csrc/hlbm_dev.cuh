@@ -138,6 +138,9 @@ struct Dev {
     const int8_t* send;       // [n] 1 if some other tile reads the node
     const uint16_t* tile_order; // per tile: local node order, nodes reading no halo first
     const int32_t* tile_interior; // per tile: number of nodes reading no halo
+    const int32_t* tile_outer_ptr; // per tile: its outer nodes (CSR over tiles)
+    const uint16_t* tile_outer_r;  // tile-local index of each
+    int tile_ocap;                 // most outer nodes in one tile
     const int32_t* outer;  // outer node ids [n_outer]
     const int32_t* outer_of; // node -> outer index, -1 elsewhere
     const int32_t* seg_a;  // wall segments
@@ -270,7 +273,7 @@ template <typename T> void launch_refill(const Dev<T>& d, const StepArgs& a, cud
 template <typename T> void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> int fv_tile_capacity();
 template <typename T> cudaError_t launch_fv_persistent(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
-template <typename T> size_t fv_smem_bytes(int tile_cap, int halo_cap, int roff, int n_sub);
+template <typename T> size_t fv_smem_bytes(int tile_cap, int halo_cap, int roff, int n_sub, int ocap);
 template <typename T> int fv_tile_max();  // nodes per tile of the shared-memory FV kernel
 template <typename T> void launch_build_ell(const Coef<T>* coef, const int32_t* src, const int32_t* col, Coef<T>* ell,
                                             int64_t count, cudaStream_t s);

@@ -335,16 +335,21 @@ __device__ __forceinline__ void fv_wall(const Dev<T>& d, T U, T V, T (&fn)[9]) {
     for (int i = 0; i < 9; ++i) fn[i] += feq_dev<T>(i, dr, rr, U, V) - feq_dev<T>(i, dr, rr, ux, uy);
 }
 
-// outer nodes: the lattice state interpolated linearly in time (eq. 182, Dirichlet reading)
+// outer nodes: the lattice state interpolated linearly in time (eq. 182,
+// Dirichlet reading); sn[j * stride], j < 12, is the state at t and
+// sn[(12 + j) * stride] the one at t + 1
 template <typename T>
-__device__ __forceinline__ void fv_outer(const Dev<T>& d, int P, int m, T (&fn)[9]) {
-    const int o = d.outer_of[P];
-    const int64_t no = d.n_outer;
+__device__ __forceinline__ void fv_outer_from(const Dev<T>& d, const T* sn, int64_t stride, int m, T (&fn)[9]) {
     const T th = T(m + 1) / T(d.n_sub);
     T st[12];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * d.snap[j * no + o] + th * d.snap[(12 + j) * no + o];
+    for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * sn[j * stride] + th * sn[(12 + j) * stride];
     f_from_state(d, st, fn);
+}
+
+template <typename T>
+__device__ __forceinline__ void fv_outer(const Dev<T>& d, int P, int m, T (&fn)[9]) {
+    fv_outer_from(d, d.snap + d.outer_of[P], (int64_t)d.n_outer, m, fn);
 }
 
 template <typename T>
@@ -502,23 +507,26 @@ cudaError_t launch_fv_persistent(const Dev<T>& d, const StepArgs& a, cudaStream_
 // overlaps the first part.  Only nodes read by other tiles are written to
 // global memory each sub-step, into record buffer (m+1)%2; the final state
 // of every node goes to buffer n%2.
-constexpr int kSmemThreads = 512;
-constexpr int kSR = 12;  // values per record in shared memory
-// own nodes per thread: tile_n <= kSlots<T> * kSmemThreads
+// threads per block and own nodes per thread (tile_n <= kSlots * threads):
+// FP32 1024 x 2 fits 64 registers per thread; FP64 512 x 1
 template <typename T>
-constexpr int kSlots = sizeof(T) == 4 ? 3 : 1;
+constexpr int kSmemThreads = sizeof(T) == 4 ? 1024 : 512;
+template <typename T>
+constexpr int kSlots = sizeof(T) == 4 ? 2 : 1;
+constexpr int kSR = 12;  // values per record in shared memory
+constexpr int kSnap = 24;  // outer-node feed values (12 at t, 12 at t + 1)
 
 template <typename T>
 int fv_tile_max() {
-    return kSlots<T> * kSmemThreads;
+    return kSlots<T> * kSmemThreads<T>;
 }
 
 struct TileSmem {
-    size_t own, halo, ecol, ecoef, cpp, order, kind, send, hid, uv, total;
+    size_t own, halo, ecol, ecoef, cpp, order, kind, send, hid, uv, omap, osnap, total;
 };
 
 template <typename T>
-__host__ __device__ inline TileSmem tile_smem_layout(int cap, int hcap, int roff, int n_sub) {
+__host__ __device__ inline TileSmem tile_smem_layout(int cap, int hcap, int roff, int n_sub, int ocap) {
     auto up = [](size_t x) { return (x + 15) / 16 * 16; };
     TileSmem L;
     size_t o = 0;
@@ -532,6 +540,8 @@ __host__ __device__ inline TileSmem tile_smem_layout(int cap, int hcap, int roff
     o = up(o + sizeof(T) * (size_t)cap);
     L.uv = o;
     o = up(o + sizeof(T) * 2 * (size_t)n_sub);
+    L.osnap = o;
+    o = up(o + sizeof(T) * kSnap * (size_t)ocap);
     L.hid = o;
     o = up(o + sizeof(int32_t) * (size_t)hcap);
     L.ecol = o;
@@ -542,13 +552,15 @@ __host__ __device__ inline TileSmem tile_smem_layout(int cap, int hcap, int roff
     o = up(o + (size_t)cap);
     L.send = o;
     o = up(o + (size_t)cap);
+    L.omap = o;
+    o = up(o + sizeof(int16_t) * (size_t)cap);
     L.total = o;
     return L;
 }
 
 template <typename T>
-size_t fv_smem_bytes(int tile_cap, int halo_cap, int roff, int n_sub) {
-    return tile_smem_layout<T>(tile_cap, halo_cap, roff, n_sub).total;
+size_t fv_smem_bytes(int tile_cap, int halo_cap, int roff, int n_sub, int ocap) {
+    return tile_smem_layout<T>(tile_cap, halo_cap, roff, n_sub, ocap).total;
 }
 
 // 16-byte (float) or 2 x 16-byte (double) vector load and store
@@ -610,11 +622,12 @@ __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned cha
 }
 
 template <typename T>
-__device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r,
-                                               int p0, int m, T (&fn)[9]) {
+__device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r, int m,
+                                               T (&fn)[9]) {
     const int8_t kind = reinterpret_cast<const int8_t*>(sm + L.kind)[r];
     if (kind == HLBM_NODE_OUTER) {
-        fv_outer(d, p0 + r, m, fn);
+        const int q = reinterpret_cast<const int16_t*>(sm + L.omap)[r];
+        fv_outer_from(d, reinterpret_cast<const T*>(sm + L.osnap) + kSnap * q, 1, m, fn);
         return;
     }
     fv_node_tile(d, sm, L, r, fn);
@@ -625,11 +638,11 @@ __device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs a, T* g0, T* g1) {
+__global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepArgs a, T* g0, T* g1) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int abort_sh;
     const int cap = d.tile_cap, hcap = d.halo_cap, roff = d.ell_width - 1;
-    const TileSmem L = tile_smem_layout<T>(cap, hcap, roff, d.n_sub);
+    const TileSmem L = tile_smem_layout<T>(cap, hcap, roff, d.n_sub, d.tile_ocap);
     T* own = reinterpret_cast<T*>(sm + L.own);
     T* halo = reinterpret_cast<T*>(sm + L.halo);
     T* uv = reinterpret_cast<T*>(sm + L.uv);
@@ -649,9 +662,9 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
     // matrices, kinds, send flags, node order, halo ids
     for (int m = tid; m < d.n_sub; m += nt) wall_velocity(d, a, m, uv[m], uv[d.n_sub + m]);
     for (int x = tid; x < 3 * tile_n; x += nt) {
-        const int r = x / 3, c = x - 3 * r;
-        const Vec4<T> v = ld4(g0 + (int64_t)kRec * (p0 + r) + 4 * c);
-        st4(own + (size_t)kSR * r + 4 * c, v.x, v.y, v.z, v.w);
+        const int sl = x / 3, c = x - 3 * sl;
+        const Vec4<T> v = ld4(g0 + (int64_t)kRec * (p0 + d.tile_order[p0 + sl]) + 4 * c);
+        st4(own + (size_t)kSR * sl + 4 * c, v.x, v.y, v.z, v.w);
     }
     {
         const Coef<T>* ell = d.ell + (int64_t)d.ell_width * p0;
@@ -674,12 +687,23 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
         int8_t* kd = reinterpret_cast<int8_t*>(sm + L.kind);
         int8_t* sd = reinterpret_cast<int8_t*>(sm + L.send);
         uint16_t* od = reinterpret_cast<uint16_t*>(sm + L.order);
-        for (int r = tid; r < tile_n; r += nt) {
-            kd[r] = d.kind[p0 + r];
-            sd[r] = d.send[p0 + r];
-            od[r] = d.tile_order[p0 + r];
+        for (int sl = tid; sl < tile_n; sl += nt) {
+            const int r = d.tile_order[p0 + sl];
+            kd[sl] = d.kind[p0 + r];
+            sd[sl] = d.send[p0 + r];
+            od[sl] = (uint16_t)r;
         }
         for (int h = tid; h < halo_n; h += nt) hid[h] = d.halo_ids[h0 + h];
+        // the outer nodes' feed (written by k_feed before this launch)
+        const int o0 = d.tile_outer_ptr[tile], on = d.tile_outer_ptr[tile + 1] - o0;
+        int16_t* om = reinterpret_cast<int16_t*>(sm + L.omap);
+        T* osn = reinterpret_cast<T*>(sm + L.osnap);
+        for (int q = tid; q < on; q += nt) om[d.tile_outer_r[o0 + q]] = (int16_t)q;
+        const int64_t no = d.n_outer;
+        for (int x = tid; x < kSnap * on; x += nt) {
+            const int q = x / kSnap, j = x - kSnap * q;
+            osn[x] = d.snap[j * no + d.outer_of[p0 + d.tile_order[p0 + d.tile_outer_r[o0 + q]]]];
+        }
     }
     if (tid == 0) abort_sh = 0;
     __syncthreads();
@@ -691,7 +715,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
 #pragma unroll
         for (int s = 0; s < kSlots<T>; ++s) {
             const int x = tid + s * nt;
-            if (x < n_int) fv_update_slot(d, sm, L, order[x], p0, m, fn[s]);
+            if (x < n_int) fv_update_slot(d, sm, L, x, m, fn[s]);
         }
         // wait for the neighbour tiles to publish state m, then load the halo
         if (m > 0 && tid < 32) {
@@ -732,7 +756,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
 #pragma unroll
         for (int s = 0; s < kSlots<T>; ++s) {
             const int x = tid + s * nt;
-            if (x >= n_int && x < tile_n) fv_update_slot(d, sm, L, order[x], p0, m, fn[s]);
+            if (x >= n_int && x < tile_n) fv_update_slot(d, sm, L, x, m, fn[s]);
         }
         __syncthreads();
         // publish state m+1
@@ -742,15 +766,14 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_fv_tiles(Dev<T> d, StepArgs
         for (int s = 0; s < kSlots<T>; ++s) {
             const int x = tid + s * nt;
             if (x < tile_n) {
-                const int r = order[x];
                 T z[3];
                 z_of(fn[s], d.rho0, z);
-                T* o = own + (size_t)kSR * r;
+                T* o = own + (size_t)kSR * x;
                 st4(o, fn[s][0], fn[s][1], fn[s][2], fn[s][3]);
                 st4(o + 4, fn[s][4], fn[s][5], fn[s][6], fn[s][7]);
                 st4(o + 8, fn[s][8], z[0], z[1], z[2]);
-                if (last || send[r]) {
-                    T* rec = gout + (int64_t)kRec * (p0 + r);
+                if (last || send[x]) {
+                    T* rec = gout + (int64_t)kRec * (p0 + order[x]);
                     st4(rec, fn[s][0], fn[s][1], fn[s][2], fn[s][3]);
                     st4(rec + 4, fn[s][4], fn[s][5], fn[s][6], fn[s][7]);
                     st4(rec + 8, fn[s][8], z[0], z[1], z[2]);
@@ -810,7 +833,7 @@ int fv_smem_tile_capacity(size_t smem) {
         cudaGetLastError();
         return 0;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tiles<T>, kSmemThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tiles<T>, kSmemThreads<T>, smem);
     return sms * per;
 }
 
@@ -821,8 +844,9 @@ cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
     T* b0 = (T*)d.fu_in;
     T* b1 = d.fu_out;
     void* args[] = {&dd, &aa, &b0, &b1};
-    size_t smem = fv_smem_bytes<T>(d.tile_cap, d.halo_cap, d.ell_width - 1, d.n_sub);
-    return cudaLaunchCooperativeKernel((const void*)k_fv_tiles<T>, dim3(d.n_tiles), dim3(kSmemThreads), args, smem, s);
+    size_t smem = fv_smem_bytes<T>(d.tile_cap, d.halo_cap, d.ell_width - 1, d.n_sub, d.tile_ocap);
+    return cudaLaunchCooperativeKernel((const void*)k_fv_tiles<T>, dim3(d.n_tiles), dim3(kSmemThreads<T>), args, smem,
+                                       s);
 }
 
 // ------------------------------------------------------------- force
@@ -977,7 +1001,7 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
     template void launch_feed<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                               \
     template int fv_tile_capacity<T>();                                                                       \
     template cudaError_t launch_fv_persistent<T>(const Dev<T>&, const StepArgs&, cudaStream_t);               \
-    template size_t fv_smem_bytes<T>(int, int, int, int);                                                     \
+    template size_t fv_smem_bytes<T>(int, int, int, int, int);                                                     \
     template int fv_tile_max<T>();                                                                            \
     template void launch_build_ell<T>(const Coef<T>*, const int32_t*, const int32_t*, Coef<T>*, int64_t,       \
                                       cudaStream_t);                                                          \
