@@ -448,6 +448,13 @@ int build_tiles(hlbm* h, int n_tiles_req) {
                 if (h->col[e] < p0 || h->col[e] >= p1) interior = false;
             (interior ? in : bd).push_back((uint16_t)(q - p0));
         }
+        // within each group, the caller's node order: meshes built layer by
+        // layer (O- and C-grids) then give slots that run along a layer, so
+        // the j-th neighbours of consecutive slots are consecutive as well
+        // and a warp's gathers spread over the shared-memory banks
+        auto by_caller = [&](uint16_t a, uint16_t b) { return h->perm[p0 + a] < h->perm[p0 + b]; };
+        std::sort(in.begin(), in.end(), by_caller);
+        std::sort(bd.begin(), bd.end(), by_caller);
         tile_interior[k] = (int32_t)in.size();
         std::copy(in.begin(), in.end(), tile_order.begin() + p0);
         std::copy(bd.begin(), bd.end(), tile_order.begin() + p0 + in.size());
