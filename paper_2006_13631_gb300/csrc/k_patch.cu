@@ -396,6 +396,16 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// 16-byte global -> shared copy that bypasses L1; completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 constexpr int kFvThreads = 256;
 constexpr long kMaxSpins = 1L << 23;  // with 128 ns sleeps: about a second
 
@@ -522,7 +532,7 @@ int fv_tile_max() {
 }
 
 struct TileSmem {
-    size_t own, halo, ecol, ecoef, cpp, order, kind, send, hid, uv, omap, osnap, total;
+    size_t own, halo, ecol, ecoef, cpp, order, kind, send, hid, uv, omap, osnap, cnt, total;
 };
 
 template <typename T>
@@ -554,6 +564,8 @@ __host__ __device__ inline TileSmem tile_smem_layout(int cap, int hcap, int roff
     o = up(o + (size_t)cap);
     L.omap = o;
     o = up(o + sizeof(int16_t) * (size_t)cap);
+    L.cnt = o;
+    o = up(o + (size_t)cap);
     L.total = o;
     return L;
 }
@@ -609,7 +621,8 @@ __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned cha
     const uint16_t* ecol = reinterpret_cast<const uint16_t*>(sm + L.ecol);
     FvAcc<T> acc;
     fv_acc_init(acc);
-    for (int j = 0; j < roff; ++j) {
+    const int ne = reinterpret_cast<const uint8_t*>(sm + L.cnt)[r];  // off-diagonal entries of the row
+    for (int j = 0; j < ne; ++j) {
         const int e = j * cap + r;
         const int col = ecol[e];
         T f[9], z[3];
@@ -687,11 +700,13 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
         int8_t* kd = reinterpret_cast<int8_t*>(sm + L.kind);
         int8_t* sd = reinterpret_cast<int8_t*>(sm + L.send);
         uint16_t* od = reinterpret_cast<uint16_t*>(sm + L.order);
+        uint8_t* cn = reinterpret_cast<uint8_t*>(sm + L.cnt);
         for (int sl = tid; sl < tile_n; sl += nt) {
             const int r = d.tile_order[p0 + sl];
             kd[sl] = d.kind[p0 + r];
             sd[sl] = d.send[p0 + r];
             od[sl] = (uint16_t)r;
+            cn[sl] = (uint8_t)(d.row_ptr[p0 + r + 1] - d.row_ptr[p0 + r] - 1);
         }
         for (int h = tid; h < halo_n; h += nt) hid[h] = d.halo_ids[h0 + h];
         // the outer nodes' feed (written by k_feed before this launch)
@@ -717,41 +732,48 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
             const int x = tid + s * nt;
             if (x < n_int) fv_update_slot(d, sm, L, x, m, fn[s]);
         }
-        // wait for the neighbour tiles to publish state m, then load the halo
-        if (m > 0 && tid < 32) {
+        // warp 0: wait for the neighbour tiles to publish state m (lane l
+        // acquires the counters l, l + 32, ...; the warp barrier then orders
+        // every lane's later reads after all of them), then copy the halo
+        // records into shared memory asynchronously while the other warps
+        // still update their nodes
+        if (tid < 32) {
             bool ok = true;
-            for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
-                const unsigned long long* pc = d.progress + d.tile_nb[e];
-                long spins = 0;
-                while (ld_acquire(pc) < base + m) {
-                    if (*(volatile unsigned*)d.abort_flag) {
-                        ok = false;
-                        break;
+            if (m > 0) {
+                for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
+                    const unsigned long long* pc = d.progress + d.tile_nb[e];
+                    long spins = 0;
+                    while (ld_acquire(pc) < base + m) {
+                        if (*(volatile unsigned*)d.abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        if (++spins > kMaxSpins) {
+                            atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
+                            atomicExch(d.abort_flag, 1u);
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(32);
                     }
-                    if (++spins > kMaxSpins) {
-                        atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
-                        atomicExch(d.abort_flag, 1u);
-                        ok = false;
-                        break;
-                    }
-                    __nanosleep(32);
                 }
             }
-            __threadfence();
+            __syncwarp();
             ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                const T* gin = (m & 1) ? g1 : g0;
+                constexpr int kChunks = kSR * (int)sizeof(T) / 16;  // 16-byte pieces of a record
+                for (int x = tid; x < kChunks * halo_n; x += 32) {
+                    const int h = x / kChunks, c = x - kChunks * h;
+                    cp_async16(reinterpret_cast<unsigned char*>(halo) + (size_t)h * kSR * sizeof(T) + 16 * c,
+                               reinterpret_cast<const unsigned char*>(gin + (int64_t)kRec * hid[h]) + 16 * c);
+                }
+            }
+            cp_async_wait_all();
             if (tid == 0 && !ok) abort_sh = 1;
         }
         __syncthreads();
         if (abort_sh) return;
-        {
-            const T* gin = (m & 1) ? g1 : g0;
-            for (int x = tid; x < 3 * halo_n; x += nt) {
-                const int h = x / 3, c = x - 3 * h;
-                const Vec4<T> v = ld4(gin + (int64_t)kRec * hid[h] + 4 * c);
-                st4(halo + (size_t)kSR * h + 4 * c, v.x, v.y, v.z, v.w);
-            }
-        }
-        __syncthreads();
         // nodes that read the halo
 #pragma unroll
         for (int s = 0; s < kSlots<T>; ++s) {
