@@ -271,6 +271,7 @@ class Workload:
     u0x: float = 0.0         # initial uniform velocity (tests only; 0 in the paper's setup)
     u0y: float = 0.0
     lumped: int = 0          # 1: lumped collision matrix C = identity
+    outer_fv: int = 0        # 1: outer nodes take eq. 182 with its FV sums
     mesh_args: dict = field(default_factory=dict)
 
     def mesh(self) -> PatchMesh:

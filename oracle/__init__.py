@@ -43,6 +43,7 @@ class _Params(C.Structure):
         ("xy", C.POINTER(C.c_double)), ("tri", C.POINTER(C.c_int32)), ("kind", C.POINTER(C.c_int8)),
         ("n_sub", C.c_int), ("lumped", C.c_int), ("motion", C.c_int),
         ("A", C.c_double), ("omega", C.c_double), ("vx", C.c_double), ("vy", C.c_double),
+        ("outer_fv", C.c_int),
     ]
 
 
@@ -79,6 +80,8 @@ def lib():
         L.orc_fv_nnz.argtypes = [P]
         L.orc_fv_coeffs.argtypes = [P, ip, ip, dp, dp, dp, dp]
         L.orc_n_wall_segments.argtypes = [P]
+        L.orc_outer_fv.argtypes = [C.c_int, dp, C.c_int, ip, C.POINTER(C.c_int8), C.c_double, C.c_double, C.c_int,
+                                   dp, dp, dp]
         L.orc_sine_fit.argtypes = [dp, C.c_int64, C.c_int64, C.c_double, dp, dp, dp]
         L.orc_fv_periodic.argtypes = [C.c_int, dp, C.c_int, ip, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int, C.c_int, dp]
@@ -116,6 +119,20 @@ def fv_periodic(xy, tri, period_x, period_y, tau_u, dt_u, n_iter, f9, lumped=0):
     return f
 
 
+def outer_fv(xy, tri, kind, tau_u, dt_u, fin, dstar, lumped=0):
+    """R10 alone: the full eq. postcollision2_u value of every outer node
+    (other rows of the result are zero)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    kind = np.ascontiguousarray(kind, dtype=np.int8)
+    fin = np.ascontiguousarray(fin, dtype=np.float64)
+    dstar = np.ascontiguousarray(dstar, dtype=np.float64)
+    out = np.zeros_like(fin)
+    lib().orc_outer_fv(xy.shape[0], _dp(xy), tri.shape[0], _ip(tri), kind.ctypes.data_as(C.POINTER(C.c_int8)),
+                       tau_u, dt_u, lumped, _dp(fin), _dp(dstar), _dp(out))
+    return out
+
+
 def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
     f = np.ascontiguousarray(f9, dtype=np.float64).copy()
     _, ny, nx = f.shape
@@ -150,6 +167,7 @@ class Oracle:
         p.tri = _ip(self._keep[2])
         p.kind = self._keep[3].ctypes.data_as(C.POINTER(C.c_int8))
         p.n_sub, p.lumped, p.motion = w.n_sub, w.lumped, w.motion
+        p.outer_fv = int(getattr(w, "outer_fv", 0))
         p.A, p.omega, p.vx, p.vy = w.A, w.omega, w.vx, w.vy
         self._h = lib().orc_create(C.byref(p))
         self.n = self.mesh.n_nodes

@@ -36,6 +36,15 @@
  *  R9  Donor triangle = the candidate with the largest smallest barycentric
  *      coordinate, among those with smallest coordinate >= -1e-12; ties go
  *      to the lowest triangle index.  Donor cell = (floor x, floor y).
+ *  R10 Full eq. postcollision2_u (outer_fv = 1): the outer node's value is
+ *      the R2 value plus dt_u sum_k S_ik f*_k - (dt_u/tau_u) sum_k C_ik
+ *      (f*_k - f^eq(f*_k)) over its truncated control volume, where f*_k
+ *      is the R2 value of node k at theta = (m+1)/n when k is an outer
+ *      (interpolation) node, including k = P, and the patch value at
+ *      sub-step m otherwise.  f^eq(f*) of an R2 value is f^eq,s (f^neq,s
+ *      carries no mass or momentum), so f* - f^eq(f*) is the starred
+ *      non-equilibrium part of the paper.  Regular nodes read an outer
+ *      neighbour's stored value, increment included.
  */
 #include "hlbm_oracle.h"
 
@@ -114,6 +123,7 @@ struct orc {
     int32_t *bstart, *bitems;
     /* outer-node feed: rho, ux, uy, fneq[9] at t and t+1 (R2) */
     double *snap0, *snap1;
+    double* dstar; /* R2 values of the outer nodes at the current sub-step [n][9] */
     int32_t *rtype, *rdonor;
     double *Fx, *Fy;
     int64_t hcap;
@@ -691,6 +701,41 @@ static void feed_snapshots(orc_t* o, double cx, double cy) {
     }
 }
 
+/* R10: eq. postcollision2_u with its FV sums at the outer node P; dstar
+ * holds the R2 values of the outer nodes at the new sub-step, fin the patch
+ * state at sub-step m */
+static void outer_fv_update(int P, const fv_coeffs_t* fc, const int8_t* kind, const double* dstar,
+                            const double* fin, double tau_u, double dt_u, double* fout) {
+    double acc[9] = {0};
+    for (int e = fc->row_ptr[P]; e < fc->row_ptr[P + 1]; ++e) {
+        int k = fc->col[e];
+        const double* fk = kind[k] == ORC_KIND_OUTER ? dstar + 9 * k : fin + 9 * k;
+        double r, ux, uy, feq[9];
+        moments(fk, &r, &ux, &uy);
+        orc_feq(r, ux, uy, feq);
+        for (int i = 0; i < 9; ++i) {
+            double S = CX[i] * fc->gx[e] + CY[i] * fc->gy[e];
+            acc[i] += S * fk[i] - fc->cc[e] / tau_u * (fk[i] - feq[i]);
+        }
+    }
+    for (int i = 0; i < 9; ++i) fout[9 * P + i] = dstar[9 * P + i] + dt_u * acc[i];
+}
+
+int orc_outer_fv(int n_nodes, const double* xy, int n_tris, const int32_t* tri, const int8_t* kind,
+                 double tau_u, double dt_u, int lumped, const double* fin, const double* dstar, double* fout) {
+    fv_coeffs_t fc;
+    build_fv(n_nodes, xy, n_tris, tri, 0.0, 0.0, lumped, &fc);
+    for (int P = 0; P < n_nodes; ++P)
+        if (kind[P] == ORC_KIND_OUTER) outer_fv_update(P, &fc, kind, dstar, fin, tau_u, dt_u, fout);
+    free(fc.row_ptr);
+    free(fc.col);
+    free(fc.gx);
+    free(fc.gy);
+    free(fc.cc);
+    free(fc.vol);
+    return 0;
+}
+
 static void fv_substeps(orc_t* o, int64_t t) {
     int n = o->p.n_sub, nn = o->p.n_nodes;
     double dtu = 1.0 / n, tau_u = o->p.tau_s - 0.5;
@@ -706,13 +751,20 @@ static void fv_substeps(orc_t* o, int64_t t) {
             moments(fin + 9 * P, &r, &ux, &uy);
             orc_feq(r, ux, uy, o->feq_u + 9 * P);
         }
+        /* interpolation (outer) nodes: structured state, linear in time (R2) */
+        for (int P = 0; P < nn; ++P) {
+            if (o->kind[P] != ORC_KIND_OUTER) continue;
+            double st[12];
+            const double *s0 = o->snap0 + 12 * P, *s1 = o->snap1 + 12 * P;
+            for (int j = 0; j < 12; ++j) st[j] = (1.0 - theta) * s0[j] + theta * s1[j];
+            f_from_struct_state(o, st, o->dstar + 9 * P);
+        }
         for (int P = 0; P < nn; ++P) {
             if (o->kind[P] == ORC_KIND_OUTER) {
-                /* interpolation node: structured state, linear in time (R2) */
-                double st[12];
-                const double *s0 = o->snap0 + 12 * P, *s1 = o->snap1 + 12 * P;
-                for (int j = 0; j < 12; ++j) st[j] = (1.0 - theta) * s0[j] + theta * s1[j];
-                f_from_struct_state(o, st, fout + 9 * P);
+                if (o->p.outer_fv)
+                    outer_fv_update(P, &fc, o->kind, o->dstar, fin, tau_u, dtu, fout);
+                else
+                    memcpy(fout + 9 * P, o->dstar + 9 * P, 9 * sizeof(double));
                 continue;
             }
             fv_update_node(P, &fc, fin, o->feq_u, tau_u, dtu, fout);
@@ -903,6 +955,7 @@ orc_t* orc_create(const orc_params_t* p) {
     o->feq_u = malloc((size_t)n * 9 * sizeof(double));
     o->snap0 = calloc((size_t)n * 12, sizeof(double));
     o->snap1 = calloc((size_t)n * 12, sizeof(double));
+    o->dstar = calloc((size_t)n * 9, sizeof(double));
     o->rtype = calloc(n, sizeof(int32_t));
     o->rdonor = malloc(n * sizeof(int32_t));
     for (int i = 0; i < n; ++i) o->rdonor[i] = -1;
@@ -1080,6 +1133,7 @@ void orc_destroy(orc_t* o) {
     free(o->bitems);
     free(o->snap0);
     free(o->snap1);
+    free(o->dstar);
     free(o->rtype);
     free(o->rdonor);
     free(o->Fx);

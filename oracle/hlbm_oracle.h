@@ -49,6 +49,7 @@ typedef struct {
     int lumped;             /* 1: C = identity                                  */
     int motion;
     double A, omega, vx, vy;
+    int outer_fv;           /* 1: outer nodes take eq. 182 with its FV sums (R10) */
 } orc_params_t;
 
 typedef struct orc orc_t;
@@ -95,6 +96,12 @@ void orc_sine_fit(const double* F, int64_t t0, int64_t t1, double omega, double*
 int orc_fv_periodic(int n_nodes, const double* xy, int n_tris, const int32_t* tri,
                     double period_x, double period_y, double tau_u, double dt_u, int lumped,
                     int n_iter, double* f9);
+
+/* R10 alone: the full eq. postcollision2_u update of every outer node of a
+ * mesh (no periodicity) from the patch state fin and the R2 values dstar
+ * (both [n][9]); fout [n][9] receives the outer nodes' new values */
+int orc_outer_fv(int n_nodes, const double* xy, int n_tris, const int32_t* tri, const int8_t* kind,
+                 double tau_u, double dt_u, int lumped, const double* fin, const double* dstar, double* fout);
 
 /* structured LBGK alone (no patch): n_iter steps of eq. LBE on f9 [9][ny][nx] */
 int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int n_iter, double* f9);

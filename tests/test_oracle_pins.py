@@ -376,3 +376,44 @@ def test_hybrid_disk_patch_reproduces_lbgk_shear_wave():
 
     assert np.abs(puy - bil(uyr)).max() < 3e-3 * amp
     assert np.abs(pux - bil(uxr)).max() < 3e-3 * amp
+
+
+@pytest.mark.parametrize("lumped", [0, 1])
+def test_full_outer_node_update_on_linear_field_with_uniform_stress(lumped):
+    """Reading R10 (eq. postcollision2_u with its FV sums) in closed form: with
+    f*_k = w_i rho(x_k) + eps h_i, rho linear and h a pure non-equilibrium
+    mode (no mass, no momentum), the P1-exact mean gradient over the
+    truncated control volume and the unit row sums of C give
+    f_P = f*_P - dt_u c_i . grad(w_i rho) - (dt_u / tau_u) eps h_i.
+    The outer nodes' stored patch values are deliberately wrong: the update
+    must take their starred (interpolated) values instead."""
+    w = inputs.workload("lamina-small-f64")
+    m = w.mesh()
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], float)
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], float)
+    wi = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    h = cx * cx - cy * cy
+    a, b, eps = 2e-3, -1.5e-3, 1e-4
+    rho = 1.0 + a * m.xy[:, 0] + b * m.xy[:, 1]
+    fstar = wi[None, :] * rho[:, None] + eps * h[None, :]
+    outer = m.kind == 1
+    fin = fstar.copy()
+    fin[outer] = 0.5 * wi[None, :]  # not what the outer nodes' update may read
+    tau_u, dt_u = 0.1, 1.0 / 24
+    out = oracle.outer_fv(m.xy, m.tri, m.kind, tau_u, dt_u, fin, fstar, lumped)
+    expect = fstar - dt_u * wi[None, :] * (cx * a + cy * b)[None, :] - dt_u / tau_u * eps * h[None, :]
+    assert outer.sum() > 50
+    assert np.abs(out[outer] - expect[outer]).max() < 1e-14
+
+
+def test_zero_disturbance_with_full_outer_node_update():
+    """The uniform translating stream stays exact under reading R10 too: the
+    FV sums of a constant equilibrium field vanish."""
+    w = _translating_case(0.02, 0.03)
+    w.outer_fv = 1
+    o = oracle.Oracle(w)
+    o.step(60)
+    assert o.status == 0
+    r, ux, uy = o.patch_macro()
+    assert np.abs(ux - 0.02).max() < 1e-12 and np.abs(uy - 0.03).max() < 1e-12
+    assert np.abs(r - 1.0).max() < 1e-12
