@@ -347,6 +347,30 @@ def run_ours(args):
                                "stream_gbs": gbs, "stream_frac": gbs / peak if gbs else None}
                 s3.close()
         w.dtype = "f32"
+    # the outer-node and collision-matrix readings of the method on the same
+    # workload (FP32): eq. postcollision2_u with its FV sums, lumped C
+    variants = {}
+    if not args.no_reduced:
+        k_var = max(10, min(args.steps, 100))
+        for key, attr in (("outer_fv", "outer_fv"), ("lumped", "lumped")):
+            setattr(w, attr, 1)
+            with torch.cuda.stream(stream):
+                s4 = Solver(w, mesh=mesh, rho_init=rho, stream=stream.cuda_stream)
+                s4.step(args.warmup)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s4.profile(True)
+                e0.record(stream)
+                s4.step(k_var)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ph = s4.profile_read()
+                ms4 = e0.elapsed_time(e1)
+                variants[key] = {"value": (n_disc + n_u) * k_var / (ms4 / 1e3) / 1e6, "unit": UNIT, "steps": k_var,
+                                 "ms_per_step": ms4 / k_var, "fv_ms_per_step": ph["fv"][0] / k_var,
+                                 "status": s4.status}
+                s4.close()
+            setattr(w, attr, 0)
     sweep = None if args.no_sweep else run_sweep(stream, args)
     if rank != 0:
         return 0
@@ -358,7 +382,7 @@ def run_ours(args):
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)" % (9 * bytes_per * w.nx * w.ny / 1e6)},
             "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "cpu_baseline": cpu, "e2e": e2e,
-            "reduced_storage": reduced or None, "sweep": sweep,
+            "reduced_storage": reduced or None, "variants": variants or None, "sweep": sweep,
             "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}
     print(json.dumps(line), flush=True)
     if dist:

@@ -99,7 +99,13 @@ typedef struct {
  * centred at (x_c, y_c) at t = 0.  Lattice nodes inside the rounded
  * rectangle at offset delta_f (the fictitious curve) are unused.  n_sub FV
  * sub-steps are taken per lattice step (dt_s = n_sub dt_u).  lumped = 1
- * replaces the consistent collision matrix C_ik by the identity. */
+ * replaces the consistent collision matrix C_ik by the identity.
+ * outer_fv selects the update of the outer (interpolation) patch nodes,
+ * eq. postcollision2_u: 0 takes its interpolated part only,
+ * f = f^eq,s + (1 - dt_s/(2 tau_s)) f^neq,s, bilinear from the lattice and
+ * linear in time over the lattice step; 1 adds its FV sums over the node's
+ * truncated control volume, with the starred values of the paper
+ * (interpolated at interpolation nodes, the patch state elsewhere). */
 typedef struct {
     int32_t n_nodes, n_tris;
     const double* xy;
@@ -110,6 +116,7 @@ typedef struct {
     double delta_f;
     int32_t n_sub;
     int32_t lumped;
+    int32_t outer_fv;
 } hlbm_patch_t;
 
 typedef struct {

@@ -29,7 +29,7 @@ class hlbm_patch_t(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tris", C.c_int32), ("xy", _dp), ("tri", _ip),
                 ("kind", C.POINTER(C.c_int8)), ("lamina_L", C.c_double), ("lamina_T", C.c_double),
                 ("x_c", C.c_double), ("y_c", C.c_double), ("delta_f", C.c_double),
-                ("n_sub", C.c_int32), ("lumped", C.c_int32)]
+                ("n_sub", C.c_int32), ("lumped", C.c_int32), ("outer_fv", C.c_int32)]
 
 
 class hlbm_motion_t(C.Structure):

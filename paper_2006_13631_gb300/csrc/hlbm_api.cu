@@ -542,6 +542,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.tau_u = T(h->tau_s - 0.5);
     d.inv_tau_u = T(1.0 / (h->tau_s - 0.5));
     d.n_sub = p.n_sub;
+    d.outer_fv = p.outer_fv;
     d.dt_u = T(1.0 / p.n_sub);
     d.k178 = T(2.0 * (h->tau_s - 1.0) / (2.0 * h->tau_s - 1.0));
     d.kneq = T(1.0 - 1.0 / (2.0 * h->tau_s));
@@ -879,7 +880,7 @@ namespace {
 struct CkptHeader {
     char magic[8];
     uint32_t version;
-    int32_t dtype, nx, ny, n_nodes, n_tris, n_sub, bw, bh, bc_x, bc_y, motion, lumped;
+    int32_t dtype, nx, ny, n_nodes, n_tris, n_sub, bw, bh, bc_x, bc_y, motion, lumped, outer_fv, pad0;
     double tau_s, rho0, A, omega, vx, vy, lamina_L, lamina_T, x_c, y_c, delta_f;
     uint64_t mesh_hash;
     int64_t t;
@@ -924,6 +925,7 @@ CkptHeader ckpt_header(hlbm* h) {
     c.bc_y = h->grid.bc_y;
     c.motion = h->motion.kind;
     c.lumped = h->patch.lumped;
+    c.outer_fv = h->patch.outer_fv;
     c.tau_s = h->tau_s;
     c.rho0 = h->grid.rho0;
     c.A = h->motion.A;
@@ -1013,6 +1015,7 @@ int load_impl(hlbm* h, const char* path) {
     const bool same = c.dtype == m.dtype && c.nx == m.nx && c.ny == m.ny && c.n_nodes == m.n_nodes &&
                       c.n_tris == m.n_tris && c.n_sub == m.n_sub && c.bw == m.bw && c.bh == m.bh &&
                       c.bc_x == m.bc_x && c.bc_y == m.bc_y && c.motion == m.motion && c.lumped == m.lumped &&
+                      c.outer_fv == m.outer_fv &&
                       c.tau_s == m.tau_s && c.rho0 == m.rho0 && c.A == m.A && c.omega == m.omega &&
                       c.vx == m.vx && c.vy == m.vy && c.lamina_L == m.lamina_L && c.lamina_T == m.lamina_T &&
                       c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash;
@@ -1250,6 +1253,8 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
         rc = fail(h, HLBM_EINVAL, "empty patch mesh");
     else if (motion->kind < 0 || motion->kind > 2)
         rc = fail(h, HLBM_EINVAL, "unknown motion kind %d", motion->kind);
+    else if ((p.lumped != 0 && p.lumped != 1) || (p.outer_fv != 0 && p.outer_fv != 1))
+        rc = fail(h, HLBM_EINVAL, "lumped = %d and outer_fv = %d must be 0 or 1", p.lumped, p.outer_fv);
     else if (!(p.delta_f > 1.5))
         rc = fail(h, HLBM_EINVAL, "delta_f = %g must exceed 1.5 (interpolation nodes outside the body)",
                   p.delta_f);

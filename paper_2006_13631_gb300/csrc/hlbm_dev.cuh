@@ -158,6 +158,7 @@ struct Dev {
     // physics
     T rho0, tau_s, tau_u, inv_tau_u, dt_u, k178, kneq;
     int n_sub;
+    int outer_fv;  // outer nodes: 1 adds the FV sums of eq. postcollision2_u
     int motion;
     double A, omega, vx, vy;
 };

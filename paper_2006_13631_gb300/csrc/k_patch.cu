@@ -5,6 +5,8 @@
 //
 // Patch state: one record of kRec values per node, f'[0..8] (deviation from
 // w_i rho0) followed by the quadratic equilibrium terms z[0..2] (z_of).
+#include <algorithm>
+
 #include "hlbm_dev.cuh"
 
 namespace hk {
@@ -359,6 +361,33 @@ __device__ __forceinline__ void fv_node(const Dev<T>& d, const T* __restrict__ i
     T fn[9];
     if (kind == HLBM_NODE_OUTER) {
         fv_outer(d, P, m, fn);
+        if (d.outer_fv) {
+            // eq. postcollision2_u with its FV sums: interpolated values at
+            // interpolation nodes (this one included), patch values elsewhere
+            FvAcc<T> acc;
+            fv_acc_init(acc);
+            const int r0 = d.row_ptr[P], r1 = d.row_ptr[P + 1];
+            for (int e = r0 + 1; e < r1; ++e) {
+                const Coef<T> c = d.coef[e];
+                T f[9], z[3];
+                if (d.kind[c.col] == HLBM_NODE_OUTER) {
+                    fv_outer(d, c.col, m, f);
+                    z_of(f, d.rho0, z);
+                } else {
+                    const T* rec = in + (int64_t)kRec * c.col;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = rec[i];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) z[j] = rec[9 + j];
+                }
+                fv_acc_entry(acc, c.gx, c.gy, c.c, f, z);
+            }
+            T fP[9], zP[3];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fP[i] = fn[i];
+            z_of(fP, d.rho0, zP);
+            fv_acc_finish(d, acc, d.coef[r0].c, fP, zP, fn);
+        }
         store_rec(out + (int64_t)kRec * P, fn, d.rho0);
         return;
     }
@@ -634,13 +663,62 @@ __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned cha
     fv_acc_finish(d, acc, reinterpret_cast<const T*>(sm + L.cpp)[r], fP, zP, fn);
 }
 
+// eq. postcollision2_u with its FV sums at the outer node in slot r, whose
+// interpolated value fn holds on entry: the starred values are the
+// interpolated ones at interpolation nodes (own ones from the staged feed,
+// halo ones from global memory) and the patch records elsewhere
 template <typename T>
+__device__ __noinline__ void fv_outer_sums_tile(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r,
+                                                int m, T (&fn)[9]) {
+    const int cap = d.tile_cap, roff = d.ell_width - 1;
+    const T* own = reinterpret_cast<const T*>(sm + L.own);
+    const T* halo = reinterpret_cast<const T*>(sm + L.halo);
+    const T* ec = reinterpret_cast<const T*>(sm + L.ecoef);
+    const uint16_t* ecol = reinterpret_cast<const uint16_t*>(sm + L.ecol);
+    const int8_t* kd = reinterpret_cast<const int8_t*>(sm + L.kind);
+    const int16_t* om = reinterpret_cast<const int16_t*>(sm + L.omap);
+    const T* osn = reinterpret_cast<const T*>(sm + L.osnap);
+    const int32_t* hid = reinterpret_cast<const int32_t*>(sm + L.hid);
+    FvAcc<T> acc;
+    fv_acc_init(acc);
+    const int ne = reinterpret_cast<const uint8_t*>(sm + L.cnt)[r];
+    for (int j = 0; j < ne; ++j) {
+        const int e = j * cap + r;
+        const int col = ecol[e];
+        T f[9], z[3];
+        if (col < cap) {
+            if (kd[col] == HLBM_NODE_OUTER) {
+                fv_outer_from(d, osn + kSnap * om[col], 1, m, f);
+                z_of(f, d.rho0, z);
+            } else {
+                read_rec12(own + (size_t)kSR * col, f, z);
+            }
+        } else {
+            const int g = hid[col - cap];
+            if (d.kind[g] == HLBM_NODE_OUTER) {
+                fv_outer(d, g, m, f);
+                z_of(f, d.rho0, z);
+            } else {
+                read_rec12(halo + (size_t)kSR * (col - cap), f, z);
+            }
+        }
+        fv_acc_entry(acc, ec[e], ec[(roff + j) * cap + r], ec[(2 * roff + j) * cap + r], f, z);
+    }
+    T fP[9], zP[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fP[i] = fn[i];
+    z_of(fP, d.rho0, zP);
+    fv_acc_finish(d, acc, reinterpret_cast<const T*>(sm + L.cpp)[r], fP, zP, fn);
+}
+
+template <typename T, bool kOuterFv>
 __device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r, int m,
                                                T (&fn)[9]) {
     const int8_t kind = reinterpret_cast<const int8_t*>(sm + L.kind)[r];
     if (kind == HLBM_NODE_OUTER) {
         const int q = reinterpret_cast<const int16_t*>(sm + L.omap)[r];
         fv_outer_from(d, reinterpret_cast<const T*>(sm + L.osnap) + kSnap * q, 1, m, fn);
+        if constexpr (kOuterFv) fv_outer_sums_tile(d, sm, L, r, m, fn);
         return;
     }
     fv_node_tile(d, sm, L, r, fn);
@@ -650,7 +728,7 @@ __device__ __forceinline__ void fv_update_slot(const Dev<T>& d, const unsigned c
     }
 }
 
-template <typename T>
+template <typename T, bool kOuterFv>
 __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepArgs a, T* g0, T* g1) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int abort_sh;
@@ -730,7 +808,7 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
 #pragma unroll
         for (int s = 0; s < kSlots<T>; ++s) {
             const int x = tid + s * nt;
-            if (x < n_int) fv_update_slot(d, sm, L, x, m, fn[s]);
+            if (x < n_int) fv_update_slot<T, kOuterFv>(d, sm, L, x, m, fn[s]);
         }
         // warp 0: wait for the neighbour tiles to publish state m (lane l
         // acquires the counters l, l + 32, ...; the warp barrier then orders
@@ -778,7 +856,7 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
 #pragma unroll
         for (int s = 0; s < kSlots<T>; ++s) {
             const int x = tid + s * nt;
-            if (x >= n_int && x < tile_n) fv_update_slot(d, sm, L, x, m, fn[s]);
+            if (x >= n_int && x < tile_n) fv_update_slot<T, kOuterFv>(d, sm, L, x, m, fn[s]);
         }
         __syncthreads();
         // publish state m+1
@@ -844,19 +922,23 @@ int fv_smem_tile_capacity(size_t smem) {
     // the opt-in maximum less the kernel's static shared memory, so that
     // solvers with different tile sizes can all launch; residency follows
     // from the bytes each launch asks for
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, k_fv_tiles<T>) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    int cap = 1 << 30;
+    for (const void* fn : {(const void*)k_fv_tiles<T, false>, (const void*)k_fv_tiles<T, true>}) {
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const int limit = maxsm - (int)fa.sharedSizeBytes;
+        if (smem > (size_t)limit) return 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kSmemThreads<T>, smem);
+        cap = std::min(cap, sms * per);
     }
-    const int limit = maxsm - (int)fa.sharedSizeBytes;
-    if (smem > (size_t)limit) return 0;
-    if (cudaFuncSetAttribute(k_fv_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tiles<T>, kSmemThreads<T>, smem);
-    return sms * per;
+    return cap;
 }
 
 template <typename T>
@@ -867,8 +949,8 @@ cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
     T* b1 = d.fu_out;
     void* args[] = {&dd, &aa, &b0, &b1};
     size_t smem = fv_smem_bytes<T>(d.tile_cap, d.halo_cap, d.ell_width - 1, d.n_sub, d.tile_ocap);
-    return cudaLaunchCooperativeKernel((const void*)k_fv_tiles<T>, dim3(d.n_tiles), dim3(kSmemThreads<T>), args, smem,
-                                       s);
+    const void* fn = d.outer_fv ? (const void*)k_fv_tiles<T, true> : (const void*)k_fv_tiles<T, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(d.n_tiles), dim3(kSmemThreads<T>), args, smem, s);
 }
 
 // ------------------------------------------------------------- force

@@ -192,3 +192,36 @@ def test_full_size_4096_first_steps_and_sampled_geometry():
     assert np.array_equal(tg, to) and np.array_equal(dg, do)
     fx, fy = s.force()
     assert np.isfinite(fy).all()
+
+
+@pytest.mark.parametrize("dtype,steps,tol_u,tol_rho", [("f64", 60, 2e-9, 1e-12), ("f32", 200, 1e-5, 1e-5)])
+def test_parity_full_outer_node_update(dtype, steps, tol_u, tol_rho):
+    """Outer patch nodes with the FV sums of eq. postcollision2_u (reading
+    R10 of the oracle) against the oracle; same bars as the Dirichlet runs."""
+    w, s, o = pair("lamina-small-" + dtype, outer_fv=1)
+    for chunk in (1, steps // 2 - 1, steps // 2):
+        s.step(chunk)
+        o.step(chunk)
+        compare_geometry(s, o)
+    e = compare_fields(s, o, tol_u, tol_rho)
+    print(dtype, "outer_fv errors", e)
+    assert s.status == 0 and o.status == 0
+    # the two readings give different fields: the FV sums are active
+    w0, s0, _ = pair("lamina-small-" + dtype)
+    s0.step(steps)
+    assert not np.array_equal(s0.fields()[4], s.fields()[4])
+
+
+def test_zero_disturbance_with_full_outer_node_update():
+    w = inputs.Workload("zero-disturbance", 64, 60, 12.0, 0.24, 30.3, 28.2, 0.7, 10, inputs.MOTION_UNIFORM,
+                        vx=0.02, vy=0.03, delta_f=1.8, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                        u0x=0.02, u0y=0.03, dtype="f64", outer_fv=1,
+                        mesh_args=dict(n_L=24, n_T=1, n_layers=8, h1=0.2, d_out=3.6))
+    from paper_2006_13631_gb300 import Solver
+
+    s = Solver(w)
+    s.step(120)
+    assert s.status == 0
+    rs, uxs, uys, ru, uxu, uyu = s.fields()
+    assert np.abs(uxu - 0.02).max() < 1e-12 and np.abs(uyu - 0.03).max() < 1e-12
+    assert np.abs(ru - 1).max() < 1e-12
