@@ -105,7 +105,12 @@ typedef struct {
  * f = f^eq,s + (1 - dt_s/(2 tau_s)) f^neq,s, bilinear from the lattice and
  * linear in time over the lattice step; 1 adds its FV sums over the node's
  * truncated control volume, with the starred values of the paper
- * (interpolated at interpolation nodes, the patch state elsewhere). */
+ * (interpolated at interpolation nodes, the patch state elsewhere).
+ * fv_kernel picks the kernel of the FV sub-steps, HLBM_FV_*: AUTO takes the
+ * first that applies of TMEM (rows of at most 7 off-diagonal entries,
+ * outer_fv = 0), SMEM and GLOBAL; the others are for testing and
+ * hlbm_create fails with HLBM_EINVAL when the one asked for cannot run the
+ * patch.  All give the same results bit for bit. */
 typedef struct {
     int32_t n_nodes, n_tris;
     const double* xy;
@@ -117,7 +122,14 @@ typedef struct {
     int32_t n_sub;
     int32_t lumped;
     int32_t outer_fv;
+    int32_t fv_kernel;
 } hlbm_patch_t;
+
+/* kernels of the FV sub-steps (hlbm_patch_t.fv_kernel) */
+#define HLBM_FV_AUTO 0
+#define HLBM_FV_GLOBAL 1 /* records in global memory, any tile size          */
+#define HLBM_FV_SMEM 2   /* tiles in shared memory, records updated in place */
+#define HLBM_FV_TMEM 3   /* rows in tensor memory, records double-buffered   */
 
 typedef struct {
     int32_t kind; /* HLBM_MOTION_* */
@@ -197,6 +209,8 @@ typedef struct {
     int32_t box_w, box_h;  /* lattice window that follows the patch       */
     int32_t launches_per_step;
     int32_t dtype;
+    int32_t fv_kernel; /* HLBM_FV_* in use                                */
+    int32_t n_tiles;   /* FV tiles (blocks of the FV launch)               */
 } hlbm_info_t;
 int hlbm_info(hlbm_t* h, hlbm_info_t* info);
 

@@ -272,6 +272,7 @@ class Workload:
     u0y: float = 0.0
     lumped: int = 0          # 1: lumped collision matrix C = identity
     outer_fv: int = 0        # 1: outer nodes take eq. 182 with its FV sums
+    fv_kernel: int = 0       # CUDA FV kernel: 0 automatic, 1 global, 2 shared-memory, 3 tensor-memory tiles
     mesh_args: dict = field(default_factory=dict)
 
     def mesh(self) -> PatchMesh:

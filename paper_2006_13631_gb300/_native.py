@@ -8,6 +8,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhlbm.so")
 
 HLBM_OK, HLBM_EINVAL, HLBM_ECUDA, HLBM_EUNSTABLE, HLBM_EGEOM, HLBM_ENOMEM, HLBM_EIO = 0, -1, -2, -3, -4, -5, -6
+HLBM_FV_AUTO, HLBM_FV_GLOBAL, HLBM_FV_SMEM, HLBM_FV_TMEM = 0, 1, 2, 3
 HLBM_BC_WALL, HLBM_BC_OUTFLOW, HLBM_BC_PERIODIC = 0, 1, 2
 HLBM_F64, HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2, 3
 HLBM_NODE_INTERIOR, HLBM_NODE_OUTER, HLBM_NODE_WALL = 0, 1, 2
@@ -29,7 +30,7 @@ class hlbm_patch_t(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tris", C.c_int32), ("xy", _dp), ("tri", _ip),
                 ("kind", C.POINTER(C.c_int8)), ("lamina_L", C.c_double), ("lamina_T", C.c_double),
                 ("x_c", C.c_double), ("y_c", C.c_double), ("delta_f", C.c_double),
-                ("n_sub", C.c_int32), ("lumped", C.c_int32), ("outer_fv", C.c_int32)]
+                ("n_sub", C.c_int32), ("lumped", C.c_int32), ("outer_fv", C.c_int32), ("fv_kernel", C.c_int32)]
 
 
 class hlbm_motion_t(C.Structure):
@@ -41,7 +42,8 @@ class hlbm_info_t(C.Structure):
     _fields_ = [("time", C.c_int64), ("n_struct", C.c_int64), ("n_struct_disc", C.c_int64),
                 ("n_nodes", C.c_int32), ("n_tris", C.c_int32), ("nnz", C.c_int32), ("n_outer", C.c_int32),
                 ("n_wall_segments", C.c_int32), ("box_w", C.c_int32), ("box_h", C.c_int32),
-                ("launches_per_step", C.c_int32), ("dtype", C.c_int32)]
+                ("launches_per_step", C.c_int32), ("dtype", C.c_int32), ("fv_kernel", C.c_int32),
+                ("n_tiles", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

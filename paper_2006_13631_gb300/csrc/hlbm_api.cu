@@ -45,7 +45,8 @@ struct hlbm {
     std::vector<int32_t> perm;  // internal node -> caller's node (Morton order)
     int n_tiles = 0;
     std::vector<void*> tile_blocks;  // device tables of the current FV tiling
-    bool use_smem = false;      // shared-memory FV kernel (else global-memory kernel)
+    bool use_smem = false;      // a tile kernel (else the global-memory kernel)
+    int fv_kind = HLBM_FV_GLOBAL;  // HLBM_FV_* in use
     double mxmin = 0, mxmax = 0, mymin = 0, mymax = 0;
     int nnz = 0, nseg = 0;
 
@@ -294,7 +295,9 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
     // 5b. n FV sub-steps (eq. ulbe, eq. postcollision2_u)
     int ev = phase_begin(h, s);
     if (ev0) cudaEventRecord(ev0, s);
-    cudaError_t fe = h->use_smem ? launch_fv_smem<T>(d, ps.a, s) : launch_fv_persistent<T>(d, ps.a, s);
+    cudaError_t fe = h->fv_kind == HLBM_FV_TMEM   ? launch_fv_tmem<T>(d, ps.a, s)
+                     : h->fv_kind == HLBM_FV_SMEM ? launch_fv_smem<T>(d, ps.a, s)
+                                                  : launch_fv_persistent<T>(d, ps.a, s);
     if (ev1) cudaEventRecord(ev1, s);
     if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
     if (d.n_sub & 1) h->ui = 1 - h->ui;
@@ -402,10 +405,21 @@ int build_tiles(hlbm* h, int n_tiles_req) {
         }
         return cap;
     };
-    size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0), h->patch.n_sub,
-                                   outer_cap());
-    h->use_smem = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536 &&
-                  fv_smem_tile_capacity<T>(smem) >= n_tiles;
+    const int ocap0 = outer_cap();
+    const int want = h->patch.fv_kernel;  // HLBM_FV_* (0: the fastest that applies)
+    const bool tiles_ok = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536;
+    const size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0),
+                                         h->patch.n_sub, ocap0);
+    const size_t tsmem = fv_tmem_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), h->patch.n_sub, ocap0);
+    const bool tmem_ok = tiles_ok && max_row - 1 <= 7 && h->patch.outer_fv == 0 &&
+                         (want == HLBM_FV_AUTO || want == HLBM_FV_TMEM) && fv_tmem_tile_capacity<T>(tsmem) >= n_tiles;
+    const bool smem_ok = !tmem_ok && tiles_ok && (want == HLBM_FV_AUTO || want == HLBM_FV_SMEM) &&
+                         fv_smem_tile_capacity<T>(smem) >= n_tiles;
+    h->fv_kind = tmem_ok ? HLBM_FV_TMEM : smem_ok ? HLBM_FV_SMEM : HLBM_FV_GLOBAL;
+    h->use_smem = h->fv_kind != HLBM_FV_GLOBAL;
+    if (want != HLBM_FV_AUTO && want != h->fv_kind)
+        return fail(h, HLBM_EINVAL, "FV kernel %d cannot run this patch (tiles of %d nodes, rows of %d entries)", want,
+                    tile_cap, max_row);
     if (!h->use_smem) {
         int cap = fv_tile_capacity<T>();
         if (cap < 1) return fail(h, HLBM_ECUDA, "the FV kernel cannot be resident on this device");
@@ -1255,6 +1269,8 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
         rc = fail(h, HLBM_EINVAL, "unknown motion kind %d", motion->kind);
     else if ((p.lumped != 0 && p.lumped != 1) || (p.outer_fv != 0 && p.outer_fv != 1))
         rc = fail(h, HLBM_EINVAL, "lumped = %d and outer_fv = %d must be 0 or 1", p.lumped, p.outer_fv);
+    else if (p.fv_kernel < HLBM_FV_AUTO || p.fv_kernel > HLBM_FV_TMEM)
+        rc = fail(h, HLBM_EINVAL, "unknown FV kernel %d", p.fv_kernel);
     else if (!(p.delta_f > 1.5))
         rc = fail(h, HLBM_EINVAL, "delta_f = %g must exceed 1.5 (interpolation nodes outside the body)",
                   p.delta_f);
@@ -1499,6 +1515,8 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->box_h = bh;
     // refill, classify, fill, stream-collide, feed, FV sub-steps, force (2)
     info->launches_per_step = 8;
+    info->fv_kernel = h->fv_kind;
+    info->n_tiles = h->n_tiles;
     info->dtype = h->dtype;
     return HLBM_OK;
 }

@@ -280,6 +280,10 @@ template <typename T> void launch_build_ell(const Coef<T>* coef, const int32_t* 
                                             int64_t count, cudaStream_t s);
 template <typename T> int fv_smem_tile_capacity(size_t smem);
 template <typename T> cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+// tensor-memory FV kernel: rows with at most 7 off-diagonal entries, Dirichlet outer nodes
+template <typename T> size_t fv_tmem_smem_bytes(int tile_cap, int halo_cap, int n_sub, int ocap);
+template <typename T> int fv_tmem_tile_capacity(size_t smem);
+template <typename T> cudaError_t launch_fv_tmem(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s);  // 2 launches
 template <typename T> void launch_patch_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                               double* f9, cudaStream_t s);

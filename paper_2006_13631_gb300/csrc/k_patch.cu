@@ -888,6 +888,398 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-memory variant of k_fv_tiles.  Each thread's own FV rows (per
+// off-diagonal entry g_Pk, C_Pk and the tile-local column; C_PP and the
+// entry count) live in tensor memory (TMEM), which a thread reads from its
+// own lane with tcgen05.ld.  That frees the shared memory the coefficients
+// took, so the records are double-buffered: sub-step m reads buffer m%2 and
+// each thread writes its nodes' new records into the other buffer as soon
+// as they are computed.  A sub-step then needs two block barriers (halo in,
+// sub-step done) and no separate publish pass.
+//
+// TMEM: the block allocates all 512 columns.  Warp w reads lanes
+// 32 (w % 4) .. 32 (w % 4) + 31 (one per thread) and its own column range
+// kTmemCols<T> * (w / 4) .. + kTmemCols<T>: one slot of kTmemSlotWords<T>
+// words per node the thread updates.
+template <typename T>
+constexpr int kTmemEntryWords = sizeof(T) == 4 ? 4 : 8;  // gx, gy, c, col (FP64: 2 words each, col, pad)
+template <typename T>
+constexpr int kTmemSlotWords = sizeof(T) == 4 ? 32 : 64;
+template <typename T>
+constexpr int kTmemCols = kSlots<T> * kTmemSlotWords<T>;
+constexpr int kTmemMaxEntries = 7;  // off-diagonal entries a row may have in this kernel
+static_assert(1024 / 32 / 4 * kTmemCols<float> == 512, "TMEM columns (FP32)");
+static_assert(512 / 32 / 4 * kTmemCols<double> <= 512, "TMEM columns (FP64)");
+
+__device__ __forceinline__ void tmem_alloc_512(uint32_t* smem_dst) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(dst) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_512(uint32_t taddr) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 4 words from this thread's lane, columns taddr .. taddr + 3; complete on return
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t e) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b),
+                 "r"(c), "r"(e)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ uint32_t lo_word(T v) {
+    if constexpr (sizeof(T) == 4)
+        return __float_as_uint(v);
+    else
+        return (uint32_t)__double2loint(v);
+}
+template <typename T>
+__device__ __forceinline__ uint32_t hi_word(T v) {
+    if constexpr (sizeof(T) == 4)
+        return 0u;
+    else
+        return (uint32_t)__double2hiint(v);
+}
+template <typename T>
+__device__ __forceinline__ T from_words(uint32_t lo, uint32_t hi) {
+    if constexpr (sizeof(T) == 4)
+        return __uint_as_float(lo);
+    else
+        return __hiloint2double((int)hi, (int)lo);
+}
+
+// one FV entry of the thread's slot: (g_x, g_y, C, column)
+template <typename T>
+__device__ __forceinline__ void tmem_entry(uint32_t taddr, T& gx, T& gy, T& c, int& col) {
+    if constexpr (sizeof(T) == 4) {
+        uint32_t v[4];
+        tmem_ld4(taddr, v);
+        gx = from_words<T>(v[0], 0);
+        gy = from_words<T>(v[1], 0);
+        c = from_words<T>(v[2], 0);
+        col = (int)v[3];
+    } else {
+        uint32_t v[8];
+        tmem_ld8(taddr, v);
+        gx = from_words<T>(v[0], v[1]);
+        gy = from_words<T>(v[2], v[3]);
+        c = from_words<T>(v[4], v[5]);
+        col = (int)v[6];
+    }
+}
+
+struct TmemSmem {
+    size_t own0, own1, halo, uv, osnap, hid, order, kind, send, omap, total;
+};
+
+template <typename T>
+__host__ __device__ inline TmemSmem tmem_smem_layout(int cap, int hcap, int n_sub, int ocap) {
+    auto up = [](size_t x) { return (x + 15) / 16 * 16; };
+    TmemSmem L;
+    size_t o = 0;
+    L.own0 = o;
+    o = up(o + sizeof(T) * kSR * (size_t)cap);
+    L.own1 = o;
+    o = up(o + sizeof(T) * kSR * (size_t)cap);
+    L.halo = o;
+    o = up(o + sizeof(T) * kSR * (size_t)hcap);
+    L.uv = o;
+    o = up(o + sizeof(T) * 2 * (size_t)n_sub);
+    L.osnap = o;
+    o = up(o + sizeof(T) * kSnap * (size_t)ocap);
+    L.hid = o;
+    o = up(o + sizeof(int32_t) * (size_t)hcap);
+    L.order = o;
+    o = up(o + sizeof(uint16_t) * (size_t)cap);
+    L.kind = o;
+    o = up(o + (size_t)cap);
+    L.send = o;
+    o = up(o + (size_t)cap);
+    L.omap = o;
+    o = up(o + sizeof(int16_t) * (size_t)cap);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+size_t fv_tmem_smem_bytes(int tile_cap, int halo_cap, int n_sub, int ocap) {
+    return tmem_smem_layout<T>(tile_cap, halo_cap, n_sub, ocap).total;
+}
+
+// The update of the node in slot r of a warp-uniform call (lanes with
+// valid = false take part in the TMEM loads only) and its write into the
+// next record buffer and, when other tiles read it or on the last
+// sub-step, into global buffer gout.
+template <typename T>
+__device__ __forceinline__ void fv_tmem_node(const Dev<T>& d, const unsigned char* sm, const TmemSmem& L,
+                                             const T* cur, T* nxt, uint32_t tslot, bool valid, int r, int m, T* gout,
+                                             bool last, int p0) {
+    const int cap = d.tile_cap;
+    const int8_t kind = valid ? reinterpret_cast<const int8_t*>(sm + L.kind)[r] : (int8_t)HLBM_NODE_OUTER;
+    uint32_t hdr[4];
+    tmem_ld4(tslot + kTmemMaxEntries * kTmemEntryWords<T>, hdr);
+    const T cP = from_words<T>(hdr[0], hdr[1]);
+    const int ne = (valid && kind != HLBM_NODE_OUTER) ? (int)hdr[2] : 0;
+    const int nem = __reduce_max_sync(0xffffffffu, (unsigned)ne);
+    T fn[9];
+    FvAcc<T> acc;
+    fv_acc_init(acc);
+    const T* halo = reinterpret_cast<const T*>(sm + L.halo) - (size_t)kSR * cap;
+#pragma unroll
+    for (int j = 0; j < kTmemMaxEntries; ++j) {
+        if (j >= nem) break;
+        T gx, gy, c;
+        int col;
+        tmem_entry<T>(tslot + j * kTmemEntryWords<T>, gx, gy, c, col);
+        if (j < ne) {
+            T f[9], z[3];
+            read_rec12((col < cap ? cur : halo) + (size_t)kSR * col, f, z);
+            fv_acc_entry(acc, gx, gy, c, f, z);
+        }
+    }
+    if (!valid) return;
+    if (kind == HLBM_NODE_OUTER) {
+        const int q = reinterpret_cast<const int16_t*>(sm + L.omap)[r];
+        fv_outer_from(d, reinterpret_cast<const T*>(sm + L.osnap) + kSnap * q, 1, m, fn);
+    } else {
+        T fP[9], zP[3];
+        read_rec12(cur + (size_t)kSR * r, fP, zP);
+        fv_acc_finish(d, acc, cP, fP, zP, fn);
+        if (kind == HLBM_NODE_WALL) {
+            const T* uv = reinterpret_cast<const T*>(sm + L.uv);
+            fv_wall(d, uv[m], uv[d.n_sub + m], fn);
+        }
+    }
+    T z[3];
+    z_of(fn, d.rho0, z);
+    T* o = nxt + (size_t)kSR * r;
+    st4(o, fn[0], fn[1], fn[2], fn[3]);
+    st4(o + 4, fn[4], fn[5], fn[6], fn[7]);
+    st4(o + 8, fn[8], z[0], z[1], z[2]);
+    if (last || reinterpret_cast<const int8_t*>(sm + L.send)[r]) {
+        T* rec = gout + (int64_t)kRec * (p0 + reinterpret_cast<const uint16_t*>(sm + L.order)[r]);
+        st4(rec, fn[0], fn[1], fn[2], fn[3]);
+        st4(rec + 4, fn[4], fn[5], fn[6], fn[7]);
+        st4(rec + 8, fn[8], z[0], z[1], z[2]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tmem(Dev<T> d, StepArgs a, T* g0, T* g1) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int abort_sh;
+    __shared__ uint32_t tmem_base_sh;
+    const int cap = d.tile_cap, hcap = d.halo_cap;
+    const TmemSmem L = tmem_smem_layout<T>(cap, hcap, d.n_sub, d.tile_ocap);
+    T* own0 = reinterpret_cast<T*>(sm + L.own0);
+    T* own1 = reinterpret_cast<T*>(sm + L.own1);
+    T* halo = reinterpret_cast<T*>(sm + L.halo);
+    T* uv = reinterpret_cast<T*>(sm + L.uv);
+    int32_t* hid = reinterpret_cast<int32_t*>(sm + L.hid);
+    const int tile = blockIdx.x;
+    const int p0 = d.tile_start[tile], p1 = d.tile_start[tile + 1], tile_n = p1 - p0;
+    const int h0 = d.halo_ptr[tile], halo_n = d.halo_ptr[tile + 1] - h0;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5;
+    const int rounds = (tile_n + nt - 1) / nt;
+    const int n_int = min(d.tile_interior[tile], (rounds - 1) * nt);
+    // ---- TMEM for the block
+    if (warp == 0) tmem_alloc_512(&tmem_base_sh);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tbase = tmem_base_sh;
+    const uint32_t twarp = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kTmemCols<T> * (warp >> 2));
+    // ---- set-up: wall velocity, records (buffer 0), kinds, flags, order, halo ids, outer feed
+    for (int m = tid; m < d.n_sub; m += nt) wall_velocity(d, a, m, uv[m], uv[d.n_sub + m]);
+    for (int x = tid; x < 3 * tile_n; x += nt) {
+        const int sl = x / 3, c = x - 3 * sl;
+        const Vec4<T> v = ld4(g0 + (int64_t)kRec * (p0 + d.tile_order[p0 + sl]) + 4 * c);
+        st4(own0 + (size_t)kSR * sl + 4 * c, v.x, v.y, v.z, v.w);
+    }
+    {
+        int8_t* kd = reinterpret_cast<int8_t*>(sm + L.kind);
+        int8_t* sd = reinterpret_cast<int8_t*>(sm + L.send);
+        uint16_t* od = reinterpret_cast<uint16_t*>(sm + L.order);
+        for (int sl = tid; sl < tile_n; sl += nt) {
+            const int r = d.tile_order[p0 + sl];
+            kd[sl] = d.kind[p0 + r];
+            sd[sl] = d.send[p0 + r];
+            od[sl] = (uint16_t)r;
+        }
+        for (int h = tid; h < halo_n; h += nt) hid[h] = d.halo_ids[h0 + h];
+        const int o0 = d.tile_outer_ptr[tile], on = d.tile_outer_ptr[tile + 1] - o0;
+        int16_t* om = reinterpret_cast<int16_t*>(sm + L.omap);
+        T* osn = reinterpret_cast<T*>(sm + L.osnap);
+        for (int q = tid; q < on; q += nt) om[d.tile_outer_r[o0 + q]] = (int16_t)q;
+        const int64_t no = d.n_outer;
+        for (int x = tid; x < kSnap * on; x += nt) {
+            const int q = x / kSnap, j = x - kSnap * q;
+            osn[x] = d.snap[j * no + d.outer_of[p0 + d.tile_order[p0 + d.tile_outer_r[o0 + q]]]];
+        }
+        // this thread's rows into its TMEM slots (every lane stores; lanes
+        // without a node store zeros)
+        const Coef<T>* ell = d.ell + (int64_t)d.ell_width * p0;
+#pragma unroll
+        for (int s = 0; s < kSlots<T>; ++s) {
+            const int x = tid + s * nt;
+            const bool have = x < tile_n;
+            const uint32_t tslot = twarp + (uint32_t)(s * kTmemSlotWords<T>);
+            const int q = have ? p0 + d.tile_order[p0 + x] : 0;
+            const int ne = have ? d.row_ptr[q + 1] - d.row_ptr[q] - 1 : 0;
+            for (int j = 0; j < kTmemMaxEntries; ++j) {
+                Coef<T> c{};
+                c.col = x;
+                c.gx = c.gy = c.c = T(0);
+                if (have && j < ne) c = ell[(int64_t)(j + 1) * tile_n + x];
+                const uint32_t t = tslot + (uint32_t)(j * kTmemEntryWords<T>);
+                if constexpr (sizeof(T) == 4) {
+                    tmem_st4(t, lo_word(c.gx), lo_word(c.gy), lo_word(c.c), (uint32_t)c.col);
+                } else {
+                    tmem_st4(t, lo_word(c.gx), hi_word(c.gx), lo_word(c.gy), hi_word(c.gy));
+                    tmem_st4(t + 4, lo_word(c.c), hi_word(c.c), (uint32_t)c.col, 0u);
+                }
+            }
+            const T cP = have ? ell[x].c : T(0);
+            tmem_st4(tslot + kTmemMaxEntries * kTmemEntryWords<T>, lo_word(cP), hi_word(cP), (uint32_t)ne, 0u);
+        }
+        tmem_wait_st();
+    }
+    if (tid == 0) abort_sh = 0;
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned long long base = (unsigned long long)a.t * (unsigned long long)d.n_sub;
+    const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
+    for (int m = 0; m < d.n_sub; ++m) {
+        const T* cur = (m & 1) ? own1 : own0;
+        T* nxt = (m & 1) ? own0 : own1;
+        T* gout = (m & 1) ? g0 : g1;
+        const bool last = (m == d.n_sub - 1);
+        // nodes that read no halo (warp-uniform calls)
+#pragma unroll
+        for (int s = 0; s < kSlots<T>; ++s) {
+            const int x = tid + s * nt;
+            const bool v = x < n_int;
+            if (__any_sync(0xffffffffu, v))
+                fv_tmem_node(d, sm, L, cur, nxt, twarp + (uint32_t)(s * kTmemSlotWords<T>), v, x, m, gout, last,
+                             p0);
+        }
+        // warp 0: neighbour wait and halo copy, as in k_fv_tiles
+        if (warp == 0) {
+            bool ok = true;
+            if (m > 0) {
+                for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
+                    const unsigned long long* pc = d.progress + d.tile_nb[e];
+                    long spins = 0;
+                    while (ld_acquire(pc) < base + m) {
+                        if (*(volatile unsigned*)d.abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        if (++spins > kMaxSpins) {
+                            atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
+                            atomicExch(d.abort_flag, 1u);
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+            }
+            __syncwarp();
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                const T* gin = (m & 1) ? g1 : g0;
+                constexpr int kChunks = kSR * (int)sizeof(T) / 16;
+                for (int x = tid; x < kChunks * halo_n; x += 32) {
+                    const int h = x / kChunks, c = x - kChunks * h;
+                    cp_async16(reinterpret_cast<unsigned char*>(halo) + (size_t)h * kSR * sizeof(T) + 16 * c,
+                               reinterpret_cast<const unsigned char*>(gin + (int64_t)kRec * hid[h]) + 16 * c);
+                }
+            }
+            cp_async_wait_all();
+            if (tid == 0 && !ok) abort_sh = 1;
+        }
+        __syncthreads();
+        if (abort_sh) break;
+        // nodes that read the halo
+#pragma unroll
+        for (int s = 0; s < kSlots<T>; ++s) {
+            const int x = tid + s * nt;
+            const bool v = x >= n_int && x < tile_n;
+            if (__any_sync(0xffffffffu, v))
+                fv_tmem_node(d, sm, L, cur, nxt, twarp + (uint32_t)(s * kTmemSlotWords<T>), v, x, m, gout, last,
+                             p0);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release(d.progress + tile, base + m + 1);
+        }
+    }
+    // ---- release TMEM (also after an abort: every warp is past its last tcgen05.ld)
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 0) tmem_dealloc_512(tbase);
+}
+
+template <typename T>
+int fv_tmem_tile_capacity(size_t smem) {
+    if (smem == 0) return 0;
+    int dev = 0, sms = 0, per = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_fv_tmem<T>) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int limit = maxsm - (int)fa.sharedSizeBytes;
+    if (smem > (size_t)limit) return 0;
+    if (cudaFuncSetAttribute(k_fv_tmem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tmem<T>, kSmemThreads<T>, smem);
+    // each block allocates all 512 TMEM columns of its SM, so a second block
+    // on the same SM would wait for the first: only run where one fits
+    return per == 1 ? sms : 0;
+}
+
+template <typename T>
+cudaError_t launch_fv_tmem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
+    Dev<T> dd = d;
+    StepArgs aa = a;
+    T* b0 = (T*)d.fu_in;
+    T* b1 = d.fu_out;
+    void* args[] = {&dd, &aa, &b0, &b1};
+    size_t smem = fv_tmem_smem_bytes<T>(d.tile_cap, d.halo_cap, d.n_sub, d.tile_ocap);
+    return cudaLaunchCooperativeKernel((const void*)k_fv_tmem<T>, dim3(d.n_tiles), dim3(kSmemThreads<T>), args, smem,
+                                       s);
+}
+
 // ELL copy of the FV matrices for the shared-memory kernel: entry i takes
 // CSR entry src[i] with tile-local column col[i] (src -1: padding, zero)
 template <typename T>
@@ -1111,6 +1503,9 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
                                       cudaStream_t);                                                          \
     template int fv_smem_tile_capacity<T>(size_t);                                                            \
     template cudaError_t launch_fv_smem<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
+    template size_t fv_tmem_smem_bytes<T>(int, int, int, int);                                                \
+    template int fv_tmem_tile_capacity<T>(size_t);                                                            \
+    template cudaError_t launch_fv_tmem<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \
     template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);
 HLBM_INST(float)

@@ -53,7 +53,7 @@ def _dp(a):
 
 def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
     """grid: nx, ny, bc_x, bc_y, dtype ('f64'|'f32'|'f16'|'bf16'), rho0, u0x, u0y, rho_init, ux_init, uy_init
-    patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped, outer_fv
+    patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped, outer_fv, fv_kernel
     motion: kind, A, omega, vx, vy.  Returns an opaque handle (keeps the host copies alive
     for the duration of the call only)."""
     lib = N.load()
@@ -87,6 +87,7 @@ def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream
     p.delta_f = float(patch["delta_f"])
     p.n_sub, p.lumped = int(patch["n_sub"]), int(patch.get("lumped", 0))
     p.outer_fv = int(patch.get("outer_fv", 0))
+    p.fv_kernel = int(patch.get("fv_kernel", 0))
     m = N.hlbm_motion_t()
     m.kind = int(motion.get("kind", N.HLBM_MOTION_STATIC))
     m.A, m.omega = float(motion.get("A", 0.0)), float(motion.get("omega", 0.0))
@@ -213,7 +214,7 @@ class Solver:
                     ux_init=None if u_init is None else u_init[0], uy_init=None if u_init is None else u_init[1])
         patch = dict(xy=self.mesh.xy, tri=self.mesh.tri, kind=self.mesh.kind, lamina_L=w.L, lamina_T=w.T,
                      x_c=w.xc, y_c=w.yc, delta_f=w.delta_f, n_sub=w.n_sub, lumped=w.lumped,
-                     outer_fv=getattr(w, "outer_fv", 0))
+                     outer_fv=getattr(w, "outer_fv", 0), fv_kernel=getattr(w, "fv_kernel", 0))
         motion = dict(kind=w.motion, A=w.A, omega=w.omega, vx=w.vx, vy=w.vy)
         self.h = hlbm_create(grid, patch, w.tau_s, motion, self.stream)
         self.n = self.mesh.n_nodes
