@@ -166,10 +166,10 @@ _KERNEL_SOURCES = {
                         "// ------------------------------------------------------------- readback"),
                        ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
                         "// ---------------------------------------------------------------- layout")],
-    "fv_tiles": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
-                  "// ------------------------------------------------------------- force"),
-                 ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
-                  "// ---------------------------------------------------------------- layout")],
+    "fv_tmem": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
+                 "// ------------------------------------------------------------- force"),
+                ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
+                 "// ---------------------------------------------------------------- layout")],
 }
 
 
@@ -290,8 +290,10 @@ def run_ours(args):
     fv_flop = FV_FLOP_PER_ENTRY * nnz * w.n_sub  # per launch (one lattice step)
     fv_tflops = fv_flop / (fv_ms / args.steps / 1e3) / 1e12 if fv_ms else None
     alu_peak = FP32_ALU_TFLOPS if w.dtype == "f32" else FP64_ALU_TFLOPS
-    roof = {"bound": "alu", "kernel": "k_fv_tiles", "achieved": fv_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": fv_tflops / alu_peak if fv_tflops else None, "traffic": kernel_traffic("fv_tiles", w.name),
+    fv_kernel = {1: "k_fv_steps", 2: "k_fv_tiles", 3: "k_fv_tmem"}.get(info["fv_kernel"], "?")
+    roof = {"bound": "alu", "kernel": fv_kernel, "achieved": fv_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": fv_tflops / alu_peak if fv_tflops else None,
+            "traffic": kernel_traffic("fv_tmem", w.name) if fv_kernel == "k_fv_tmem" else None,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
             "flop_per_launch": fv_flop, "ms_per_launch": fv_ms / args.steps, "dominant_phase": dom,
             "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases}}
