@@ -306,6 +306,35 @@ def harmonic_params(L: float, KC: float, beta: float, tau: float | None = None, 
     return A, omega, tau
 
 
+# the (beta, eps) points of the paper's parametric study (Sec. 2): eps in
+# {0.02, 0.03, 0.04, 0.05, 0.075, 0.1}, beta in {20, ..., 300}, the pairs
+# inside its harmonic-response limit (eq. betalimit)
+PAPER_BETAS = (20.0, 50.0, 100.0, 150.0, 200.0, 250.0, 300.0)
+PAPER_EPS = (0.02, 0.03, 0.04, 0.05, 0.075, 0.1)
+
+
+def paper_points():
+    return [(b, e) for b in PAPER_BETAS for e in PAPER_EPS if b < 2.6 * e ** -1.6]
+
+
+def paper_point_workload(beta: float, eps: float, L: float = 32.0, tau_max: float = 0.8) -> Workload:
+    """The validation case at (beta, eps) with chord L (domain 5L, thickness
+    L/100, FP64), with the peak lamina speed lowered from 0.02 where needed
+    to keep tau_s <= tau_max (small beta and eps otherwise give tau_s > 1,
+    where the coupled scheme is unstable under these readings)."""
+    KC = 2.0 * math.pi * eps
+    nu_max = (tau_max - 0.5) / 3.0
+    vmax = min(0.02, nu_max * KC * beta / L)
+    A, om, tau = harmonic_params(L, KC, beta, vmax=vmax)
+    n = int(5 * L)
+    w = Workload(f"paper-{beta:g}-{eps:g}-{L:g}", n, n, L, L / 100.0, 0.5 * n + 0.3, 0.5 * n + 0.2, tau, 50,
+                 MOTION_HARMONIC, A=A, omega=om, delta_f=2.0, dtype="f64",
+                 mesh_args=dict(n_L=int(2 * L), n_T=2, n_layers=14, h1=0.2, d_out=4.0))
+    w.n_sub = stable_substeps(w.mesh(), tau - 0.5, minimum=50)
+    w.steps = int(math.floor(4 * w.period)) + 1
+    return w
+
+
 def workload(name: str) -> Workload:
     """Named synthetic workloads (sizes of the paper's lamina problem)."""
     if name == "lamina-256-f64":

@@ -133,6 +133,14 @@ def outer_fv(xy, tri, kind, tau_u, dt_u, fin, dstar, lumped=0):
     return out
 
 
+def theta_semi_analytic(beta, eps):
+    """eq. hydro_tot with eq. hydro_gamma and eq. hydro_delta (Sec. 2.1):
+    Theta = 1.02 + 2.45 beta^-1/2 - i (2.49 beta^-1/2 + 0.879 beta^3/4 eps^2)."""
+    beta = np.asarray(beta, dtype=np.float64)
+    eps = np.asarray(eps, dtype=np.float64)
+    return 1.02 + 2.45 * beta ** -0.5 - 1j * (2.49 * beta ** -0.5 + 0.879 * beta ** 0.75 * eps ** 2)
+
+
 def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
     f = np.ascontiguousarray(f9, dtype=np.float64).copy()
     _, ny, nx = f.shape

@@ -417,3 +417,21 @@ def test_zero_disturbance_with_full_outer_node_update():
     r, ux, uy = o.patch_macro()
     assert np.abs(ux - 0.02).max() < 1e-12 and np.abs(uy - 0.03).max() < 1e-12
     assert np.abs(r - 1.0).max() < 1e-12
+
+
+def test_paper_theta_fixture_against_semi_analytic_form():
+    """The 35 MG-HLBM values printed in the paper (tests/golden) lie within the
+    paper's own spread around eq. hydro_tot (Re within 3.5 %, -Im within 16 %),
+    follow its trends (Re falls and -Im rises with eps at fixed beta for
+    eps <= 0.05), and cover exactly the study points inside eq. betalimit."""
+    import os
+
+    d = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_theta_mg_hlbm.txt"))
+    beta, eps, re, mim = d.T
+    assert [tuple(x) for x in d[:, :2]] == inputs.paper_points()
+    th = oracle.theta_semi_analytic(beta, eps)
+    assert np.abs(re / th.real - 1).max() < 0.035
+    assert np.abs(mim / -th.imag - 1).max() < 0.16
+    for b in np.unique(beta):
+        sel = (beta == b) & (eps <= 0.05)
+        assert np.all(np.diff(re[sel]) < 0) and np.all(np.diff(mim[sel]) > 0)
