@@ -23,6 +23,7 @@ import numpy as np
 MOTION_STATIC = 0
 MOTION_HARMONIC = 1
 MOTION_UNIFORM = 2
+MOTION_INDUCED = 3
 # boundary kinds for the Cartesian domain sides
 BC_WALL = 0
 BC_OUTFLOW = 1
@@ -273,6 +274,12 @@ class Workload:
     lumped: int = 0          # 1: lumped collision matrix C = identity
     outer_fv: int = 0        # 1: outer nodes take eq. 182 with its FV sums
     fv_kernel: int = 0       # CUDA FV kernel: 0 automatic, 1 global, 2 shared-memory, 3 tensor-memory tiles
+    # INDUCED motion: m y'' + c y' + k y = F_y (per unit length), y(0) = y0, y'(0) = v0
+    mass: float = 1.0
+    stiffness: float = 0.0
+    damping: float = 0.0
+    y0: float = 0.0
+    v0: float = 0.0
     mesh_args: dict = field(default_factory=dict)
 
     def mesh(self) -> PatchMesh:

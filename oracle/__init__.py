@@ -44,6 +44,8 @@ class _Params(C.Structure):
         ("n_sub", C.c_int), ("lumped", C.c_int), ("motion", C.c_int),
         ("A", C.c_double), ("omega", C.c_double), ("vx", C.c_double), ("vy", C.c_double),
         ("outer_fv", C.c_int),
+        ("mass", C.c_double), ("stiffness", C.c_double), ("damping", C.c_double), ("y0", C.c_double),
+        ("v0", C.c_double),
     ]
 
 
@@ -80,6 +82,7 @@ def lib():
         L.orc_fv_nnz.argtypes = [P]
         L.orc_fv_coeffs.argtypes = [P, ip, ip, dp, dp, dp, dp]
         L.orc_n_wall_segments.argtypes = [P]
+        L.orc_motion_history.argtypes = [P, C.c_int64, dp, dp]
         L.orc_outer_fv.argtypes = [C.c_int, dp, C.c_int, ip, C.POINTER(C.c_int8), C.c_double, C.c_double, C.c_int,
                                    dp, dp, dp]
         L.orc_sine_fit.argtypes = [dp, C.c_int64, C.c_int64, C.c_double, dp, dp, dp]
@@ -176,6 +179,8 @@ class Oracle:
         p.kind = self._keep[3].ctypes.data_as(C.POINTER(C.c_int8))
         p.n_sub, p.lumped, p.motion = w.n_sub, w.lumped, w.motion
         p.outer_fv = int(getattr(w, "outer_fv", 0))
+        p.mass, p.stiffness, p.damping = float(w.mass), float(w.stiffness), float(w.damping)
+        p.y0, p.v0 = float(w.y0), float(w.v0)
         p.A, p.omega, p.vx, p.vy = w.A, w.omega, w.vx, w.vy
         self._h = lib().orc_create(C.byref(p))
         self.n = self.mesh.n_nodes
@@ -242,6 +247,13 @@ class Oracle:
         fx, fy = np.empty(n), np.empty(n)
         lib().orc_force(self._h, _dp(fx), _dp(fy))
         return fx, fy
+
+    def motion(self):
+        """(y, v) of the lamina at integer times 0..t."""
+        n = self.time + 1
+        y, v = np.empty(n), np.empty(n)
+        lib().orc_motion_history(self._h, n, _dp(y), _dp(v))
+        return y, v
 
     def gamma(self, discard=1.0, fit=3.0):
         re, im, r = C.c_double(), C.c_double(), C.c_double()

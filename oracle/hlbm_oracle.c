@@ -45,6 +45,12 @@
  *      carries no mass or momentum), so f* - f^eq(f*) is the starred
  *      non-equilibrium part of the paper.  Regular nodes read an outer
  *      neighbour's stored value, increment included.
+ *  R11 INDUCED motion (the paper's outlook, Sec. 7): the lamina is a rigid
+ *      body on a spring and damper, m y'' + c y' + k y = F_y, integrated
+ *      once per lattice step by symplectic Euler with the force at the
+ *      start of the step: v(t+1) = v(t) + (F_y(t) - c v(t) - k y(t))/m,
+ *      y(t+1) = y(t) + v(t+1).  The patch sits at y(t) during step t; the
+ *      wall velocity at sub-step m is v(t) + theta (v(t+1) - v(t)).
  */
 #include "hlbm_oracle.h"
 
@@ -129,6 +135,8 @@ struct orc {
     int64_t hcap;
     int64_t t;
     double Xprev, Yprev;
+    double *Yh, *Vh; /* INDUCED motion: y and v at integer times (R11) */
+    int64_t mcap;
     int status;
 };
 
@@ -158,6 +166,16 @@ static void motion_vel(const orc_params_t* p, double time, double* U, double* V)
     } else {
         *U = 0.0;
         *V = 0.0;
+    }
+}
+
+/* position at integer time t; INDUCED motion reads the history (R11) */
+static void lamina_pos(const orc_t* o, int64_t t, double* X, double* Y) {
+    if (o->p.motion == ORC_MOTION_INDUCED) {
+        *X = 0.0;
+        *Y = o->Yh[t];
+    } else {
+        motion_pos(&o->p, t, X, Y);
     }
 }
 
@@ -743,7 +761,12 @@ static void fv_substeps(orc_t* o, int64_t t) {
     for (int m = 0; m < n; ++m) {
         double theta = (double)(m + 1) / (double)n;
         double U, V;
-        motion_vel(&o->p, (double)t + theta, &U, &V);
+        if (o->p.motion == ORC_MOTION_INDUCED) {
+            U = 0.0;
+            V = o->Vh[t] + theta * (o->Vh[t + 1] - o->Vh[t]);
+        } else {
+            motion_vel(&o->p, (double)t + theta, &U, &V);
+        }
         const double* fin = o->fu[o->ucur];
         double* fout = o->fu[1 - o->ucur];
         for (int P = 0; P < nn; ++P) {
@@ -977,8 +1000,13 @@ orc_t* orc_create(const orc_params_t* p) {
         for (int i = 0; i < 9; ++i) o->fs[0][i * o->N + s] = feq[i];
     }
     o->cur = 0;
+    o->mcap = 1024;
+    o->Yh = calloc((size_t)o->mcap, sizeof(double));
+    o->Vh = calloc((size_t)o->mcap, sizeof(double));
+    o->Yh[0] = p->motion == ORC_MOTION_INDUCED ? p->y0 : 0.0;
+    o->Vh[0] = p->motion == ORC_MOTION_INDUCED ? p->v0 : 0.0;
     double X, Y;
-    motion_pos(&o->p, 0, &X, &Y);
+    lamina_pos(o, 0, &X, &Y);
     double cx = p->xc + X, cy = p->yc + Y;
     classify(o, cx, cy, o->cls_cur);
     memcpy(o->cls_prev, o->cls_cur, o->N);
@@ -999,8 +1027,21 @@ orc_t* orc_create(const orc_params_t* p) {
 int orc_step(orc_t* o, int64_t nsteps) {
     for (int64_t s = 0; s < nsteps; ++s) {
         int64_t t = o->t;
+        if (o->p.motion == ORC_MOTION_INDUCED) {
+            /* R11: one symplectic Euler step with the force at t */
+            if (t + 2 > o->mcap) {
+                o->mcap = 2 * (t + 2) + 1024;
+                o->Yh = realloc(o->Yh, (size_t)o->mcap * sizeof(double));
+                o->Vh = realloc(o->Vh, (size_t)o->mcap * sizeof(double));
+            }
+            const orc_params_t* q = &o->p;
+            double a = (o->Fy[t] - q->damping * o->Vh[t] - q->stiffness * o->Yh[t]) / q->mass;
+            o->Vh[t + 1] = o->Vh[t] + a;
+            o->Yh[t + 1] = o->Yh[t] + o->Vh[t + 1];
+            if (!(fabs(o->Vh[t + 1]) < 1.0)) o->status |= ORC_ERR_FAST_MOTION;
+        }
         double X, Y;
-        motion_pos(&o->p, t, &X, &Y);
+        lamina_pos(o, t, &X, &Y);
         double cx = o->p.xc + X, cy = o->p.yc + Y;
         if (t > 0) {
             refill(o, o->Xprev, o->Yprev, X, Y);
@@ -1019,19 +1060,32 @@ int orc_step(orc_t* o, int64_t nsteps) {
     return o->status;
 }
 
+void orc_motion_history(const orc_t* o, int64_t count, double* y, double* v) {
+    for (int64_t t = 0; t < count; ++t) {
+        double X, Y, U = 0.0, V = 0.0;
+        lamina_pos(o, t, &X, &Y);
+        if (o->p.motion == ORC_MOTION_INDUCED)
+            V = o->Vh[t];
+        else
+            motion_vel(&o->p, (double)t, &U, &V);
+        y[t] = Y;
+        v[t] = V;
+    }
+}
+
 /* geometry only, for any time t >= 1 without advancing the run: the node
  * classes of step t and the refill types and donors of the relocation
  * t-1 -> t (Sec. 4) */
 void orc_classify_at(orc_t* o, int64_t t, int8_t* cls) {
     double X, Y;
-    motion_pos(&o->p, t, &X, &Y);
+    lamina_pos(o, t, &X, &Y);
     classify(o, o->p.xc + X, o->p.yc + Y, cls);
 }
 
 void orc_relocate_at(const orc_t* o, int64_t t, int32_t* type, int32_t* donor) {
     double X0, Y0, X1, Y1;
-    motion_pos(&o->p, t - 1, &X0, &Y0);
-    motion_pos(&o->p, t, &X1, &Y1);
+    lamina_pos(o, t - 1, &X0, &Y0);
+    lamina_pos(o, t, &X1, &Y1);
     double dX = X1 - X0, dY = Y1 - Y0;
     double cx = o->p.xc + X1, cy = o->p.yc + Y1;
     double a = 0.5 * o->p.L, b = 0.5 * o->p.T;
@@ -1131,6 +1185,8 @@ void orc_destroy(orc_t* o) {
     free(o->seg_ny);
     free(o->bstart);
     free(o->bitems);
+    free(o->Yh);
+    free(o->Vh);
     free(o->snap0);
     free(o->snap1);
     free(o->dstar);

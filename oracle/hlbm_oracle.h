@@ -19,7 +19,7 @@ extern "C" {
 #endif
 
 enum { ORC_BC_WALL = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
-enum { ORC_MOTION_STATIC = 0, ORC_MOTION_HARMONIC = 1, ORC_MOTION_UNIFORM = 2 };
+enum { ORC_MOTION_STATIC = 0, ORC_MOTION_HARMONIC = 1, ORC_MOTION_UNIFORM = 2, ORC_MOTION_INDUCED = 3 };
 enum { ORC_KIND_INTERIOR = 0, ORC_KIND_OUTER = 1, ORC_KIND_WALL = 2 };
 enum { ORC_DISC = 0, ORC_INTERP = 1, ORC_UNUSED = 2 };
 /* status bits */
@@ -28,7 +28,8 @@ enum {
     ORC_ERR_DONOR_NOT_COMPUTED = 2, /* bilinear donor not a computed node      */
     ORC_ERR_PULL_SOURCE = 4,        /* streaming source is an unused node      */
     ORC_ERR_NONFINITE = 8,          /* NaN / Inf in the force                   */
-    ORC_ERR_UNUSED_TO_DISC = 16     /* node jumped unused -> disc in one step  */
+    ORC_ERR_UNUSED_TO_DISC = 16,    /* node jumped unused -> disc in one step  */
+    ORC_ERR_FAST_MOTION = 64        /* INDUCED lamina moved >= 1 per step       */
 };
 
 typedef struct {
@@ -50,6 +51,8 @@ typedef struct {
     int motion;
     double A, omega, vx, vy;
     int outer_fv;           /* 1: outer nodes take eq. 182 with its FV sums (R10) */
+    /* INDUCED motion (R11): m y'' + c y' + k y = F_y, y(0) = y0, y'(0) = v0 */
+    double mass, stiffness, damping, y0, v0;
 } orc_params_t;
 
 typedef struct orc orc_t;
@@ -57,6 +60,9 @@ typedef struct orc orc_t;
 orc_t* orc_create(const orc_params_t* p);
 void orc_destroy(orc_t* o);
 int orc_step(orc_t* o, int64_t nsteps);
+/* lamina position and velocity at integer times 0..t (+1 for the position:
+ * INDUCED motion knows y(t+1) once step t has started) */
+void orc_motion_history(const orc_t* o, int64_t count, double* y, double* v);
 int orc_status(const orc_t* o);
 int64_t orc_time(const orc_t* o);
 

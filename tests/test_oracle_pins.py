@@ -435,3 +435,49 @@ def test_paper_theta_fixture_against_semi_analytic_form():
     for b in np.unique(beta):
         sel = (beta == b) & (eps <= 0.05)
         assert np.all(np.diff(re[sel]) < 0) and np.all(np.diff(mim[sel]) > 0)
+
+
+def _induced_case(mass, stiffness, y0=1.0, v0=0.0):
+    w = inputs.workload("lamina-small-f64")
+    w.motion, w.A, w.omega = inputs.MOTION_INDUCED, 0.0, 0.0
+    w.mass, w.stiffness, w.y0, w.v0 = mass, stiffness, y0, v0
+    return w
+
+
+def test_induced_motion_integrator_closed_form():
+    """Reading R11: for a body far heavier than the fluid force can move, the
+    symplectic Euler recurrence v' = v - (k/m) y, y' = y + v' is a rotation
+    with cos(W) = 1 - w^2/2, w^2 = k/m, so y(t) = y0 cos(W t) + B sin(W t)
+    with y(1) = (1 - w^2) y0 + v0 fixing B."""
+    w2 = (2 * math.pi / 180.0) ** 2
+    m = 1e15
+    y0, v0 = 1.0, 0.002
+    o = oracle.Oracle(_induced_case(m, m * w2, y0, v0))
+    o.step(200)
+    assert o.status == 0
+    y, v = o.motion()
+    W = math.acos(1 - w2 / 2)
+    B = ((1 - w2) * y0 + v0 - y0 * math.cos(W)) / math.sin(W)
+    t = np.arange(len(y))
+    assert np.abs(y - (y0 * np.cos(W * t) + B * np.sin(W * t))).max() < 1e-9
+
+
+def test_induced_free_decay_has_added_mass_and_damping():
+    """A spring-mounted lamina released in fluid at rest (reading R11) swings
+    with a period longer than in vacuum (added mass, Re Theta > 0) and with
+    shrinking swings (viscous damping, Im Theta < 0); a fluid force of the
+    wrong sign would shorten the period and feed the motion."""
+    L = 24.0
+    m = math.pi / 4 * L * L
+    T0 = 150.0
+    o = oracle.Oracle(_induced_case(m, m * (2 * math.pi / T0) ** 2, 1.5))
+    o.step(330)
+    assert o.status == 0
+    y, _ = o.motion()
+    ext = [i for i in range(1, len(y) - 1) if abs(y[i]) >= abs(y[i - 1]) and abs(y[i]) >= abs(y[i + 1])
+           and (y[i] - y[i - 1]) * (y[i + 1] - y[i]) <= 0]
+    amps = np.abs(y[[0] + ext])
+    assert len(amps) >= 3 and np.all(np.diff(amps) < 0)
+    zc = [i for i in range(1, len(y)) if y[i - 1] > 0 >= y[i] or y[i - 1] < 0 <= y[i]]
+    period = 2 * np.diff(zc).mean()
+    assert period > 1.1 * T0
