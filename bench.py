@@ -16,6 +16,7 @@ Under torchrun every rank runs its own replica of the workload on its GPU
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import subprocess
@@ -354,8 +355,15 @@ def run_ours(args):
     variants = {}
     if not args.no_reduced:
         k_var = max(10, min(args.steps, 100))
-        for key, attr in (("outer_fv", "outer_fv"), ("lumped", "lumped")):
-            setattr(w, attr, 1)
+        for key, attr in (("outer_fv", "outer_fv"), ("lumped", "lumped"), ("induced", "motion")):
+            saved = (w.motion, w.A, w.omega)
+            if key == "induced":
+                # spring-mounted lamina moved by the fluid force (one force read-back per step)
+                w.motion, w.A, w.omega = 3, 0.0, 0.0
+                w.mass = math.pi / 4 * w.L * w.L
+                w.stiffness, w.y0 = w.mass * (2 * math.pi / 2000.0) ** 2, 2.0
+            else:
+                setattr(w, attr, 1)
             with torch.cuda.stream(stream):
                 s4 = Solver(w, mesh=mesh, rho_init=rho, stream=stream.cuda_stream)
                 s4.step(args.warmup)
@@ -372,7 +380,10 @@ def run_ours(args):
                                  "ms_per_step": ms4 / k_var, "fv_ms_per_step": ph["fv"][0] / k_var,
                                  "status": s4.status}
                 s4.close()
-            setattr(w, attr, 0)
+            if key == "induced":
+                w.motion, w.A, w.omega = saved
+            else:
+                setattr(w, attr, 0)
     sweep = None if args.no_sweep else run_sweep(stream, args)
     if rank != 0:
         return 0

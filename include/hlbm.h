@@ -69,6 +69,7 @@ extern "C" {
 #define HLBM_MOTION_STATIC 0
 #define HLBM_MOTION_HARMONIC 1 /* X = 0, Y = A sin(w t)                   */
 #define HLBM_MOTION_UNIFORM 2  /* X = vx t, Y = vy t                      */
+#define HLBM_MOTION_INDUCED 3  /* X = 0, m Y'' + c Y' + k Y = F_y (below)  */
 
 /* status bits reported by hlbm_status (device-side checks) */
 #define HLBM_ST_FILL_NOT_LOCATED 1u   /* eq. 178 node outside the patch     */
@@ -131,10 +132,23 @@ typedef struct {
 #define HLBM_FV_SMEM 2   /* tiles in shared memory, records updated in place */
 #define HLBM_FV_TMEM 3   /* rows in tensor memory, records double-buffered   */
 
+/* Lamina motion.  HARMONIC: A, omega; UNIFORM: vx, vy.  INDUCED (the paper's
+ * outlook towards fluid-structure interaction, Sec. 7): a rigid lamina on a
+ * spring and damper moved by the fluid, m Y'' + c Y' + k Y = F_y per unit
+ * length (lattice units, rho0 = 1), Y(0) = y0, Y'(0) = v0.  Each lattice step
+ * t takes one symplectic Euler step with the force at t:
+ * v(t+1) = v(t) + (F_y(t) - c v(t) - k Y(t)) / m, Y(t+1) = Y(t) + v(t+1);
+ * the patch sits at Y(t) during step t and the wall velocity of sub-step j
+ * is v(t) + (j+1)/n (v(t+1) - v(t)).  hlbm_step then reads F_y(t) back from
+ * the device every step (it synchronises the stream) and fails with
+ * HLBM_EINVAL when |v| would take the patch's outer nodes past their
+ * donors (|v| > outer-boundary distance - delta_f - 1.5) or the window off
+ * the lattice. */
 typedef struct {
     int32_t kind; /* HLBM_MOTION_* */
     double A, omega;
     double vx, vy;
+    double mass, stiffness, damping, y0, v0;
 } hlbm_motion_t;
 
 typedef struct hlbm hlbm_t;
@@ -211,6 +225,7 @@ typedef struct {
     int32_t dtype;
     int32_t fv_kernel; /* HLBM_FV_* in use                                */
     int32_t n_tiles;   /* FV tiles (blocks of the FV launch)               */
+    double y, vy;      /* lamina displacement and velocity at `time`       */
 } hlbm_info_t;
 int hlbm_info(hlbm_t* h, hlbm_info_t* info);
 

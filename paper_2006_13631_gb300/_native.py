@@ -12,7 +12,7 @@ HLBM_FV_AUTO, HLBM_FV_GLOBAL, HLBM_FV_SMEM, HLBM_FV_TMEM = 0, 1, 2, 3
 HLBM_BC_WALL, HLBM_BC_OUTFLOW, HLBM_BC_PERIODIC = 0, 1, 2
 HLBM_F64, HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2, 3
 HLBM_NODE_INTERIOR, HLBM_NODE_OUTER, HLBM_NODE_WALL = 0, 1, 2
-HLBM_MOTION_STATIC, HLBM_MOTION_HARMONIC, HLBM_MOTION_UNIFORM = 0, 1, 2
+HLBM_MOTION_STATIC, HLBM_MOTION_HARMONIC, HLBM_MOTION_UNIFORM, HLBM_MOTION_INDUCED = 0, 1, 2, 3
 HLBM_ST_FILL_NOT_LOCATED, HLBM_ST_DONOR_NOT_COMPUTED, HLBM_ST_NONFINITE, HLBM_ST_UNUSED_TO_DISC = 1, 2, 8, 16
 PHASES = ("move", "stream", "fv", "force")
 
@@ -35,7 +35,8 @@ class hlbm_patch_t(C.Structure):
 
 class hlbm_motion_t(C.Structure):
     _fields_ = [("kind", C.c_int32), ("A", C.c_double), ("omega", C.c_double),
-                ("vx", C.c_double), ("vy", C.c_double)]
+                ("vx", C.c_double), ("vy", C.c_double), ("mass", C.c_double), ("stiffness", C.c_double),
+                ("damping", C.c_double), ("y0", C.c_double), ("v0", C.c_double)]
 
 
 class hlbm_info_t(C.Structure):
@@ -43,7 +44,7 @@ class hlbm_info_t(C.Structure):
                 ("n_nodes", C.c_int32), ("n_tris", C.c_int32), ("nnz", C.c_int32), ("n_outer", C.c_int32),
                 ("n_wall_segments", C.c_int32), ("box_w", C.c_int32), ("box_h", C.c_int32),
                 ("launches_per_step", C.c_int32), ("dtype", C.c_int32), ("fv_kernel", C.c_int32),
-                ("n_tiles", C.c_int32)]
+                ("n_tiles", C.c_int32), ("y", C.c_double), ("vy", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -63,6 +63,9 @@ struct hlbm {
 
     int64_t t = 0;
     double Xprev = 0, Yprev = 0;
+    // INDUCED motion: lamina displacement and velocity at t, and the largest
+    // velocity the patch's outer nodes allow
+    double Yi = 0, Vi = 0, vmax_induced = 0;
     int pbx0 = 0, pby0 = 0;
     int ci = 0;  // cls[ci]: latest class
     int si = 0;  // sbox[si]: state at the current time
@@ -223,6 +226,7 @@ struct PendingStep {
     StepArgs a;
     int ncls;
     double X, Y;
+    double Ynext, Vnext;  // INDUCED motion at t+1
 };
 
 template <typename T>
@@ -241,8 +245,27 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
         h->force_cap = cap;
     }
     double X, Y;
-    motion_pos(h->motion, t, &X, &Y);
     StepArgs a{};
+    if (h->motion.kind == HLBM_MOTION_INDUCED) {
+        // one symplectic Euler step of the lamina with the force at t
+        double f[2];
+        cudaError_t e = cudaMemcpyAsync(f, h->force + 2 * t, sizeof f, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_check(h, e, "force read-back");
+        const hlbm_motion_t& m = h->motion;
+        const double acc = (f[1] - m.damping * h->Vi - m.stiffness * h->Yi) / m.mass;
+        ps.Vnext = h->Vi + acc;
+        ps.Ynext = h->Yi + ps.Vnext;
+        if (!std::isfinite(ps.Vnext) || std::fabs(ps.Vnext) > h->vmax_induced)
+            return fail(h, HLBM_EINVAL, "step %lld: the lamina's velocity %g exceeds the %g the patch allows",
+                        (long long)t, ps.Vnext, h->vmax_induced);
+        X = 0.0;
+        Y = h->Yi;
+        a.v0 = h->Vi;
+        a.v1 = ps.Vnext;
+    } else {
+        motion_pos(h->motion, t, &X, &Y);
+    }
     a.t = t;
     a.cx = h->patch.x_c + X;
     a.cy = h->patch.y_c + Y;
@@ -326,6 +349,10 @@ int step_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
     h->pby0 = ps.a.by0;
     h->Xprev = ps.X;
     h->Yprev = ps.Y;
+    if (h->motion.kind == HLBM_MOTION_INDUCED) {
+        h->Yi = ps.Ynext;
+        h->Vi = ps.Vnext;
+    }
     h->t = ps.a.t + 1;
     return HLBM_OK;
 }
@@ -837,6 +864,12 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     launch_init_struct<T>(d, drho, dux, duy, g->u0x, g->u0y, s);
     double X0, Y0;
     motion_pos(h->motion, 0, &X0, &Y0);
+    if (h->motion.kind == HLBM_MOTION_INDUCED) {
+        X0 = 0.0;
+        Y0 = h->motion.y0;
+        h->Yi = h->motion.y0;
+        h->Vi = h->motion.v0;
+    }
     StepArgs a{};
     a.t = 0;
     a.cx = p.x_c + X0;
@@ -901,6 +934,8 @@ struct CkptHeader {
     double Xprev, Yprev;
     int32_t pbx0, pby0, ci, si, ui, fi;
     uint32_t status, pad;
+    double mass, stiffness, damping, y0, v0;  // INDUCED motion parameters
+    double Yi, Vi;                            // and its state at t
 };
 constexpr char kCkptMagic[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
 
@@ -926,7 +961,7 @@ CkptHeader ckpt_header(hlbm* h) {
     Dev<T>& d = dev_of<T>(h);
     CkptHeader c{};
     std::memcpy(c.magic, kCkptMagic, 8);
-    c.version = 1;
+    c.version = 2;
     c.dtype = h->dtype;
     c.nx = d.nx;
     c.ny = d.ny;
@@ -955,6 +990,13 @@ CkptHeader ckpt_header(hlbm* h) {
     c.t = h->t;
     c.Xprev = h->Xprev;
     c.Yprev = h->Yprev;
+    c.mass = h->motion.mass;
+    c.stiffness = h->motion.stiffness;
+    c.damping = h->motion.damping;
+    c.y0 = h->motion.y0;
+    c.v0 = h->motion.v0;
+    c.Yi = h->Yi;
+    c.Vi = h->Vi;
     c.pbx0 = h->pbx0;
     c.pby0 = h->pby0;
     c.ci = h->ci;
@@ -1021,7 +1063,7 @@ int load_impl(hlbm* h, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(h, HLBM_EIO, "cannot open %s", path);
     CkptHeader c{};
-    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 1) {
+    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 2) {
         std::fclose(fp);
         return fail(h, HLBM_EIO, "%s is not a solver checkpoint", path);
     }
@@ -1029,7 +1071,8 @@ int load_impl(hlbm* h, const char* path) {
     const bool same = c.dtype == m.dtype && c.nx == m.nx && c.ny == m.ny && c.n_nodes == m.n_nodes &&
                       c.n_tris == m.n_tris && c.n_sub == m.n_sub && c.bw == m.bw && c.bh == m.bh &&
                       c.bc_x == m.bc_x && c.bc_y == m.bc_y && c.motion == m.motion && c.lumped == m.lumped &&
-                      c.outer_fv == m.outer_fv &&
+                      c.outer_fv == m.outer_fv && c.mass == m.mass && c.stiffness == m.stiffness &&
+                      c.damping == m.damping && c.y0 == m.y0 && c.v0 == m.v0 &&
                       c.tau_s == m.tau_s && c.rho0 == m.rho0 && c.A == m.A && c.omega == m.omega &&
                       c.vx == m.vx && c.vy == m.vy && c.lamina_L == m.lamina_L && c.lamina_T == m.lamina_T &&
                       c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash;
@@ -1086,6 +1129,8 @@ int load_impl(hlbm* h, const char* path) {
     h->t = c.t;
     h->Xprev = c.Xprev;
     h->Yprev = c.Yprev;
+    h->Yi = c.Yi;
+    h->Vi = c.Vi;
     h->pbx0 = c.pbx0;
     h->pby0 = c.pby0;
     h->ci = c.ci;
@@ -1265,7 +1310,7 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
         rc = fail(h, HLBM_EINVAL, "tau_s = 1/2 makes eq. 178 singular");
     else if (p.n_nodes < 3 || p.n_tris < 1 || !p.xy || !p.tri || !p.kind)
         rc = fail(h, HLBM_EINVAL, "empty patch mesh");
-    else if (motion->kind < 0 || motion->kind > 2)
+    else if (motion->kind < 0 || motion->kind > 3)
         rc = fail(h, HLBM_EINVAL, "unknown motion kind %d", motion->kind);
     else if ((p.lumped != 0 && p.lumped != 1) || (p.outer_fv != 0 && p.outer_fv != 1))
         rc = fail(h, HLBM_EINVAL, "lumped = %d and outer_fv = %d must be 0 or 1", p.lumped, p.outer_fv);
@@ -1299,6 +1344,14 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
         double dmax = 0.0;
         if (motion->kind == HLBM_MOTION_HARMONIC) dmax = std::fabs(motion->A * motion->omega);
         if (motion->kind == HLBM_MOTION_UNIFORM) dmax = std::hypot(motion->vx, motion->vy);
+        if (motion->kind == HLBM_MOTION_INDUCED) {
+            dmax = std::fabs(motion->v0);
+            h->vmax_induced = std::min(0.999, dmin_outer - p.delta_f - 1.5);
+            if (!(motion->mass > 0.0) || !std::isfinite(motion->mass) || !(motion->stiffness >= 0.0) ||
+                !(motion->damping >= 0.0) || !std::isfinite(motion->stiffness) || !std::isfinite(motion->damping) ||
+                !std::isfinite(motion->y0) || !std::isfinite(motion->v0))
+                rc = fail(h, HLBM_EINVAL, "INDUCED motion needs mass > 0, stiffness >= 0, damping >= 0, finite y0, v0");
+        }
         // outer nodes' bilinear donors (within sqrt 2 < 1.5 of the node) must
         // be discretization nodes at t and t+1
         if (dmin_outer < 1e299 && !(dmin_outer > p.delta_f + 1.5 + dmax))
@@ -1517,6 +1570,17 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->launches_per_step = 8;
     info->fv_kernel = h->fv_kind;
     info->n_tiles = h->n_tiles;
+    if (h->motion.kind == HLBM_MOTION_INDUCED) {
+        info->y = h->Yi;
+        info->vy = h->Vi;
+    } else {
+        double X, Y;
+        motion_pos(h->motion, h->t, &X, &Y);
+        info->y = Y;
+        info->vy = h->motion.kind == HLBM_MOTION_HARMONIC
+                       ? h->motion.A * h->motion.omega * std::cos(h->motion.omega * (double)h->t)
+                       : h->motion.kind == HLBM_MOTION_UNIFORM ? h->motion.vy : 0.0;
+    }
     info->dtype = h->dtype;
     return HLBM_OK;
 }

@@ -83,6 +83,7 @@ struct StepArgs {
     int bx0, by0;   // window of this step (class and new state)
     int pbx0, pby0; // window of the previous step (previous class and state)
     int first;      // 1 at t == 0
+    double v0, v1;  // INDUCED motion: lamina velocity at t and t+1
 };
 
 template <typename T>

@@ -439,7 +439,7 @@ constexpr int kFvThreads = 256;
 constexpr long kMaxSpins = 1L << 23;  // with 128 ns sleeps: about a second
 
 // Lamina velocity at the end of sub-step m, t + (m+1)/n (the wall nodes'
-// Dirichlet value, eq. 182).
+// Dirichlet value, eq. 182); INDUCED motion interpolates v(t) -> v(t+1).
 template <typename T>
 __device__ __forceinline__ void wall_velocity(const Dev<T>& d, const StepArgs& a, int m, T& U, T& V) {
     const double time = double(a.t) + double(m + 1) / double(d.n_sub);
@@ -450,6 +450,8 @@ __device__ __forceinline__ void wall_velocity(const Dev<T>& d, const StepArgs& a
     } else if (d.motion == HLBM_MOTION_UNIFORM) {
         U = T(d.vx);
         V = T(d.vy);
+    } else if (d.motion == HLBM_MOTION_INDUCED) {
+        V = T(a.v0 + double(m + 1) / double(d.n_sub) * (a.v1 - a.v0));
     }
 }
 

@@ -54,7 +54,7 @@ def _dp(a):
 def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
     """grid: nx, ny, bc_x, bc_y, dtype ('f64'|'f32'|'f16'|'bf16'), rho0, u0x, u0y, rho_init, ux_init, uy_init
     patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped, outer_fv, fv_kernel
-    motion: kind, A, omega, vx, vy.  Returns an opaque handle (keeps the host copies alive
+    motion: kind, A, omega, vx, vy, mass, stiffness, damping, y0, v0.  Returns an opaque handle (keeps the host copies alive
     for the duration of the call only)."""
     lib = N.load()
     keep = []
@@ -92,6 +92,9 @@ def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream
     m.kind = int(motion.get("kind", N.HLBM_MOTION_STATIC))
     m.A, m.omega = float(motion.get("A", 0.0)), float(motion.get("omega", 0.0))
     m.vx, m.vy = float(motion.get("vx", 0.0)), float(motion.get("vy", 0.0))
+    m.mass = float(motion.get("mass", 1.0))
+    m.stiffness, m.damping = float(motion.get("stiffness", 0.0)), float(motion.get("damping", 0.0))
+    m.y0, m.v0 = float(motion.get("y0", 0.0)), float(motion.get("v0", 0.0))
     h = C.c_void_p()
     _check(lib.hlbm_create(C.byref(g), C.byref(p), float(tau_s), C.byref(m), C.c_void_p(cuda_stream or None),
                            C.byref(h)))
@@ -215,7 +218,9 @@ class Solver:
         patch = dict(xy=self.mesh.xy, tri=self.mesh.tri, kind=self.mesh.kind, lamina_L=w.L, lamina_T=w.T,
                      x_c=w.xc, y_c=w.yc, delta_f=w.delta_f, n_sub=w.n_sub, lumped=w.lumped,
                      outer_fv=getattr(w, "outer_fv", 0), fv_kernel=getattr(w, "fv_kernel", 0))
-        motion = dict(kind=w.motion, A=w.A, omega=w.omega, vx=w.vx, vy=w.vy)
+        motion = dict(kind=w.motion, A=w.A, omega=w.omega, vx=w.vx, vy=w.vy, mass=getattr(w, "mass", 1.0),
+                      stiffness=getattr(w, "stiffness", 0.0), damping=getattr(w, "damping", 0.0),
+                      y0=getattr(w, "y0", 0.0), v0=getattr(w, "v0", 0.0))
         self.h = hlbm_create(grid, patch, w.tau_s, motion, self.stream)
         self.n = self.mesh.n_nodes
 

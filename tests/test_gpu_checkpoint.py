@@ -80,3 +80,29 @@ def test_restart_refuses_other_inputs_and_foreign_files(tmp_path):
     with pytest.raises(HLBMError) as e:
         a.load(str(cut))
     assert e.value.code == -6
+
+
+def test_restart_of_an_induced_motion_run(tmp_path):
+    """The lamina's displacement and velocity travel with the checkpoint."""
+    import math
+
+    from paper_2006_13631_gb300 import Solver
+
+    w = inputs.workload("lamina-small-f32")
+    w.motion, w.A, w.omega = inputs.MOTION_INDUCED, 0.0, 0.0
+    w.mass = math.pi / 4 * w.L * w.L
+    w.stiffness = w.mass * (2 * math.pi / 150.0) ** 2
+    w.y0 = 1.5
+    mesh, rho = w.mesh(), w.rho_init()
+    a = Solver(w, mesh=mesh, rho_init=rho)
+    a.step(23)
+    path = str(tmp_path / "ck_induced.bin")
+    a.save(path)
+    a.step(30)
+    b = Solver(w, mesh=mesh, rho_init=rho)
+    b.load(path)
+    b.step(30)
+    sa, sb = _state(a), _state(b)
+    for k in sa:
+        assert np.array_equal(np.asarray(sa[k]), np.asarray(sb[k])), k
+    assert a.info()["y"] == b.info()["y"] and a.info()["vy"] == b.info()["vy"]
