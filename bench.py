@@ -385,6 +385,7 @@ def run_ours(args):
             else:
                 setattr(w, attr, 0)
     sweep = None if args.no_sweep else run_sweep(stream, args)
+    gradient = None if args.no_gradient else run_gradient(stream, args)
     if rank != 0:
         return 0
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.workload)
@@ -395,7 +396,7 @@ def run_ours(args):
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)" % (9 * bytes_per * w.nx * w.ny / 1e6)},
             "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "cpu_baseline": cpu, "e2e": e2e,
-            "reduced_storage": reduced or None, "variants": variants or None, "sweep": sweep,
+            "reduced_storage": reduced or None, "variants": variants or None, "sweep": sweep, "gradient": gradient,
             "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}
     print(json.dumps(line), flush=True)
     if dist:
@@ -453,6 +454,39 @@ def run_sweep(stream, args):
             "instances_with_status": bad}
 
 
+def run_gradient(stream, args):
+    """Theta and its gradient in (A, omega, tau_s) on the 1024^2 gradient case
+    (chord 32, KC 0.5, beta 800, tau_s 0.506, n 96, FP32, 4 periods) by central
+    differences over seven solvers stepped as one sweep, against one forward
+    solve of the same case."""
+    import torch
+
+    import inputs
+    from paper_2006_13631_gb300 import Solver, hlbm_theta_gradient, workload_inputs
+
+    w = inputs.workload("lamina-1024-gradient")
+    mesh, rho = w.mesh(), w.rho_init()
+    with torch.cuda.stream(stream):
+        s = Solver(w, mesh=mesh, rho_init=rho, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(w.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1)
+        th_f = s.gamma(1.0, 3.0)
+        s.close()
+        grid, patch, motion = workload_inputs(w, mesh, rho)
+        th, grad, ms = hlbm_theta_gradient(grid, patch, w.tau_s, motion, w.steps, 1.0, 3.0, 1e-4,
+                                           stream.cuda_stream)
+    return {"workload": w.name, "steps": w.steps, "theta": [th.real, th.imag],
+            "dtheta_dA": [grad[0].real, grad[0].imag], "dtheta_domega": [grad[1].real, grad[1].imag],
+            "dtheta_dtau": [grad[2].real, grad[2].imag], "forward_ms": fwd_ms, "gradient_ms": ms,
+            "gradient_over_forward": ms / fwd_ms, "method": "central differences, 7 solves in one sweep",
+            "forward_theta": [th_f[0], th_f[1]]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,6 +499,7 @@ def main():
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16/BF16 lattice-storage runs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-instance KC/beta sweep")
     ap.add_argument("--sweep-steps", type=int, default=10)
+    ap.add_argument("--no-gradient", action="store_true", help="skip the Theta-gradient case")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

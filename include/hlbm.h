@@ -270,6 +270,25 @@ int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms);
 const char* hlbm_sweep_last_error(const hlbm_sweep_t* w);
 void hlbm_sweep_destroy(hlbm_sweep_t* w);
 
+/* Gradient of the hydrodynamic function with respect to the motion's A and
+ * omega and to tau_s, by central differences: seven solvers (the base point
+ * and each parameter moved by -/+ rel_step times its value) are created from
+ * the given inputs (as hlbm_create), stepped nsteps together as one sweep
+ * (hlbm_sweep_*), and each fitted over the same steps
+ * [ceil(discard_periods T), floor((discard_periods + fit_periods) T)] of the
+ * base period T = 2 pi / omega, with its own omega and A in the fit and the
+ * normalisation (Sec. 2.1).  theta[2] receives (Re, Im) Theta at the base
+ * point; grad[6] receives d(Re, Im)/dA, d(Re, Im)/domega, d(Re, Im)/dtau_s.
+ * sweep_ms (may be NULL) receives the device time of the seven solves.
+ * HARMONIC motion only; 0 < rel_step < 0.1.  The discrete decisions of the
+ * method (node classes, donors) make Theta piecewise smooth in A and omega:
+ * the quotient is that of the moved runs, jumps included.  Errors as for
+ * hlbm_create (message: hlbm_last_error(NULL)); everything created is
+ * released before the call returns. */
+int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s,
+                        const hlbm_motion_t* motion, int64_t nsteps, double discard_periods, double fit_periods,
+                        double rel_step, void* cuda_stream, double* theta, double* grad, double* sweep_ms);
+
 /* Least-squares fit F(t) = a sin(w t) + b cos(w t) over t = t0..t1 of the
  * samples F(t) = samples[t * stride] (DEVICE memory, caller-owned, at least
  * t1 * stride + 1 doubles), the fit hlbm_gamma performs, for callers that

@@ -371,6 +371,15 @@ def workload(name: str) -> Workload:
                      mesh_args=dict(n_L=60, n_T=2, n_layers=12, h1=0.2, d_out=4.0))
         w.steps = 200
         return w
+    if name == "lamina-1024-gradient":
+        # the gradient case: 1024^2, chord 32, thickness chord/50, KC 0.5, beta 800,
+        # peak speed 0.025 (tau_s 0.506), n = 96, FP32, 4 periods (2560 steps)
+        A, om, tau = harmonic_params(32.0, 0.5, 800.0, vmax=0.025)
+        w = Workload(name, 1024, 1024, 32.0, 0.64, 512.3, 512.2, tau, 96, MOTION_HARMONIC, A=A, omega=om,
+                     delta_f=2.0, dtype="f32",
+                     mesh_args=dict(n_L=64, n_T=2, n_layers=15, h1=0.25, d_out=4.0))
+        w.steps = int(round(4 * w.period))
+        return w
     if name == "lamina-small-f64":
         w = workload("lamina-small-f32")
         w.name, w.dtype = name, "f64"

@@ -7,6 +7,7 @@ import this package; the product path (``paper_2006_13631_gb300``) never does.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -134,6 +135,41 @@ def outer_fv(xy, tri, kind, tau_u, dt_u, fin, dstar, lumped=0):
     lib().orc_outer_fv(xy.shape[0], _dp(xy), tri.shape[0], _ip(tri), kind.ctypes.data_as(C.POINTER(C.c_int8)),
                        tau_u, dt_u, lumped, _dp(fin), _dp(dstar), _dp(out))
     return out
+
+
+def theta_fd_gradient(w, nsteps, discard=1.0, fit=3.0, rel_step=1e-4, mesh=None, rho_init=None):
+    """Theta of workload w and d(Re, Im Theta)/d(A, omega, tau_s) by central
+    differences: seven oracle runs (the base point and each parameter moved by
+    -/+ rel_step of its value), each fitted (Sec. 2.1) over the same steps
+    [ceil(discard T), floor((discard + fit) T)] of the base period, with its
+    own omega and A.  Returns (theta complex, grad [3] complex)."""
+    import copy
+
+    mesh = mesh if mesh is not None else w.mesh()
+    rho = rho_init if rho_init is not None else w.rho_init()
+    base = (w.A, w.omega, w.tau_s)
+    steps = [rel_step * abs(v) for v in base]
+    Tp = 2.0 * math.pi / w.omega
+    t0, t1 = int(math.ceil(discard * Tp)), int(math.floor((discard + fit) * Tp))
+    th = []
+    for i in range(7):
+        v = copy.copy(w)
+        if i > 0:
+            k, sgn = (i - 1) // 2, (-1.0 if i % 2 == 1 else 1.0)
+            if k == 0:
+                v.A = w.A + sgn * steps[0]
+            elif k == 1:
+                v.omega = w.omega + sgn * steps[1]
+            else:
+                v.tau_s = w.tau_s + sgn * steps[2]
+        o = Oracle(v, mesh=mesh, rho_init=rho)
+        o.step(nsteps)
+        _, fy = o.force()
+        a, b, _ = sine_fit(fy, t0, t1, v.omega)
+        N = 0.25 * math.pi * v.rho0 * v.omega ** 2 * v.L ** 2 * v.A
+        th.append(complex(a / N, b / N))
+    grad = np.array([(th[2 + 2 * k] - th[1 + 2 * k]) / (2.0 * steps[k]) for k in range(3)])
+    return th[0], grad
 
 
 def theta_semi_analytic(beta, eps):

@@ -1414,15 +1414,11 @@ int hlbm_force(hlbm_t* h, int64_t first, int64_t count, double* fx, double* fy) 
     return HLBM_OK;
 }
 
-int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re, double* im, double* rms) {
-    if (!h || !re || !im) return HLBM_EINVAL;
-    if (h->motion.kind != HLBM_MOTION_HARMONIC || !(h->motion.omega > 0) || h->motion.A == 0.0)
-        return fail(h, HLBM_EINVAL, "the hydrodynamic function needs harmonic motion");
+namespace {
+// Theta from the fit of the force history over the steps t0..t1 (Sec. 2.1)
+int theta_window(hlbm* h, int64_t t0, int64_t t1, double* re, double* im, double* rms) {
     const double PI = 3.14159265358979323846;
-    double Tp = 2.0 * PI / h->motion.omega;
-    int64_t t0 = (int64_t)std::ceil(discard_periods * Tp);
-    int64_t t1 = (int64_t)std::floor((discard_periods + fit_periods) * Tp);
-    if (t1 > h->t || t1 <= t0)
+    if (t1 > h->t || t1 <= t0 || t0 < 0)
         return fail(h, HLBM_EINVAL, "fit window [%lld, %lld] is not inside the %lld steps taken", (long long)t0,
                     (long long)t1, (long long)h->t);
     launch_gamma_sums(h->force, t0, t1, h->motion.omega, h->scratch, h->stream);
@@ -1448,6 +1444,95 @@ int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re
     if (rc != HLBM_OK) return rc;
     if (st & HLBM_ST_NONFINITE) return fail(h, HLBM_EUNSTABLE, "the force became NaN/Inf: the run diverged");
     return HLBM_OK;
+}
+}  // namespace
+
+int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re, double* im, double* rms) {
+    if (!h || !re || !im) return HLBM_EINVAL;
+    if (h->motion.kind != HLBM_MOTION_HARMONIC || !(h->motion.omega > 0) || h->motion.A == 0.0)
+        return fail(h, HLBM_EINVAL, "the hydrodynamic function needs harmonic motion");
+    const double PI = 3.14159265358979323846;
+    double Tp = 2.0 * PI / h->motion.omega;
+    int64_t t0 = (int64_t)std::ceil(discard_periods * Tp);
+    int64_t t1 = (int64_t)std::floor((discard_periods + fit_periods) * Tp);
+    return theta_window(h, t0, t1, re, im, rms);
+}
+
+int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s,
+                        const hlbm_motion_t* motion, int64_t nsteps, double discard_periods, double fit_periods,
+                        double rel_step, void* cuda_stream, double* theta, double* grad, double* sweep_ms) {
+    std::string& err = g_create_err;
+    if (!grid || !patch || !motion || !theta || !grad || nsteps < 1 || !(rel_step > 0.0) || !(rel_step < 0.1)) {
+        err = "hlbm_theta_gradient: invalid argument";
+        return HLBM_EINVAL;
+    }
+    if (motion->kind != HLBM_MOTION_HARMONIC || !(motion->omega > 0) || motion->A == 0.0) {
+        err = "hlbm_theta_gradient: the hydrodynamic function needs harmonic motion";
+        return HLBM_EINVAL;
+    }
+    // the base point and (A, omega, tau_s) each moved by -/+ rel_step of their value
+    const double base[3] = {motion->A, motion->omega, tau_s};
+    double step[3];
+    for (int k = 0; k < 3; ++k) step[k] = rel_step * std::fabs(base[k]);
+    std::vector<hlbm*> inst(7, nullptr);
+    int rc = HLBM_OK;
+    for (int i = 0; i < 7 && rc == HLBM_OK; ++i) {
+        hlbm_motion_t m = *motion;
+        double ts = tau_s;
+        if (i > 0) {
+            const int k = (i - 1) / 2;
+            const double dp = (i % 2 == 1 ? -1.0 : 1.0) * step[k];
+            if (k == 0) m.A += dp;
+            if (k == 1) m.omega += dp;
+            if (k == 2) ts += dp;
+        }
+        rc = hlbm_create(grid, patch, ts, &m, cuda_stream, &inst[i]);
+    }
+    hlbm_sweep* w = nullptr;
+    if (rc == HLBM_OK) rc = hlbm_sweep_create(7, inst.data(), cuda_stream, &w);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == HLBM_OK && sweep_ms) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, (cudaStream_t)cuda_stream);
+    }
+    if (rc == HLBM_OK) {
+        rc = hlbm_sweep_step(w, nsteps);
+        if (rc != HLBM_OK) err = w->err;
+    }
+    if (rc == HLBM_OK && sweep_ms) {
+        cudaEventRecord(e1, (cudaStream_t)cuda_stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *sweep_ms = ms;
+    }
+    // one fit window for all seven runs, in steps of the base period
+    const double PI = 3.14159265358979323846;
+    const double Tp = 2.0 * PI / motion->omega;
+    const int64_t t0 = (int64_t)std::ceil(discard_periods * Tp);
+    const int64_t t1 = (int64_t)std::floor((discard_periods + fit_periods) * Tp);
+    double re[7] = {0}, im[7] = {0};
+    for (int i = 0; i < 7 && rc == HLBM_OK; ++i) {
+        rc = theta_window(inst[i], t0, t1, &re[i], &im[i], nullptr);
+        if (rc != HLBM_OK) err = inst[i]->err;
+    }
+    if (rc == HLBM_OK) {
+        theta[0] = re[0];
+        theta[1] = im[0];
+        for (int k = 0; k < 3; ++k) {
+            grad[2 * k] = (re[2 + 2 * k] - re[1 + 2 * k]) / (2.0 * step[k]);
+            grad[2 * k + 1] = (im[2 + 2 * k] - im[1 + 2 * k]) / (2.0 * step[k]);
+        }
+    } else if (err.empty()) {
+        err = "hlbm_theta_gradient failed";
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (w) hlbm_sweep_destroy(w);
+    for (hlbm* h : inst)
+        if (h) hlbm_destroy(h);
+    return rc;
 }
 
 int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double* rho_u, double* ux_u,

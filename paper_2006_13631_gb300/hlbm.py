@@ -51,12 +51,9 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
 
 
-def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
-    """grid: nx, ny, bc_x, bc_y, dtype ('f64'|'f32'|'f16'|'bf16'), rho0, u0x, u0y, rho_init, ux_init, uy_init
-    patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped, outer_fv, fv_kernel
-    motion: kind, A, omega, vx, vy, mass, stiffness, damping, y0, v0.  Returns an opaque handle (keeps the host copies alive
-    for the duration of the call only)."""
-    lib = N.load()
+def _structs(grid: dict, patch: dict, motion: dict):
+    """ctypes structs of the inputs and the host arrays they point to, which
+    the caller keeps alive for the duration of the call."""
     keep = []
 
     def arr(x, dt):
@@ -95,10 +92,31 @@ def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream
     m.mass = float(motion.get("mass", 1.0))
     m.stiffness, m.damping = float(motion.get("stiffness", 0.0)), float(motion.get("damping", 0.0))
     m.y0, m.v0 = float(motion.get("y0", 0.0)), float(motion.get("v0", 0.0))
+    return g, p, m, keep
+
+
+def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
+    """grid: nx, ny, bc_x, bc_y, dtype ('f64'|'f32'|'f16'|'bf16'), rho0, u0x, u0y, rho_init, ux_init, uy_init
+    patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped, outer_fv, fv_kernel
+    motion: kind, A, omega, vx, vy, mass, stiffness, damping, y0, v0.  Returns an opaque handle."""
+    g, p, m, keep = _structs(grid, patch, motion)
     h = C.c_void_p()
-    _check(lib.hlbm_create(C.byref(g), C.byref(p), float(tau_s), C.byref(m), C.c_void_p(cuda_stream or None),
-                           C.byref(h)))
+    _check(N.load().hlbm_create(C.byref(g), C.byref(p), float(tau_s), C.byref(m), C.c_void_p(cuda_stream or None),
+                                C.byref(h)))
     return h
+
+
+def hlbm_theta_gradient(grid: dict, patch: dict, tau_s: float, motion: dict, nsteps: int, discard=1.0, fit=3.0,
+                        rel_step=1e-4, cuda_stream: int = 0):
+    """Theta and d(Re, Im Theta)/d(A, omega, tau_s) by central differences over
+    seven solvers stepped as one sweep.  Returns (theta complex, grad [3]
+    complex, device ms of the solves)."""
+    g, p, m, keep = _structs(grid, patch, motion)
+    th, gr, ms = np.zeros(2), np.zeros(6), np.zeros(1)
+    _check(N.load().hlbm_theta_gradient(C.byref(g), C.byref(p), float(tau_s), C.byref(m), int(nsteps), float(discard),
+                                        float(fit), float(rel_step), C.c_void_p(cuda_stream or None), _dp(th), _dp(gr),
+                                        _dp(ms)))
+    return complex(th[0], th[1]), gr[0::2] + 1j * gr[1::2], float(ms[0])
 
 
 def hlbm_step(h, nsteps: int):
@@ -197,6 +215,23 @@ def hlbm_load(h, path: str):
     _check(N.load().hlbm_load(h, os.fsencode(path)), h)
 
 
+def workload_inputs(w, mesh=None, rho_init=None, u_init=None):
+    """(grid, patch, motion) dicts of hlbm_create from a workload description
+    (an object with the attributes of ``inputs.Workload``)."""
+    mesh = mesh if mesh is not None else w.mesh()
+    rho = rho_init if rho_init is not None else w.rho_init()
+    grid = dict(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, dtype=w.dtype, rho0=w.rho0, u0x=w.u0x,
+                u0y=w.u0y, rho_init=rho,
+                ux_init=None if u_init is None else u_init[0], uy_init=None if u_init is None else u_init[1])
+    patch = dict(xy=mesh.xy, tri=mesh.tri, kind=mesh.kind, lamina_L=w.L, lamina_T=w.T,
+                 x_c=w.xc, y_c=w.yc, delta_f=w.delta_f, n_sub=w.n_sub, lumped=w.lumped,
+                 outer_fv=getattr(w, "outer_fv", 0), fv_kernel=getattr(w, "fv_kernel", 0))
+    motion = dict(kind=w.motion, A=w.A, omega=w.omega, vx=w.vx, vy=w.vy, mass=getattr(w, "mass", 1.0),
+                  stiffness=getattr(w, "stiffness", 0.0), damping=getattr(w, "damping", 0.0),
+                  y0=getattr(w, "y0", 0.0), v0=getattr(w, "v0", 0.0))
+    return grid, patch, motion
+
+
 class Solver:
     """Convenience owner of one hlbm handle built from a workload description
     (an object with the attributes of ``inputs.Workload``)."""
@@ -210,17 +245,8 @@ class Solver:
             use_torch_allocator()
         self.w = w
         self.mesh = mesh if mesh is not None else w.mesh()
-        rho = rho_init if rho_init is not None else w.rho_init()
         self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-        grid = dict(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, dtype=w.dtype, rho0=w.rho0, u0x=w.u0x,
-                    u0y=w.u0y, rho_init=rho,
-                    ux_init=None if u_init is None else u_init[0], uy_init=None if u_init is None else u_init[1])
-        patch = dict(xy=self.mesh.xy, tri=self.mesh.tri, kind=self.mesh.kind, lamina_L=w.L, lamina_T=w.T,
-                     x_c=w.xc, y_c=w.yc, delta_f=w.delta_f, n_sub=w.n_sub, lumped=w.lumped,
-                     outer_fv=getattr(w, "outer_fv", 0), fv_kernel=getattr(w, "fv_kernel", 0))
-        motion = dict(kind=w.motion, A=w.A, omega=w.omega, vx=w.vx, vy=w.vy, mass=getattr(w, "mass", 1.0),
-                      stiffness=getattr(w, "stiffness", 0.0), damping=getattr(w, "damping", 0.0),
-                      y0=getattr(w, "y0", 0.0), v0=getattr(w, "v0", 0.0))
+        grid, patch, motion = workload_inputs(w, self.mesh, rho_init, u_init)
         self.h = hlbm_create(grid, patch, w.tau_s, motion, self.stream)
         self.n = self.mesh.n_nodes
 

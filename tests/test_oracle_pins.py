@@ -481,3 +481,16 @@ def test_induced_free_decay_has_added_mass_and_damping():
     zc = [i for i in range(1, len(y)) if y[i - 1] > 0 >= y[i] or y[i - 1] < 0 <= y[i]]
     period = 2 * np.diff(zc).mean()
     assert period > 1.1 * T0
+
+
+def test_fd_gradient_in_tau_converges():
+    """The central-difference derivative of Theta in tau_s (which moves no
+    node, so Theta is smooth in it) agrees at relative steps 1e-3 and 1e-4 to
+    the O(h^2) of the quotient; the base Theta is the plain fit's."""
+    w = inputs.workload("lamina-256-f64")
+    w.steps = 48
+    th1, g1 = oracle.theta_fd_gradient(w, 48, discard=0.5, fit=1.5, rel_step=1e-3)
+    th2, g2 = oracle.theta_fd_gradient(w, 48, discard=0.5, fit=1.5, rel_step=1e-4)
+    assert th1 == th2
+    assert abs(g1[2] - g2[2]) < 1e-3 * abs(g2[2])
+    assert abs(g2[2]) > 1e-3
