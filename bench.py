@@ -422,6 +422,8 @@ def run_sweep(stream, args):
         sub = sum(w.n_sub * i["n_nodes"] for w, i in zip(ws, infos))
         sw = Sweep(solvers, stream=stream.cuda_stream)
         picks = sw.tune(trial_steps=1)
+        # solvers of similar sub-step counts share FV launches (the others keep the tuned tiles)
+        n_packs = sw.pack()
         sw.step(args.warmup)
         k = max(1, args.sweep_steps)
         torch.cuda.synchronize()
@@ -451,6 +453,7 @@ def run_sweep(stream, args):
             "fv_ms_per_step": float(fv.sum()), "lattice_nodes": lat, "patch_nodes": pat,
             "fv_node_substeps_per_step": sub, "n_sub_range": [min(w.n_sub for w in ws), max(w.n_sub for w in ws)],
             "throughput_only": sum(1 for w in ws if w.throughput_only), "tile_nodes_chosen": hist,
+            "fv_packs": n_packs,
             "instances_with_status": bad}
 
 

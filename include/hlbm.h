@@ -267,6 +267,16 @@ int hlbm_sweep_step(hlbm_sweep_t* w, int64_t nsteps);
 int hlbm_sweep_tune(hlbm_sweep_t* w, int32_t trial_steps, int32_t* tile_nodes);
 /* nsteps sweep steps with the FV time of each instance summed into fv_ms[n]. */
 int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms);
+/* Packs the sweep's solvers into shared FV launches (enable = 1): solvers of
+ * the same precision whose sub-step counts lie within 25 % of each other,
+ * up to 16, are retiled so that together they take one block per SM, and
+ * each lattice step runs their FV sub-steps in one cooperative launch of the
+ * tensor-memory kernel (each solver keeps its own tables, counters and
+ * buffers).  Solvers with outer_fv = 1 or a forced fv_kernel stay alone.
+ * enable = 0 undoes it (default tiling).  n_packs (may be NULL) receives
+ * the number of packs.  Results do not change: a node's arithmetic does not
+ * depend on its tile or launch.  hlbm_sweep_tune after this call undoes it. */
+int hlbm_sweep_pack(hlbm_sweep_t* w, int32_t enable, int32_t* n_packs);
 const char* hlbm_sweep_last_error(const hlbm_sweep_t* w);
 void hlbm_sweep_destroy(hlbm_sweep_t* w);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "hlbm_sweep_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "hlbm_sweep_tune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "hlbm_sweep_fv_time": (C.c_int, [C.c_void_p, C.c_int64, _dp]),
+    "hlbm_sweep_pack": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "hlbm_sweep_last_error": (C.c_char_p, [C.c_void_p]),
     "hlbm_sweep_destroy": (None, [C.c_void_p]),
     "hlbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),

@@ -329,6 +329,14 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
     return HLBM_OK;
 }
 
+// the bookkeeping of step_fv when the FV sub-steps ran in a packed launch
+template <typename T>
+void step_fv_packed_done(hlbm* h) {
+    Dev<T>& d = dev_of<T>(h);
+    if (d.n_sub & 1) h->ui = 1 - h->ui;
+    bind(h, d);
+}
+
 template <typename T>
 int step_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
     Dev<T>& d = dev_of<T>(h);
@@ -1198,6 +1206,9 @@ struct hlbm_sweep {
     cudaEvent_t ev_main = nullptr;
     std::vector<double> fv_ms;          // FV time of each instance, summed since the last reset
     std::vector<int32_t> tile_nodes;    // target nodes per FV tile chosen by the tuner (0: default)
+    std::vector<std::vector<int>> packs; // instances whose FV sub-steps share one launch
+    std::vector<int> pack_of;           // instance -> pack index, -1 when launched alone
+    std::vector<cudaEvent_t> ev_pack;   // one per pack: its launch is done
     std::string err;
 };
 
@@ -1214,6 +1225,35 @@ int inst_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
 }
 int inst_retile(hlbm* h, int tiles) {
     return h->dtype != HLBM_F64 ? build_tiles<float>(h, tiles) : build_tiles<double>(h, tiles);
+}
+
+// The FV sub-steps of pack p's instances in one cooperative launch of the
+// tensor-memory kernel on the sweep's FV stream.
+template <typename T>
+int pack_fv(hlbm_sweep* w, size_t p, const std::vector<PendingStep>& ps) {
+    const std::vector<int>& mem = w->packs[p];
+    FvPack<T> pk{};
+    pk.n = (int)mem.size();
+    int blocks = 0;
+    size_t smem = 0;
+    for (int k = 0; k < pk.n; ++k) {
+        hlbm* h = w->inst[mem[k]];
+        Dev<T>& d = dev_of<T>(h);
+        pk.block0[k] = blocks;
+        pk.d[k] = d;
+        pk.a[k] = ps[mem[k]].a;
+        pk.g0[k] = (T*)d.fu_in;
+        pk.g1[k] = d.fu_out;
+        blocks += d.n_tiles;
+        smem = std::max(smem, fv_tmem_smem_bytes<T>(d.tile_cap, d.halo_cap, d.n_sub, d.tile_ocap));
+    }
+    cudaError_t e = launch_fv_tmem_pack<T>(pk, blocks, smem, w->fv);
+    if (e != cudaSuccess) {
+        w->err = std::string("packed FV launch: ") + cudaGetErrorString(e);
+        return HLBM_ECUDA;
+    }
+    for (int i : mem) step_fv_packed_done<T>(w->inst[i]);
+    return HLBM_OK;
 }
 
 // One step of every instance.  Instance i issues its lattice part on its
@@ -1233,7 +1273,17 @@ int sweep_one_step(hlbm_sweep* w, bool time_fv) {
         }
         cudaEventRecord(w->ev_lat[i], w->streams[i]);
     }
+    for (size_t p = 0; p < w->packs.size(); ++p) {
+        for (int i : w->packs[p]) cudaStreamWaitEvent(w->fv, w->ev_lat[i], 0);
+        int rc = w->inst[w->packs[p][0]]->dtype != HLBM_F64 ? pack_fv<float>(w, p, ps) : pack_fv<double>(w, p, ps);
+        if (rc != HLBM_OK) return rc;
+        cudaEventRecord(w->ev_pack[p], w->fv);
+    }
     for (size_t i = 0; i < n; ++i) {
+        if (w->pack_of.size() == n && w->pack_of[i] >= 0) {
+            cudaEventRecord(w->ev_fv[i], w->fv);  // after its pack's launch on the same stream
+            continue;
+        }
         cudaStreamWaitEvent(w->fv, w->ev_lat[i], 0);
         int rc = inst_fv(w->inst[i], w->fv, ps[i], time_fv ? w->fv_t0[i] : nullptr, time_fv ? w->fv_t1[i] : nullptr);
         if (rc != HLBM_OK) {
@@ -1490,6 +1540,10 @@ int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, doub
     }
     hlbm_sweep* w = nullptr;
     if (rc == HLBM_OK) rc = hlbm_sweep_create(7, inst.data(), cuda_stream, &w);
+    if (rc == HLBM_OK) {
+        rc = hlbm_sweep_pack(w, 1, nullptr);
+        if (rc != HLBM_OK) err = w->err;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == HLBM_OK && sweep_ms) {
         cudaEventCreate(&e0);
@@ -1763,6 +1817,12 @@ int hlbm_sweep_step(hlbm_sweep_t* w, int64_t nsteps) {
 
 int hlbm_sweep_tune(hlbm_sweep_t* w, int32_t trial_steps, int32_t* tile_nodes) {
     if (!w || trial_steps < 1) return HLBM_EINVAL;
+    // the tuner times every solver's own launch: no packs
+    for (cudaEvent_t e : w->ev_pack)
+        if (e) cudaEventDestroy(e);
+    w->ev_pack.clear();
+    w->packs.clear();
+    w->pack_of.assign(w->inst.size(), -1);
     const int candidates[] = {256, 512, 1024, 1536};
     const size_t n = w->inst.size();
     std::vector<double> best(n, 1e300);
@@ -1805,6 +1865,99 @@ int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms) {
     return rc;
 }
 
+int hlbm_sweep_pack(hlbm_sweep_t* w, int32_t enable, int32_t* n_packs) {
+    if (!w) return HLBM_EINVAL;
+    for (cudaEvent_t e : w->ev_pack)
+        if (e) cudaEventDestroy(e);
+    w->ev_pack.clear();
+    w->packs.clear();
+    const int n = (int)w->inst.size();
+    w->pack_of.assign(n, -1);
+    int rc = HLBM_OK;
+    if (enable) {
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        std::vector<int> order;
+        for (int i = 0; i < n; ++i)
+            if (w->inst[i]->patch.outer_fv == 0 && w->inst[i]->patch.fv_kernel == HLBM_FV_AUTO) order.push_back(i);
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            const hlbm *ha = w->inst[a], *hb = w->inst[b];
+            if ((ha->dtype == HLBM_F64) != (hb->dtype == HLBM_F64)) return ha->dtype != HLBM_F64;
+            if (ha->patch.n_sub != hb->patch.n_sub) return ha->patch.n_sub < hb->patch.n_sub;
+            return a < b;
+        });
+        auto tile_max = [](const hlbm* h) { return h->dtype != HLBM_F64 ? fv_tile_max<float>() : fv_tile_max<double>(); };
+        auto min_tiles = [&](const hlbm* h) { return (h->patch.n_nodes + tile_max(h) - 1) / tile_max(h); };
+        size_t k = 0;
+        while (k < order.size() && rc == HLBM_OK) {
+            // a group: same precision, sub-step counts within 25 %, at most
+            // kFvPackMax solvers, one block per SM in all
+            std::vector<int> g{order[k]};
+            int need = min_tiles(w->inst[order[k]]);
+            const hlbm* h0 = w->inst[order[k]];
+            size_t j = k + 1;
+            while (j < order.size()) {
+                const hlbm* h = w->inst[order[j]];
+                if ((h->dtype == HLBM_F64) != (h0->dtype == HLBM_F64) || h->patch.n_sub * 4 > h0->patch.n_sub * 5 ||
+                    (int)g.size() >= kFvPackMax || need + min_tiles(h) > sms)
+                    break;
+                need += min_tiles(h);
+                g.push_back(order[j]);
+                ++j;
+            }
+            k = j;
+            if (g.size() < 2) continue;
+            // share the SMs in proportion to each solver's FV work
+            double wsum = 0;
+            for (int i : g) wsum += (double)w->inst[i]->patch.n_nodes * w->inst[i]->patch.n_sub;
+            std::vector<int> tiles;
+            int tsum = 0;
+            for (int i : g) {
+                const hlbm* h = w->inst[i];
+                int t = (int)std::floor(sms * (double)h->patch.n_nodes * h->patch.n_sub / wsum);
+                t = std::min(t, std::max(1, h->patch.n_nodes / 64));
+                t = std::max(t, min_tiles(h));
+                tiles.push_back(t);
+                tsum += t;
+            }
+            while (tsum > sms) {
+                size_t big = 0;
+                for (size_t q = 0; q < g.size(); ++q)
+                    if (tiles[q] - min_tiles(w->inst[g[q]]) > tiles[big] - min_tiles(w->inst[g[big]])) big = q;
+                if (tiles[big] <= min_tiles(w->inst[g[big]])) break;
+                --tiles[big];
+                --tsum;
+            }
+            bool ok = tsum <= sms;
+            for (size_t q = 0; q < g.size() && ok && rc == HLBM_OK; ++q) {
+                rc = inst_retile(w->inst[g[q]], tiles[q]);
+                ok = rc == HLBM_OK && w->inst[g[q]]->fv_kind == HLBM_FV_TMEM && w->inst[g[q]]->n_tiles == tiles[q];
+            }
+            if (rc != HLBM_OK) {
+                w->err = "packing: " + w->inst[g[0]]->err;
+                break;
+            }
+            if (!ok) {
+                for (int i : g) rc = rc == HLBM_OK ? inst_retile(w->inst[i], 0) : rc;
+                continue;
+            }
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                rc = HLBM_ECUDA;
+                break;
+            }
+            w->ev_pack.push_back(e);
+            for (int i : g) w->pack_of[i] = (int)w->packs.size();
+            w->packs.push_back(g);
+        }
+    } else {
+        for (int i = 0; i < n && rc == HLBM_OK; ++i) rc = inst_retile(w->inst[i], 0);
+    }
+    if (n_packs) *n_packs = (int32_t)w->packs.size();
+    return rc;
+}
+
 const char* hlbm_sweep_last_error(const hlbm_sweep_t* w) { return w ? w->err.c_str() : "null sweep"; }
 
 void hlbm_sweep_destroy(hlbm_sweep_t* w) {
@@ -1819,7 +1972,7 @@ void hlbm_sweep_destroy(hlbm_sweep_t* w) {
         cudaStreamSynchronize(w->fv);
         cudaStreamDestroy(w->fv);
     }
-    for (auto* v : {&w->ev_lat, &w->ev_fv, &w->ev_done, &w->fv_t0, &w->fv_t1})
+    for (auto* v : {&w->ev_lat, &w->ev_fv, &w->ev_done, &w->fv_t0, &w->fv_t1, &w->ev_pack})
         for (cudaEvent_t e : *v)
             if (e) cudaEventDestroy(e);
     if (w->ev_main) cudaEventDestroy(w->ev_main);

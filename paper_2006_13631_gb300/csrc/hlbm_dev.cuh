@@ -285,6 +285,18 @@ template <typename T> cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs
 template <typename T> size_t fv_tmem_smem_bytes(int tile_cap, int halo_cap, int n_sub, int ocap);
 template <typename T> int fv_tmem_tile_capacity(size_t smem);
 template <typename T> cudaError_t launch_fv_tmem(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+// several solvers' FV sub-steps in one launch of the tensor-memory kernel
+constexpr int kFvPackMax = 16;
+template <typename T>
+struct FvPack {
+    int n;                   // items
+    int block0[kFvPackMax];  // first block of each item (its tile 0)
+    Dev<T> d[kFvPackMax];
+    StepArgs a[kFvPackMax];
+    T* g0[kFvPackMax];       // record buffers: sub-step m reads g0 when m is even
+    T* g1[kFvPackMax];
+};
+template <typename T> cudaError_t launch_fv_tmem_pack(const FvPack<T>& pk, int blocks, size_t smem, cudaStream_t s);
 template <typename T> void launch_force(const Dev<T>& d, int64_t t_out, cudaStream_t s);  // 2 launches
 template <typename T> void launch_patch_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                               double* f9, cudaStream_t s);

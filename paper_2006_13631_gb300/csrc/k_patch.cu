@@ -1086,11 +1086,11 @@ __device__ __forceinline__ void fv_tmem_node(const Dev<T>& d, const unsigned cha
     }
 }
 
+// The body of the tensor-memory FV kernel for tile `tile` of the solver d
+// (one block); k_fv_tmem runs one solver, k_fv_tmem_pack several.
 template <typename T>
-__global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tmem(Dev<T> d, StepArgs a, T* g0, T* g1) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ int abort_sh;
-    __shared__ uint32_t tmem_base_sh;
+__device__ __forceinline__ void fv_tmem_body(const Dev<T>& d, const StepArgs& a, T* g0, T* g1, const int tile,
+                                             unsigned char* sm, int& abort_sh, uint32_t& tmem_base_sh) {
     const int cap = d.tile_cap, hcap = d.halo_cap;
     const TmemSmem L = tmem_smem_layout<T>(cap, hcap, d.n_sub, d.tile_ocap);
     T* own0 = reinterpret_cast<T*>(sm + L.own0);
@@ -1098,7 +1098,6 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tmem(Dev<T> d, StepAr
     T* halo = reinterpret_cast<T*>(sm + L.halo);
     T* uv = reinterpret_cast<T*>(sm + L.uv);
     int32_t* hid = reinterpret_cast<int32_t*>(sm + L.hid);
-    const int tile = blockIdx.x;
     const int p0 = d.tile_start[tile], p1 = d.tile_start[tile + 1], tile_n = p1 - p0;
     const int h0 = d.halo_ptr[tile], halo_n = d.halo_ptr[tile + 1] - h0;
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5;
@@ -1247,27 +1246,61 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tmem(Dev<T> d, StepAr
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tmem(Dev<T> d, StepArgs a, T* g0, T* g1) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int abort_sh;
+    __shared__ uint32_t tmem_base_sh;
+    fv_tmem_body<T>(d, a, g0, g1, blockIdx.x, sm, abort_sh, tmem_base_sh);
+}
+
+// Several solvers' FV sub-steps in one cooperative launch: block b runs
+// tile b - block0 of the item whose range [block0, next block0) holds b.
+// Each item keeps its own tables, counters, sub-step count and buffers;
+// items only share the GPU.
+template <typename T>
+__global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tmem_pack(const __grid_constant__ FvPack<T> pk) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int abort_sh;
+    __shared__ uint32_t tmem_base_sh;
+    int i = 0;
+    while (i + 1 < pk.n && pk.block0[i + 1] <= (int)blockIdx.x) ++i;
+    fv_tmem_body<T>(pk.d[i], pk.a[i], pk.g0[i], pk.g1[i], (int)blockIdx.x - pk.block0[i], sm, abort_sh,
+                    tmem_base_sh);
+}
+
+template <typename T>
+cudaError_t launch_fv_tmem_pack(const FvPack<T>& pk, int blocks, size_t smem, cudaStream_t s) {
+    FvPack<T> p = pk;
+    void* args[] = {&p};
+    return cudaLaunchCooperativeKernel((const void*)k_fv_tmem_pack<T>, dim3(blocks), dim3(kSmemThreads<T>), args,
+                                       smem, s);
+}
+
+template <typename T>
 int fv_tmem_tile_capacity(size_t smem) {
     if (smem == 0) return 0;
     int dev = 0, sms = 0, per = 0, maxsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, k_fv_tmem<T>) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    const int limit = maxsm - (int)fa.sharedSizeBytes;
-    if (smem > (size_t)limit) return 0;
-    if (cudaFuncSetAttribute(k_fv_tmem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_tmem<T>, kSmemThreads<T>, smem);
     // each block allocates all 512 TMEM columns of its SM, so a second block
     // on the same SM would wait for the first: only run where one fits
-    return per == 1 ? sms : 0;
+    for (const void* fn : {(const void*)k_fv_tmem<T>, (const void*)k_fv_tmem_pack<T>}) {
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const int limit = maxsm - (int)fa.sharedSizeBytes;
+        if (smem > (size_t)limit) return 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kSmemThreads<T>, smem);
+        if (per != 1) return 0;
+    }
+    return sms;
 }
 
 template <typename T>
@@ -1508,6 +1541,7 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
     template size_t fv_tmem_smem_bytes<T>(int, int, int, int);                                                \
     template int fv_tmem_tile_capacity<T>(size_t);                                                            \
     template cudaError_t launch_fv_tmem<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
+    template cudaError_t launch_fv_tmem_pack<T>(const FvPack<T>&, int, size_t, cudaStream_t);                 \
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \
     template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);
 HLBM_INST(float)

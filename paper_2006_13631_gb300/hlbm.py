@@ -344,6 +344,12 @@ class Sweep:
         self._check(N.load().hlbm_sweep_tune(self.h, int(trial_steps), out))
         return list(out)
 
+    def pack(self, enable: bool = True):
+        """Share FV launches between solvers (hlbm_sweep_pack); returns the number of packs."""
+        out = C.c_int32()
+        self._check(N.load().hlbm_sweep_pack(self.h, int(bool(enable)), C.byref(out)))
+        return out.value
+
     def fv_time(self, nsteps: int = 1):
         out = np.zeros(len(self.solvers))
         self._check(N.load().hlbm_sweep_fv_time(self.h, int(nsteps), _dp(out)))

@@ -79,6 +79,23 @@ def test_sweep_equals_individual_steps():
     torch.cuda.synchronize()
     for a, b in zip(alone, batch):
         _same(_state(a), _state(b))
+    # packed: the FP32-arithmetic solvers with 26 sub-steps (FP32 and BF16
+    # storage) share one FV launch; still the same results
+    assert sw.pack() == 1
+    for k in (3, 6):
+        sw.step(k)
+        for s in alone:
+            s.step(k)
+        torch.cuda.synchronize()
+        for a, b in zip(alone, batch):
+            assert b.status == 0
+            _same(_state(a), _state(b))
+    assert sw.pack(False) == 0
+    sw.step(2)
+    for s in alone:
+        s.step(2)
+    for a, b in zip(alone, batch):
+        _same(_state(a), _state(b))
     sw.close()
 
 
