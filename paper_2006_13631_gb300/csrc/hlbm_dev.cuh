@@ -189,6 +189,19 @@ __device__ __forceinline__ int locate_dev(const Dev<T>& d, double qx, double qy,
     double best_min = -1.0e300;
     for (int e = d.bstart[b]; e < d.bstart[b + 1]; ++e) {
         int k = d.bitems[e];
+        // FP32 estimate from vertex a: lambda = (1, 0, 0) + grad lambda . (q - a).
+        // Its error (a few 1e-6 for any triangle of the bin) is far below the
+        // -1e-3 under which a triangle is skipped, so every triangle the exact
+        // test below would accept (smallest coordinate >= -1e-12) gets it.
+        {
+            const double* g = d.trigeo + 8 * (int64_t)k;
+            const float* gr = d.trigrad + 6 * (int64_t)k;
+            const float px = float(__dsub_rn(qx, g[0])), py = float(__dsub_rn(qy, g[1]));
+            const float e0 = 1.0f + fmaf(gr[0], px, gr[1] * py);
+            const float e1 = fmaf(gr[2], px, gr[3] * py);
+            const float e2 = fmaf(gr[4], px, gr[5] * py);
+            if (fminf(e0, fminf(e1, e2)) < -1e-3f) continue;
+        }
         double la, lb, lc;
         bary_rn(d.trigeo + 8 * (int64_t)k, qx, qy, la, lb, lc);
         double mn = la < lb ? la : lb;
@@ -220,6 +233,39 @@ __device__ __forceinline__ int locate_from_node(const Dev<T>& d, int P, double q
     // holding q (estimate below -1e-5, far beyond its ~1e-7 error); the
     // others take the exact FP64 test
     const float dx = float(__dsub_rn(qx, d.xy[2 * P])), dy = float(__dsub_rn(qy, d.xy[2 * P + 1]));
+    if constexpr (sizeof(T) == 4) {
+        // FP32 populations: when a single star triangle survives the estimate
+        // and holds q clearly inside (every estimate above 1e-5), the exact
+        // test can only accept it, so its decision is taken without FP64;
+        // the estimates serve as the (FP32) interpolation weights
+        int count = 0, k1 = -1, slot1 = 0;
+        float m1 = 0.f, est[3] = {0.f, 0.f, 0.f};
+        for (int i = d.tstart[P]; i < d.tstart[P + 1] && count < 2; ++i) {
+            const int k = d.tlist[i];
+            const int32_t* v = d.tri + 3 * k;
+            const int slot = v[0] == P ? 0 : (v[1] == P ? 1 : 2);
+            const float* gr = d.trigrad + 6 * (int64_t)k;
+            const float l0 = fmaf(gr[0], dx, gr[1] * dy) + (slot == 0 ? 1.0f : 0.0f);
+            const float l1 = fmaf(gr[2], dx, gr[3] * dy) + (slot == 1 ? 1.0f : 0.0f);
+            const float l2 = fmaf(gr[4], dx, gr[5] * dy) + (slot == 2 ? 1.0f : 0.0f);
+            const float mn = fminf(l0, fminf(l1, l2));
+            if (mn < -1e-5f) continue;
+            if (++count == 1) {
+                k1 = k;
+                slot1 = slot;
+                m1 = mn;
+                est[0] = l0;
+                est[1] = l1;
+                est[2] = l2;
+            }
+        }
+        if (count == 1 && m1 > 1e-5f && est[slot1] > 1e-5f) {
+            lam[0] = est[0];
+            lam[1] = est[1];
+            lam[2] = est[2];
+            return k1;
+        }
+    }
     for (int e = d.tstart[P]; e < d.tstart[P + 1]; ++e) {
         int k = d.tlist[e];
         const int32_t* v = d.tri + 3 * k;
