@@ -224,6 +224,63 @@ __device__ __forceinline__ int locate_dev(const Dev<T>& d, double qx, double qy,
 // the star can come within the 1e-12 tolerance (triangles do not overlap);
 // that triangle is then the answer of the full search as well, with the
 // same coordinates.  Otherwise the full search runs.
+// locate_dev with the candidates of the bin spread over the lanes of a warp
+// (all 32 lanes call it with the same point): the same exact test, and the
+// same choice (largest smallest coordinate, ties to the earliest candidate,
+// i.e. the lowest triangle index).  Every lane returns the result.
+template <typename T>
+__device__ __forceinline__ int locate_warp(const Dev<T>& d, double qx, double qy, double lam[3]) {
+    const int lane = threadIdx.x & 31;
+    int bi = (int)floor(__ddiv_rn(__dsub_rn(qx, d.gbx0), d.gbh));
+    int bj = (int)floor(__ddiv_rn(__dsub_rn(qy, d.gby0), d.gbh));
+    if (bi < 0 || bj < 0 || bi >= d.gnbx || bj >= d.gnby) return -1;
+    const int b = bj * d.gnbx + bi;
+    int best_e = 0x7fffffff, best = -1;
+    double best_min = -1.0e300, l0 = 0, l1 = 0, l2 = 0;
+    for (int e = d.bstart[b] + lane; e < d.bstart[b + 1]; e += 32) {
+        const int k = d.bitems[e];
+        const double* g = d.trigeo + 8 * (int64_t)k;
+        const float* gr = d.trigrad + 6 * (int64_t)k;
+        const float px = float(__dsub_rn(qx, g[0])), py = float(__dsub_rn(qy, g[1]));
+        const float e0 = 1.0f + fmaf(gr[0], px, gr[1] * py);
+        const float e1 = fmaf(gr[2], px, gr[3] * py);
+        const float e2 = fmaf(gr[4], px, gr[5] * py);
+        if (fminf(e0, fminf(e1, e2)) < -1e-3f) continue;  // as in locate_dev
+        double la, lb, lc;
+        bary_rn(g, qx, qy, la, lb, lc);
+        double mn = la < lb ? la : lb;
+        if (lc < mn) mn = lc;
+        if (mn >= -1e-12 && mn > best_min) {  // lanes see their candidates in increasing e
+            best_min = mn;
+            best_e = e;
+            best = k;
+            l0 = la;
+            l1 = lb;
+            l2 = lc;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, best_min, off);
+        const int oe = __shfl_xor_sync(0xffffffffu, best_e, off);
+        const int ok = __shfl_xor_sync(0xffffffffu, best, off);
+        const double o0 = __shfl_xor_sync(0xffffffffu, l0, off);
+        const double o1 = __shfl_xor_sync(0xffffffffu, l1, off);
+        const double o2 = __shfl_xor_sync(0xffffffffu, l2, off);
+        if (om > best_min || (om == best_min && oe < best_e)) {
+            best_min = om;
+            best_e = oe;
+            best = ok;
+            l0 = o0;
+            l1 = o1;
+            l2 = o2;
+        }
+    }
+    lam[0] = l0;
+    lam[1] = l1;
+    lam[2] = l2;
+    return best;
+}
+
 template <typename T>
 __device__ __forceinline__ int locate_from_node(const Dev<T>& d, int P, double qx, double qy, double lam[3]) {
     int best = -1, best_slot = 0;

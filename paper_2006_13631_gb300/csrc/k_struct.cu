@@ -135,8 +135,10 @@ void launch_classify(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 // barycentric over the enclosing patch triangle.
 template <typename T, typename S>
 __global__ void k_fill(Dev<T> d, StepArgs a) {
+    // one warp per window node: the warp's lanes share the point location
     S* A = reinterpret_cast<S*>(d.fA);
-    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (b >= d.bplane) return;
     int8_t c = d.cls_cur[b];
     if (c == CLS_UNUSED) return;
@@ -148,15 +150,14 @@ __global__ void k_fill(Dev<T> d, StepArgs a) {
             if (px < (unsigned)d.bw && py < (unsigned)d.bh) prev = d.cls_prev[(int64_t)py * d.bw + px];
         }
         if (prev == CLS_DISC) return;
-        if (prev == CLS_UNUSED) atomicOr(d.status, HLBM_ST_UNUSED_TO_DISC);
+        if (prev == CLS_UNUSED && lane == 0) atomicOr(d.status, HLBM_ST_UNUSED_TO_DISC);
     }
     int64_t s = (int64_t)y * d.pitch + x;
     double lam[3];
-    int k = locate_dev(d, __dsub_rn((double)x, a.cx), __dsub_rn((double)y, a.cy), lam);
+    int k = locate_warp(d, __dsub_rn((double)x, a.cx), __dsub_rn((double)y, a.cy), lam);
     if (k < 0) {
-        atomicOr(d.status, HLBM_ST_FILL_NOT_LOCATED);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Store<T, S>::st(A, i * d.plane + s, T(0), d.fscale);
+        if (lane == 0) atomicOr(d.status, HLBM_ST_FILL_NOT_LOCATED);
+        if (lane < 9) Store<T, S>::st(A, lane * d.plane + s, T(0), d.fscale);
         return;
     }
     T st[12];
@@ -179,12 +180,13 @@ __global__ void k_fill(Dev<T> d, StepArgs a) {
     const T rr = d.rho0 + st[0];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        Store<T, S>::st(A, i * d.plane + s, feq_dev<T>(i, st[0], rr, st[1], st[2]) + d.k178 * st[3 + i], d.fscale);
+        if (lane == i)
+            Store<T, S>::st(A, i * d.plane + s, feq_dev<T>(i, st[0], rr, st[1], st[2]) + d.k178 * st[3 + i], d.fscale);
 }
 
 template <typename T>
 void launch_fill(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
-    with_store(d, [&]<typename S>() { k_fill<T, S><<<(unsigned)((d.bplane + 127) / 128), 128, 0, s>>>(d, a); });
+    with_store(d, [&]<typename S>() { k_fill<T, S><<<(unsigned)((d.bplane * 32 + 127) / 128), 128, 0, s>>>(d, a); });
 }
 
 // ------------------------------------------------------ stream-collide
