@@ -30,8 +30,14 @@ def _check(rc: int, h=None):
 
 
 def use_torch_allocator():
-    """Route the library's device allocations through torch's caching allocator."""
+    """Route the library's device allocations through torch's caching allocator.
+
+    Installed once per process: every solver keeps the callbacks it was created
+    with, so they must outlive all solvers (a second install would free the
+    first pair under solvers still holding them)."""
     global _callbacks
+    if _callbacks is not None:
+        return
     import torch
 
     def _alloc(nbytes, stream, ctx):
