@@ -280,6 +280,14 @@ class Workload:
     damping: float = 0.0
     y0: float = 0.0
     v0: float = 0.0
+    # two-level lattice: the nx x ny lattice (nx, ny odd) is a fine box whose
+    # node (0, 0) sits on node (ox, oy) of an nxc x nyc lattice of twice the
+    # spacing; bc_x, bc_y then belong to that coarse lattice
+    refine: int = 0
+    nxc: int = 0
+    nyc: int = 0
+    ox: int = 0
+    oy: int = 0
     mesh_args: dict = field(default_factory=dict)
 
     def mesh(self) -> PatchMesh:

@@ -47,6 +47,8 @@ class _Params(C.Structure):
         ("outer_fv", C.c_int),
         ("mass", C.c_double), ("stiffness", C.c_double), ("damping", C.c_double), ("y0", C.c_double),
         ("v0", C.c_double),
+        ("refine", C.c_int), ("nxc", C.c_int), ("nyc", C.c_int), ("ox", C.c_int), ("oy", C.c_int),
+        ("uxc_init", C.POINTER(C.c_double)), ("uyc_init", C.POINTER(C.c_double)),
     ]
 
 
@@ -70,7 +72,7 @@ def lib():
         L.orc_time.restype = C.c_int64
         for name in ("orc_struct_f", "orc_patch_f"):
             getattr(L, name).argtypes = [P, dp]
-        for name in ("orc_struct_macro", "orc_patch_macro"):
+        for name in ("orc_struct_macro", "orc_patch_macro", "orc_coarse_macro"):
             getattr(L, name).argtypes = [P, dp, dp, dp]
         L.orc_struct_class.argtypes = [P, C.POINTER(C.c_int8)]
         L.orc_classify_at.argtypes = [P, C.c_int64, C.POINTER(C.c_int8)]
@@ -190,7 +192,7 @@ def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
 class Oracle:
     """Serial FP64 MG-HLBM run for one workload (see ``inputs.Workload``)."""
 
-    def __init__(self, w, mesh=None, rho_init=None, u_init=None):
+    def __init__(self, w, mesh=None, rho_init=None, u_init=None, uc_init=None):
         self.w = w
         self.mesh = mesh if mesh is not None else w.mesh()
         rho = rho_init if rho_init is not None else w.rho_init()
@@ -218,6 +220,13 @@ class Oracle:
         p.mass, p.stiffness, p.damping = float(w.mass), float(w.stiffness), float(w.damping)
         p.y0, p.v0 = float(w.y0), float(w.v0)
         p.A, p.omega, p.vx, p.vy = w.A, w.omega, w.vx, w.vy
+        p.refine = int(getattr(w, "refine", 0))
+        if p.refine:
+            p.nxc, p.nyc, p.ox, p.oy = w.nxc, w.nyc, w.ox, w.oy
+            if uc_init is not None:
+                self._keep += [np.ascontiguousarray(uc_init[0], dtype=np.float64),
+                               np.ascontiguousarray(uc_init[1], dtype=np.float64)]
+                p.uxc_init, p.uyc_init = _dp(self._keep[-2]), _dp(self._keep[-1])
         self._h = lib().orc_create(C.byref(p))
         self.n = self.mesh.n_nodes
 
@@ -246,6 +255,12 @@ class Oracle:
     def struct_macro(self):
         r, ux, uy = (np.empty((self.w.ny, self.w.nx)) for _ in range(3))
         lib().orc_struct_macro(self._h, _dp(r), _dp(ux), _dp(uy))
+        return r, ux, uy
+
+    def coarse_macro(self):
+        """rho, ux, uy [nyc, nxc] of the coarse lattice at the last even time (R12)."""
+        r, ux, uy = (np.empty((self.w.nyc, self.w.nxc)) for _ in range(3))
+        lib().orc_coarse_macro(self._h, _dp(r), _dp(ux), _dp(uy))
         return r, ux, uy
 
     def struct_class(self):

@@ -51,6 +51,20 @@
  *      start of the step: v(t+1) = v(t) + (F_y(t) - c v(t) - k y(t))/m,
  *      y(t+1) = y(t) + v(t+1).  The patch sits at y(t) during step t; the
  *      wall velocity at sub-step m is v(t) + theta (v(t+1) - v(t)).
+ *  R12 Two-level lattice (the paper's refinement levels, Sec. 5; the
+ *      coupling is not given there): the lattice around the patch is a fine
+ *      box inside a coarse lattice of twice the spacing and twice the time
+ *      step (acoustic scaling, same lattice velocities), tau_c - 1/2 =
+ *      (tau_s - 1/2)/2 for the same viscosity.  Non-equilibrium parts scale
+ *      as tau dx (f^neq = -tau dt D f^eq); for post-collision populations,
+ *      f^neq_c = 2 (tau_c - 1)/(tau_s - 1) f^neq_f (tau_s != 1).  Per coarse
+ *      step (two fine steps t = 2T, 2T+1): the coarse lattice streams and
+ *      collides T -> T+1; the fine box's outermost ring takes, before each
+ *      fine step, the post-collision f^eq(rho, u) + f^neq_f rebuilt from the
+ *      coarse (rho, u, f^neq), linear along the box edge and, at t = 2T+1,
+ *      the mean of coarse times T and T+1, and is not streamed itself; after
+ *      the second fine step, the coarse nodes strictly inside the box take
+ *      the post-collision state of the fine node they sit on.
  */
 #include "hlbm_oracle.h"
 
@@ -136,6 +150,9 @@ struct orc {
     int64_t t;
     double Xprev, Yprev;
     double *Yh, *Vh; /* INDUCED motion: y and v at integer times (R11) */
+    double* fc[2];   /* R12: coarse post-collision state [9][nyc][nxc]; fc[ccur] at time t/2 */
+    int ccur;
+    int64_t Nc;
     int64_t mcap;
     int status;
 };
@@ -501,6 +518,134 @@ static double pull(int nx, int ny, int bcx, int bcy, const double* post, int64_t
     return post[i * N + s];
 }
 
+/* ------------------------------------------------------------------------ */
+/* two-level lattice (R12)                                                   */
+/* ------------------------------------------------------------------------ */
+static double tau_coarse(double tau_s) { return 0.5 + 0.5 * (tau_s - 0.5); }
+
+static int is_ring(const orc_t* o, int x, int y) {
+    return o->p.refine && (x == 0 || y == 0 || x == o->p.nx - 1 || y == o->p.ny - 1);
+}
+
+/* rho, ux, uy, f^neq of coarse node s at buffer b */
+static void coarse_state(const orc_t* o, int b, int64_t s, double* st) {
+    double f[9], fneq[9];
+    for (int i = 0; i < 9; ++i) f[i] = o->fc[b][i * o->Nc + s];
+    state_of(f, &st[0], &st[1], &st[2], fneq);
+    for (int i = 0; i < 9; ++i) st[3 + i] = fneq[i];
+}
+
+/* coarse nodes and weights giving a value at fine coordinate X along one
+ * axis: the coarse node itself (X even) or the cubic Lagrange midpoint rule
+ * over the four nearest coarse nodes (X odd) */
+static int axis_weights(int X, int* idx, double* w) {
+    if (X % 2 == 0) {
+        idx[0] = X / 2;
+        w[0] = 1.0;
+        return 1;
+    }
+    const int I0 = (X - 1) / 2;
+    const double cw[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
+    for (int k = 0; k < 4; ++k) {
+        idx[k] = I0 - 1 + k;
+        w[k] = cw[k];
+    }
+    return 4;
+}
+
+/* post-collision populations of fine ring node (x, y) at fine time t:
+ * rho, u and f^neq of the coarse lattice at the node's position (cubic
+ * along the box edge; at odd t the mean of coarse times t/2 -/+ 1/2), then
+ * f^eq(rho, u) + f^neq rescaled to the fine lattice */
+static void ghost_post(const orc_t* o, int x, int y, int64_t t, double* post) {
+    const int nxc = o->p.nxc;
+    int I[4], J[4];
+    double wi[4], wj[4];
+    const int ni = axis_weights(2 * o->p.ox + x, I, wi);
+    const int nj = axis_weights(2 * o->p.oy + y, J, wj);
+    double st[12] = {0};
+    const int nb = (t % 2 == 0) ? 1 : 2;
+    const int bufs[2] = {o->ccur, 1 - o->ccur};
+    for (int q = 0; q < nb; ++q)
+        for (int c = 0; c < nj; ++c)
+            for (int a = 0; a < ni; ++a) {
+                double w = wi[a] * wj[c] / nb, sc[12];
+                coarse_state(o, bufs[q], (int64_t)J[c] * nxc + I[a], sc);
+                for (int j = 0; j < 12; ++j) st[j] += w * sc[j];
+            }
+    const double ts = o->p.tau_s, tc = tau_coarse(ts);
+    const double acf = (ts - 1.0) / (2.0 * (tc - 1.0));
+    double feq[9];
+    orc_feq(st[0], st[1], st[2], feq);
+    for (int i = 0; i < 9; ++i) post[i] = feq[i] + acf * st[3 + i];
+}
+
+/* the fine ring of buffer b takes its post-collision ghost for fine time t;
+ * the pre-collision array holds it there (its moments are the ring's rho, u) */
+static void fill_ring(orc_t* o, int b, int64_t t) {
+    const int nx = o->p.nx, ny = o->p.ny;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!is_ring(o, x, y)) continue;
+            double post[9];
+            ghost_post(o, x, y, t, post);
+            for (int i = 0; i < 9; ++i) o->fs[b][i * o->N + (int64_t)y * nx + x] = post[i];
+        }
+}
+
+/* coarse stream and collide T -> T+1 from fc[ccur] into fc[1 - ccur] */
+static void coarse_step(orc_t* o) {
+    const int nxc = o->p.nxc, nyc = o->p.nyc;
+    const int64_t N = o->Nc;
+    const double* post = o->fc[o->ccur];
+    double* out = o->fc[1 - o->ccur];
+    const double tc = tau_coarse(o->p.tau_s);
+    int bad = 0;
+    for (int y = 0; y < nyc; ++y)
+        for (int x = 0; x < nxc; ++x) {
+            double f[9], q[9];
+            for (int i = 0; i < 9; ++i) f[i] = pull(nxc, nyc, o->p.bc_x, o->p.bc_y, post, N, x, y, i, NULL, &bad);
+            bgk_collide(f, tc, q);
+            for (int i = 0; i < 9; ++i) out[i * N + (int64_t)y * nxc + x] = q[i];
+        }
+}
+
+/* coarse nodes strictly inside the fine box take the post-collision state of
+ * the fine node under them (fine pre-collision state fs[cur] at an even
+ * time, collided); written into coarse buffer b */
+static void restrict_fine(orc_t* o, int b) {
+    const int nx = o->p.nx, nxc = o->p.nxc;
+    const double ts = o->p.tau_s, tc = tau_coarse(ts);
+    const double afc = 2.0 * (tc - 1.0) / (ts - 1.0);
+    for (int J = o->p.oy + 1; J < o->p.oy + (o->p.ny - 1) / 2; ++J)
+        for (int I = o->p.ox + 1; I < o->p.ox + (nx - 1) / 2; ++I) {
+            const int x = 2 * (I - o->p.ox), y = 2 * (J - o->p.oy);
+            const int64_t s = (int64_t)y * nx + x, sc = (int64_t)J * nxc + I;
+            double post[9];
+            if (o->cls_cur[s] == ORC_DISC) {
+                double f[9];
+                for (int i = 0; i < 9; ++i) f[i] = o->fs[o->cur][i * o->N + s];
+                bgk_collide(f, ts, post);
+            } else {
+                orc_feq(o->p.rho0, 0.0, 0.0, post); /* under the body: never read */
+            }
+            double r, ux, uy, fneq[9], feq[9];
+            state_of(post, &r, &ux, &uy, fneq);
+            orc_feq(r, ux, uy, feq);
+            for (int i = 0; i < 9; ++i) o->fc[b][i * o->Nc + sc] = feq[i] + afc * fneq[i];
+        }
+}
+
+void orc_coarse_macro(const orc_t* o, double* rho, double* ux, double* uy) {
+    for (int64_t s = 0; s < o->Nc; ++s) {
+        double st[12];
+        coarse_state(o, o->ccur, s, st);
+        rho[s] = st[0];
+        ux[s] = st[1];
+        uy[s] = st[2];
+    }
+}
+
 int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int n_iter, double* f9) {
     int64_t N = (int64_t)nx * ny;
     double* post = malloc((size_t)N * 9 * sizeof(double));
@@ -686,7 +831,9 @@ static void structured_step(orc_t* o, double cx, double cy) {
             int8_t c = o->cls_cur[s];
             if (c == ORC_UNUSED) continue;
             double post[9];
-            if (c == ORC_INTERP || o->cls_prev[s] != ORC_DISC) {
+            if (is_ring(o, x, y)) {
+                for (int i = 0; i < 9; ++i) post[i] = f[i * N + s]; /* R12: the ring holds its ghost */
+            } else if (c == ORC_INTERP || o->cls_prev[s] != ORC_DISC) {
                 if (c == ORC_DISC && o->cls_prev[s] == ORC_UNUSED) o->status |= ORC_ERR_UNUSED_TO_DISC;
                 post_from_patch(o, x, y, cx, cy, post);
             } else {
@@ -700,7 +847,7 @@ static void structured_step(orc_t* o, double cx, double cy) {
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int64_t s = (int64_t)y * nx + x;
-            if (o->cls_cur[s] != ORC_DISC) continue;
+            if (o->cls_cur[s] != ORC_DISC || is_ring(o, x, y)) continue;
             for (int i = 0; i < 9; ++i)
                 fn[i * N + s] = pull(nx, ny, o->p.bc_x, o->p.bc_y, o->fpost, N, x, y, i, o->cls_cur, &bad);
         }
@@ -1020,6 +1167,18 @@ orc_t* orc_create(const orc_params_t* p) {
     o->t = 0;
     o->Xprev = X;
     o->Yprev = Y;
+    if (p->refine) { /* R12: coarse lattice at equilibrium, then the box restricted onto it */
+        o->Nc = (int64_t)p->nxc * p->nyc;
+        for (int b = 0; b < 2; ++b) o->fc[b] = calloc((size_t)o->Nc * 9, sizeof(double));
+        for (int64_t sc = 0; sc < o->Nc; ++sc) {
+            double feq[9];
+            orc_feq(p->rho0, p->uxc_init ? p->uxc_init[sc] : p->u0x, p->uyc_init ? p->uyc_init[sc] : p->u0y, feq);
+            for (int i = 0; i < 9; ++i) o->fc[0][i * o->Nc + sc] = feq[i];
+        }
+        o->ccur = 0;
+        restrict_fine(o, 0);
+        fill_ring(o, 0, 0);
+    }
     record_force(o);
     return o;
 }
@@ -1040,6 +1199,7 @@ int orc_step(orc_t* o, int64_t nsteps) {
             o->Yh[t + 1] = o->Yh[t] + o->Vh[t + 1];
             if (!(fabs(o->Vh[t + 1]) < 1.0)) o->status |= ORC_ERR_FAST_MOTION;
         }
+        if (o->p.refine && t % 2 == 0) coarse_step(o); /* R12: T -> T+1 */
         double X, Y;
         lamina_pos(o, t, &X, &Y);
         double cx = o->p.xc + X, cy = o->p.yc + Y;
@@ -1056,6 +1216,11 @@ int orc_step(orc_t* o, int64_t nsteps) {
         o->Yprev = Y;
         o->t = t + 1;
         record_force(o);
+        if (o->p.refine && o->t % 2 == 0) { /* R12: restriction at T+1 */
+            restrict_fine(o, 1 - o->ccur);
+            o->ccur = 1 - o->ccur;
+        }
+        if (o->p.refine) fill_ring(o, o->cur, o->t);
     }
     return o->status;
 }
@@ -1187,6 +1352,8 @@ void orc_destroy(orc_t* o) {
     free(o->bitems);
     free(o->Yh);
     free(o->Vh);
+    free(o->fc[0]);
+    free(o->fc[1]);
     free(o->snap0);
     free(o->snap1);
     free(o->dstar);

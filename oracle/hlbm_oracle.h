@@ -53,6 +53,14 @@ typedef struct {
     int outer_fv;           /* 1: outer nodes take eq. 182 with its FV sums (R10) */
     /* INDUCED motion (R11): m y'' + c y' + k y = F_y, y(0) = y0, y'(0) = v0 */
     double mass, stiffness, damping, y0, v0;
+    /* two-level lattice (R12): refine = 1 makes the nx x ny lattice a fine box
+     * whose node (0, 0) sits on coarse node (ox, oy) of an nxc x nyc lattice of
+     * twice the spacing (bc_x, bc_y then apply to the coarse lattice; nx, ny
+     * odd); the coarse lattice starts at equilibrium with rho0 and the
+     * velocity uxc_init / uyc_init ([nyc*nxc], or NULL for u0) */
+    int refine, nxc, nyc, ox, oy;
+    const double* uxc_init;
+    const double* uyc_init;
 } orc_params_t;
 
 typedef struct orc orc_t;
@@ -69,6 +77,8 @@ int64_t orc_time(const orc_t* o);
 /* structured fields at the current time (pre-collision state) */
 void orc_struct_f(const orc_t* o, double* f9);               /* [9][ny][nx] */
 void orc_struct_macro(const orc_t* o, double* rho, double* ux, double* uy);
+/* R12: the coarse lattice's rho, u [nyc*nxc] at the last even fine time */
+void orc_coarse_macro(const orc_t* o, double* rho, double* ux, double* uy);
 void orc_struct_class(const orc_t* o, int8_t* cls);          /* class of the last step */
 /* patch fields at the current time */
 void orc_patch_f(const orc_t* o, double* f9);                /* [n][9] */

@@ -494,3 +494,108 @@ def test_fd_gradient_in_tau_converges():
     assert th1 == th2
     assert abs(g1[2] - g2[2]) < 1e-3 * abs(g2[2])
     assert abs(g2[2]) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# R12: two-level lattice (the structured refinement levels of Sec. 5)
+# --------------------------------------------------------------------------
+def _void_mesh():
+    """One triangle of outer nodes and no wall: with a zero-size lamina and a
+    tiny fictitious offset no lattice node is covered, so the run is the
+    lattice alone."""
+    xy = np.array([[-0.2, -0.2], [0.2, -0.2], [0.0, 0.2]])
+    return inputs.PatchMesh(xy, np.array([[0, 1, 2]], np.int32), np.full(3, inputs.KIND_OUTER, np.int8),
+                            np.zeros(3, np.int32))
+
+
+def _tgv(X, Y, U, k):
+    return -U * np.cos(k * X) * np.sin(k * Y), U * np.sin(k * X) * np.cos(k * Y)
+
+
+def _tgv_error(tau_f, refine, nc=48, box=49, o=12, T=200, U=1e-3):
+    """Max-norm velocity error, relative to the decayed amplitude, of a
+    Taylor-Green vortex (period nc coarse units, periodic) after T coarse
+    steps: u = U e^{-2 nu k^2 t} (-cos kx sin ky, sin kx cos ky), nu = (tau_c -
+    1/2)/3 in coarse units.  refine=0 runs the uniform coarse lattice."""
+    k = 2.0 * math.pi / nc
+    tau_c = 0.5 + 0.5 * (tau_f - 0.5)
+    dec = math.exp(-2.0 * (tau_c - 0.5) / 3.0 * k * k * T)
+    Xc, Yc = np.meshgrid(np.arange(nc) * 1.0, np.arange(nc) * 1.0)
+    if not refine:
+        w = inputs.Workload("tgv-coarse", nc, nc, 0.0, 0.0, nc / 2 + 0.3, nc / 2 + 0.3, tau_c, 1,
+                            inputs.MOTION_HARMONIC, delta_f=0.1, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC)
+        ob = oracle.Oracle(w, mesh=_void_mesh(), rho_init=np.ones((nc, nc)), u_init=_tgv(Xc, Yc, U, k))
+        ob.step(T)
+        assert ob.status == 0
+        _, ux, uy = ob.struct_macro()
+        ex, ey = _tgv(Xc, Yc, U * dec, k)
+        return max(np.abs(ux - ex).max(), np.abs(uy - ey).max()) / (U * dec), None
+    w = inputs.Workload("tgv-refined", box, box, 0.0, 0.0, 24.3, 24.3, tau_f, 1, inputs.MOTION_HARMONIC,
+                        delta_f=0.1, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC, refine=1, nxc=nc, nyc=nc,
+                        ox=o, oy=o)
+    xs = o + np.arange(box) / 2.0
+    Xf, Yf = np.meshgrid(xs, xs)
+    ob = oracle.Oracle(w, mesh=_void_mesh(), rho_init=np.ones((box, box)), u_init=_tgv(Xf, Yf, U, k),
+                       uc_init=_tgv(Xc, Yc, U, k))
+    ob.step(2 * T)
+    assert ob.status == 0
+    _, ux, uy = ob.struct_macro()
+    ex, ey = _tgv(Xf, Yf, U * dec, k)
+    ef = max(np.abs(ux - ex).max(), np.abs(uy - ey).max()) / (U * dec)
+    _, uxc, uyc = ob.coarse_macro()
+    ex, ey = _tgv(Xc, Yc, U * dec, k)
+    ec = max(np.abs(uxc - ex).max(), np.abs(uyc - ey).max()) / (U * dec)
+    return ef, ec
+
+
+@pytest.mark.parametrize("tau_f", [0.8, 1.3])
+def test_two_level_taylor_green_vortex(tau_f):
+    """The decaying Taylor-Green vortex (a closed form of the Navier-Stokes
+    equations) across a fine box inside a coarse lattice: the box, ring
+    included, is markedly more accurate than the uniform coarse lattice
+    (which it cannot be if the fine solution does not feed back, or if the
+    ring's rho, u, f^neq are rescaled, interpolated in space or in time
+    wrongly), and the coarse lattice keeps the uniform coarse lattice's
+    accuracy."""
+    e_uniform, _ = _tgv_error(tau_f, 0)
+    e_fine, e_coarse = _tgv_error(tau_f, 1)
+    assert e_uniform < 4e-3
+    assert e_fine < 0.65 * e_uniform
+    assert e_coarse < 1.3 * e_uniform
+
+
+def test_two_level_taylor_green_vortex_converges_at_second_order():
+    e1, _ = _tgv_error(0.8, 1)
+    e2, _ = _tgv_error(0.8, 1, nc=96, box=97, o=24, T=800)
+    assert e1 / e2 > 2.7
+
+
+def test_two_level_zero_disturbance_with_translating_lamina():
+    """Uniform stream on both levels with the lamina and its patch
+    translating along: every node of both lattices stays at f^eq(rho0, u0),
+    so the ring's rescaled f^neq and the restriction vanish exactly as they
+    must for a uniform state."""
+    w = _translating_case(0.02, 0.03)
+    w.nx, w.ny = 65, 61
+    w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 50, 48, 8, 8
+    uc = (np.full((48, 50), 0.02), np.full((48, 50), 0.03))
+    o = oracle.Oracle(w, rho_init=np.ones((61, 65)), u_init=(np.full((61, 65), 0.02), np.full((61, 65), 0.03)),
+                      uc_init=uc)
+    o.step(41)
+    assert o.status == 0
+    r, ux, uy = o.struct_macro()
+    disc = o.struct_class() == oracle.DISC
+    assert np.abs(ux[disc] - 0.02).max() < 1e-12 and np.abs(uy[disc] - 0.03).max() < 1e-12
+    assert np.abs(r[disc] - 1.0).max() < 1e-12
+    # coarse nodes over a fine node that was not computed (under the lamina)
+    # hold f^eq(rho0, 0); the rest must carry the stream
+    cov = np.zeros((48, 50), bool)
+    cov[8:8 + 31, 8:8 + 33] = ~disc[::2, ::2]
+    cov = np.pad(cov, 1)
+    cov = np.logical_or.reduce([cov[1 + a:49 + a, 1 + b:51 + b] for a in (-1, 0, 1) for b in (-1, 0, 1)])
+    assert 0 < cov.sum() < 80
+    r, ux, uy = o.coarse_macro()
+    assert np.abs(ux[~cov] - 0.02).max() < 1e-12 and np.abs(uy[~cov] - 0.03).max() < 1e-12
+    assert np.abs(r - 1.0).max() < 1e-12
+    r, ux, uy = o.patch_macro()
+    assert np.abs(ux - 0.02).max() < 1e-12 and np.abs(r - 1.0).max() < 1e-12
