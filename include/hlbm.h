@@ -91,6 +91,27 @@ typedef struct {
     const double* rho_init;
     const double* ux_init;
     const double* uy_init;
+    /* Two structured refinement levels (Sec. 5 runs its lattice on nested
+     * levels; the coupling is not given there).  refine = 1 makes the
+     * nx x ny lattice (nx, ny odd) a fine box whose node (0, 0) sits on node
+     * (ox, oy) of an nxc x nyc coarse lattice of twice the spacing and time
+     * step; bc_x, bc_y then apply to the coarse lattice, and tau_c - 1/2 =
+     * (tau_s - 1/2)/2 keeps the viscosity.  Each coarse step the box's
+     * outermost ring is rebuilt from the coarse rho, u and post-collision
+     * f^neq rescaled by (tau_s - 1)/(2 (tau_c - 1)) (cubic along the box
+     * edge, the mean of two coarse times at odd fine times), and the coarse
+     * nodes strictly inside the box take the fine post-collision state with
+     * f^neq rescaled back.  The coarse lattice starts at equilibrium with
+     * rho0 and uxc_init / uyc_init ([nyc*nxc], NULL: u0x, u0y), then takes
+     * the box's initial state.  hlbm_create fails with HLBM_EINVAL unless
+     * nx, ny are odd and at least 9, ox, oy >= 1, ox + (nx+1)/2 <= nxc - 1,
+     * oy + (ny+1)/2 <= nyc - 1, and tau_s differs from 1 and 3/2 by more
+     * than 1e-3. */
+    int32_t refine;
+    int32_t nxc, nyc;
+    int32_t ox, oy;
+    const double* uxc_init;
+    const double* uyc_init;
 } hlbm_grid_t;
 
 /* Body-fitted triangular patch around the lamina (Sec. 3, Sec. 4).
@@ -199,6 +220,12 @@ int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re
 int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double* rho_u,
                     double* ux_u, double* uy_u);
 
+/* Coarse lattice of a refined solver (hlbm_grid_t.refine = 1): rho, ux, uy
+ * [nyc*nxc] at the last even time (time - time % 2).  Coarse nodes over a
+ * fine node that was not computed hold rho0 and zero velocity.  HLBM_EINVAL
+ * for a solver without refinement. */
+int hlbm_get_coarse_fields(hlbm_t* h, double* rho, double* ux, double* uy);
+
 /* Node classes of the last step on the whole lattice [ny*nx]:
  * 0 discretization, 1 interpolation, 2 unused (Sec. 4). */
 int hlbm_get_class(hlbm_t* h, int8_t* cls);
@@ -226,6 +253,7 @@ typedef struct {
     int32_t fv_kernel; /* HLBM_FV_* in use                                */
     int32_t n_tiles;   /* FV tiles (blocks of the FV launch)               */
     double y, vy;      /* lamina displacement and velocity at `time`       */
+    int64_t n_coarse;  /* coarse lattice nodes (0 without refinement)      */
 } hlbm_info_t;
 int hlbm_info(hlbm_t* h, hlbm_info_t* info);
 

@@ -392,6 +392,24 @@ def workload(name: str) -> Workload:
         w = workload("lamina-small-f32")
         w.name, w.dtype = name, "f64"
         return w
+    if name.startswith("lamina-small-refined-"):
+        # the small case's 203x157 lattice as a fine box inside a 204x160
+        # coarse lattice of twice the spacing (box at coarse node (51, 40))
+        w = workload("lamina-small-f32")
+        w.name, w.dtype = name, name.split("-")[-1]
+        w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 204, 160, 51, 40
+        return w
+    if name == "lamina-4096-refined-f32":
+        # the 4096^2 workload's domain and lamina on two levels: a 2048^2
+        # coarse lattice of spacing 2 with a 1025^2 fine box (8 chords wide)
+        # around the lamina; the lamina centre is at (2048.3, 2048.2) in
+        # fine units of the whole domain, as in the uniform lattice
+        w = workload("lamina-4096-f32")
+        w.name = name
+        w.nx = w.ny = 1025
+        w.xc, w.yc = 512.3, 512.2
+        w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 2048, 2048, 768, 768
+        return w
     if name.startswith("lamina-1024-"):
         # the physics of the 256^2 FP64 workload (tau 0.6, beta 500, KC 0.25) at
         # 1024^2 with chord 32, thickness chord/50, 4 periods; the suffix names

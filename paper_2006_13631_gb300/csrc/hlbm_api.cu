@@ -52,6 +52,14 @@ struct hlbm {
 
     Dev<float> df{};
     Dev<double> dd{};
+    // two-level lattice: the coarse lattice (window-less), its population
+    // buffers (cbuf[cci] holds coarse time t/2 rounded down) and coupling
+    bool refine = false;
+    Dev<float> cf{};
+    Dev<double> cd{};
+    void* cbuf[2] = {nullptr, nullptr};
+    int cci = 0;
+    Refine ref{};
     void* fbuf[2] = {nullptr, nullptr};  // lattice populations
     void* sbox[2] = {nullptr, nullptr};  // window states
     int8_t* cls[2] = {nullptr, nullptr};
@@ -171,6 +179,17 @@ Dev<float>& dev_of<float>(hlbm* h) {
 template <>
 Dev<double>& dev_of<double>(hlbm* h) {
     return h->dd;
+}
+
+template <typename T>
+Dev<T>& cdev_of(hlbm* h);
+template <>
+Dev<float>& cdev_of<float>(hlbm* h) {
+    return h->cf;
+}
+template <>
+Dev<double>& cdev_of<double>(hlbm* h) {
+    return h->cd;
 }
 
 template <typename T>
@@ -301,8 +320,29 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
     phase_end(h, HLBM_PHASE_MOVE, ev, t > 0 ? 3 : 1, s);
     // 4. stream-collide t -> t+1 (eq. LBE)
     ev = phase_begin(h, s);
+    int nl = 1;
+    if (h->refine && (t & 1) == 0) {
+        // coarse lattice T -> T+1 (T = t/2)
+        Dev<T>& c = cdev_of<T>(h);
+        c.fA = (T*)h->cbuf[h->cci];
+        c.fB = (T*)h->cbuf[1 - h->cci];
+        StepArgs ac{};
+        launch_stream_collide<T>(c, ac, s);
+        ++nl;
+    }
     launch_stream_collide<T>(d, a, s);
-    phase_end(h, HLBM_PHASE_STREAM, ev, 1, s);
+    if (h->refine) {
+        if (t & 1) {
+            // the box's post-collision state at t+1 onto coarse time T+1
+            launch_restrict<T>(d, h->ref, d.fB, h->cbuf[1 - h->cci], a.bx0, a.by0, s);
+            h->cci = 1 - h->cci;
+            ++nl;
+        }
+        // the ring at t+1: coarse T+1 (t odd) or the mean of T and T+1
+        launch_ring<T>(d, h->ref, h->cbuf[h->cci], (t & 1) ? nullptr : h->cbuf[1 - h->cci], d.fB, s);
+        ++nl;
+    }
+    phase_end(h, HLBM_PHASE_STREAM, ev, nl, s);
     // 5a. the outer nodes' feed from the lattice at t and t+1
     launch_feed<T>(d, a, s);
     ps.a = a;
@@ -584,8 +624,10 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     const size_t lat_elem = g->dtype == HLBM_F16 || g->dtype == HLBM_BF16 ? 2 : sizeof(T);
     d.pitch = (g->nx + 31) / 32 * 32;
     d.plane = (int64_t)d.pitch * g->ny;
-    d.bc_x = g->bc_x;
-    d.bc_y = g->bc_y;
+    // with refinement the boundary kinds belong to the coarse lattice; the
+    // fine ring is rebuilt from it every step, whatever the fine pull wrote
+    d.bc_x = g->refine ? HLBM_BC_OUTFLOW : g->bc_x;
+    d.bc_y = g->refine ? HLBM_BC_OUTFLOW : g->bc_y;
     d.rho0 = T(g->rho0);
     d.tau_s = T(h->tau_s);
     d.tau_u = T(h->tau_s - 0.5);
@@ -818,6 +860,35 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         if (!h->fbuf[b] || !h->sbox[b] || !h->cls[b] || !h->fu[b])
             return fail(h, HLBM_ENOMEM, "device allocation failed (lattice %zu bytes per buffer)", fbytes);
     }
+    if (g->refine) {
+        Dev<T>& c = cdev_of<T>(h);
+        c = d;
+        c.nx = g->nxc;
+        c.ny = g->nyc;
+        c.pitch = (g->nxc + 31) / 32 * 32;
+        c.plane = (int64_t)c.pitch * g->nyc;
+        c.bc_x = g->bc_x;
+        c.bc_y = g->bc_y;
+        const double tau_c = 0.5 + 0.5 * (h->tau_s - 0.5);
+        c.tau_s = T(tau_c);
+        c.bw = c.bh = 0;  // no window: every coarse node is a discretization node
+        c.bplane = 0;
+        h->refine = true;
+        h->ref.nxc = g->nxc;
+        h->ref.nyc = g->nyc;
+        h->ref.pitch = c.pitch;
+        h->ref.plane = c.plane;
+        h->ref.ox = g->ox;
+        h->ref.oy = g->oy;
+        h->ref.acf = (h->tau_s - 1.0) / (2.0 * (tau_c - 1.0));
+        h->ref.afc = 2.0 * (tau_c - 1.0) / (h->tau_s - 1.0);
+        const size_t cbytes = (size_t)9 * c.plane * lat_elem;
+        for (int b = 0; b < 2; ++b) {
+            h->cbuf[b] = dev_alloc(h, cbytes);
+            if (!h->cbuf[b]) return fail(h, HLBM_ENOMEM, "device allocation failed (coarse lattice %zu bytes)", cbytes);
+            cudaMemsetAsync(h->cbuf[b], 0, cbytes, s);
+        }
+    }
     d.xy = upload(h, h->xy.data(), h->xy.size(), &rc);
     d.kind = upload(h, h->kind.data(), h->kind.size(), &rc);
     d.tri = upload(h, h->tri.data(), h->tri.size(), &rc);
@@ -894,6 +965,23 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     launch_classify<T>(d, a, s);
     d.sbox_old = (const T*)h->sbox[0];
     launch_patch_init<T>(d, a, s);
+    double* dcux = nullptr;
+    double* dcuy = nullptr;
+    if (h->refine) {
+        // coarse lattice: equilibrium at rho0 and its initial velocity, then
+        // the box's initial state restricted onto it and the ring from it
+        const size_t Nc = (size_t)g->nxc * g->nyc;
+        dcux = g->uxc_init ? upload(h, g->uxc_init, Nc, &rc) : nullptr;
+        dcuy = g->uyc_init ? upload(h, g->uyc_init, Nc, &rc) : nullptr;
+        if (rc != HLBM_OK) return rc;
+        Dev<T>& c = cdev_of<T>(h);
+        c.fA = (T*)h->cbuf[0];
+        c.fB = (T*)h->cbuf[1];
+        launch_init_struct<T>(c, nullptr, dcux, dcuy, g->u0x, g->u0y, s);
+        launch_restrict<T>(d, h->ref, d.fA, h->cbuf[0], a.bx0, a.by0, s);
+        launch_ring<T>(d, h->ref, h->cbuf[0], nullptr, d.fA, s);
+        h->cci = 0;
+    }
     h->ui = 1;
     bind(h, d);
     launch_force<T>(d, 0, s);
@@ -904,6 +992,8 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     dev_free(h, drho);
     dev_free(h, dux);
     dev_free(h, duy);
+    dev_free(h, dcux);
+    dev_free(h, dcuy);
     h->t = 0;
     h->Xprev = X0;
     h->Yprev = Y0;
@@ -944,6 +1034,7 @@ struct CkptHeader {
     uint32_t status, pad;
     double mass, stiffness, damping, y0, v0;  // INDUCED motion parameters
     double Yi, Vi;                            // and its state at t
+    int32_t refine, nxc, nyc, ox, oy, cci;    // two-level lattice
 };
 constexpr char kCkptMagic[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
 
@@ -969,7 +1060,7 @@ CkptHeader ckpt_header(hlbm* h) {
     Dev<T>& d = dev_of<T>(h);
     CkptHeader c{};
     std::memcpy(c.magic, kCkptMagic, 8);
-    c.version = 2;
+    c.version = 3;
     c.dtype = h->dtype;
     c.nx = d.nx;
     c.ny = d.ny;
@@ -1011,6 +1102,12 @@ CkptHeader ckpt_header(hlbm* h) {
     c.si = h->si;
     c.ui = h->ui;
     c.fi = h->fi;
+    c.refine = h->refine ? 1 : 0;
+    c.nxc = h->ref.nxc;
+    c.nyc = h->ref.nyc;
+    c.ox = h->ref.ox;
+    c.oy = h->ref.oy;
+    c.cci = h->cci;
     return c;
 }
 
@@ -1021,6 +1118,14 @@ std::vector<std::pair<void*, size_t>> ckpt_sections(hlbm* h, int64_t t) {
     const size_t lat = (d.store ? 2 : sizeof(T)) * 9 * (size_t)d.plane;
     const size_t box = sizeof(T) * 9 * (size_t)d.bplane;
     const size_t rec = sizeof(T) * kRec * (size_t)d.n;
+    if (h->refine) {
+        const size_t clat = (d.store ? 2 : sizeof(T)) * 9 * (size_t)h->ref.plane;
+        return {{h->fbuf[0], lat},         {h->fbuf[1], lat},         {h->sbox[0], box},
+                {h->sbox[1], box},         {h->cls[0], (size_t)d.bplane}, {h->cls[1], (size_t)d.bplane},
+                {h->fu[0], rec},           {h->fu[1], rec},           {d.rtype, sizeof(int32_t) * (size_t)d.n},
+                {d.rdonor, sizeof(int32_t) * (size_t)d.n}, {h->force, 2 * sizeof(double) * (size_t)(t + 1)},
+                {h->cbuf[0], clat},        {h->cbuf[1], clat}};
+    }
     return {{h->fbuf[0], lat},
             {h->fbuf[1], lat},
             {h->sbox[0], box},
@@ -1071,7 +1176,7 @@ int load_impl(hlbm* h, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(h, HLBM_EIO, "cannot open %s", path);
     CkptHeader c{};
-    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 2) {
+    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 3) {
         std::fclose(fp);
         return fail(h, HLBM_EIO, "%s is not a solver checkpoint", path);
     }
@@ -1083,8 +1188,9 @@ int load_impl(hlbm* h, const char* path) {
                       c.damping == m.damping && c.y0 == m.y0 && c.v0 == m.v0 &&
                       c.tau_s == m.tau_s && c.rho0 == m.rho0 && c.A == m.A && c.omega == m.omega &&
                       c.vx == m.vx && c.vy == m.vy && c.lamina_L == m.lamina_L && c.lamina_T == m.lamina_T &&
-                      c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash;
-    if (!same || c.t < 0 || ((c.ci | c.si | c.ui | c.fi) & ~1)) {
+                      c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash &&
+                      c.refine == m.refine && c.nxc == m.nxc && c.nyc == m.nyc && c.ox == m.ox && c.oy == m.oy;
+    if (!same || c.t < 0 || ((c.ci | c.si | c.ui | c.fi | c.cci) & ~1)) {
         std::fclose(fp);
         return fail(h, HLBM_EINVAL, "%s was written by a solver with other inputs", path);
     }
@@ -1145,6 +1251,7 @@ int load_impl(hlbm* h, const char* path) {
     h->si = c.si;
     h->ui = c.ui;
     h->fi = c.fi;
+    h->cci = c.cci;
     Dev<T>& d = dev_of<T>(h);
     e = cudaMemcpyAsync(h->status, &c.status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
     // the FV kernel counts sub-steps from t * n_sub
@@ -1369,6 +1476,19 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
     else if (!(p.delta_f > 1.5))
         rc = fail(h, HLBM_EINVAL, "delta_f = %g must exceed 1.5 (interpolation nodes outside the body)",
                   p.delta_f);
+    else if (grid->refine != 0 && grid->refine != 1)
+        rc = fail(h, HLBM_EINVAL, "refine = %d must be 0 or 1", grid->refine);
+    else if (grid->refine &&
+             (grid->nx % 2 == 0 || grid->ny % 2 == 0 || grid->nx < 9 || grid->ny < 9 || grid->ox < 1 ||
+              grid->oy < 1 || grid->ox + (grid->nx + 1) / 2 > grid->nxc - 1 ||
+              grid->oy + (grid->ny + 1) / 2 > grid->nyc - 1))
+        rc = fail(h, HLBM_EINVAL,
+                  "fine box %dx%d at coarse node (%d, %d) must have odd sizes >= 9 and keep one coarse node "
+                  "to the edges of the %dx%d coarse lattice",
+                  grid->nx, grid->ny, grid->ox, grid->oy, grid->nxc, grid->nyc);
+    else if (grid->refine && (std::fabs(tau_s - 1.0) <= 1e-3 || std::fabs(tau_s - 1.5) <= 1e-3))
+        rc = fail(h, HLBM_EINVAL, "tau_s = %g: the f^neq rescaling between levels needs tau_s != 1 and != 3/2",
+                  tau_s);
     if (rc == HLBM_OK) {
         h->xy.assign(p.xy, p.xy + 2 * (size_t)p.n_nodes);
         h->tri.assign(p.tri, p.tri + 3 * (size_t)p.n_tris);
@@ -1622,6 +1742,29 @@ int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double
     return rc;
 }
 
+int hlbm_get_coarse_fields(hlbm_t* h, double* rho, double* ux, double* uy) {
+    if (!h) return HLBM_EINVAL;
+    if (!h->refine) return fail(h, HLBM_EINVAL, "the solver has no coarse lattice");
+    const size_t N = (size_t)h->ref.nxc * h->ref.nyc;
+    double* buf = (double*)dev_alloc(h, 3 * N * sizeof(double));
+    if (!buf) return fail(h, HLBM_ENOMEM, "readback buffer");
+    if (h->dtype != HLBM_F64) {
+        h->cf.fA = (float*)h->cbuf[h->cci];
+        launch_struct_macro<float>(h->cf, buf, buf + N, buf + 2 * N, h->stream);
+    } else {
+        h->cd.fA = (double*)h->cbuf[h->cci];
+        launch_struct_macro<double>(h->cd, buf, buf + N, buf + 2 * N, h->stream);
+    }
+    double* dst[3] = {rho, ux, uy};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (dst[k]) e = cudaMemcpyAsync(dst[k], buf + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    int rc = e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "coarse field readback");
+    dev_free(h, buf);
+    return rc;
+}
+
 int hlbm_get_patch_f(hlbm_t* h, double* f9) {
     if (!h || !f9) return HLBM_EINVAL;
     const size_t n = h->patch.n_nodes;
@@ -1706,7 +1849,8 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->box_w = bw;
     info->box_h = bh;
     // refill, classify, fill, stream-collide, feed, FV sub-steps, force (2)
-    info->launches_per_step = 8;
+    info->launches_per_step = h->refine ? 10 : 8;  // refined: + ring, and per two steps coarse + restriction
+    info->n_coarse = h->refine ? (int64_t)h->ref.nxc * h->ref.nyc : 0;
     info->fv_kernel = h->fv_kind;
     info->n_tiles = h->n_tiles;
     if (h->motion.kind == HLBM_MOTION_INDUCED) {

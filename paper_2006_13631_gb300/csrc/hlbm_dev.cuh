@@ -360,6 +360,18 @@ __device__ __forceinline__ bool inside_curve(const Dev<T>& d, int x, int y, doub
     return __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)) < d.df2;
 }
 
+// ------------------------------------------------------ two-level lattice
+// Coarse lattice of a refined solver: sizes and layout of its population
+// buffers ([9][plane] with row pitch `pitch`, same storage type as the fine
+// lattice), the coarse node under fine node (0, 0), and the rescaling of
+// post-collision f^neq from coarse to fine (acf) and fine to coarse (afc).
+struct Refine {
+    int nxc, nyc, pitch;
+    int64_t plane;
+    int ox, oy;
+    double acf, afc;
+};
+
 // ---------------------------------------------------------------- launchers
 template <typename T> void launch_init_struct(const Dev<T>& d, const double* rho, const double* ux,
                                               const double* uy, double u0x, double u0y,
@@ -372,6 +384,13 @@ template <typename T> void launch_fill(const Dev<T>& d, const StepArgs& a, cudaS
 template <typename T> void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                                cudaStream_t s);
+// fine ring from coarse buffer c0 (c1 = NULL) or the mean of c0 and c1
+template <typename T> void launch_ring(const Dev<T>& d, const Refine& r, const void* c0, const void* c1,
+                                       void* dst, cudaStream_t s);
+// coarse nodes strictly inside the box from fine buffer src, classes of the
+// window at (bx0, by0)
+template <typename T> void launch_restrict(const Dev<T>& d, const Refine& r, const void* src, void* dst,
+                                           int bx0, int by0, cudaStream_t s);
 template <typename T> void launch_fv_coeffs(const Dev<T>& d, int lumped, Coef<T>* coef, cudaStream_t s);
 template <typename T> void launch_patch_init(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_refill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);

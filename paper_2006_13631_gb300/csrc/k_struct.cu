@@ -395,6 +395,136 @@ void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy, c
     with_store(d, [&]<typename S>() { k_struct_macro<T, S><<<grid, 256, 0, s>>>(d, rho, ux, uy); });
 }
 
+// ------------------------------------------------- two-level lattice
+// The fine lattice is a box inside a coarse lattice of twice the spacing
+// and twice the time step (Sec. 5 refinement levels), tau_c - 1/2 =
+// (tau_s - 1/2)/2.  Post-collision non-equilibrium parts scale as
+// (tau - 1) dx: f^neq_c = 2 (tau_c - 1)/(tau_s - 1) f^neq_f.
+
+// coarse nodes and weights of fine coordinate X along one axis: the coarse
+// node itself (X even) or the cubic midpoint rule (-1, 9, 9, -1)/16
+__device__ __forceinline__ int axis_stencil(int X, int* idx, double* w) {
+    if ((X & 1) == 0) {
+        idx[0] = X >> 1;
+        w[0] = 1.0;
+        return 1;
+    }
+    const int i0 = (X - 1) >> 1;
+    idx[0] = i0 - 1;
+    idx[1] = i0;
+    idx[2] = i0 + 1;
+    idx[3] = i0 + 2;
+    w[0] = w[3] = -1.0 / 16.0;
+    w[1] = w[2] = 9.0 / 16.0;
+    return 4;
+}
+
+// Ring of the fine box (x = 0, nx-1 or y = 0, ny-1): the post-collision
+// ghost f^eq(rho, u) + acf f^neq with rho, u, f^neq of the coarse lattice at
+// the node (cubic along the box edge), from coarse buffer c0 alone (even
+// fine time) or the mean of c0 and c1 (odd fine time), written to dst.
+template <typename T, typename S>
+__global__ void k_ring(Dev<T> d, Refine r, const void* c0v, const void* c1v, void* dstv) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nring = 2 * d.nx + 2 * (d.ny - 2);
+    if (k >= nring) return;
+    int x, y;
+    if (k < d.nx) {
+        x = (int)k;
+        y = 0;
+    } else if (k < 2 * d.nx) {
+        x = (int)k - d.nx;
+        y = d.ny - 1;
+    } else if (k < 2 * d.nx + d.ny - 2) {
+        x = 0;
+        y = 1 + (int)k - 2 * d.nx;
+    } else {
+        x = d.nx - 1;
+        y = 1 + (int)k - 2 * d.nx - (d.ny - 2);
+    }
+    int I[4], J[4];
+    double wi[4], wj[4];
+    const int ni = axis_stencil(2 * r.ox + x, I, wi);
+    const int nj = axis_stencil(2 * r.oy + y, J, wj);
+    const S* src[2] = {reinterpret_cast<const S*>(c0v), reinterpret_cast<const S*>(c1v)};
+    const int nb = c1v ? 2 : 1;
+    T adr = T(0), aux = T(0), auy = T(0), aneq[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) aneq[i] = T(0);
+    for (int q = 0; q < nb; ++q)
+        for (int c = 0; c < nj; ++c)
+            for (int a = 0; a < ni; ++a) {
+                const int64_t sc = (int64_t)J[c] * r.pitch + I[a];
+                T f[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = Store<T, S>::ld(src[q], i * r.plane + sc, d.finv);
+                T dr, rr, vx, vy;
+                moments_dev(f, d.rho0, dr, rr, vx, vy);
+                const T w = T(wi[a] * wj[c] / nb);
+                adr += w * dr;
+                aux += w * vx;
+                auy += w * vy;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) aneq[i] += w * (f[i] - feq_dev<T>(i, dr, rr, vx, vy));
+            }
+    const T rr = d.rho0 + adr, acf = T(r.acf);
+    S* dst = reinterpret_cast<S*>(dstv);
+    const int64_t s = (int64_t)y * d.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        Store<T, S>::st(dst, i * d.plane + s, feq_dev<T>(i, adr, rr, aux, auy) + acf * aneq[i], d.fscale);
+}
+
+template <typename T>
+void launch_ring(const Dev<T>& d, const Refine& r, const void* c0, const void* c1, void* dst, cudaStream_t s) {
+    const int nring = 2 * d.nx + 2 * (d.ny - 2);
+    with_store(d, [&]<typename S>() { k_ring<T, S><<<(nring + 127) / 128, 128, 0, s>>>(d, r, c0, c1, dst); });
+}
+
+// Coarse nodes strictly inside the box take the post-collision state of the
+// fine node under them, f^eq + afc f^neq, read from the fine buffer src;
+// nodes over a fine node that the last step did not compute (class in the
+// window at (bx0, by0)) take f^eq(rho0, 0), i.e. zero deviations.
+template <typename T, typename S>
+__global__ void k_restrict(Dev<T> d, Refine r, const void* srcv, void* dstv, int bx0, int by0) {
+    const int niw = (d.nx - 1) / 2 - 1, njw = (d.ny - 1) / 2 - 1;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= (int64_t)niw * njw) return;
+    const int ii = (int)(k % niw) + 1, jj = (int)(k / niw) + 1;
+    const int x = 2 * ii, y = 2 * jj;
+    const int64_t sc = (int64_t)(r.oy + jj) * r.pitch + (r.ox + ii);
+    S* dst = reinterpret_cast<S*>(dstv);
+    const unsigned rx = (unsigned)(x - bx0), ry = (unsigned)(y - by0);
+    if (rx < (unsigned)d.bw && ry < (unsigned)d.bh && d.cls_cur[(int64_t)ry * d.bw + rx] != CLS_DISC) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Store<T, S>::st(dst, i * r.plane + sc, T(0), d.fscale);
+        return;
+    }
+    const S* src = reinterpret_cast<const S*>(srcv);
+    const int64_t s = (int64_t)y * d.pitch + x;
+    T f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = Store<T, S>::ld(src, i * d.plane + s, d.finv);
+    T dr, rr, vx, vy;
+    moments_dev(f, d.rho0, dr, rr, vx, vy);
+    const T afc = T(r.afc);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T eq = feq_dev<T>(i, dr, rr, vx, vy);
+        Store<T, S>::st(dst, i * r.plane + sc, eq + afc * (f[i] - eq), d.fscale);
+    }
+}
+
+template <typename T>
+void launch_restrict(const Dev<T>& d, const Refine& r, const void* src, void* dst, int bx0, int by0,
+                     cudaStream_t s) {
+    const int64_t n = (int64_t)((d.nx - 1) / 2 - 1) * ((d.ny - 1) / 2 - 1);
+    if (n <= 0) return;
+    with_store(d, [&]<typename S>() {
+        k_restrict<T, S><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d, r, src, dst, bx0, by0);
+    });
+}
+
 #define HLBM_INST(T)                                                                                     \
     template void launch_init_struct<T>(const Dev<T>&, const double*, const double*, const double*, double, \
                                         double, cudaStream_t);                                          \
@@ -403,7 +533,9 @@ void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy, c
     template void launch_classify<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                      \
     template void launch_fill<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                          \
     template void launch_stream_collide<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                \
-    template void launch_struct_macro<T>(const Dev<T>&, double*, double*, double*, cudaStream_t);
+    template void launch_struct_macro<T>(const Dev<T>&, double*, double*, double*, cudaStream_t);        \
+    template void launch_ring<T>(const Dev<T>&, const Refine&, const void*, const void*, void*, cudaStream_t); \
+    template void launch_restrict<T>(const Dev<T>&, const Refine&, const void*, void*, int, int, cudaStream_t);
 HLBM_INST(float)
 HLBM_INST(double)
 
