@@ -384,6 +384,7 @@ def run_ours(args):
                 w.motion, w.A, w.omega = saved
             else:
                 setattr(w, attr, 0)
+    refined = None if args.no_refined else run_refined(stream, args, ms / args.steps, w)
     sweep = None if args.no_sweep else run_sweep(stream, args)
     gradient = None if args.no_gradient else run_gradient(stream, args)
     if rank != 0:
@@ -396,12 +397,52 @@ def run_ours(args):
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)" % (9 * bytes_per * w.nx * w.ny / 1e6)},
             "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "cpu_baseline": cpu, "e2e": e2e,
-            "reduced_storage": reduced or None, "variants": variants or None, "sweep": sweep, "gradient": gradient,
+            "reduced_storage": reduced or None, "variants": variants or None, "refined": refined, "sweep": sweep,
+            "gradient": gradient,
             "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_refined(stream, args, uniform_ms_per_step, uniform):
+    """The headline domain on two structured levels (Sec. 5 refinement): a
+    2048^2 coarse lattice of spacing 2 and a 1025^2 fine box around the
+    lamina, against the uniform 4096^2 lattice step timed above.  Node
+    updates per step: fine discretization nodes + half the coarse nodes +
+    the patch; fine-equivalent MLUPS counts the uniform lattice's nodes."""
+    import torch
+
+    import inputs
+    from paper_2006_13631_gb300 import Solver
+
+    if uniform.name != "lamina-4096-f32":
+        return None
+    w = inputs.workload("lamina-4096-refined-f32")
+    k = 2 * max(5, min(args.steps, 300) // 2)
+    with torch.cuda.stream(stream):
+        s = Solver(w, stream=stream.cuda_stream)
+        s.step(2 * max(2, args.warmup // 2))
+        torch.cuda.synchronize()
+        info = s.info()
+        s.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ph = s.profile_read()
+        s.profile(False)
+        ms = e0.elapsed_time(e1)
+        status = s.status
+        s.close()
+    updates = info["n_struct_disc"] + info["n_coarse"] / 2 + info["n_nodes"]
+    return {"workload": w.name, "coarse": f"{w.nxc}x{w.nyc}", "fine_box": f"{w.nx}x{w.ny}", "steps": k,
+            "ms_per_step": ms / k, "speedup_vs_uniform": uniform_ms_per_step / (ms / k),
+            "mlups": updates * k / (ms / 1e3) / 1e6,
+            "mlups_fine_equivalent": (uniform.nx * uniform.ny + info["n_nodes"]) * k / (ms / 1e3) / 1e6,
+            "phase_ms_per_step": {p: ph[p][0] / k for p in ph}, "status": status}
 
 
 def run_sweep(stream, args):
@@ -501,6 +542,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16/BF16 lattice-storage runs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-instance KC/beta sweep")
+    ap.add_argument("--no-refined", action="store_true", help="skip the two-level lattice run")
     ap.add_argument("--sweep-steps", type=int, default=10)
     ap.add_argument("--no-gradient", action="store_true", help="skip the Theta-gradient case")
     args = ap.parse_args()

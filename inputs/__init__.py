@@ -410,6 +410,15 @@ def workload(name: str) -> Workload:
         w.xc, w.yc = 512.3, 512.2
         w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 2048, 2048, 768, 768
         return w
+    if name.startswith("lamina-1024-refined-"):
+        # the 1024^2 workload's domain on two levels: a 512^2 coarse lattice
+        # of spacing 2 with a 257^2 fine box (8 chords wide) around the lamina
+        w = workload("lamina-1024-" + name.split("-")[-1])
+        w.name = name
+        w.nx = w.ny = 257
+        w.xc, w.yc = 128.3, 128.2
+        w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 512, 512, 192, 192
+        return w
     if name.startswith("lamina-1024-"):
         # the physics of the 256^2 FP64 workload (tau 0.6, beta 500, KC 0.25) at
         # 1024^2 with chord 32, thickness chord/50, 4 periods; the suffix names

@@ -173,3 +173,29 @@ def test_two_level_arguments_are_checked():
     with pytest.raises(HLBMError) as e:
         s.coarse_macro() if False else __import__("paper_2006_13631_gb300").hlbm_get_coarse_fields(s.h, 4, 4)
     assert e.value.code == -1
+
+
+def test_two_level_theta_agrees_with_the_uniform_lattice():
+    """The point of the levels (Sec. 5): the far field on a lattice of twice
+    the spacing leaves the hydrodynamic function of the uniform lattice
+    unchanged.  1024^2 domain, chord 32, KC 0.25, beta 500, tau 0.6, FP64,
+    8 periods (fit over the last 3); a fine box of 4 chords in a 512^2
+    coarse lattice.  Measured on a GB300: |Theta_2 - Theta_1| = 0.23 % of
+    |Theta_1| (box of 8 chords: 0.04 %)."""
+    from paper_2006_13631_gb300 import Solver
+
+    u = inputs.workload("lamina-1024-f64")
+    steps = int(round(8 * u.period))
+    s = Solver(u)
+    s.step(steps)
+    re1, im1, _ = s.gamma(discard=5.0, fit=3.0)
+    s.close()
+    w = inputs.workload("lamina-1024-refined-f64")
+    w.nx = w.ny = 129
+    w.xc, w.yc = 64.3, 64.2
+    w.ox = w.oy = 256 - 32
+    r = Solver(w)
+    r.step(steps)
+    re2, im2, _ = r.gamma(discard=5.0, fit=3.0)
+    assert r.status == 0
+    assert abs(complex(re2 - re1, im2 - im1)) < 5e-3 * abs(complex(re1, im1))
