@@ -248,7 +248,7 @@ typedef struct {
     int64_t n_struct_disc; /* discretization nodes in the last step       */
     int32_t n_nodes, n_tris, nnz, n_outer, n_wall_segments;
     int32_t box_w, box_h;  /* lattice window that follows the patch       */
-    int32_t launches_per_step;
+    int32_t launches_per_step; /* kernels per step (two levels: even steps)    */
     int32_t dtype;
     int32_t fv_kernel; /* HLBM_FV_* in use                                */
     int32_t n_tiles;   /* FV tiles (blocks of the FV launch)               */

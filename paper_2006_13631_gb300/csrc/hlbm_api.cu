@@ -332,14 +332,21 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
     }
     launch_stream_collide<T>(d, a, s);
     if (h->refine) {
+        // t odd: the box's post-collision state at t+1 onto coarse time T+1,
+        // which then becomes the current coarse buffer; the ring at t+1 from
+        // coarse T+1 (t odd) or the mean of T and T+1 (t even)
+        Couple cp{};
         if (t & 1) {
-            // the box's post-collision state at t+1 onto coarse time T+1
-            launch_restrict<T>(d, h->ref, d.fB, h->cbuf[1 - h->cci], a.bx0, a.by0, s);
+            cp.rsrc = d.fB;
+            cp.rdst = h->cbuf[1 - h->cci];
+            cp.bx0 = a.bx0;
+            cp.by0 = a.by0;
             h->cci = 1 - h->cci;
-            ++nl;
         }
-        // the ring at t+1: coarse T+1 (t odd) or the mean of T and T+1
-        launch_ring<T>(d, h->ref, h->cbuf[h->cci], (t & 1) ? nullptr : h->cbuf[1 - h->cci], d.fB, s);
+        cp.c0 = h->cbuf[h->cci];
+        cp.c1 = (t & 1) ? nullptr : h->cbuf[1 - h->cci];
+        cp.ring_dst = d.fB;
+        launch_couple<T>(d, h->ref, cp, s);
         ++nl;
     }
     phase_end(h, HLBM_PHASE_STREAM, ev, nl, s);
@@ -978,8 +985,14 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         c.fA = (T*)h->cbuf[0];
         c.fB = (T*)h->cbuf[1];
         launch_init_struct<T>(c, nullptr, dcux, dcuy, g->u0x, g->u0y, s);
-        launch_restrict<T>(d, h->ref, d.fA, h->cbuf[0], a.bx0, a.by0, s);
-        launch_ring<T>(d, h->ref, h->cbuf[0], nullptr, d.fA, s);
+        Couple cp{};
+        cp.rsrc = d.fA;
+        cp.rdst = h->cbuf[0];
+        cp.bx0 = a.bx0;
+        cp.by0 = a.by0;
+        cp.c0 = h->cbuf[0];
+        cp.ring_dst = d.fA;
+        launch_couple<T>(d, h->ref, cp, s);
         h->cci = 0;
     }
     h->ui = 1;
@@ -1849,7 +1862,8 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->box_w = bw;
     info->box_h = bh;
     // refill, classify, fill, stream-collide, feed, FV sub-steps, force (2)
-    info->launches_per_step = h->refine ? 10 : 8;  // refined: + ring, and per two steps coarse + restriction
+    // refined: + the coupling launch, + the coarse lattice on even steps (counted here)
+    info->launches_per_step = h->refine ? 10 : 8;
     info->n_coarse = h->refine ? (int64_t)h->ref.nxc * h->ref.nyc : 0;
     info->fv_kernel = h->fv_kind;
     info->n_tiles = h->n_tiles;

@@ -384,13 +384,19 @@ template <typename T> void launch_fill(const Dev<T>& d, const StepArgs& a, cudaS
 template <typename T> void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                                cudaStream_t s);
-// fine ring from coarse buffer c0 (c1 = NULL) or the mean of c0 and c1
-template <typename T> void launch_ring(const Dev<T>& d, const Refine& r, const void* c0, const void* c1,
-                                       void* dst, cudaStream_t s);
-// coarse nodes strictly inside the box from fine buffer src, classes of the
-// window at (bx0, by0)
-template <typename T> void launch_restrict(const Dev<T>& d, const Refine& r, const void* src, void* dst,
-                                           int bx0, int by0, cudaStream_t s);
+// One coupling launch: the fine ring (into ring_dst) from coarse buffer c0
+// (c1 = NULL) or the mean of c0 and c1; when rsrc is set, also the coarse
+// nodes strictly inside the box (into rdst) from fine buffer rsrc, with the
+// classes of the window at (bx0, by0).
+struct Couple {
+    const void* c0;
+    const void* c1;
+    void* ring_dst;
+    const void* rsrc;
+    void* rdst;
+    int bx0, by0;
+};
+template <typename T> void launch_couple(const Dev<T>& d, const Refine& r, const Couple& c, cudaStream_t s);
 template <typename T> void launch_fv_coeffs(const Dev<T>& d, int lumped, Coef<T>* coef, cudaStream_t s);
 template <typename T> void launch_patch_init(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_refill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);

@@ -401,106 +401,109 @@ void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy, c
 // (tau_s - 1/2)/2.  Post-collision non-equilibrium parts scale as
 // (tau - 1) dx: f^neq_c = 2 (tau_c - 1)/(tau_s - 1) f^neq_f.
 
-// coarse nodes and weights of fine coordinate X along one axis: the coarse
-// node itself (X even) or the cubic midpoint rule (-1, 9, 9, -1)/16
-__device__ __forceinline__ int axis_stencil(int X, int* idx, double* w) {
-    if ((X & 1) == 0) {
-        idx[0] = X >> 1;
-        w[0] = 1.0;
-        return 1;
-    }
-    const int i0 = (X - 1) >> 1;
-    idx[0] = i0 - 1;
-    idx[1] = i0;
-    idx[2] = i0 + 1;
-    idx[3] = i0 + 2;
-    w[0] = w[3] = -1.0 / 16.0;
-    w[1] = w[2] = 9.0 / 16.0;
-    return 4;
-}
-
-// Ring of the fine box (x = 0, nx-1 or y = 0, ny-1): the post-collision
-// ghost f^eq(rho, u) + acf f^neq with rho, u, f^neq of the coarse lattice at
-// the node (cubic along the box edge), from coarse buffer c0 alone (even
-// fine time) or the mean of c0 and c1 (odd fine time), written to dst.
+// One launch couples the levels after a fine stream-collide:
+//  - blocks [0, ring_blocks): the fine box's outermost ring (x = 0, nx-1 or
+//    y = 0, ny-1) takes the post-collision ghost f^eq(rho, u) + acf f^neq,
+//    with rho, u, f^neq of the coarse lattice at the node: the coarse node
+//    itself at even positions, the cubic midpoint rule (-1, 9, 9, -1)/16
+//    along the box edge at odd ones; from coarse buffer c0 alone, or the
+//    mean of c0 and c1 (odd fine times).  Four lanes share a ring node, one
+//    per stencil point, and combine their sums with two shuffles.
+//  - the other blocks (only when rsrc is set): the coarse nodes strictly
+//    inside the box take the post-collision state of the fine node under
+//    them, f^eq + afc f^neq; nodes over a fine node that the last step did
+//    not compute (class in the window at (bx0, by0)) take f^eq(rho0, 0),
+//    i.e. zero deviations.
+// The ring reads coarse nodes on or outside the box's footprint and the
+// restriction writes only nodes strictly inside it, so the two never touch
+// the same coarse node.
 template <typename T, typename S>
-__global__ void k_ring(Dev<T> d, Refine r, const void* c0v, const void* c1v, void* dstv) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int nring = 2 * d.nx + 2 * (d.ny - 2);
-    if (k >= nring) return;
-    int x, y;
-    if (k < d.nx) {
-        x = (int)k;
-        y = 0;
-    } else if (k < 2 * d.nx) {
-        x = (int)k - d.nx;
-        y = d.ny - 1;
-    } else if (k < 2 * d.nx + d.ny - 2) {
-        x = 0;
-        y = 1 + (int)k - 2 * d.nx;
-    } else {
-        x = d.nx - 1;
-        y = 1 + (int)k - 2 * d.nx - (d.ny - 2);
-    }
-    int I[4], J[4];
-    double wi[4], wj[4];
-    const int ni = axis_stencil(2 * r.ox + x, I, wi);
-    const int nj = axis_stencil(2 * r.oy + y, J, wj);
-    const S* src[2] = {reinterpret_cast<const S*>(c0v), reinterpret_cast<const S*>(c1v)};
-    const int nb = c1v ? 2 : 1;
-    T adr = T(0), aux = T(0), auy = T(0), aneq[9];
+__global__ void __launch_bounds__(128) k_couple(Dev<T> d, Refine r, Couple c, int ring_blocks) {
+    if ((int)blockIdx.x < ring_blocks) {
+        const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int lane4 = threadIdx.x & 3;
+        const int64_t k = g >> 2;
+        const int nring = 2 * d.nx + 2 * (d.ny - 2);
+        const bool live = k < nring;
+        int x = 0, y = 0;
+        if (k < d.nx) {
+            x = (int)k;
+        } else if (k < 2 * d.nx) {
+            x = (int)k - d.nx;
+            y = d.ny - 1;
+        } else if (k < 2 * d.nx + d.ny - 2) {
+            y = 1 + (int)k - 2 * d.nx;
+        } else {
+            x = d.nx - 1;
+            y = 1 + (int)k - 2 * d.nx - (d.ny - 2);
+        }
+        // the stencil runs along the edge: x on the bottom and top rows
+        // (corners included), y on the side columns; the fine coordinate
+        // across the edge is even (nx, ny odd), i.e. on a coarse line
+        const bool along_x = (y == 0 || y == d.ny - 1);
+        const int X = 2 * r.ox + x, Y = 2 * r.oy + y;
+        const int P = along_x ? X : Y;
+        int I = X >> 1, J = Y >> 1;
+        T w = T(0);
+        if ((P & 1) == 0) {
+            w = lane4 == 0 ? T(1) : T(0);
+        } else {
+            const int p = ((P - 1) >> 1) - 1 + lane4;
+            if (along_x)
+                I = p;
+            else
+                J = p;
+            w = (lane4 == 0 || lane4 == 3) ? T(-1.0 / 16.0) : T(9.0 / 16.0);
+        }
+        T acc[12];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) aneq[i] = T(0);
-    for (int q = 0; q < nb; ++q)
-        for (int c = 0; c < nj; ++c)
-            for (int a = 0; a < ni; ++a) {
-                const int64_t sc = (int64_t)J[c] * r.pitch + I[a];
+        for (int j = 0; j < 12; ++j) acc[j] = T(0);
+        if (live && w != T(0)) {
+            const int nb = c.c1 ? 2 : 1;
+            const T wq = nb == 2 ? w * T(0.5) : w;
+            const int64_t sc = (int64_t)J * r.pitch + I;
+            for (int q = 0; q < nb; ++q) {
+                const S* src = reinterpret_cast<const S*>(q == 0 ? c.c0 : c.c1);
                 T f[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = Store<T, S>::ld(src[q], i * r.plane + sc, d.finv);
+                for (int i = 0; i < 9; ++i) f[i] = Store<T, S>::ld(src, i * r.plane + sc, d.finv);
                 T dr, rr, vx, vy;
                 moments_dev(f, d.rho0, dr, rr, vx, vy);
-                const T w = T(wi[a] * wj[c] / nb);
-                adr += w * dr;
-                aux += w * vx;
-                auy += w * vy;
+                acc[0] += wq * dr;
+                acc[1] += wq * vx;
+                acc[2] += wq * vy;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) aneq[i] += w * (f[i] - feq_dev<T>(i, dr, rr, vx, vy));
+                for (int i = 0; i < 9; ++i) acc[3 + i] += wq * (f[i] - feq_dev<T>(i, dr, rr, vx, vy));
             }
-    const T rr = d.rho0 + adr, acf = T(r.acf);
-    S* dst = reinterpret_cast<S*>(dstv);
-    const int64_t s = (int64_t)y * d.pitch + x;
+        }
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        Store<T, S>::st(dst, i * d.plane + s, feq_dev<T>(i, adr, rr, aux, auy) + acf * aneq[i], d.fscale);
-}
-
-template <typename T>
-void launch_ring(const Dev<T>& d, const Refine& r, const void* c0, const void* c1, void* dst, cudaStream_t s) {
-    const int nring = 2 * d.nx + 2 * (d.ny - 2);
-    with_store(d, [&]<typename S>() { k_ring<T, S><<<(nring + 127) / 128, 128, 0, s>>>(d, r, c0, c1, dst); });
-}
-
-// Coarse nodes strictly inside the box take the post-collision state of the
-// fine node under them, f^eq + afc f^neq, read from the fine buffer src;
-// nodes over a fine node that the last step did not compute (class in the
-// window at (bx0, by0)) take f^eq(rho0, 0), i.e. zero deviations.
-template <typename T, typename S>
-__global__ void k_restrict(Dev<T> d, Refine r, const void* srcv, void* dstv, int bx0, int by0) {
+        for (int j = 0; j < 12; ++j) {
+            acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 1);
+            acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 2);
+        }
+        if (!live) return;
+        const T rr = d.rho0 + acc[0], acf = T(r.acf);
+        S* dst = reinterpret_cast<S*>(c.ring_dst);
+        const int64_t s = (int64_t)y * d.pitch + x;
+        for (int i = lane4; i < 9; i += 4)
+            Store<T, S>::st(dst, i * d.plane + s, feq_dev<T>(i, acc[0], rr, acc[1], acc[2]) + acf * acc[3 + i],
+                            d.fscale);
+        return;
+    }
     const int niw = (d.nx - 1) / 2 - 1, njw = (d.ny - 1) / 2 - 1;
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t k = ((int64_t)blockIdx.x - ring_blocks) * blockDim.x + threadIdx.x;
     if (k >= (int64_t)niw * njw) return;
     const int ii = (int)(k % niw) + 1, jj = (int)(k / niw) + 1;
     const int x = 2 * ii, y = 2 * jj;
     const int64_t sc = (int64_t)(r.oy + jj) * r.pitch + (r.ox + ii);
-    S* dst = reinterpret_cast<S*>(dstv);
-    const unsigned rx = (unsigned)(x - bx0), ry = (unsigned)(y - by0);
+    S* dst = reinterpret_cast<S*>(c.rdst);
+    const unsigned rx = (unsigned)(x - c.bx0), ry = (unsigned)(y - c.by0);
     if (rx < (unsigned)d.bw && ry < (unsigned)d.bh && d.cls_cur[(int64_t)ry * d.bw + rx] != CLS_DISC) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) Store<T, S>::st(dst, i * r.plane + sc, T(0), d.fscale);
         return;
     }
-    const S* src = reinterpret_cast<const S*>(srcv);
+    const S* src = reinterpret_cast<const S*>(c.rsrc);
     const int64_t s = (int64_t)y * d.pitch + x;
     T f[9];
 #pragma unroll
@@ -516,13 +519,12 @@ __global__ void k_restrict(Dev<T> d, Refine r, const void* srcv, void* dstv, int
 }
 
 template <typename T>
-void launch_restrict(const Dev<T>& d, const Refine& r, const void* src, void* dst, int bx0, int by0,
-                     cudaStream_t s) {
-    const int64_t n = (int64_t)((d.nx - 1) / 2 - 1) * ((d.ny - 1) / 2 - 1);
-    if (n <= 0) return;
-    with_store(d, [&]<typename S>() {
-        k_restrict<T, S><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d, r, src, dst, bx0, by0);
-    });
+void launch_couple(const Dev<T>& d, const Refine& r, const Couple& c, cudaStream_t s) {
+    const int64_t nring = 2 * (int64_t)d.nx + 2 * (d.ny - 2);
+    const int ring_blocks = (int)((4 * nring + 127) / 128);
+    const int64_t ninner = c.rsrc ? (int64_t)((d.nx - 1) / 2 - 1) * ((d.ny - 1) / 2 - 1) : 0;
+    const int blocks = ring_blocks + (int)((ninner + 127) / 128);
+    with_store(d, [&]<typename S>() { k_couple<T, S><<<blocks, 128, 0, s>>>(d, r, c, ring_blocks); });
 }
 
 #define HLBM_INST(T)                                                                                     \
@@ -534,8 +536,7 @@ void launch_restrict(const Dev<T>& d, const Refine& r, const void* src, void* ds
     template void launch_fill<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                          \
     template void launch_stream_collide<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                \
     template void launch_struct_macro<T>(const Dev<T>&, double*, double*, double*, cudaStream_t);        \
-    template void launch_ring<T>(const Dev<T>&, const Refine&, const void*, const void*, void*, cudaStream_t); \
-    template void launch_restrict<T>(const Dev<T>&, const Refine&, const void*, void*, int, int, cudaStream_t);
+    template void launch_couple<T>(const Dev<T>&, const Refine&, const Couple&, cudaStream_t);
 HLBM_INST(float)
 HLBM_INST(double)
 
