@@ -280,14 +280,11 @@ class Workload:
     damping: float = 0.0
     y0: float = 0.0
     v0: float = 0.0
-    # two-level lattice: the nx x ny lattice (nx, ny odd) is a fine box whose
-    # node (0, 0) sits on node (ox, oy) of an nxc x nyc lattice of twice the
-    # spacing; bc_x, bc_y then belong to that coarse lattice
-    refine: int = 0
-    nxc: int = 0
-    nyc: int = 0
-    ox: int = 0
-    oy: int = 0
+    # nested lattice levels: entry k-1 = (nx, ny, ox, oy) of level k, a lattice
+    # of twice the spacing of level k-1 (level 0 is the nx x ny lattice) that
+    # holds level k-1's node (0, 0) at its node (ox, oy); every level inside
+    # another has odd sizes, and bc_x, bc_y belong to the coarsest
+    levels: list = field(default_factory=list)
     mesh_args: dict = field(default_factory=dict)
 
     def mesh(self) -> PatchMesh:
@@ -397,7 +394,7 @@ def workload(name: str) -> Workload:
         # coarse lattice of twice the spacing (box at coarse node (51, 40))
         w = workload("lamina-small-f32")
         w.name, w.dtype = name, name.split("-")[-1]
-        w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 204, 160, 51, 40
+        w.levels = [(204, 160, 51, 40)]
         return w
     if name == "lamina-4096-refined-f32":
         # the 4096^2 workload's domain and lamina on two levels: a 2048^2
@@ -408,7 +405,7 @@ def workload(name: str) -> Workload:
         w.name = name
         w.nx = w.ny = 1025
         w.xc, w.yc = 512.3, 512.2
-        w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 2048, 2048, 768, 768
+        w.levels = [(2048, 2048, 768, 768)]
         return w
     if name.startswith("lamina-1024-refined-"):
         # the 1024^2 workload's domain on two levels: a 512^2 coarse lattice
@@ -417,7 +414,7 @@ def workload(name: str) -> Workload:
         w.name = name
         w.nx = w.ny = 257
         w.xc, w.yc = 128.3, 128.2
-        w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 512, 512, 192, 192
+        w.levels = [(512, 512, 192, 192)]
         return w
     if name.startswith("lamina-1024-"):
         # the physics of the 256^2 FP64 workload (tau 0.6, beta 500, KC 0.25) at

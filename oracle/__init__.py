@@ -18,6 +18,7 @@ _SRC = os.path.join(_HERE, "hlbm_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libhlbm_oracle.so")
 
 DISC, INTERP, UNUSED = 0, 1, 2
+MAX_LEVELS = 4
 
 
 def build(force: bool = False) -> str:
@@ -47,8 +48,10 @@ class _Params(C.Structure):
         ("outer_fv", C.c_int),
         ("mass", C.c_double), ("stiffness", C.c_double), ("damping", C.c_double), ("y0", C.c_double),
         ("v0", C.c_double),
-        ("refine", C.c_int), ("nxc", C.c_int), ("nyc", C.c_int), ("ox", C.c_int), ("oy", C.c_int),
-        ("uxc_init", C.POINTER(C.c_double)), ("uyc_init", C.POINTER(C.c_double)),
+        ("n_levels", C.c_int), ("lv_nx", C.c_int * MAX_LEVELS), ("lv_ny", C.c_int * MAX_LEVELS),
+        ("lv_ox", C.c_int * MAX_LEVELS), ("lv_oy", C.c_int * MAX_LEVELS),
+        ("lv_rho", C.POINTER(C.c_double) * MAX_LEVELS), ("lv_ux", C.POINTER(C.c_double) * MAX_LEVELS),
+        ("lv_uy", C.POINTER(C.c_double) * MAX_LEVELS),
     ]
 
 
@@ -72,8 +75,9 @@ def lib():
         L.orc_time.restype = C.c_int64
         for name in ("orc_struct_f", "orc_patch_f"):
             getattr(L, name).argtypes = [P, dp]
-        for name in ("orc_struct_macro", "orc_patch_macro", "orc_coarse_macro"):
+        for name in ("orc_struct_macro", "orc_patch_macro"):
             getattr(L, name).argtypes = [P, dp, dp, dp]
+        L.orc_level_macro.argtypes = [P, C.c_int, dp, dp, dp]
         L.orc_struct_class.argtypes = [P, C.POINTER(C.c_int8)]
         L.orc_classify_at.argtypes = [P, C.c_int64, C.POINTER(C.c_int8)]
         L.orc_relocate_at.argtypes = [P, C.c_int64, ip, ip]
@@ -192,7 +196,7 @@ def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
 class Oracle:
     """Serial FP64 MG-HLBM run for one workload (see ``inputs.Workload``)."""
 
-    def __init__(self, w, mesh=None, rho_init=None, u_init=None, uc_init=None):
+    def __init__(self, w, mesh=None, rho_init=None, u_init=None, level_u_init=None, level_rho_init=None):
         self.w = w
         self.mesh = mesh if mesh is not None else w.mesh()
         rho = rho_init if rho_init is not None else w.rho_init()
@@ -220,13 +224,19 @@ class Oracle:
         p.mass, p.stiffness, p.damping = float(w.mass), float(w.stiffness), float(w.damping)
         p.y0, p.v0 = float(w.y0), float(w.v0)
         p.A, p.omega, p.vx, p.vy = w.A, w.omega, w.vx, w.vy
-        p.refine = int(getattr(w, "refine", 0))
-        if p.refine:
-            p.nxc, p.nyc, p.ox, p.oy = w.nxc, w.nyc, w.ox, w.oy
-            if uc_init is not None:
-                self._keep += [np.ascontiguousarray(uc_init[0], dtype=np.float64),
-                               np.ascontiguousarray(uc_init[1], dtype=np.float64)]
-                p.uxc_init, p.uyc_init = _dp(self._keep[-2]), _dp(self._keep[-1])
+        levels = list(getattr(w, "levels", []))
+        if len(levels) > MAX_LEVELS:
+            raise ValueError(f"at most {MAX_LEVELS} coarser levels")
+        p.n_levels = len(levels)
+        for k, (nx, ny, ox, oy) in enumerate(levels):
+            p.lv_nx[k], p.lv_ny[k], p.lv_ox[k], p.lv_oy[k] = nx, ny, ox, oy
+            if level_u_init is not None and level_u_init[k] is not None:
+                self._keep += [np.ascontiguousarray(level_u_init[k][0], dtype=np.float64),
+                               np.ascontiguousarray(level_u_init[k][1], dtype=np.float64)]
+                p.lv_ux[k], p.lv_uy[k] = _dp(self._keep[-2]), _dp(self._keep[-1])
+            if level_rho_init is not None and level_rho_init[k] is not None:
+                self._keep.append(np.ascontiguousarray(level_rho_init[k], dtype=np.float64))
+                p.lv_rho[k] = _dp(self._keep[-1])
         self._h = lib().orc_create(C.byref(p))
         self.n = self.mesh.n_nodes
 
@@ -257,10 +267,11 @@ class Oracle:
         lib().orc_struct_macro(self._h, _dp(r), _dp(ux), _dp(uy))
         return r, ux, uy
 
-    def coarse_macro(self):
-        """rho, ux, uy [nyc, nxc] of the coarse lattice at the last even time (R12)."""
-        r, ux, uy = (np.empty((self.w.nyc, self.w.nxc)) for _ in range(3))
-        lib().orc_coarse_macro(self._h, _dp(r), _dp(ux), _dp(uy))
+    def level_macro(self, k=1):
+        """rho, ux, uy of coarser level k (1..len(w.levels)) at its current time (R12)."""
+        nx, ny = self.w.levels[k - 1][:2]
+        r, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+        lib().orc_level_macro(self._h, int(k), _dp(r), _dp(ux), _dp(uy))
         return r, ux, uy
 
     def struct_class(self):

@@ -51,11 +51,12 @@
  *      start of the step: v(t+1) = v(t) + (F_y(t) - c v(t) - k y(t))/m,
  *      y(t+1) = y(t) + v(t+1).  The patch sits at y(t) during step t; the
  *      wall velocity at sub-step m is v(t) + theta (v(t+1) - v(t)).
- *  R12 Two-level lattice (the paper's refinement levels, Sec. 5; the
+ *  R12 Nested lattice levels (the paper's refinement levels, Sec. 5; the
  *      coupling is not given there): the lattice around the patch is a fine
- *      box inside a coarse lattice of twice the spacing and twice the time
- *      step (acoustic scaling, same lattice velocities), tau_c - 1/2 =
- *      (tau_s - 1/2)/2 for the same viscosity.  Non-equilibrium parts scale
+ *      box inside a lattice of twice the spacing and twice the time step
+ *      (acoustic scaling, same lattice velocities), tau_c - 1/2 =
+ *      (tau_s - 1/2)/2 for the same viscosity, which may itself be a box
+ *      inside a coarser one, and so on; each pair couples as follows.  Non-equilibrium parts scale
  *      as tau dx (f^neq = -tau dt D f^eq); for post-collision populations,
  *      f^neq_c = 2 (tau_c - 1)/(tau_s - 1) f^neq_f (tau_s != 1).  Per coarse
  *      step (two fine steps t = 2T, 2T+1): the coarse lattice streams and
@@ -116,6 +117,15 @@ static void state_of(const double* f, double* rho, double* ux, double* uy, doubl
 /* ------------------------------------------------------------------------ */
 /* oracle state                                                              */
 /* ------------------------------------------------------------------------ */
+/* R12: one coarser lattice level, post-collision populations [9][ny][nx];
+ * f[cur] at the level's current time */
+typedef struct {
+    int nx, ny, ox, oy;
+    int64_t N;
+    double* f[2];
+    int cur;
+} orc_level_t;
+
 struct orc {
     orc_params_t p;
     double* xy;
@@ -150,9 +160,7 @@ struct orc {
     int64_t t;
     double Xprev, Yprev;
     double *Yh, *Vh; /* INDUCED motion: y and v at integer times (R11) */
-    double* fc[2];   /* R12: coarse post-collision state [9][nyc][nxc]; fc[ccur] at time t/2 */
-    int ccur;
-    int64_t Nc;
+    orc_level_t lv[ORC_MAX_LEVELS]; /* R12: coarser levels 1..n_levels */
     int64_t mcap;
     int status;
 };
@@ -519,18 +527,26 @@ static double pull(int nx, int ny, int bcx, int bcy, const double* post, int64_t
 }
 
 /* ------------------------------------------------------------------------ */
-/* two-level lattice (R12)                                                   */
+/* nested lattice levels (R12)                                               */
 /* ------------------------------------------------------------------------ */
-static double tau_coarse(double tau_s) { return 0.5 + 0.5 * (tau_s - 0.5); }
+/* level 0 is the nx x ny lattice around the patch; level k >= 1 is
+ * o->lv[k - 1], with twice the spacing and time step of level k - 1 */
+static double tau_level(const orc_t* o, int k) { return 0.5 + ldexp(o->p.tau_s - 0.5, -k); }
 
-static int is_ring(const orc_t* o, int x, int y) {
-    return o->p.refine && (x == 0 || y == 0 || x == o->p.nx - 1 || y == o->p.ny - 1);
+static int level_nx(const orc_t* o, int k) { return k == 0 ? o->p.nx : o->lv[k - 1].nx; }
+static int level_ny(const orc_t* o, int k) { return k == 0 ? o->p.ny : o->lv[k - 1].ny; }
+
+/* the outermost ring of level k < n_levels takes its values from level k+1 */
+static int is_ring_k(const orc_t* o, int k, int x, int y) {
+    return k < o->p.n_levels && (x == 0 || y == 0 || x == level_nx(o, k) - 1 || y == level_ny(o, k) - 1);
 }
+static int is_ring(const orc_t* o, int x, int y) { return is_ring_k(o, 0, x, y); }
 
-/* rho, ux, uy, f^neq of coarse node s at buffer b */
-static void coarse_state(const orc_t* o, int b, int64_t s, double* st) {
+/* rho, ux, uy, f^neq of node s of level k >= 1, buffer b */
+static void level_state(const orc_t* o, int k, int b, int64_t s, double* st) {
+    const orc_level_t* L = &o->lv[k - 1];
     double f[9], fneq[9];
-    for (int i = 0; i < 9; ++i) f[i] = o->fc[b][i * o->Nc + s];
+    for (int i = 0; i < 9; ++i) f[i] = L->f[b][i * L->N + s];
     state_of(f, &st[0], &st[1], &st[2], fneq);
     for (int i = 0; i < 9; ++i) st[3 + i] = fneq[i];
 }
@@ -553,93 +569,110 @@ static int axis_weights(int X, int* idx, double* w) {
     return 4;
 }
 
-/* post-collision populations of fine ring node (x, y) at fine time t:
- * rho, u and f^neq of the coarse lattice at the node's position (cubic
- * along the box edge; at odd t the mean of coarse times t/2 -/+ 1/2), then
- * f^eq(rho, u) + f^neq rescaled to the fine lattice */
-static void ghost_post(const orc_t* o, int x, int y, int64_t t, double* post) {
-    const int nxc = o->p.nxc;
+/* post-collision populations of ring node (x, y) of level k at its time tk:
+ * rho, u and f^neq of level k+1 at the node's position (cubic along the box
+ * edge; at odd tk the mean of level k+1's times tk/2 -/+ 1/2), then
+ * f^eq(rho, u) + f^neq rescaled to level k */
+static void ghost_post(const orc_t* o, int k, int x, int y, int64_t tk, double* post) {
+    const orc_level_t* C = &o->lv[k]; /* level k+1 */
     int I[4], J[4];
     double wi[4], wj[4];
-    const int ni = axis_weights(2 * o->p.ox + x, I, wi);
-    const int nj = axis_weights(2 * o->p.oy + y, J, wj);
+    const int ni = axis_weights(2 * C->ox + x, I, wi);
+    const int nj = axis_weights(2 * C->oy + y, J, wj);
     double st[12] = {0};
-    const int nb = (t % 2 == 0) ? 1 : 2;
-    const int bufs[2] = {o->ccur, 1 - o->ccur};
+    const int nb = (tk % 2 == 0) ? 1 : 2;
+    const int bufs[2] = {C->cur, 1 - C->cur};
     for (int q = 0; q < nb; ++q)
         for (int c = 0; c < nj; ++c)
             for (int a = 0; a < ni; ++a) {
                 double w = wi[a] * wj[c] / nb, sc[12];
-                coarse_state(o, bufs[q], (int64_t)J[c] * nxc + I[a], sc);
+                level_state(o, k + 1, bufs[q], (int64_t)J[c] * C->nx + I[a], sc);
                 for (int j = 0; j < 12; ++j) st[j] += w * sc[j];
             }
-    const double ts = o->p.tau_s, tc = tau_coarse(ts);
-    const double acf = (ts - 1.0) / (2.0 * (tc - 1.0));
+    const double tf = tau_level(o, k), tc = tau_level(o, k + 1);
+    const double acf = (tf - 1.0) / (2.0 * (tc - 1.0));
     double feq[9];
     orc_feq(st[0], st[1], st[2], feq);
     for (int i = 0; i < 9; ++i) post[i] = feq[i] + acf * st[3 + i];
 }
 
-/* the fine ring of buffer b takes its post-collision ghost for fine time t;
- * the pre-collision array holds it there (its moments are the ring's rho, u) */
-static void fill_ring(orc_t* o, int b, int64_t t) {
-    const int nx = o->p.nx, ny = o->p.ny;
+/* the ring of level k takes its post-collision ghost for its time tk, into
+ * the current buffer (level 0: the pre-collision array, whose moments are
+ * then the ring's rho and u) */
+static void fill_ring(orc_t* o, int k, int64_t tk) {
+    const int nx = level_nx(o, k), ny = level_ny(o, k);
+    double* dst = k == 0 ? o->fs[o->cur] : o->lv[k - 1].f[o->lv[k - 1].cur];
+    const int64_t N = k == 0 ? o->N : o->lv[k - 1].N;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
-            if (!is_ring(o, x, y)) continue;
+            if (!is_ring_k(o, k, x, y)) continue;
             double post[9];
-            ghost_post(o, x, y, t, post);
-            for (int i = 0; i < 9; ++i) o->fs[b][i * o->N + (int64_t)y * nx + x] = post[i];
+            ghost_post(o, k, x, y, tk, post);
+            for (int i = 0; i < 9; ++i) dst[i * N + (int64_t)y * nx + x] = post[i];
         }
 }
 
-/* coarse stream and collide T -> T+1 from fc[ccur] into fc[1 - ccur] */
-static void coarse_step(orc_t* o) {
-    const int nxc = o->p.nxc, nyc = o->p.nyc;
-    const int64_t N = o->Nc;
-    const double* post = o->fc[o->ccur];
-    double* out = o->fc[1 - o->ccur];
-    const double tc = tau_coarse(o->p.tau_s);
+/* level k >= 1 streams and collides from f[cur] into f[1 - cur]; the
+ * coarsest level has the lattice's boundaries, a finer one zero-gradient
+ * edges (its ring is rebuilt afterwards) */
+static void level_step(orc_t* o, int k) {
+    orc_level_t* L = &o->lv[k - 1];
+    const int coarsest = k == o->p.n_levels;
+    const int bcx = coarsest ? o->p.bc_x : ORC_BC_OUTFLOW, bcy = coarsest ? o->p.bc_y : ORC_BC_OUTFLOW;
+    const double* post = L->f[L->cur];
+    double* out = L->f[1 - L->cur];
+    const double tc = tau_level(o, k);
     int bad = 0;
-    for (int y = 0; y < nyc; ++y)
-        for (int x = 0; x < nxc; ++x) {
+    for (int y = 0; y < L->ny; ++y)
+        for (int x = 0; x < L->nx; ++x) {
             double f[9], q[9];
-            for (int i = 0; i < 9; ++i) f[i] = pull(nxc, nyc, o->p.bc_x, o->p.bc_y, post, N, x, y, i, NULL, &bad);
+            for (int i = 0; i < 9; ++i) f[i] = pull(L->nx, L->ny, bcx, bcy, post, L->N, x, y, i, NULL, &bad);
             bgk_collide(f, tc, q);
-            for (int i = 0; i < 9; ++i) out[i * N + (int64_t)y * nxc + x] = q[i];
+            for (int i = 0; i < 9; ++i) out[i * L->N + (int64_t)y * L->nx + x] = q[i];
         }
 }
 
-/* coarse nodes strictly inside the fine box take the post-collision state of
- * the fine node under them (fine pre-collision state fs[cur] at an even
- * time, collided); written into coarse buffer b */
-static void restrict_fine(orc_t* o, int b) {
-    const int nx = o->p.nx, nxc = o->p.nxc;
-    const double ts = o->p.tau_s, tc = tau_coarse(ts);
-    const double afc = 2.0 * (tc - 1.0) / (ts - 1.0);
-    for (int J = o->p.oy + 1; J < o->p.oy + (o->p.ny - 1) / 2; ++J)
-        for (int I = o->p.ox + 1; I < o->p.ox + (nx - 1) / 2; ++I) {
-            const int x = 2 * (I - o->p.ox), y = 2 * (J - o->p.oy);
-            const int64_t s = (int64_t)y * nx + x, sc = (int64_t)J * nxc + I;
+/* the nodes of level k+1 strictly inside level k's box take the
+ * post-collision state of the level-k node under them, f^eq + f^neq
+ * rescaled, into level k+1's buffer b.  Level 0's state is its pre-collision
+ * array at an even time, collided; a level-0 node that is not computed
+ * (under the lamina) gives f^eq(rho0, 0), which nothing retained reads. */
+static void restrict_level(orc_t* o, int k, int b) {
+    orc_level_t* C = &o->lv[k];
+    const int nx = level_nx(o, k), ny = level_ny(o, k);
+    const double tf = tau_level(o, k), tc = tau_level(o, k + 1);
+    const double afc = 2.0 * (tc - 1.0) / (tf - 1.0);
+    for (int J = C->oy + 1; J < C->oy + (ny - 1) / 2; ++J)
+        for (int I = C->ox + 1; I < C->ox + (nx - 1) / 2; ++I) {
+            const int x = 2 * (I - C->ox), y = 2 * (J - C->oy);
+            const int64_t sc = (int64_t)J * C->nx + I;
             double post[9];
-            if (o->cls_cur[s] == ORC_DISC) {
-                double f[9];
-                for (int i = 0; i < 9; ++i) f[i] = o->fs[o->cur][i * o->N + s];
-                bgk_collide(f, ts, post);
+            if (k == 0) {
+                const int64_t s = (int64_t)y * nx + x;
+                if (o->cls_cur[s] == ORC_DISC) {
+                    double f[9];
+                    for (int i = 0; i < 9; ++i) f[i] = o->fs[o->cur][i * o->N + s];
+                    bgk_collide(f, tf, post);
+                } else {
+                    orc_feq(o->p.rho0, 0.0, 0.0, post);
+                }
             } else {
-                orc_feq(o->p.rho0, 0.0, 0.0, post); /* under the body: never read */
+                const orc_level_t* F = &o->lv[k - 1];
+                const int64_t s = (int64_t)y * F->nx + x;
+                for (int i = 0; i < 9; ++i) post[i] = F->f[F->cur][i * F->N + s];
             }
             double r, ux, uy, fneq[9], feq[9];
             state_of(post, &r, &ux, &uy, fneq);
             orc_feq(r, ux, uy, feq);
-            for (int i = 0; i < 9; ++i) o->fc[b][i * o->Nc + sc] = feq[i] + afc * fneq[i];
+            for (int i = 0; i < 9; ++i) C->f[b][i * C->N + sc] = feq[i] + afc * fneq[i];
         }
 }
 
-void orc_coarse_macro(const orc_t* o, double* rho, double* ux, double* uy) {
-    for (int64_t s = 0; s < o->Nc; ++s) {
+void orc_level_macro(const orc_t* o, int k, double* rho, double* ux, double* uy) {
+    const orc_level_t* L = &o->lv[k - 1];
+    for (int64_t s = 0; s < L->N; ++s) {
         double st[12];
-        coarse_state(o, o->ccur, s, st);
+        level_state(o, k, L->cur, s, st);
         rho[s] = st[0];
         ux[s] = st[1];
         uy[s] = st[2];
@@ -1167,18 +1200,29 @@ orc_t* orc_create(const orc_params_t* p) {
     o->t = 0;
     o->Xprev = X;
     o->Yprev = Y;
-    if (p->refine) { /* R12: coarse lattice at equilibrium, then the box restricted onto it */
-        o->Nc = (int64_t)p->nxc * p->nyc;
-        for (int b = 0; b < 2; ++b) o->fc[b] = calloc((size_t)o->Nc * 9, sizeof(double));
-        for (int64_t sc = 0; sc < o->Nc; ++sc) {
+    /* R12: coarser levels at equilibrium, then each restricted from the one
+     * inside it (finest first) and every ring rebuilt */
+    for (int k = 1; k <= p->n_levels; ++k) {
+        orc_level_t* L = &o->lv[k - 1];
+        L->nx = p->lv_nx[k - 1];
+        L->ny = p->lv_ny[k - 1];
+        L->ox = p->lv_ox[k - 1];
+        L->oy = p->lv_oy[k - 1];
+        L->N = (int64_t)L->nx * L->ny;
+        for (int b = 0; b < 2; ++b) L->f[b] = calloc((size_t)L->N * 9, sizeof(double));
+        for (int64_t sc = 0; sc < L->N; ++sc) {
             double feq[9];
-            orc_feq(p->rho0, p->uxc_init ? p->uxc_init[sc] : p->u0x, p->uyc_init ? p->uyc_init[sc] : p->u0y, feq);
-            for (int i = 0; i < 9; ++i) o->fc[0][i * o->Nc + sc] = feq[i];
+            orc_feq(p->lv_rho[k - 1] ? p->lv_rho[k - 1][sc] : p->rho0, p->lv_ux[k - 1] ? p->lv_ux[k - 1][sc] : p->u0x,
+                    p->lv_uy[k - 1] ? p->lv_uy[k - 1][sc] : p->u0y, feq);
+            for (int i = 0; i < 9; ++i) L->f[0][i * L->N + sc] = feq[i];
         }
-        o->ccur = 0;
-        restrict_fine(o, 0);
-        fill_ring(o, 0, 0);
+        L->cur = 0;
+        o->p.lv_rho[k - 1] = NULL;
+        o->p.lv_ux[k - 1] = NULL;
+        o->p.lv_uy[k - 1] = NULL;
     }
+    for (int k = 0; k < p->n_levels; ++k) restrict_level(o, k, 0);
+    for (int k = 0; k < p->n_levels; ++k) fill_ring(o, k, 0);
     record_force(o);
     return o;
 }
@@ -1199,7 +1243,9 @@ int orc_step(orc_t* o, int64_t nsteps) {
             o->Yh[t + 1] = o->Yh[t] + o->Vh[t + 1];
             if (!(fabs(o->Vh[t + 1]) < 1.0)) o->status |= ORC_ERR_FAST_MOTION;
         }
-        if (o->p.refine && t % 2 == 0) coarse_step(o); /* R12: T -> T+1 */
+        /* R12: every level whose step starts now, coarsest first */
+        for (int k = o->p.n_levels; k >= 1; --k)
+            if (t % ((int64_t)1 << k) == 0) level_step(o, k);
         double X, Y;
         lamina_pos(o, t, &X, &Y);
         double cx = o->p.xc + X, cy = o->p.yc + Y;
@@ -1216,11 +1262,15 @@ int orc_step(orc_t* o, int64_t nsteps) {
         o->Yprev = Y;
         o->t = t + 1;
         record_force(o);
-        if (o->p.refine && o->t % 2 == 0) { /* R12: restriction at T+1 */
-            restrict_fine(o, 1 - o->ccur);
-            o->ccur = 1 - o->ccur;
-        }
-        if (o->p.refine) fill_ring(o, o->cur, o->t);
+        /* R12: restriction onto every level that level k has caught up with
+         * (finest first), then the rings of the levels that just stepped */
+        for (int k = 0; k < o->p.n_levels; ++k)
+            if (o->t % ((int64_t)1 << (k + 1)) == 0) {
+                restrict_level(o, k, 1 - o->lv[k].cur);
+                o->lv[k].cur = 1 - o->lv[k].cur;
+            }
+        for (int k = 0; k < o->p.n_levels; ++k)
+            if (o->t % ((int64_t)1 << k) == 0) fill_ring(o, k, o->t >> k);
     }
     return o->status;
 }
@@ -1352,8 +1402,10 @@ void orc_destroy(orc_t* o) {
     free(o->bitems);
     free(o->Yh);
     free(o->Vh);
-    free(o->fc[0]);
-    free(o->fc[1]);
+    for (int k = 0; k < o->p.n_levels; ++k) {
+        free(o->lv[k].f[0]);
+        free(o->lv[k].f[1]);
+    }
     free(o->snap0);
     free(o->snap1);
     free(o->dstar);

@@ -22,6 +22,7 @@ enum { ORC_BC_WALL = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
 enum { ORC_MOTION_STATIC = 0, ORC_MOTION_HARMONIC = 1, ORC_MOTION_UNIFORM = 2, ORC_MOTION_INDUCED = 3 };
 enum { ORC_KIND_INTERIOR = 0, ORC_KIND_OUTER = 1, ORC_KIND_WALL = 2 };
 enum { ORC_DISC = 0, ORC_INTERP = 1, ORC_UNUSED = 2 };
+enum { ORC_MAX_LEVELS = 4 };
 /* status bits */
 enum {
     ORC_ERR_FILL_NOT_LOCATED = 1,   /* eq. 178 node outside the patch          */
@@ -53,14 +54,18 @@ typedef struct {
     int outer_fv;           /* 1: outer nodes take eq. 182 with its FV sums (R10) */
     /* INDUCED motion (R11): m y'' + c y' + k y = F_y, y(0) = y0, y'(0) = v0 */
     double mass, stiffness, damping, y0, v0;
-    /* two-level lattice (R12): refine = 1 makes the nx x ny lattice a fine box
-     * whose node (0, 0) sits on coarse node (ox, oy) of an nxc x nyc lattice of
-     * twice the spacing (bc_x, bc_y then apply to the coarse lattice; nx, ny
-     * odd); the coarse lattice starts at equilibrium with rho0 and the
-     * velocity uxc_init / uyc_init ([nyc*nxc], or NULL for u0) */
-    int refine, nxc, nyc, ox, oy;
-    const double* uxc_init;
-    const double* uyc_init;
+    /* nested lattice levels (R12): n_levels coarser lattices around the
+     * nx x ny lattice.  Level k (1..n_levels) has twice the spacing and time
+     * step of level k-1, lv_nx[k-1] x lv_ny[k-1] nodes, and holds node (0, 0)
+     * of level k-1 at its node (lv_ox[k-1], lv_oy[k-1]); every level inside
+     * another has odd sizes.  bc_x, bc_y apply to the coarsest level.  Level
+     * k starts at equilibrium with the density lv_rho[k-1] and the velocity
+     * lv_ux[k-1], lv_uy[k-1] ([ny*nx] each, or NULL for rho0 and u0). */
+    int n_levels;
+    int lv_nx[ORC_MAX_LEVELS], lv_ny[ORC_MAX_LEVELS], lv_ox[ORC_MAX_LEVELS], lv_oy[ORC_MAX_LEVELS];
+    const double* lv_rho[ORC_MAX_LEVELS];
+    const double* lv_ux[ORC_MAX_LEVELS];
+    const double* lv_uy[ORC_MAX_LEVELS];
 } orc_params_t;
 
 typedef struct orc orc_t;
@@ -77,8 +82,9 @@ int64_t orc_time(const orc_t* o);
 /* structured fields at the current time (pre-collision state) */
 void orc_struct_f(const orc_t* o, double* f9);               /* [9][ny][nx] */
 void orc_struct_macro(const orc_t* o, double* rho, double* ux, double* uy);
-/* R12: the coarse lattice's rho, u [nyc*nxc] at the last even fine time */
-void orc_coarse_macro(const orc_t* o, double* rho, double* ux, double* uy);
+/* R12: rho, u of level k (1..n_levels) [ny_k*nx_k] at its current time
+ * (the fine time rounded down to a multiple of 2^k) */
+void orc_level_macro(const orc_t* o, int k, double* rho, double* ux, double* uy);
 void orc_struct_class(const orc_t* o, int8_t* cls);          /* class of the last step */
 /* patch fields at the current time */
 void orc_patch_f(const orc_t* o, double* f9);                /* [n][9] */

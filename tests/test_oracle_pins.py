@@ -512,40 +512,42 @@ def _tgv(X, Y, U, k):
     return -U * np.cos(k * X) * np.sin(k * Y), U * np.sin(k * X) * np.cos(k * Y)
 
 
-def _tgv_error(tau_f, refine, nc=48, box=49, o=12, T=200, U=1e-3):
+def _tgv_error(tau_f, n_levels, uniform=False, nc=48, box=49, o=12, T=200, U=1e-3):
     """Max-norm velocity error, relative to the decayed amplitude, of a
-    Taylor-Green vortex (period nc coarse units, periodic) after T coarse
-    steps: u = U e^{-2 nu k^2 t} (-cos kx sin ky, sin kx cos ky), nu = (tau_c -
-    1/2)/3 in coarse units.  refine=0 runs the uniform coarse lattice."""
+    Taylor-Green vortex (period nc units of the coarsest level, periodic)
+    after T steps of the coarsest level: u = U e^{-2 nu k^2 t} (-cos kx sin ky,
+    sin kx cos ky), nu = (tau_c - 1/2)/3 in its units, tau_c - 1/2 =
+    (tau_f - 1/2)/2^n_levels.  Each finer level is a box x box lattice at node
+    (o, o) of the next coarser one.  uniform=True runs the coarsest lattice
+    alone (with tau_c).  Returns the errors of level 0, 1, ..., coarsest."""
     k = 2.0 * math.pi / nc
-    tau_c = 0.5 + 0.5 * (tau_f - 0.5)
+    tau_c = 0.5 + (tau_f - 0.5) / 2 ** n_levels
     dec = math.exp(-2.0 * (tau_c - 0.5) / 3.0 * k * k * T)
+
+    def err(X, Y, ux, uy):
+        ex, ey = _tgv(X, Y, U * dec, k)
+        return max(np.abs(ux - ex).max(), np.abs(uy - ey).max()) / (U * dec)
+
     Xc, Yc = np.meshgrid(np.arange(nc) * 1.0, np.arange(nc) * 1.0)
-    if not refine:
+    if uniform:
         w = inputs.Workload("tgv-coarse", nc, nc, 0.0, 0.0, nc / 2 + 0.3, nc / 2 + 0.3, tau_c, 1,
                             inputs.MOTION_HARMONIC, delta_f=0.1, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC)
         ob = oracle.Oracle(w, mesh=_void_mesh(), rho_init=np.ones((nc, nc)), u_init=_tgv(Xc, Yc, U, k))
         ob.step(T)
         assert ob.status == 0
-        _, ux, uy = ob.struct_macro()
-        ex, ey = _tgv(Xc, Yc, U * dec, k)
-        return max(np.abs(ux - ex).max(), np.abs(uy - ey).max()) / (U * dec), None
-    w = inputs.Workload("tgv-refined", box, box, 0.0, 0.0, 24.3, 24.3, tau_f, 1, inputs.MOTION_HARMONIC,
-                        delta_f=0.1, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC, refine=1, nxc=nc, nyc=nc,
-                        ox=o, oy=o)
-    xs = o + np.arange(box) / 2.0
-    Xf, Yf = np.meshgrid(xs, xs)
-    ob = oracle.Oracle(w, mesh=_void_mesh(), rho_init=np.ones((box, box)), u_init=_tgv(Xf, Yf, U, k),
-                       uc_init=_tgv(Xc, Yc, U, k))
-    ob.step(2 * T)
+        return [err(Xc, Yc, *ob.struct_macro()[1:])]
+    coords = _level_coords(n_levels, nc, box, o)
+    w = inputs.Workload("tgv-levels", box, box, 0.0, 0.0, box // 2 + 0.3, box // 2 + 0.3, tau_f, 1,
+                        inputs.MOTION_HARMONIC, delta_f=0.1, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                        levels=[(box, box, o, o)] * (n_levels - 1) + [(nc, nc, o, o)])
+    ob = oracle.Oracle(w, mesh=_void_mesh(), rho_init=np.ones((box, box)), u_init=_tgv(*coords[0], U, k),
+                       level_u_init=[_tgv(*coords[j], U, k) for j in range(1, n_levels + 1)])
+    ob.step(T * 2 ** n_levels)
     assert ob.status == 0
-    _, ux, uy = ob.struct_macro()
-    ex, ey = _tgv(Xf, Yf, U * dec, k)
-    ef = max(np.abs(ux - ex).max(), np.abs(uy - ey).max()) / (U * dec)
-    _, uxc, uyc = ob.coarse_macro()
-    ex, ey = _tgv(Xc, Yc, U * dec, k)
-    ec = max(np.abs(uxc - ex).max(), np.abs(uyc - ey).max()) / (U * dec)
-    return ef, ec
+    out = [err(*coords[0], *ob.struct_macro()[1:])]
+    for j in range(1, n_levels + 1):
+        out.append(err(*coords[j], *ob.level_macro(j)[1:]))
+    return out
 
 
 @pytest.mark.parametrize("tau_f", [0.8, 1.3])
@@ -557,11 +559,67 @@ def test_two_level_taylor_green_vortex(tau_f):
     ring's rho, u, f^neq are rescaled, interpolated in space or in time
     wrongly), and the coarse lattice keeps the uniform coarse lattice's
     accuracy."""
-    e_uniform, _ = _tgv_error(tau_f, 0)
+    (e_uniform,) = _tgv_error(tau_f, 1, uniform=True)
     e_fine, e_coarse = _tgv_error(tau_f, 1)
     assert e_uniform < 4e-3
     assert e_fine < 0.65 * e_uniform
     assert e_coarse < 1.3 * e_uniform
+
+
+@pytest.mark.parametrize("tau_f", [0.8, 1.3])
+def test_three_level_taylor_green_vortex(tau_f):
+    """Three nested levels (spacings 1, 2, 4): each level's time, tau and
+    rescaling, the order of the restrictions (finest first) and the steps
+    (coarsest first) all enter.  The finest box is below 0.3x the uniform
+    coarsest lattice's error, the middle level below it, the coarsest within
+    1.5x of it."""
+    (e_uniform,) = _tgv_error(tau_f, 2, uniform=True)
+    e0, e1, e2 = _tgv_error(tau_f, 2)
+    assert e0 < 0.3 * e_uniform
+    assert e1 < 0.8 * e_uniform
+    assert e2 < 1.5 * e_uniform
+
+
+def _level_coords(n_levels, nc, box, o):
+    """Node coordinates of each level (0 = finest) in units of the coarsest."""
+    Xc, Yc = np.meshgrid(np.arange(nc) * 1.0, np.arange(nc) * 1.0)
+    out = []
+    for j in range(n_levels):
+        off = sum(o * 2.0 ** (m - n_levels) for m in range(j + 1, n_levels + 1))
+        xs = off + np.arange(box) * 2.0 ** (j - n_levels)
+        out.append(np.meshgrid(xs, xs))
+    return out + [(Xc, Yc)]
+
+
+@pytest.mark.parametrize("tau_f,n_levels", [(0.8, 1), (0.8, 2), (1.3, 2)])
+def test_levels_carry_a_standing_sound_wave(tau_f, n_levels):
+    """A standing sound wave rho = 1 + d cos(kx) crosses every level edge.
+    Linear acoustics with the lattice's shear and bulk viscosity nu
+    (momentum flux nu (grad u + grad u^T) in 2D): rho' = d cos kx e^{-nu k^2 t}
+    (cos wt + (nu k^2 / w) sin wt), w = c_s k.  Unlike the slow vortex, the
+    wave changes within one coarse step, so the ghosts' time levels matter:
+    without the mean at odd level times, or with a level's ring timed by the
+    finest level's clock, the error grows to 2-3e-2 of d; here it stays at
+    the uniform lattice's 2e-3."""
+    nc, box, o, T, d = 48, 49, 12, 60, 1e-4
+    k = 2.0 * math.pi / nc
+    nu = (0.5 + (tau_f - 0.5) / 2 ** n_levels - 0.5) / 3.0
+    om = math.sqrt(CS2) * k
+
+    def exact(X):
+        return d * np.cos(k * X) * math.exp(-nu * k * k * T) * (math.cos(om * T) + nu * k * k / om * math.sin(om * T))
+
+    C = _level_coords(n_levels, nc, box, o)
+    w = inputs.Workload("sound", box, box, 0.0, 0.0, box // 2 + 0.3, box // 2 + 0.3, tau_f, 1, inputs.MOTION_HARMONIC,
+                        delta_f=0.1, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                        levels=[(box, box, o, o)] * (n_levels - 1) + [(nc, nc, o, o)])
+    ob = oracle.Oracle(w, mesh=_void_mesh(), rho_init=1 + d * np.cos(k * C[0][0]),
+                       level_rho_init=[1 + d * np.cos(k * C[j][0]) for j in range(1, n_levels + 1)])
+    ob.step(T * 2 ** n_levels)
+    assert ob.status == 0
+    errs = [np.abs(ob.struct_macro()[0] - 1 - exact(C[0][0])).max() / d]
+    errs += [np.abs(ob.level_macro(j)[0] - 1 - exact(C[j][0])).max() / d for j in range(1, n_levels + 1)]
+    assert max(errs) < 5e-3, errs
 
 
 def test_two_level_taylor_green_vortex_converges_at_second_order():
@@ -570,32 +628,36 @@ def test_two_level_taylor_green_vortex_converges_at_second_order():
     assert e1 / e2 > 2.7
 
 
-def test_two_level_zero_disturbance_with_translating_lamina():
-    """Uniform stream on both levels with the lamina and its patch
-    translating along: every node of both lattices stays at f^eq(rho0, u0),
-    so the ring's rescaled f^neq and the restriction vanish exactly as they
+@pytest.mark.parametrize("levels", [[(50, 48, 8, 8)], [(51, 49, 8, 8), (36, 34, 4, 4)]])
+def test_levels_zero_disturbance_with_translating_lamina(levels):
+    """Uniform stream on every level with the lamina and its patch
+    translating along: every node of every lattice stays at f^eq(rho0, u0),
+    so the rings' rescaled f^neq and the restrictions vanish exactly as they
     must for a uniform state."""
     w = _translating_case(0.02, 0.03)
     w.nx, w.ny = 65, 61
-    w.refine, w.nxc, w.nyc, w.ox, w.oy = 1, 50, 48, 8, 8
-    uc = (np.full((48, 50), 0.02), np.full((48, 50), 0.03))
+    w.levels = levels
     o = oracle.Oracle(w, rho_init=np.ones((61, 65)), u_init=(np.full((61, 65), 0.02), np.full((61, 65), 0.03)),
-                      uc_init=uc)
-    o.step(41)
+                      level_u_init=[(np.full((ny, nx), 0.02), np.full((ny, nx), 0.03)) for nx, ny, _, _ in levels])
+    o.step(4 * 10 + 1)
     assert o.status == 0
     r, ux, uy = o.struct_macro()
     disc = o.struct_class() == oracle.DISC
     assert np.abs(ux[disc] - 0.02).max() < 1e-12 and np.abs(uy[disc] - 0.03).max() < 1e-12
     assert np.abs(r[disc] - 1.0).max() < 1e-12
-    # coarse nodes over a fine node that was not computed (under the lamina)
-    # hold f^eq(rho0, 0); the rest must carry the stream
-    cov = np.zeros((48, 50), bool)
-    cov[8:8 + 31, 8:8 + 33] = ~disc[::2, ::2]
-    cov = np.pad(cov, 1)
-    cov = np.logical_or.reduce([cov[1 + a:49 + a, 1 + b:51 + b] for a in (-1, 0, 1) for b in (-1, 0, 1)])
-    assert 0 < cov.sum() < 80
-    r, ux, uy = o.coarse_macro()
-    assert np.abs(ux[~cov] - 0.02).max() < 1e-12 and np.abs(uy[~cov] - 0.03).max() < 1e-12
-    assert np.abs(r - 1.0).max() < 1e-12
+    # nodes over a finer node that was not computed (under the lamina) hold
+    # f^eq(rho0, 0) and pass it on to the next level; the rest carry the stream
+    covered = ~disc
+    fnx, fny = 65, 61
+    for k, (nx, ny, ox, oy) in enumerate(levels, start=1):
+        cov = np.zeros((ny, nx), bool)
+        cov[oy:oy + (fny + 1) // 2, ox:ox + (fnx + 1) // 2] = covered[::2, ::2]
+        cov = np.pad(cov, 1)
+        cov = np.logical_or.reduce([cov[1 + a:ny + 1 + a, 1 + b:nx + 1 + b] for a in (-1, 0, 1) for b in (-1, 0, 1)])
+        assert 0 < cov.sum() < 80
+        r, ux, uy = o.level_macro(k)
+        assert np.abs(ux[~cov] - 0.02).max() < 1e-12 and np.abs(uy[~cov] - 0.03).max() < 1e-12, k
+        assert np.abs(r - 1.0).max() < 1e-12
+        covered, fnx, fny = cov, nx, ny
     r, ux, uy = o.patch_macro()
     assert np.abs(ux - 0.02).max() < 1e-12 and np.abs(r - 1.0).max() < 1e-12
