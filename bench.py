@@ -252,8 +252,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         info = s.info()
         # node updates per step: lattice discretization nodes, the patch, and
-        # on two levels half the coarse lattice (it steps every second step)
-        n_disc, n_u = info["n_struct_disc"] + info["n_coarse"] // 2, info["n_nodes"]
+        # each coarser level's nodes / 2^k (level k steps every 2^k steps)
+        n_disc, n_u = info["n_struct_disc"] + int(info["coarse_updates"]), info["n_nodes"]
         sampler = ClockSampler(local)
         sampler.start()
         time.sleep(0.5)
@@ -400,7 +400,7 @@ def run_ours(args):
             "config": {"workload": w.name, "lattice": f"{w.nx}x{w.ny}", "chord": w.L, "patch_nodes": n_u,
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)"
-                             % (9 * bytes_per * (w.nx * w.ny + w.nxc * w.nyc) / 1e6)},
+                             % (9 * bytes_per * (w.nx * w.ny + sum(a * b for a, b, _, _ in w.levels)) / 1e6)},
             "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "cpu_baseline": cpu, "e2e": e2e,
             "reduced_storage": reduced or None, "variants": variants or None, "refined": refined, "sweep": sweep,
             "gradient": gradient,
@@ -412,10 +412,11 @@ def run_ours(args):
 
 
 def run_refined(stream, args, uniform_ms_per_step, uniform):
-    """The headline domain on two structured levels (Sec. 5 refinement): a
-    2048^2 coarse lattice of spacing 2 and a 1025^2 fine box around the
-    lamina, against the uniform 4096^2 lattice step timed above.  Node
-    updates per step: fine discretization nodes + half the coarse nodes +
+    """The headline domain on nested structured levels (Sec. 5): two levels
+    (a 2048^2 lattice of spacing 2 and a 1025^2 box) and the paper's four
+    (513^2 boxes of spacing 1, 2, 4 and a 512^2 lattice of spacing 8),
+    against the uniform 4096^2 lattice step timed above.  Node updates per
+    step: level-0 discretization nodes + each coarser level's nodes / 2^k +
     the patch; fine-equivalent MLUPS counts the uniform lattice's nodes."""
     import torch
 
@@ -424,30 +425,34 @@ def run_refined(stream, args, uniform_ms_per_step, uniform):
 
     if uniform.name != "lamina-4096-f32":
         return None
-    w = inputs.workload("lamina-4096-refined-f32")
-    k = 2 * max(5, min(args.steps, 300) // 2)
-    with torch.cuda.stream(stream):
-        s = Solver(w, stream=stream.cuda_stream)
-        s.step(2 * max(2, args.warmup // 2))
-        torch.cuda.synchronize()
-        info = s.info()
-        s.profile(True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(k)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ph = s.profile_read()
-        s.profile(False)
-        ms = e0.elapsed_time(e1)
-        status = s.status
-        s.close()
-    updates = info["n_struct_disc"] + info["n_coarse"] / 2 + info["n_nodes"]
-    return {"workload": w.name, "coarse": f"{w.nxc}x{w.nyc}", "fine_box": f"{w.nx}x{w.ny}", "steps": k,
-            "ms_per_step": ms / k, "speedup_vs_uniform": uniform_ms_per_step / (ms / k),
-            "mlups": updates * k / (ms / 1e3) / 1e6,
-            "mlups_fine_equivalent": (uniform.nx * uniform.ny + info["n_nodes"]) * k / (ms / 1e3) / 1e6,
-            "phase_ms_per_step": {p: ph[p][0] / k for p in ph}, "status": status}
+    out = {}
+    for name in ("lamina-4096-refined-f32", "lamina-4096-levels4-f32"):
+        w = inputs.workload(name)
+        period = 2 ** len(w.levels)
+        k = period * max(1, min(args.steps, 320) // period)
+        with torch.cuda.stream(stream):
+            s = Solver(w, stream=stream.cuda_stream)
+            s.step(period * max(1, -(-args.warmup // period)))
+            torch.cuda.synchronize()
+            info = s.info()
+            s.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ph = s.profile_read()
+            s.profile(False)
+            ms = e0.elapsed_time(e1)
+            status = s.status
+            s.close()
+        updates = info["n_struct_disc"] + info["coarse_updates"] + info["n_nodes"]
+        out[name] = {"levels": [f"{w.nx}x{w.ny}"] + [f"{a}x{b}" for a, b, _, _ in w.levels], "steps": k,
+                     "ms_per_step": ms / k, "speedup_vs_uniform": uniform_ms_per_step / (ms / k),
+                     "mlups": updates * k / (ms / 1e3) / 1e6,
+                     "mlups_fine_equivalent": (uniform.nx * uniform.ny + info["n_nodes"]) * k / (ms / 1e3) / 1e6,
+                     "phase_ms_per_step": {p: ph[p][0] / k for p in ph}, "status": status}
+    return out
 
 
 def run_sweep(stream, args):
@@ -547,7 +552,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16/BF16 lattice-storage runs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-instance KC/beta sweep")
-    ap.add_argument("--no-refined", action="store_true", help="skip the two-level lattice run")
+    ap.add_argument("--no-refined", action="store_true", help="skip the nested-level lattice runs")
     ap.add_argument("--sweep-steps", type=int, default=10)
     ap.add_argument("--no-gradient", action="store_true", help="skip the Theta-gradient case")
     args = ap.parse_args()

@@ -82,6 +82,34 @@ extern "C" {
  * rho_init / ux_init / uy_init: optional host arrays [ny*nx] of the initial
  * density and velocity (the state starts at equilibrium); NULL selects rho0
  * and (u0x, u0y) everywhere. */
+/* One coarser lattice level around the solver's lattice (level 0).  Level k
+ * (levels[k-1]) has twice the spacing and time step of level k-1, nx x ny
+ * nodes, and holds node (0, 0) of level k-1 at its node (ox, oy); its
+ * relaxation time is tau_k = 1/2 + (tau_s - 1/2)/2^k (same viscosity).
+ * Each step of level k-1's box, its outermost ring is rebuilt from level k
+ * (rho, u and post-collision f^neq rescaled by (tau_{k-1} - 1)/(2 (tau_k - 1));
+ * the four-point cubic midpoint rule along the box edge; at odd times of
+ * level k-1 the mean of level k's two times around it), and whenever level
+ * k-1 has caught up with level k, level k's nodes strictly inside the box
+ * take level k-1's post-collision state with f^neq rescaled back.  Every
+ * level inside another has odd nx, ny; the boundary kinds of hlbm_grid_t
+ * apply to the coarsest level.  Level k starts at equilibrium with rho_init,
+ * ux_init, uy_init ([ny*nx], NULL: rho0, u0x, u0y) and then takes level
+ * k-1's initial state inside the box.  hlbm_create fails with HLBM_EINVAL
+ * unless each box has odd sizes of at least 9 and keeps to the edges of the
+ * level around it a margin of one node (two when that level is itself inside
+ * another: the cubic rule must not reach a ring), n_levels <=
+ * HLBM_MAX_LEVELS, and every tau_k (k = 0 .. n_levels) differs from 1 by
+ * more than 1e-3. */
+#define HLBM_MAX_LEVELS 4
+typedef struct {
+    int32_t nx, ny;
+    int32_t ox, oy;
+    const double* rho_init;
+    const double* ux_init;
+    const double* uy_init;
+} hlbm_level_t;
+
 typedef struct {
     int32_t nx, ny;
     int32_t bc_x, bc_y; /* sides x = 0, nx-1 and y = 0, ny-1 */
@@ -91,27 +119,11 @@ typedef struct {
     const double* rho_init;
     const double* ux_init;
     const double* uy_init;
-    /* Two structured refinement levels (Sec. 5 runs its lattice on nested
-     * levels; the coupling is not given there).  refine = 1 makes the
-     * nx x ny lattice (nx, ny odd) a fine box whose node (0, 0) sits on node
-     * (ox, oy) of an nxc x nyc coarse lattice of twice the spacing and time
-     * step; bc_x, bc_y then apply to the coarse lattice, and tau_c - 1/2 =
-     * (tau_s - 1/2)/2 keeps the viscosity.  Each coarse step the box's
-     * outermost ring is rebuilt from the coarse rho, u and post-collision
-     * f^neq rescaled by (tau_s - 1)/(2 (tau_c - 1)) (cubic along the box
-     * edge, the mean of two coarse times at odd fine times), and the coarse
-     * nodes strictly inside the box take the fine post-collision state with
-     * f^neq rescaled back.  The coarse lattice starts at equilibrium with
-     * rho0 and uxc_init / uyc_init ([nyc*nxc], NULL: u0x, u0y), then takes
-     * the box's initial state.  hlbm_create fails with HLBM_EINVAL unless
-     * nx, ny are odd and at least 9, ox, oy >= 1, ox + (nx+1)/2 <= nxc - 1,
-     * oy + (ny+1)/2 <= nyc - 1, and tau_s differs from 1 and 3/2 by more
-     * than 1e-3. */
-    int32_t refine;
-    int32_t nxc, nyc;
-    int32_t ox, oy;
-    const double* uxc_init;
-    const double* uyc_init;
+    /* Nested structured refinement levels (Sec. 5 runs its lattice on four
+     * levels; the coupling is not given there): n_levels coarser lattices,
+     * levels[0] first (see hlbm_level_t).  0 = one uniform lattice. */
+    int32_t n_levels;
+    const hlbm_level_t* levels;
 } hlbm_grid_t;
 
 /* Body-fitted triangular patch around the lamina (Sec. 3, Sec. 4).
@@ -220,11 +232,11 @@ int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re
 int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double* rho_u,
                     double* ux_u, double* uy_u);
 
-/* Coarse lattice of a refined solver (hlbm_grid_t.refine = 1): rho, ux, uy
- * [nyc*nxc] at the last even time (time - time % 2).  Coarse nodes over a
- * fine node that was not computed hold rho0 and zero velocity.  HLBM_EINVAL
- * for a solver without refinement. */
-int hlbm_get_coarse_fields(hlbm_t* h, double* rho, double* ux, double* uy);
+/* Coarser lattice level k (1 .. n_levels): rho, ux, uy [ny_k*nx_k] at its
+ * current time (the solver's time rounded down to a multiple of 2^k).
+ * Nodes over a node of the finer level that was not computed (under the
+ * lamina) hold rho0 and zero velocity.  HLBM_EINVAL for another k. */
+int hlbm_get_level_fields(hlbm_t* h, int32_t level, double* rho, double* ux, double* uy);
 
 /* Node classes of the last step on the whole lattice [ny*nx]:
  * 0 discretization, 1 interpolation, 2 unused (Sec. 4). */
@@ -248,12 +260,14 @@ typedef struct {
     int64_t n_struct_disc; /* discretization nodes in the last step       */
     int32_t n_nodes, n_tris, nnz, n_outer, n_wall_segments;
     int32_t box_w, box_h;  /* lattice window that follows the patch       */
-    int32_t launches_per_step; /* kernels per step (two levels: even steps)    */
+    int32_t launches_per_step; /* kernels per step (with levels: the most)     */
     int32_t dtype;
     int32_t fv_kernel; /* HLBM_FV_* in use                                */
     int32_t n_tiles;   /* FV tiles (blocks of the FV launch)               */
     double y, vy;      /* lamina displacement and velocity at `time`       */
-    int64_t n_coarse;  /* coarse lattice nodes (0 without refinement)      */
+    int32_t n_levels;       /* coarser lattice levels                     */
+    int64_t n_coarse;       /* nodes of all coarser levels                */
+    double coarse_updates;  /* their node updates per step, sum N_k / 2^k */
 } hlbm_info_t;
 int hlbm_info(hlbm_t* h, hlbm_info_t* info);
 

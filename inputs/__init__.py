@@ -396,6 +396,23 @@ def workload(name: str) -> Workload:
         w.name, w.dtype = name, name.split("-")[-1]
         w.levels = [(204, 160, 51, 40)]
         return w
+    if name.startswith("lamina-small-levels3-"):
+        # the small case's lattice inside two coarser levels (spacings 2, 4)
+        w = workload("lamina-small-f32")
+        w.name, w.dtype = name, name.split("-")[-1]
+        w.levels = [(211, 167, 52, 43), (216, 176, 53, 44)]
+        return w
+    if name == "lamina-4096-levels4-f32":
+        # the 4096^2 workload's domain and lamina on the paper's four levels
+        # (Sec. 5): 513^2 boxes of spacing 1, 2, 4 (4, 8, 16 chords wide) and
+        # a 512^2 lattice of spacing 8 over the whole domain; the lamina
+        # centre is at (2048.3, 2048.2) of the whole domain
+        w = workload("lamina-4096-f32")
+        w.name = name
+        w.nx = w.ny = 513
+        w.xc, w.yc = 256.3, 256.2
+        w.levels = [(513, 513, 128, 128), (513, 513, 128, 128), (512, 512, 128, 128)]
+        return w
     if name == "lamina-4096-refined-f32":
         # the 4096^2 workload's domain and lamina on two levels: a 2048^2
         # coarse lattice of spacing 2 with a 1025^2 fine box (8 chords wide)
@@ -406,6 +423,15 @@ def workload(name: str) -> Workload:
         w.nx = w.ny = 1025
         w.xc, w.yc = 512.3, 512.2
         w.levels = [(2048, 2048, 768, 768)]
+        return w
+    if name.startswith("lamina-1024-levels4-"):
+        # the 1024^2 workload's domain on four levels: 129^2 boxes of spacing
+        # 1, 2, 4 (4, 8, 16 chords) and a 128^2 lattice of spacing 8
+        w = workload("lamina-1024-" + name.split("-")[-1])
+        w.name = name
+        w.nx = w.ny = 129
+        w.xc, w.yc = 64.3, 64.2
+        w.levels = [(129, 129, 32, 32), (129, 129, 32, 32), (128, 128, 32, 32)]
         return w
     if name.startswith("lamina-1024-refined-"):
         # the 1024^2 workload's domain on two levels: a 512^2 coarse lattice

@@ -20,12 +20,19 @@ _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 
 
+MAX_LEVELS = 4
+
+
+class hlbm_level_t(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ox", C.c_int32), ("oy", C.c_int32),
+                ("rho_init", _dp), ("ux_init", _dp), ("uy_init", _dp)]
+
+
 class hlbm_grid_t(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
                 ("dtype", C.c_int32), ("rho0", C.c_double), ("u0x", C.c_double), ("u0y", C.c_double),
                 ("rho_init", _dp), ("ux_init", _dp), ("uy_init", _dp),
-                ("refine", C.c_int32), ("nxc", C.c_int32), ("nyc", C.c_int32), ("ox", C.c_int32),
-                ("oy", C.c_int32), ("uxc_init", _dp), ("uyc_init", _dp)]
+                ("n_levels", C.c_int32), ("levels", C.POINTER(hlbm_level_t))]
 
 
 class hlbm_patch_t(C.Structure):
@@ -46,7 +53,8 @@ class hlbm_info_t(C.Structure):
                 ("n_nodes", C.c_int32), ("n_tris", C.c_int32), ("nnz", C.c_int32), ("n_outer", C.c_int32),
                 ("n_wall_segments", C.c_int32), ("box_w", C.c_int32), ("box_h", C.c_int32),
                 ("launches_per_step", C.c_int32), ("dtype", C.c_int32), ("fv_kernel", C.c_int32),
-                ("n_tiles", C.c_int32), ("y", C.c_double), ("vy", C.c_double), ("n_coarse", C.c_int64)]
+                ("n_tiles", C.c_int32), ("y", C.c_double), ("vy", C.c_double), ("n_levels", C.c_int32),
+                ("n_coarse", C.c_int64), ("coarse_updates", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -61,7 +69,7 @@ SIGNATURES = {
     "hlbm_force": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp, _dp]),
     "hlbm_gamma": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _dp, _dp, _dp]),
     "hlbm_get_fields": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp]),
-    "hlbm_get_coarse_fields": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+    "hlbm_get_level_fields": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp, _dp]),
     "hlbm_get_class": (C.c_int, [C.c_void_p, C.POINTER(C.c_int8)]),
     "hlbm_get_refill": (C.c_int, [C.c_void_p, _ip, _ip]),
     "hlbm_get_patch_f": (C.c_int, [C.c_void_p, _dp]),

@@ -52,14 +52,17 @@ struct hlbm {
 
     Dev<float> df{};
     Dev<double> dd{};
-    // two-level lattice: the coarse lattice (window-less), its population
-    // buffers (cbuf[cci] holds coarse time t/2 rounded down) and coupling
-    bool refine = false;
-    Dev<float> cf{};
-    Dev<double> cd{};
-    void* cbuf[2] = {nullptr, nullptr};
-    int cci = 0;
-    Refine ref{};
+    // nested lattice levels: lv[k-1] is level k (twice the spacing of level
+    // k-1), a window-less lattice with population buffers buf[cur] at its
+    // current time and buf[1 - cur] at its next; ref couples it with level k-1
+    struct Level {
+        Dev<float> df{};
+        Dev<double> dd{};
+        void* buf[2] = {nullptr, nullptr};
+        int cur = 0;
+        Refine ref{};
+    };
+    std::vector<Level> lv;
     void* fbuf[2] = {nullptr, nullptr};  // lattice populations
     void* sbox[2] = {nullptr, nullptr};  // window states
     int8_t* cls[2] = {nullptr, nullptr};
@@ -182,14 +185,54 @@ Dev<double>& dev_of<double>(hlbm* h) {
 }
 
 template <typename T>
-Dev<T>& cdev_of(hlbm* h);
+Dev<T>& ldev_of(hlbm::Level& L);
 template <>
-Dev<float>& cdev_of<float>(hlbm* h) {
-    return h->cf;
+Dev<float>& ldev_of<float>(hlbm::Level& L) {
+    return L.df;
 }
 template <>
-Dev<double>& cdev_of<double>(hlbm* h) {
-    return h->cd;
+Dev<double>& ldev_of<double>(hlbm::Level& L) {
+    return L.dd;
+}
+
+// Levels around the solver's lattice.  level_step: level k >= 1 streams
+// and collides its current buffer into its next.  level_couple: for the
+// pair (k, k+1) after a step of the finest lattice that brought the time
+// to t1, the restriction of level k onto level k+1 when level k has caught
+// up with it (then level k+1's buffers swap), and level k's ring at its new
+// time when level k has just stepped.  fine_now is level 0's current buffer.
+template <typename T>
+void level_step(hlbm* h, int k, cudaStream_t s) {
+    hlbm::Level& L = h->lv[k - 1];
+    Dev<T>& c = ldev_of<T>(L);
+    c.fA = (T*)L.buf[L.cur];
+    c.fB = (T*)L.buf[1 - L.cur];
+    StepArgs ac{};
+    launch_stream_collide<T>(c, ac, s);
+}
+
+template <typename T>
+bool level_couple(hlbm* h, int k, int64_t t1, void* fine_now, int bx0, int by0, bool initial, cudaStream_t s) {
+    hlbm::Level& C = h->lv[k];  // level k+1
+    const bool restrict_now = initial || t1 % ((int64_t)2 << k) == 0;
+    const bool ring_now = initial || t1 % ((int64_t)1 << k) == 0;
+    if (!ring_now) return false;
+    Dev<T>& d = k == 0 ? dev_of<T>(h) : ldev_of<T>(h->lv[k - 1]);
+    void* fnow = k == 0 ? fine_now : h->lv[k - 1].buf[h->lv[k - 1].cur];
+    Couple cp{};
+    if (restrict_now) {
+        cp.rsrc = fnow;
+        cp.rdst = C.buf[initial ? C.cur : 1 - C.cur];
+        cp.bx0 = bx0;
+        cp.by0 = by0;
+        if (!initial) C.cur = 1 - C.cur;
+    }
+    const int64_t tk = initial ? 0 : t1 >> k;
+    cp.c0 = C.buf[C.cur];
+    cp.c1 = (tk & 1) ? C.buf[1 - C.cur] : nullptr;
+    cp.ring_dst = fnow;
+    launch_couple<T>(d, C.ref, cp, s);
+    return true;
 }
 
 template <typename T>
@@ -321,34 +364,16 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
     // 4. stream-collide t -> t+1 (eq. LBE)
     ev = phase_begin(h, s);
     int nl = 1;
-    if (h->refine && (t & 1) == 0) {
-        // coarse lattice T -> T+1 (T = t/2)
-        Dev<T>& c = cdev_of<T>(h);
-        c.fA = (T*)h->cbuf[h->cci];
-        c.fB = (T*)h->cbuf[1 - h->cci];
-        StepArgs ac{};
-        launch_stream_collide<T>(c, ac, s);
-        ++nl;
-    }
-    launch_stream_collide<T>(d, a, s);
-    if (h->refine) {
-        // t odd: the box's post-collision state at t+1 onto coarse time T+1,
-        // which then becomes the current coarse buffer; the ring at t+1 from
-        // coarse T+1 (t odd) or the mean of T and T+1 (t even)
-        Couple cp{};
-        if (t & 1) {
-            cp.rsrc = d.fB;
-            cp.rdst = h->cbuf[1 - h->cci];
-            cp.bx0 = a.bx0;
-            cp.by0 = a.by0;
-            h->cci = 1 - h->cci;
+    // the levels whose step starts now, coarsest first
+    for (int k = (int)h->lv.size(); k >= 1; --k)
+        if (t % ((int64_t)1 << k) == 0) {
+            level_step<T>(h, k, s);
+            ++nl;
         }
-        cp.c0 = h->cbuf[h->cci];
-        cp.c1 = (t & 1) ? nullptr : h->cbuf[1 - h->cci];
-        cp.ring_dst = d.fB;
-        launch_couple<T>(d, h->ref, cp, s);
-        ++nl;
-    }
+    launch_stream_collide<T>(d, a, s);
+    // restrictions (finest first) and the rings of the levels that just stepped
+    for (int k = 0; k < (int)h->lv.size(); ++k)
+        nl += level_couple<T>(h, k, t + 1, d.fB, a.bx0, a.by0, false, s) ? 1 : 0;
     phase_end(h, HLBM_PHASE_STREAM, ev, nl, s);
     // 5a. the outer nodes' feed from the lattice at t and t+1
     launch_feed<T>(d, a, s);
@@ -631,10 +656,10 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     const size_t lat_elem = g->dtype == HLBM_F16 || g->dtype == HLBM_BF16 ? 2 : sizeof(T);
     d.pitch = (g->nx + 31) / 32 * 32;
     d.plane = (int64_t)d.pitch * g->ny;
-    // with refinement the boundary kinds belong to the coarse lattice; the
-    // fine ring is rebuilt from it every step, whatever the fine pull wrote
-    d.bc_x = g->refine ? HLBM_BC_OUTFLOW : g->bc_x;
-    d.bc_y = g->refine ? HLBM_BC_OUTFLOW : g->bc_y;
+    // with levels the boundary kinds belong to the coarsest one; the ring of
+    // every finer level is rebuilt every step, whatever its pull wrote
+    d.bc_x = g->n_levels ? HLBM_BC_OUTFLOW : g->bc_x;
+    d.bc_y = g->n_levels ? HLBM_BC_OUTFLOW : g->bc_y;
     d.rho0 = T(g->rho0);
     d.tau_s = T(h->tau_s);
     d.tau_u = T(h->tau_s - 0.5);
@@ -867,34 +892,38 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         if (!h->fbuf[b] || !h->sbox[b] || !h->cls[b] || !h->fu[b])
             return fail(h, HLBM_ENOMEM, "device allocation failed (lattice %zu bytes per buffer)", fbytes);
     }
-    if (g->refine) {
-        Dev<T>& c = cdev_of<T>(h);
+    h->lv.resize(g->n_levels);
+    for (int k = 1; k <= g->n_levels; ++k) {
+        const hlbm_level_t& G = g->levels[k - 1];
+        hlbm::Level& L = h->lv[k - 1];
+        Dev<T>& c = ldev_of<T>(L);
         c = d;
-        c.nx = g->nxc;
-        c.ny = g->nyc;
-        c.pitch = (g->nxc + 31) / 32 * 32;
-        c.plane = (int64_t)c.pitch * g->nyc;
-        c.bc_x = g->bc_x;
-        c.bc_y = g->bc_y;
-        const double tau_c = 0.5 + 0.5 * (h->tau_s - 0.5);
+        c.nx = G.nx;
+        c.ny = G.ny;
+        c.pitch = (G.nx + 31) / 32 * 32;
+        c.plane = (int64_t)c.pitch * G.ny;
+        const bool coarsest = k == g->n_levels;
+        c.bc_x = coarsest ? g->bc_x : HLBM_BC_OUTFLOW;
+        c.bc_y = coarsest ? g->bc_y : HLBM_BC_OUTFLOW;
+        const double tau_f = 0.5 + std::ldexp(h->tau_s - 0.5, -(k - 1)), tau_c = 0.5 + std::ldexp(h->tau_s - 0.5, -k);
         c.tau_s = T(tau_c);
-        c.bw = c.bh = 0;  // no window: every coarse node is a discretization node
+        c.bw = c.bh = 0;  // no window: every node of a coarser level is computed
         c.bplane = 0;
-        h->refine = true;
-        h->ref.nxc = g->nxc;
-        h->ref.nyc = g->nyc;
-        h->ref.pitch = c.pitch;
-        h->ref.plane = c.plane;
-        h->ref.ox = g->ox;
-        h->ref.oy = g->oy;
-        h->ref.acf = (h->tau_s - 1.0) / (2.0 * (tau_c - 1.0));
-        h->ref.afc = 2.0 * (tau_c - 1.0) / (h->tau_s - 1.0);
+        L.ref.nxc = G.nx;
+        L.ref.nyc = G.ny;
+        L.ref.pitch = c.pitch;
+        L.ref.plane = c.plane;
+        L.ref.ox = G.ox;
+        L.ref.oy = G.oy;
+        L.ref.acf = (tau_f - 1.0) / (2.0 * (tau_c - 1.0));
+        L.ref.afc = 2.0 * (tau_c - 1.0) / (tau_f - 1.0);
         const size_t cbytes = (size_t)9 * c.plane * lat_elem;
         for (int b = 0; b < 2; ++b) {
-            h->cbuf[b] = dev_alloc(h, cbytes);
-            if (!h->cbuf[b]) return fail(h, HLBM_ENOMEM, "device allocation failed (coarse lattice %zu bytes)", cbytes);
-            cudaMemsetAsync(h->cbuf[b], 0, cbytes, s);
+            L.buf[b] = dev_alloc(h, cbytes);
+            if (!L.buf[b]) return fail(h, HLBM_ENOMEM, "device allocation failed (level %d, %zu bytes)", k, cbytes);
+            cudaMemsetAsync(L.buf[b], 0, cbytes, s);
         }
+        L.cur = 0;
     }
     d.xy = upload(h, h->xy.data(), h->xy.size(), &rc);
     d.kind = upload(h, h->kind.data(), h->kind.size(), &rc);
@@ -972,30 +1001,25 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     launch_classify<T>(d, a, s);
     d.sbox_old = (const T*)h->sbox[0];
     launch_patch_init<T>(d, a, s);
-    double* dcux = nullptr;
-    double* dcuy = nullptr;
-    if (h->refine) {
-        // coarse lattice: equilibrium at rho0 and its initial velocity, then
-        // the box's initial state restricted onto it and the ring from it
-        const size_t Nc = (size_t)g->nxc * g->nyc;
-        dcux = g->uxc_init ? upload(h, g->uxc_init, Nc, &rc) : nullptr;
-        dcuy = g->uyc_init ? upload(h, g->uyc_init, Nc, &rc) : nullptr;
+    // coarser levels: equilibrium at their initial state, then each takes
+    // the initial state of the level inside it (finest first) and rebuilds
+    // that level's ring
+    std::vector<double*> lvinit;
+    for (int k = 1; k <= g->n_levels; ++k) {
+        const hlbm_level_t& G = g->levels[k - 1];
+        const size_t Nc = (size_t)G.nx * G.ny;
+        double* lr = G.rho_init ? upload(h, G.rho_init, Nc, &rc) : nullptr;
+        double* lx = G.ux_init ? upload(h, G.ux_init, Nc, &rc) : nullptr;
+        double* ly = G.uy_init ? upload(h, G.uy_init, Nc, &rc) : nullptr;
+        lvinit.insert(lvinit.end(), {lr, lx, ly});
         if (rc != HLBM_OK) return rc;
-        Dev<T>& c = cdev_of<T>(h);
-        c.fA = (T*)h->cbuf[0];
-        c.fB = (T*)h->cbuf[1];
-        launch_init_struct<T>(c, nullptr, dcux, dcuy, g->u0x, g->u0y, s);
-        Couple cp{};
-        cp.rsrc = d.fA;
-        cp.rdst = h->cbuf[0];
-        cp.bx0 = a.bx0;
-        cp.by0 = a.by0;
-        cp.c0 = h->cbuf[0];
-        cp.ring_dst = d.fA;
-        launch_couple<T>(d, h->ref, cp, s);
-        h->cci = 0;
+        Dev<T>& c = ldev_of<T>(h->lv[k - 1]);
+        c.fA = (T*)h->lv[k - 1].buf[0];
+        c.fB = (T*)h->lv[k - 1].buf[1];
+        launch_init_struct<T>(c, lr, lx, ly, g->u0x, g->u0y, s);
     }
-    h->ui = 1;
+    for (int k = 0; k < g->n_levels; ++k) level_couple<T>(h, k, 0, d.fA, a.bx0, a.by0, true, s);
+    h->ui = 1;  // the type-1 fill wrote the patch into fu[1]
     bind(h, d);
     launch_force<T>(d, 0, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -1005,8 +1029,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     dev_free(h, drho);
     dev_free(h, dux);
     dev_free(h, duy);
-    dev_free(h, dcux);
-    dev_free(h, dcuy);
+    for (double* p : lvinit) dev_free(h, p);
     h->t = 0;
     h->Xprev = X0;
     h->Yprev = Y0;
@@ -1047,7 +1070,8 @@ struct CkptHeader {
     uint32_t status, pad;
     double mass, stiffness, damping, y0, v0;  // INDUCED motion parameters
     double Yi, Vi;                            // and its state at t
-    int32_t refine, nxc, nyc, ox, oy, cci;    // two-level lattice
+    int32_t n_levels, lv_cur[HLBM_MAX_LEVELS]; // nested levels and their current buffers
+    int32_t lv_dim[HLBM_MAX_LEVELS][4];       // nx, ny, ox, oy of each
 };
 constexpr char kCkptMagic[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
 
@@ -1073,7 +1097,7 @@ CkptHeader ckpt_header(hlbm* h) {
     Dev<T>& d = dev_of<T>(h);
     CkptHeader c{};
     std::memcpy(c.magic, kCkptMagic, 8);
-    c.version = 3;
+    c.version = 4;
     c.dtype = h->dtype;
     c.nx = d.nx;
     c.ny = d.ny;
@@ -1115,12 +1139,14 @@ CkptHeader ckpt_header(hlbm* h) {
     c.si = h->si;
     c.ui = h->ui;
     c.fi = h->fi;
-    c.refine = h->refine ? 1 : 0;
-    c.nxc = h->ref.nxc;
-    c.nyc = h->ref.nyc;
-    c.ox = h->ref.ox;
-    c.oy = h->ref.oy;
-    c.cci = h->cci;
+    c.n_levels = (int32_t)h->lv.size();
+    for (size_t k = 0; k < h->lv.size(); ++k) {
+        c.lv_cur[k] = h->lv[k].cur;
+        c.lv_dim[k][0] = h->lv[k].ref.nxc;
+        c.lv_dim[k][1] = h->lv[k].ref.nyc;
+        c.lv_dim[k][2] = h->lv[k].ref.ox;
+        c.lv_dim[k][3] = h->lv[k].ref.oy;
+    }
     return c;
 }
 
@@ -1131,25 +1157,17 @@ std::vector<std::pair<void*, size_t>> ckpt_sections(hlbm* h, int64_t t) {
     const size_t lat = (d.store ? 2 : sizeof(T)) * 9 * (size_t)d.plane;
     const size_t box = sizeof(T) * 9 * (size_t)d.bplane;
     const size_t rec = sizeof(T) * kRec * (size_t)d.n;
-    if (h->refine) {
-        const size_t clat = (d.store ? 2 : sizeof(T)) * 9 * (size_t)h->ref.plane;
-        return {{h->fbuf[0], lat},         {h->fbuf[1], lat},         {h->sbox[0], box},
-                {h->sbox[1], box},         {h->cls[0], (size_t)d.bplane}, {h->cls[1], (size_t)d.bplane},
-                {h->fu[0], rec},           {h->fu[1], rec},           {d.rtype, sizeof(int32_t) * (size_t)d.n},
-                {d.rdonor, sizeof(int32_t) * (size_t)d.n}, {h->force, 2 * sizeof(double) * (size_t)(t + 1)},
-                {h->cbuf[0], clat},        {h->cbuf[1], clat}};
+    std::vector<std::pair<void*, size_t>> secs = {
+        {h->fbuf[0], lat},  {h->fbuf[1], lat},  {h->sbox[0], box},
+        {h->sbox[1], box},  {h->cls[0], (size_t)d.bplane}, {h->cls[1], (size_t)d.bplane},
+        {h->fu[0], rec},    {h->fu[1], rec},    {d.rtype, sizeof(int32_t) * (size_t)d.n},
+        {d.rdonor, sizeof(int32_t) * (size_t)d.n}, {h->force, 2 * sizeof(double) * (size_t)(t + 1)}};
+    for (auto& L : h->lv) {
+        const size_t clat = (d.store ? 2 : sizeof(T)) * 9 * (size_t)L.ref.plane;
+        secs.push_back({L.buf[0], clat});
+        secs.push_back({L.buf[1], clat});
     }
-    return {{h->fbuf[0], lat},
-            {h->fbuf[1], lat},
-            {h->sbox[0], box},
-            {h->sbox[1], box},
-            {h->cls[0], (size_t)d.bplane},
-            {h->cls[1], (size_t)d.bplane},
-            {h->fu[0], rec},
-            {h->fu[1], rec},
-            {d.rtype, sizeof(int32_t) * (size_t)d.n},
-            {d.rdonor, sizeof(int32_t) * (size_t)d.n},
-            {h->force, 2 * sizeof(double) * (size_t)(t + 1)}};
+    return secs;
 }
 
 constexpr size_t kCkptChunk = size_t(64) << 20;
@@ -1189,7 +1207,7 @@ int load_impl(hlbm* h, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(h, HLBM_EIO, "cannot open %s", path);
     CkptHeader c{};
-    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 3) {
+    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 4) {
         std::fclose(fp);
         return fail(h, HLBM_EIO, "%s is not a solver checkpoint", path);
     }
@@ -1202,8 +1220,10 @@ int load_impl(hlbm* h, const char* path) {
                       c.tau_s == m.tau_s && c.rho0 == m.rho0 && c.A == m.A && c.omega == m.omega &&
                       c.vx == m.vx && c.vy == m.vy && c.lamina_L == m.lamina_L && c.lamina_T == m.lamina_T &&
                       c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash &&
-                      c.refine == m.refine && c.nxc == m.nxc && c.nyc == m.nyc && c.ox == m.ox && c.oy == m.oy;
-    if (!same || c.t < 0 || ((c.ci | c.si | c.ui | c.fi | c.cci) & ~1)) {
+                      c.n_levels == m.n_levels && std::memcmp(c.lv_dim, m.lv_dim, sizeof c.lv_dim) == 0;
+    int lv_bits = 0;
+    for (int k = 0; k < HLBM_MAX_LEVELS; ++k) lv_bits |= c.lv_cur[k];
+    if (!same || c.t < 0 || ((c.ci | c.si | c.ui | c.fi | lv_bits) & ~1)) {
         std::fclose(fp);
         return fail(h, HLBM_EINVAL, "%s was written by a solver with other inputs", path);
     }
@@ -1264,7 +1284,7 @@ int load_impl(hlbm* h, const char* path) {
     h->si = c.si;
     h->ui = c.ui;
     h->fi = c.fi;
-    h->cci = c.cci;
+    for (size_t k = 0; k < h->lv.size(); ++k) h->lv[k].cur = c.lv_cur[k];
     Dev<T>& d = dev_of<T>(h);
     e = cudaMemcpyAsync(h->status, &c.status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
     // the FV kernel counts sub-steps from t * n_sub
@@ -1489,19 +1509,27 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
     else if (!(p.delta_f > 1.5))
         rc = fail(h, HLBM_EINVAL, "delta_f = %g must exceed 1.5 (interpolation nodes outside the body)",
                   p.delta_f);
-    else if (grid->refine != 0 && grid->refine != 1)
-        rc = fail(h, HLBM_EINVAL, "refine = %d must be 0 or 1", grid->refine);
-    else if (grid->refine &&
-             (grid->nx % 2 == 0 || grid->ny % 2 == 0 || grid->nx < 9 || grid->ny < 9 || grid->ox < 1 ||
-              grid->oy < 1 || grid->ox + (grid->nx + 1) / 2 > grid->nxc - 1 ||
-              grid->oy + (grid->ny + 1) / 2 > grid->nyc - 1))
-        rc = fail(h, HLBM_EINVAL,
-                  "fine box %dx%d at coarse node (%d, %d) must have odd sizes >= 9 and keep one coarse node "
-                  "to the edges of the %dx%d coarse lattice",
-                  grid->nx, grid->ny, grid->ox, grid->oy, grid->nxc, grid->nyc);
-    else if (grid->refine && (std::fabs(tau_s - 1.0) <= 1e-3 || std::fabs(tau_s - 1.5) <= 1e-3))
-        rc = fail(h, HLBM_EINVAL, "tau_s = %g: the f^neq rescaling between levels needs tau_s != 1 and != 3/2",
-                  tau_s);
+    else if (grid->n_levels < 0 || grid->n_levels > HLBM_MAX_LEVELS || (grid->n_levels && !grid->levels))
+        rc = fail(h, HLBM_EINVAL, "n_levels = %d must be 0 .. %d with the levels given", grid->n_levels,
+                  HLBM_MAX_LEVELS);
+    for (int k = 1; rc == HLBM_OK && k <= grid->n_levels; ++k) {
+        // level k-1 (the box) inside level k
+        const hlbm_level_t& G = grid->levels[k - 1];
+        const int bx = k == 1 ? grid->nx : grid->levels[k - 2].nx, by = k == 1 ? grid->ny : grid->levels[k - 2].ny;
+        const int m = k == grid->n_levels ? 1 : 2;
+        if (bx % 2 == 0 || by % 2 == 0 || bx < 9 || by < 9 || G.ox < m || G.oy < m ||
+            G.ox + (bx + 1) / 2 > G.nx - m || G.oy + (by + 1) / 2 > G.ny - m)
+            rc = fail(h, HLBM_EINVAL,
+                      "level %d: the %dx%d box at node (%d, %d) must have odd sizes >= 9 and keep %d node(s) to the "
+                      "edges of the %dx%d level around it",
+                      k - 1, bx, by, G.ox, G.oy, m, G.nx, G.ny);
+    }
+    for (int k = 0; rc == HLBM_OK && grid->n_levels > 0 && k <= grid->n_levels; ++k) {
+        const double tk = 0.5 + std::ldexp(tau_s - 0.5, -k);
+        if (std::fabs(tk - 1.0) <= 1e-3)
+            rc = fail(h, HLBM_EINVAL, "tau of level %d is %g: the f^neq rescaling between levels needs tau != 1", k,
+                      tk);
+    }
     if (rc == HLBM_OK) {
         h->xy.assign(p.xy, p.xy + 2 * (size_t)p.n_nodes);
         h->tri.assign(p.tri, p.tri + 3 * (size_t)p.n_tris);
@@ -1755,25 +1783,27 @@ int hlbm_get_fields(hlbm_t* h, double* rho_s, double* ux_s, double* uy_s, double
     return rc;
 }
 
-int hlbm_get_coarse_fields(hlbm_t* h, double* rho, double* ux, double* uy) {
+int hlbm_get_level_fields(hlbm_t* h, int32_t level, double* rho, double* ux, double* uy) {
     if (!h) return HLBM_EINVAL;
-    if (!h->refine) return fail(h, HLBM_EINVAL, "the solver has no coarse lattice");
-    const size_t N = (size_t)h->ref.nxc * h->ref.nyc;
+    if (level < 1 || level > (int)h->lv.size())
+        return fail(h, HLBM_EINVAL, "level %d: the solver has %zu coarser levels", level, h->lv.size());
+    hlbm::Level& L = h->lv[level - 1];
+    const size_t N = (size_t)L.ref.nxc * L.ref.nyc;
     double* buf = (double*)dev_alloc(h, 3 * N * sizeof(double));
     if (!buf) return fail(h, HLBM_ENOMEM, "readback buffer");
     if (h->dtype != HLBM_F64) {
-        h->cf.fA = (float*)h->cbuf[h->cci];
-        launch_struct_macro<float>(h->cf, buf, buf + N, buf + 2 * N, h->stream);
+        L.df.fA = (float*)L.buf[L.cur];
+        launch_struct_macro<float>(L.df, buf, buf + N, buf + 2 * N, h->stream);
     } else {
-        h->cd.fA = (double*)h->cbuf[h->cci];
-        launch_struct_macro<double>(h->cd, buf, buf + N, buf + 2 * N, h->stream);
+        L.dd.fA = (double*)L.buf[L.cur];
+        launch_struct_macro<double>(L.dd, buf, buf + N, buf + 2 * N, h->stream);
     }
     double* dst[3] = {rho, ux, uy};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         if (dst[k]) e = cudaMemcpyAsync(dst[k], buf + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    int rc = e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "coarse field readback");
+    int rc = e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "level field readback");
     dev_free(h, buf);
     return rc;
 }
@@ -1862,9 +1892,17 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     info->box_w = bw;
     info->box_h = bh;
     // refill, classify, fill, stream-collide, feed, FV sub-steps, force (2)
-    // refined: + the coupling launch, + the coarse lattice on even steps (counted here)
-    info->launches_per_step = h->refine ? 10 : 8;
-    info->n_coarse = h->refine ? (int64_t)h->ref.nxc * h->ref.nyc : 0;
+    // with levels: + one coupling launch and one stream-collide per level
+    // at a step where all of them start (every 2^n_levels steps)
+    info->launches_per_step = 8 + 2 * (int32_t)h->lv.size();
+    info->n_levels = (int32_t)h->lv.size();
+    info->n_coarse = 0;
+    info->coarse_updates = 0.0;
+    for (size_t k = 0; k < h->lv.size(); ++k) {
+        const int64_t nk = (int64_t)h->lv[k].ref.nxc * h->lv[k].ref.nyc;
+        info->n_coarse += nk;
+        info->coarse_updates += std::ldexp((double)nk, -(int)(k + 1));
+    }
     info->fv_kernel = h->fv_kind;
     info->n_tiles = h->n_tiles;
     if (h->motion.kind == HLBM_MOTION_INDUCED) {

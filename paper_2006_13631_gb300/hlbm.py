@@ -79,12 +79,17 @@ def _structs(grid: dict, patch: dict, motion: dict):
     g.rho_init = _dp(arr(grid.get("rho_init"), np.float64))
     g.ux_init = _dp(arr(grid.get("ux_init"), np.float64))
     g.uy_init = _dp(arr(grid.get("uy_init"), np.float64))
-    g.refine = int(grid.get("refine", 0))
-    if g.refine:
-        g.nxc, g.nyc = int(grid["nxc"]), int(grid["nyc"])
-        g.ox, g.oy = int(grid["ox"]), int(grid["oy"])
-        g.uxc_init = _dp(arr(grid.get("uxc_init"), np.float64))
-        g.uyc_init = _dp(arr(grid.get("uyc_init"), np.float64))
+    levels = grid.get("levels") or []
+    g.n_levels = len(levels)
+    if levels:
+        lv = (N.hlbm_level_t * len(levels))()
+        keep.append(lv)
+        for k, L in enumerate(levels):
+            lv[k].nx, lv[k].ny, lv[k].ox, lv[k].oy = int(L["nx"]), int(L["ny"]), int(L["ox"]), int(L["oy"])
+            lv[k].rho_init = _dp(arr(L.get("rho_init"), np.float64))
+            lv[k].ux_init = _dp(arr(L.get("ux_init"), np.float64))
+            lv[k].uy_init = _dp(arr(L.get("uy_init"), np.float64))
+        g.levels = C.cast(lv, C.POINTER(N.hlbm_level_t))
     p = N.hlbm_patch_t()
     xy, tri, kind = arr(patch["xy"], np.float64), arr(patch["tri"], np.int32), arr(patch["kind"], np.int8)
     p.n_nodes, p.n_tris = xy.shape[0], tri.shape[0]
@@ -109,7 +114,7 @@ def _structs(grid: dict, patch: dict, motion: dict):
 
 def hlbm_create(grid: dict, patch: dict, tau_s: float, motion: dict, cuda_stream: int = 0):
     """grid: nx, ny, bc_x, bc_y, dtype ('f64'|'f32'|'f16'|'bf16'), rho0, u0x, u0y, rho_init, ux_init, uy_init,
-    and for two levels refine=1, nxc, nyc, ox, oy, uxc_init, uyc_init
+    and levels: a list of dicts nx, ny, ox, oy, rho_init, ux_init, uy_init (coarser levels, finest first)
     patch: xy [n,2], tri [m,3], kind [n], lamina_L, lamina_T, x_c, y_c, delta_f, n_sub, lumped, outer_fv, fv_kernel
     motion: kind, A, omega, vx, vy, mass, stiffness, damping, y0, v0.  Returns an opaque handle."""
     g, p, m, keep = _structs(grid, patch, motion)
@@ -160,9 +165,9 @@ def hlbm_get_fields(h, nx: int, ny: int, n_nodes: int):
     return out
 
 
-def hlbm_get_coarse_fields(h, nxc: int, nyc: int):
-    out = [np.empty((nyc, nxc)) for _ in range(3)]
-    _check(N.load().hlbm_get_coarse_fields(h, *[_dp(o) for o in out]), h)
+def hlbm_get_level_fields(h, level: int, nx: int, ny: int):
+    out = [np.empty((ny, nx)) for _ in range(3)]
+    _check(N.load().hlbm_get_level_fields(h, int(level), *[_dp(o) for o in out]), h)
     return out
 
 
@@ -234,7 +239,7 @@ def hlbm_load(h, path: str):
     _check(N.load().hlbm_load(h, os.fsencode(path)), h)
 
 
-def workload_inputs(w, mesh=None, rho_init=None, u_init=None, uc_init=None):
+def workload_inputs(w, mesh=None, rho_init=None, u_init=None, level_u_init=None, level_rho_init=None):
     """(grid, patch, motion) dicts of hlbm_create from a workload description
     (an object with the attributes of ``inputs.Workload``)."""
     mesh = mesh if mesh is not None else w.mesh()
@@ -242,10 +247,13 @@ def workload_inputs(w, mesh=None, rho_init=None, u_init=None, uc_init=None):
     grid = dict(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, dtype=w.dtype, rho0=w.rho0, u0x=w.u0x,
                 u0y=w.u0y, rho_init=rho,
                 ux_init=None if u_init is None else u_init[0], uy_init=None if u_init is None else u_init[1])
-    if getattr(w, "refine", 0):
-        grid.update(refine=1, nxc=w.nxc, nyc=w.nyc, ox=w.ox, oy=w.oy,
-                    uxc_init=None if uc_init is None else uc_init[0],
-                    uyc_init=None if uc_init is None else uc_init[1])
+    levels = list(getattr(w, "levels", []))
+    if levels:
+        grid["levels"] = [dict(nx=nx, ny=ny, ox=ox, oy=oy,
+                               rho_init=None if level_rho_init is None else level_rho_init[k],
+                               ux_init=None if level_u_init is None or level_u_init[k] is None else level_u_init[k][0],
+                               uy_init=None if level_u_init is None or level_u_init[k] is None else level_u_init[k][1])
+                          for k, (nx, ny, ox, oy) in enumerate(levels)]
     patch = dict(xy=mesh.xy, tri=mesh.tri, kind=mesh.kind, lamina_L=w.L, lamina_T=w.T,
                  x_c=w.xc, y_c=w.yc, delta_f=w.delta_f, n_sub=w.n_sub, lumped=w.lumped,
                  outer_fv=getattr(w, "outer_fv", 0), fv_kernel=getattr(w, "fv_kernel", 0))
@@ -259,7 +267,8 @@ class Solver:
     """Convenience owner of one hlbm handle built from a workload description
     (an object with the attributes of ``inputs.Workload``)."""
 
-    def __init__(self, w, mesh=None, rho_init=None, u_init=None, stream: int | None = None, uc_init=None):
+    def __init__(self, w, mesh=None, rho_init=None, u_init=None, stream: int | None = None, level_u_init=None,
+                 level_rho_init=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -269,7 +278,7 @@ class Solver:
         self.w = w
         self.mesh = mesh if mesh is not None else w.mesh()
         self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-        grid, patch, motion = workload_inputs(w, self.mesh, rho_init, u_init, uc_init)
+        grid, patch, motion = workload_inputs(w, self.mesh, rho_init, u_init, level_u_init, level_rho_init)
         self.h = hlbm_create(grid, patch, w.tau_s, motion, self.stream)
         self.n = self.mesh.n_nodes
 
@@ -313,9 +322,10 @@ class Solver:
     def struct_macro(self):
         return tuple(self.fields()[:3])
 
-    def coarse_macro(self):
-        """rho, ux, uy [nyc, nxc] of the coarse lattice at the last even time."""
-        return tuple(hlbm_get_coarse_fields(self.h, self.w.nxc, self.w.nyc))
+    def level_macro(self, k: int = 1):
+        """rho, ux, uy of coarser level k (1..len(w.levels)) at its current time."""
+        nx, ny = self.w.levels[k - 1][:2]
+        return tuple(hlbm_get_level_fields(self.h, k, nx, ny))
 
     def patch_macro(self):
         return tuple(self.fields()[3:])
