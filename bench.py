@@ -287,8 +287,8 @@ def run_ours(args):
     dom = max(phases, key=lambda p: phases[p][0])
     st_ms, st_n = phases["stream"]
     stream_bytes = 18 * bytes_per * n_disc  # 9 populations read + 9 written per discretization node
-    # per step: one launch on a single level; on two levels the phase also
-    # holds the coarse lattice (every second step) and the coupling launch
+    # per step: one launch on a single level; with nested levels the phase
+    # also holds the coarser levels' launches and the coupling launches
     stream_gbs = stream_bytes / (st_ms / args.steps / 1e3) / 1e9 if st_n else None
     fv_ms, _ = phases["fv"]
     nnz = info["nnz"]

@@ -52,20 +52,24 @@
  *      y(t+1) = y(t) + v(t+1).  The patch sits at y(t) during step t; the
  *      wall velocity at sub-step m is v(t) + theta (v(t+1) - v(t)).
  *  R12 Nested lattice levels (the paper's refinement levels, Sec. 5; the
- *      coupling is not given there): the lattice around the patch is a fine
- *      box inside a lattice of twice the spacing and twice the time step
+ *      coupling is not given there): the lattice around the patch is a box
+ *      inside a lattice of twice the spacing and twice the time step
  *      (acoustic scaling, same lattice velocities), tau_c - 1/2 =
  *      (tau_s - 1/2)/2 for the same viscosity, which may itself be a box
- *      inside a coarser one, and so on; each pair couples as follows.  Non-equilibrium parts scale
- *      as tau dx (f^neq = -tau dt D f^eq); for post-collision populations,
- *      f^neq_c = 2 (tau_c - 1)/(tau_s - 1) f^neq_f (tau_s != 1).  Per coarse
- *      step (two fine steps t = 2T, 2T+1): the coarse lattice streams and
- *      collides T -> T+1; the fine box's outermost ring takes, before each
- *      fine step, the post-collision f^eq(rho, u) + f^neq_f rebuilt from the
- *      coarse (rho, u, f^neq), linear along the box edge and, at t = 2T+1,
- *      the mean of coarse times T and T+1, and is not streamed itself; after
- *      the second fine step, the coarse nodes strictly inside the box take
- *      the post-collision state of the fine node they sit on.
+ *      inside a coarser one, and so on.  Each pair couples as follows.
+ *      Non-equilibrium parts scale as tau dx (f^neq = -tau dt D f^eq); for
+ *      post-collision populations f^neq_c = 2 (tau_c - 1)/(tau_f - 1)
+ *      f^neq_f (tau_f, tau_c != 1).  Per coarse step (fine steps 2T, 2T+1):
+ *      the coarse lattice streams and collides T -> T+1; before each fine
+ *      step the fine box's outermost ring takes the post-collision
+ *      f^eq(rho, u) + f^neq_f rebuilt from the coarse rho, u, f^neq (the
+ *      coarse node itself at even positions, the cubic midpoint rule
+ *      (-1, 9, 9, -1)/16 along the box edge at odd ones; at odd fine times
+ *      the mean of coarse times T and T+1) and is not streamed itself; after
+ *      the second fine step the coarse nodes strictly inside the box take
+ *      the post-collision state of the fine node they sit on.  Levels step
+ *      coarsest first, restrict finest first, and rebuild their rings on
+ *      their own clocks.
  */
 #include "hlbm_oracle.h"
 

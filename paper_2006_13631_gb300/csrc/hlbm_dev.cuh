@@ -360,11 +360,12 @@ __device__ __forceinline__ bool inside_curve(const Dev<T>& d, int x, int y, doub
     return __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)) < d.df2;
 }
 
-// ------------------------------------------------------ two-level lattice
-// Coarse lattice of a refined solver: sizes and layout of its population
-// buffers ([9][plane] with row pitch `pitch`, same storage type as the fine
-// lattice), the coarse node under fine node (0, 0), and the rescaling of
-// post-collision f^neq from coarse to fine (acf) and fine to coarse (afc).
+// ------------------------------------------------------- nested levels
+// The coupling of a lattice level with the next coarser one: the coarser
+// level's sizes and the layout of its population buffers ([9][plane] with
+// row pitch `pitch`, same storage type as every level), its node under the
+// finer level's node (0, 0), and the rescaling of post-collision f^neq from
+// coarse to fine (acf) and fine to coarse (afc).
 struct Refine {
     int nxc, nyc, pitch;
     int64_t plane;

@@ -395,11 +395,11 @@ void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy, c
     with_store(d, [&]<typename S>() { k_struct_macro<T, S><<<grid, 256, 0, s>>>(d, rho, ux, uy); });
 }
 
-// ------------------------------------------------- two-level lattice
-// The fine lattice is a box inside a coarse lattice of twice the spacing
-// and twice the time step (Sec. 5 refinement levels), tau_c - 1/2 =
-// (tau_s - 1/2)/2.  Post-collision non-equilibrium parts scale as
-// (tau - 1) dx: f^neq_c = 2 (tau_c - 1)/(tau_s - 1) f^neq_f.
+// ------------------------------------------------------- nested levels
+// Each pair of adjacent levels (Sec. 5 refinement levels): the finer one is
+// a box inside the coarser, which has twice the spacing and time step and
+// tau_c - 1/2 = (tau_f - 1/2)/2.  Post-collision non-equilibrium parts
+// scale as (tau - 1) dx: f^neq_c = 2 (tau_c - 1)/(tau_f - 1) f^neq_f.
 
 // One launch couples the levels after a fine stream-collide:
 //  - blocks [0, ring_blocks): the fine box's outermost ring (x = 0, nx-1 or

@@ -497,7 +497,7 @@ def test_fd_gradient_in_tau_converges():
 
 
 # --------------------------------------------------------------------------
-# R12: two-level lattice (the structured refinement levels of Sec. 5)
+# R12: nested lattice levels (the structured refinement levels of Sec. 5)
 # --------------------------------------------------------------------------
 def _void_mesh():
     """One triangle of outer nodes and no wall: with a zero-size lamina and a
