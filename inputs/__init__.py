@@ -347,6 +347,36 @@ def paper_point_workload(beta: float, eps: float, L: float = 32.0, tau_max: floa
     return w
 
 
+def paper_point_levels_workload(beta: float, eps: float, L: float = 800.0, dtype: str = "f32",
+                                tau_max: float = 0.8) -> Workload:
+    """The validation case at (beta, eps) on the paper's four structured
+    levels (Sec. 5: chord 800, domain 5L x 5L, tau at the finest level at
+    most 0.8): boxes of spacing 1, 2 and 4 centred on the lamina, about
+    1.25L x 0.5L, 2L x L and 3L x 2L, inside a lattice of spacing 8 over
+    the whole domain.  Physics and patch as paper_point_workload."""
+    w = paper_point_workload(beta, eps, L, tau_max)
+    w.name = f"paper-levels4-{beta:g}-{eps:g}-{L:g}"
+    w.dtype = dtype
+    odd = lambda v: int(v) // 2 * 2 + 1
+    sizes = [(odd(1.25 * L), odd(0.5 * L)), (odd(2.0 * L / 2), odd(1.0 * L / 2)), (odd(3.0 * L / 4), odd(2.0 * L / 4)),
+             (int(round(5 * L / 8)), int(round(5 * L / 8)))]
+    centre = (2.5 * L + 0.3, 2.5 * L + 0.2)
+    # physical position (finest units) of node 0 of each level, the coarsest
+    # at 0 and each finer one centred, on a node of the level around it
+    origin = [(0.0, 0.0)] * 4
+    for k in (2, 1, 0):
+        ox = [int(round((centre[c] - (sizes[k][c] - 1) * 2 ** k / 2 - origin[k + 1][c]) / 2 ** (k + 1)))
+              for c in (0, 1)]
+        origin[k] = tuple(origin[k + 1][c] + ox[c] * 2 ** (k + 1) for c in (0, 1))
+        sizes[k] = sizes[k] + tuple(ox)
+    w.nx, w.ny = sizes[0][0], sizes[0][1]
+    w.xc, w.yc = centre[0] - origin[0][0], centre[1] - origin[0][1]
+    w.levels = [(sizes[1][0], sizes[1][1], sizes[0][2], sizes[0][3]),
+                (sizes[2][0], sizes[2][1], sizes[1][2], sizes[1][3]),
+                (sizes[3][0], sizes[3][1], sizes[2][2], sizes[2][3])]
+    return w
+
+
 def workload(name: str) -> Workload:
     """Named synthetic workloads (sizes of the paper's lamina problem)."""
     if name == "lamina-256-f64":

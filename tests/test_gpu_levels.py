@@ -220,3 +220,51 @@ def test_levels_theta_agrees_with_the_uniform_lattice(name, bar):
     d = abs(complex(re2 - re1, im2 - im1)) / abs(complex(re1, im1))
     print(name, "Theta", complex(re2, im2), "uniform", complex(re1, im1), "rel", d)
     assert d < bar
+
+
+def test_levels_theta_gradient_matches_oracle_fd():
+    """hlbm_theta_gradient on a lattice with a coarser level: the seven solves
+    of the central differences carry the levels along; Theta and its
+    gradient in (A, omega, tau_s) against the same quotient from seven oracle
+    runs (FP64, the 256^2 domain as a 129^2 box in a 128^2 lattice of
+    spacing 2, 48 steps, fit over 0.5-2 periods)."""
+    from paper_2006_13631_gb300 import hlbm_theta_gradient, use_torch_allocator, workload_inputs
+
+    use_torch_allocator()
+    w = inputs.workload("lamina-256-f64")
+    w.nx = w.ny = 129
+    w.xc, w.yc = 64.3, 64.2
+    w.levels = [(128, 128, 32, 32)]
+    mesh, rho = w.mesh(), w.rho_init()
+    grid, patch, motion = workload_inputs(w, mesh, rho)
+    th, grad, ms = hlbm_theta_gradient(grid, patch, w.tau_s, motion, 48, discard=0.5, fit=1.5, rel_step=1e-4)
+    tho, grado = oracle.theta_fd_gradient(w, 48, discard=0.5, fit=1.5, rel_step=1e-4, mesh=mesh, rho_init=rho)
+    print("levels theta", th, tho, "grad", grad, grado)
+    assert abs(th - tho) < 1e-8
+    assert np.abs(grad - grado).max() < 1e-4 * np.abs(grado).max()
+
+
+def test_paper_point_at_chord_800_on_four_levels():
+    """The paper's own setup (Sec. 5): chord 800, domain 5L, four structured
+    levels, tau 0.8 at the finest; the point (beta, eps) = (250, 0.02) over
+    4 periods (102 k steps, FP32), against the value the paper prints
+    (tests/golden/paper_theta_mg_hlbm.txt).  Measured on a GB300: Re +1.7 %,
+    -Im +2.7 %."""
+    from paper_2006_13631_gb300 import Solver
+
+    paper = {}
+    with open(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                         "paper_theta_mg_hlbm.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                b, e, re_, mim = map(float, line.split())
+                paper[(b, e)] = (re_, mim)
+    w = inputs.paper_point_levels_workload(250.0, 0.02)
+    s = Solver(w)
+    s.step(w.steps)
+    re_, im_, _ = s.gamma(discard=1.0, fit=3.0)
+    assert s.status == 0
+    pre, pmim = paper[(250.0, 0.02)]
+    print("chord 800 Theta", re_, im_, "paper", pre, -pmim)
+    assert abs(re_ - pre) < 0.03 * pre
+    assert abs(-im_ - pmim) < 0.05 * pmim
