@@ -268,3 +268,57 @@ def test_paper_point_at_chord_800_on_four_levels():
     print("chord 800 Theta", re_, im_, "paper", pre, -pmim)
     assert abs(re_ - pre) < 0.03 * pre
     assert abs(-im_ - pmim) < 0.05 * pmim
+
+
+def _donors_valid(mesh, dY, tg, dg, to, do):
+    """Refill records that may differ only at ties (the lamina's path comes
+    from the computed force): the types agree, and a node whose donor
+    triangle differs lies (to 1e-9) in both triangles."""
+    assert np.array_equal(tg, to)
+    diff = np.nonzero(dg != do)[0]
+    assert len(diff) <= max(2, len(dg) // 100), len(diff)
+    for i in diff:
+        assert tg[i] == 3
+        q = mesh.xy[i] + np.array([0.0, dY])
+        for k in (dg[i], do[i]):
+            a, b, c = mesh.xy[mesh.tri[k]]
+            m = np.array([[b[0] - a[0], c[0] - a[0]], [b[1] - a[1], c[1] - a[1]]])
+            l1, l2 = np.linalg.solve(m, q - a)
+            assert min(1 - l1 - l2, l1, l2) > -1e-9
+
+
+@pytest.mark.parametrize("variant", ["outer_fv", "induced"])
+def test_levels_with_the_method_variants(variant):
+    """Three levels together with the outer nodes' FV sums (reading R10) or
+    with the lamina moved by the fluid force (reading R11), FP64, against
+    the oracle: every level's fields within the FP64 bars, and for the
+    induced motion the lamina's path within 1e-10 of its displacement."""
+    import math
+
+    w = inputs.workload("lamina-small-levels3-f64")
+    if variant == "outer_fv":
+        w.outer_fv = 1
+    else:
+        w.motion, w.A, w.omega = inputs.MOTION_INDUCED, 0.0, 0.0
+        w.mass = math.pi / 4 * w.L * w.L
+        w.stiffness = w.mass * (2 * math.pi / 150.0) ** 2
+        w.y0 = 1.5
+    s, o = pair(w)
+    for c in (1, 18, 21):
+        s.step(c)
+        o.step(c)
+        if variant == "outer_fv":
+            assert np.array_equal(s.struct_class(), o.struct_class())
+        else:
+            y, _ = o.motion()
+            tg, dg = s.refill_record()
+            to, do = o.refill_record()
+            _donors_valid(w.mesh(), y[o.time - 1] - y[o.time - 2] if o.time > 1 else 0.0, tg, dg, to, do)
+        e = errors(s, o, len(w.levels))
+        assert all(v < 2e-9 for k, v in e.items() if k.endswith("_u")), e
+        assert all(v < 1e-12 for k, v in e.items() if k.endswith("_rho")), e
+    assert s.status == 0 and o.status == 0
+    if variant == "induced":
+        y, v = o.motion()
+        info = s.info()
+        assert abs(info["y"] - y[-1]) < 1e-10 * abs(w.y0) and abs(info["vy"] - v[-1]) < 1e-10 * abs(w.y0)
