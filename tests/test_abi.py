@@ -58,3 +58,35 @@ def test_create_rejects_bad_configuration_without_touching_the_gpu(lib_path):
         H.hlbm_create(grid, patch, w.tau_s, dict(kind=1, A=w.A, omega=w.omega))
     assert e.value.code == -1 and "outer patch boundary" in str(e.value)
     np.testing.assert_equal(H.N.HLBM_EINVAL, -1)
+
+
+def test_create_rejects_bad_levels_without_touching_the_gpu(lib_path):
+    """The nested-level checks of hlbm_create run before any device work:
+    even box sizes, a box without its margin (two nodes inside a level that
+    has a ring of its own, one inside the coarsest), too many levels, and a
+    level whose tau is 1 are refused with HLBM_EINVAL and a message."""
+    import inputs
+    from paper_2006_13631_gb300 import hlbm as H
+
+    w = inputs.workload("lamina-small-f32")
+    m = w.mesh()
+    patch = dict(xy=m.xy, tri=m.tri, kind=m.kind, lamina_L=w.L, lamina_T=w.T, x_c=w.xc, y_c=w.yc,
+                 delta_f=w.delta_f, n_sub=w.n_sub, lumped=0)
+    motion = dict(kind=1, A=w.A, omega=w.omega)
+
+    def refused(nx, levels, tau=w.tau_s, n_sub=None, text=""):
+        grid = dict(nx=nx, ny=w.ny, dtype="f32",
+                    levels=[dict(nx=a, ny=b, ox=c, oy=d) for a, b, c, d in levels])
+        p = dict(patch, n_sub=n_sub or patch["n_sub"])
+        with pytest.raises(H.HLBMError) as e:
+            H.hlbm_create(grid, p, tau, motion)
+        assert e.value.code == -1 and text in str(e.value), str(e.value)
+
+    refused(202, [(204, 160, 51, 40)], text="odd sizes")
+    refused(203, [(204, 160, 0, 40)], text="keep 1 node")
+    refused(203, [(204, 160, 102, 40)], text="keep 1 node")
+    # level 1 has a ring of its own (level 2 around it): two nodes of margin
+    refused(203, [(211, 167, 1, 43), (216, 176, 53, 44)], text="keep 2 node")
+    refused(203, [(210, 167, 52, 43), (216, 176, 53, 44)], text="odd sizes")
+    refused(203, [(204, 160, 51, 40)] * 5, text="n_levels")
+    refused(203, [(211, 167, 52, 43), (216, 176, 53, 44)], tau=2.5, n_sub=4, text="tau of level 2")
