@@ -591,7 +591,7 @@ def _level_coords(n_levels, nc, box, o):
     return out + [(Xc, Yc)]
 
 
-@pytest.mark.parametrize("tau_f,n_levels", [(0.8, 1), (0.8, 2), (1.3, 2)])
+@pytest.mark.parametrize("tau_f,n_levels", [(0.8, 1), (0.8, 2), (1.3, 2), (0.8, 3)])
 def test_levels_carry_a_standing_sound_wave(tau_f, n_levels):
     """A standing sound wave rho = 1 + d cos(kx) crosses every level edge.
     Linear acoustics with the lattice's shear and bulk viscosity nu
