@@ -1601,7 +1601,7 @@ int hlbm_step(hlbm_t* h, int64_t nsteps) {
 
 int hlbm_status(hlbm_t* h, uint32_t* bits) {
     if (!h || !bits) return HLBM_EINVAL;
-    unsigned v;
+    unsigned v = 0;
     int rc = sync_status(h, &v);
     *bits = v;
     return rc;
