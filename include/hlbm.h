@@ -47,6 +47,7 @@ extern "C" {
 #define HLBM_EGEOM (-4)     /* a geometric precondition failed on device  */
 #define HLBM_ENOMEM (-5)    /* device allocation failed                   */
 #define HLBM_EIO (-6)       /* a checkpoint file could not be read/written */
+#define HLBM_ETIMEOUT (-7)  /* an FV neighbour wait ran out: step abandoned */
 
 /* boundary kinds of the Cartesian domain sides (Sec. 5) */
 #define HLBM_BC_WALL 0     /* half-way bounce-back no-slip wall          */
@@ -211,18 +212,51 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
  * lattice interpolation nodes from the patch (eq. postcollision2_s), one
  * stream-collide of eq. LBE, n_sub FV sub-steps of eq. ulbe with the outer
  * patch nodes fed from the lattice (eq. postcollision2_u), and the force on
- * the lamina at the new time. */
+ * the lamina at the new time.
+ * Device status bits (HLBM_ST_*) are errors.  Once the host has seen one --
+ * through hlbm_status, hlbm_force or hlbm_gamma, or through the copy of the
+ * status word that each hlbm_step call queues at its end, which the next
+ * call reads if it has arrived (without waiting for it) -- hlbm_step steps
+ * nothing and returns HLBM_ETIMEOUT (SYNC_TIMEOUT), HLBM_EUNSTABLE
+ * (NONFINITE) or HLBM_EGEOM (the others) until hlbm_clear_status or
+ * hlbm_load. */
 int hlbm_step(hlbm_t* h, int64_t nsteps);
 
+/* Acknowledge the device status bits: synchronises the solver's stream,
+ * clears the status word and the FV kernels' abort flag, and restarts
+ * their progress counters at the current step, so that hlbm_step runs
+ * again.  The state is left as it is: after HLBM_ETIMEOUT the patch holds
+ * the sub-steps the abandoned step completed, tile by tile (restore a
+ * checkpoint with hlbm_load to go on from a consistent state). */
+int hlbm_clear_status(hlbm_t* h);
+
+/* Fault injection from the host, for tests of the error paths (nothing
+ * faults, traps or hangs the GPU):
+ *   HLBM_FAULT_STALL_TILE: during the next hlbm_step's FV launch, tile
+ *     `arg` never releases its progress counter, and the neighbour waits
+ *     give up after 4096 polls; its neighbours then set
+ *     HLBM_ST_SYNC_TIMEOUT and the abort flag and every tile returns.
+ *   HLBM_FAULT_NAN_LATTICE: NaN is copied (cudaMemcpy from the host) into
+ *     the nine populations of lattice node `arg` (= y * nx + x) that the
+ *     next stream-collide reads; it reaches the force within some steps
+ *     when the node is near the patch.
+ * HLBM_EINVAL for another kind or an argument out of range. */
+#define HLBM_FAULT_STALL_TILE 1
+#define HLBM_FAULT_NAN_LATTICE 2
+int hlbm_inject_fault(hlbm_t* h, int32_t kind, int64_t arg);
+
 /* Copy the force history (per unit length, fluid on lamina) for times
- * first .. first+count-1 into fx, fy.  Time 0 is the initial state. */
+ * first .. first+count-1 into fx, fy.  Time 0 is the initial state.
+ * Synchronises the stream; returns the error of any device status bit
+ * (see hlbm_step) after the copy. */
 int hlbm_force(hlbm_t* h, int64_t first, int64_t count, double* fx, double* fy);
 
 /* Hydrodynamic function Theta = F-hat / ((pi/4) rho0 w^2 L^2 A) from a
  * least-squares fit F_y(t) = a sin(w t) + b cos(w t) over
  * t in [discard_periods, discard_periods + fit_periods] periods (Sec. 2.1;
  * the paper discards 1 period and fits 3).  re = a/N, im = b/N; rms is the
- * fit residual in the same units.  HARMONIC motion only. */
+ * fit residual in the same units.  HARMONIC motion only.  Returns the error
+ * of any device status bit (see hlbm_step). */
 int hlbm_gamma(hlbm_t* h, double discard_periods, double fit_periods, double* re, double* im,
                double* rms);
 
@@ -344,25 +378,28 @@ int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, doub
 /* Least-squares fit F(t) = a sin(w t) + b cos(w t) over t = t0..t1 of the
  * samples F(t) = samples[t * stride] (DEVICE memory, caller-owned, at least
  * t1 * stride + 1 doubles), the fit hlbm_gamma performs, for callers that
- * must not allocate device memory: code recording a CUDA graph by stream
- * capture, code running under a fixed device-memory budget or inside a
- * framework that owns all allocations, and loops that cannot take the
- * device-wide synchronisation of cudaMalloc / cudaFree.  The paper has no
- * counterpart; it is an interface of this library.  (A solver's force
- * history interleaves F_x and F_y: pass its F_y column with stride 2.)
+ * must not allocate device memory: code running under a fixed
+ * device-memory budget or inside a framework that owns all allocations, and
+ * loops that cannot take the device-wide synchronisation of cudaMalloc /
+ * cudaFree.  The paper has no counterpart; it is an interface of this
+ * library.  (A solver's force history interleaves F_x and F_y: pass its F_y
+ * column with stride 2.)
  *
  * Allocates nothing: its intermediate sums live in a file-scope device
  * array of 257 x 8 doubles that every GPU loading the library holds until
- * the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress), so make the first call on each
- * device before any stream capture.  Calls share the array: every value a
- * call reads is written earlier in the same call, but calls that overlap
- * on the GPU (other streams or host threads) race and must be serialised
- * by the caller.  Work is queued on cuda_stream (a cudaStream_t, NULL =
- * legacy default stream), which is synchronised before a, b and rms (host
- * pointers; rms may be NULL) are written.  Returns HLBM_EINVAL for more
- * than 2^26 samples, t1 <= t0, t0 < 0, stride < 1 or omega <= 0, and
- * HLBM_ECUDA when a CUDA call fails. */
+ * the process exits.  The first call on a device (and the first after the
+ * device's context was destroyed, e.g. by cudaDeviceReset) looks up that
+ * array's device address with cudaGetSymbolAddress.  Calls share the array:
+ * every value a call reads is written earlier in the same call, but calls
+ * that overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  Work is queued on cuda_stream (a cudaStream_t,
+ * NULL = legacy default stream), which is synchronised before a, b and rms
+ * (host pointers; rms may be NULL) are written.  Returns HLBM_EINVAL for
+ * more than 2^26 samples, t1 <= t0, t0 < 0, stride < 1, omega not finite
+ * and positive, a stream that is being captured (the call reads its
+ * results back to the host), or sin(w t) and cos(w t) nearly dependent over
+ * the window (det of the normal equations below 1e-12 n^2 for n samples,
+ * e.g. w a multiple of pi); HLBM_ECUDA when a CUDA call or a launch fails. */
 int hlbm_fit_static(const double* samples, int64_t stride, int64_t t0, int64_t t1, double omega,
                     void* cuda_stream, double* a, double* b, double* rms);
 

@@ -24,6 +24,7 @@ MOTION_STATIC = 0
 MOTION_HARMONIC = 1
 MOTION_UNIFORM = 2
 MOTION_INDUCED = 3
+MOTION_HARMONIC_X = 4  # the lamina moves along its chord, x(t) = A sin(w t) (Stokes-layer test case)
 # boundary kinds for the Cartesian domain sides
 BC_WALL = 0
 BC_OUTFLOW = 1

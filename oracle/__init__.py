@@ -93,6 +93,8 @@ def lib():
         L.orc_outer_fv.argtypes = [C.c_int, dp, C.c_int, ip, C.POINTER(C.c_int8), C.c_double, C.c_double, C.c_int,
                                    dp, dp, dp]
         L.orc_sine_fit.argtypes = [dp, C.c_int64, C.c_int64, C.c_double, dp, dp, dp]
+        L.orc_theta.argtypes = [dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                C.c_double, dp, dp, dp]
         L.orc_fv_periodic.argtypes = [C.c_int, dp, C.c_int, ip, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int, C.c_int, dp]
         L.orc_lbgk.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp]
@@ -118,6 +120,17 @@ def sine_fit(F, t0, t1, omega):
     a, b, r = C.c_double(), C.c_double(), C.c_double()
     lib().orc_sine_fit(_dp(F), t0, t1, omega, C.byref(a), C.byref(b), C.byref(r))
     return a.value, b.value, r.value
+
+
+def theta(F, rho0, omega, L, A, discard=1.0, fit=3.0):
+    """Theta = F-hat / ((pi/4) rho0 w^2 L^2 A) of a force history F[t], t = 0..n-1,
+    fitted over [discard, discard + fit] periods (Sec. 2.1)."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    re, im, r = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().orc_theta(_dp(F), len(F), rho0, omega, L, A, discard, fit, C.byref(re), C.byref(im), C.byref(r))
+    if rc != 0:
+        raise ValueError(f"orc_theta failed ({rc})")
+    return complex(re.value, im.value), r.value
 
 
 def fv_periodic(xy, tri, period_x, period_y, tau_u, dt_u, n_iter, f9, lumped=0):

@@ -169,12 +169,17 @@ struct orc {
     int status;
 };
 
-/* lamina position at time t (Sec. 2: y(t) = A sin(w t)) */
+/* lamina position at time t (Sec. 2: y(t) = A sin(w t)); HARMONIC_X moves
+ * the lamina along its own chord, x(t) = A sin(w t) (Stokes' second problem
+ * for the two long faces: a test case, not the paper's motion) */
 static void motion_pos(const orc_params_t* p, int64_t t, double* X, double* Y) {
     double tt = (double)t;
     if (p->motion == ORC_MOTION_HARMONIC) {
         *X = 0.0;
         *Y = p->A * sin(p->omega * tt);
+    } else if (p->motion == ORC_MOTION_HARMONIC_X) {
+        *X = p->A * sin(p->omega * tt);
+        *Y = 0.0;
     } else if (p->motion == ORC_MOTION_UNIFORM) {
         *X = p->vx * tt;
         *Y = p->vy * tt;
@@ -189,6 +194,9 @@ static void motion_vel(const orc_params_t* p, double time, double* U, double* V)
     if (p->motion == ORC_MOTION_HARMONIC) {
         *U = 0.0;
         *V = p->A * p->omega * cos(p->omega * time);
+    } else if (p->motion == ORC_MOTION_HARMONIC_X) {
+        *U = p->A * p->omega * cos(p->omega * time);
+        *V = 0.0;
     } else if (p->motion == ORC_MOTION_UNIFORM) {
         *U = p->vx;
         *V = p->vy;
@@ -1108,21 +1116,30 @@ void orc_sine_fit(const double* F, int64_t t0, int64_t t1, double omega, double*
     *rms = sqrt(r2 / (double)(t1 - t0 + 1));
 }
 
-/* F-hat = F0 e^{i phi} = a + i b = (pi/4) rho w^2 L^2 Theta A */
-int orc_gamma(const orc_t* o, double discard_periods, double fit_periods, double* re, double* im,
-              double* rms) {
-    if (o->p.motion != ORC_MOTION_HARMONIC || o->p.omega <= 0) return -1;
-    double Tp = 2.0 * ORC_PI / o->p.omega;
+/* Theta of a force history F[0..n-1] (eq. force_phasor): the sine fit over
+ * t in [ceil(discard T), floor((discard + fit) T)], T = 2 pi / w, gives
+ * F-hat = F0 e^{i phi} = a + i b, and F-hat = (pi/4) rho w^2 L^2 Theta A. */
+int orc_theta(const double* F, int64_t n, double rho0, double omega, double L, double A, double discard_periods,
+              double fit_periods, double* re, double* im, double* rms) {
+    if (omega <= 0) return -1;
+    double Tp = 2.0 * ORC_PI / omega;
     int64_t t0 = (int64_t)ceil(discard_periods * Tp);
     int64_t t1 = (int64_t)floor((discard_periods + fit_periods) * Tp);
-    if (t1 > o->t || t1 <= t0) return -2;
+    if (t1 >= n || t1 <= t0) return -2;
     double a, b;
-    orc_sine_fit(o->Fy, t0, t1, o->p.omega, &a, &b, rms);
-    double N = 0.25 * ORC_PI * o->p.rho0 * o->p.omega * o->p.omega * o->p.L * o->p.L * o->p.A;
+    orc_sine_fit(F, t0, t1, omega, &a, &b, rms);
+    double N = 0.25 * ORC_PI * rho0 * omega * omega * L * L * A;
     *re = a / N;
     *im = b / N;
     *rms /= N;
     return 0;
+}
+
+int orc_gamma(const orc_t* o, double discard_periods, double fit_periods, double* re, double* im,
+              double* rms) {
+    if (o->p.motion != ORC_MOTION_HARMONIC) return -1;
+    return orc_theta(o->Fy, o->t + 1, o->p.rho0, o->p.omega, o->p.L, o->p.A, discard_periods, fit_periods, re, im,
+                     rms);
 }
 
 /* ------------------------------------------------------------------------ */

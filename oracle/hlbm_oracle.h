@@ -19,7 +19,8 @@ extern "C" {
 #endif
 
 enum { ORC_BC_WALL = 0, ORC_BC_OUTFLOW = 1, ORC_BC_PERIODIC = 2 };
-enum { ORC_MOTION_STATIC = 0, ORC_MOTION_HARMONIC = 1, ORC_MOTION_UNIFORM = 2, ORC_MOTION_INDUCED = 3 };
+enum { ORC_MOTION_STATIC = 0, ORC_MOTION_HARMONIC = 1, ORC_MOTION_UNIFORM = 2, ORC_MOTION_INDUCED = 3,
+       ORC_MOTION_HARMONIC_X = 4 };
 enum { ORC_KIND_INTERIOR = 0, ORC_KIND_OUTER = 1, ORC_KIND_WALL = 2 };
 enum { ORC_DISC = 0, ORC_INTERP = 1, ORC_UNUSED = 2 };
 enum { ORC_MAX_LEVELS = 4 };
@@ -97,6 +98,9 @@ void orc_force(const orc_t* o, double* fx, double* fy);
 /* hydrodynamic function from the force history (Sec. 2.1) */
 int orc_gamma(const orc_t* o, double discard_periods, double fit_periods,
               double* re, double* im, double* rms);
+/* the same from a given history F[0..n-1] of the force along the motion */
+int orc_theta(const double* F, int64_t n, double rho0, double omega, double L, double A,
+              double discard_periods, double fit_periods, double* re, double* im, double* rms);
 
 /* geometry only (no state change): classes of step t, refill record of t-1 -> t */
 void orc_classify_at(orc_t* o, int64_t t, int8_t* cls);

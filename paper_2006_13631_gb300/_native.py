@@ -8,12 +8,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhlbm.so")
 
 HLBM_OK, HLBM_EINVAL, HLBM_ECUDA, HLBM_EUNSTABLE, HLBM_EGEOM, HLBM_ENOMEM, HLBM_EIO = 0, -1, -2, -3, -4, -5, -6
+HLBM_ETIMEOUT = -7
+HLBM_FAULT_STALL_TILE, HLBM_FAULT_NAN_LATTICE = 1, 2
 HLBM_FV_AUTO, HLBM_FV_GLOBAL, HLBM_FV_SMEM, HLBM_FV_TMEM = 0, 1, 2, 3
 HLBM_BC_WALL, HLBM_BC_OUTFLOW, HLBM_BC_PERIODIC = 0, 1, 2
 HLBM_F64, HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2, 3
 HLBM_NODE_INTERIOR, HLBM_NODE_OUTER, HLBM_NODE_WALL = 0, 1, 2
 HLBM_MOTION_STATIC, HLBM_MOTION_HARMONIC, HLBM_MOTION_UNIFORM, HLBM_MOTION_INDUCED = 0, 1, 2, 3
 HLBM_ST_FILL_NOT_LOCATED, HLBM_ST_DONOR_NOT_COMPUTED, HLBM_ST_NONFINITE, HLBM_ST_UNUSED_TO_DISC = 1, 2, 8, 16
+HLBM_ST_SYNC_TIMEOUT = 32
 PHASES = ("move", "stream", "fv", "force")
 
 _dp = C.POINTER(C.c_double)
@@ -76,6 +79,8 @@ SIGNATURES = {
     "hlbm_get_fv": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp, _dp]),
     "hlbm_info": (C.c_int, [C.c_void_p, C.POINTER(hlbm_info_t)]),
     "hlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
+    "hlbm_clear_status": (C.c_int, [C.c_void_p]),
+    "hlbm_inject_fault": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "hlbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hlbm_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "hlbm_fit_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_void_p, _dp, _dp,

@@ -71,6 +71,16 @@ struct hlbm {
     int64_t force_cap = 0;
     unsigned* status = nullptr;
     double* scratch = nullptr;           // 8 doubles for reductions
+    // status bits that have reached the host; while any is set, hlbm_step
+    // refuses to step (until hlbm_clear_status or hlbm_load)
+    unsigned fault = 0;
+    unsigned* st_host = nullptr;         // pinned copy queued at the end of each hlbm_step call
+    cudaEvent_t st_event = nullptr;      // recorded after that copy
+    bool st_pending = false;
+    // fault injection for tests (hlbm_inject_fault): the next FV launch runs
+    // with this tile never releasing its counter and this spin limit
+    int inject_stall_tile = -1;
+    long inject_spin_limit = 0;
 
     int64_t t = 0;
     double Xprev = 0, Yprev = 0;
@@ -390,9 +400,16 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
     // 5b. n FV sub-steps (eq. ulbe, eq. postcollision2_u)
     int ev = phase_begin(h, s);
     if (ev0) cudaEventRecord(ev0, s);
+    if (h->inject_stall_tile >= 0) {  // one launch only
+        d.stall_tile = h->inject_stall_tile;
+        d.spin_limit = h->inject_spin_limit;
+        h->inject_stall_tile = -1;
+    }
     cudaError_t fe = h->fv_kind == HLBM_FV_TMEM   ? launch_fv_tmem<T>(d, ps.a, s)
                      : h->fv_kind == HLBM_FV_SMEM ? launch_fv_smem<T>(d, ps.a, s)
                                                   : launch_fv_persistent<T>(d, ps.a, s);
+    d.stall_tile = -1;
+    d.spin_limit = kSpinLimit;
     if (ev1) cudaEventRecord(ev1, s);
     if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
     if (d.n_sub & 1) h->ui = 1 - h->ui;
@@ -958,6 +975,8 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         !d.abort_flag)
         return fail(h, HLBM_ENOMEM, "device allocation failed");
     d.coef = coefv;
+    d.spin_limit = kSpinLimit;
+    d.stall_tile = -1;
     cudaMemsetAsync(d.abort_flag, 0, 16, s);
     cudaMemsetAsync(h->status, 0, 64, s);
     cudaMemsetAsync(d.rtype, 0, (size_t)n * sizeof(int32_t), s);
@@ -1046,7 +1065,52 @@ int sync_status(hlbm* h, unsigned* bits) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "status readback");
     *bits = v;
+    h->fault |= v;
     return HLBM_OK;
+}
+
+// The error a set of status bits stands for: a neighbour wait that ran out
+// (the FV sub-steps of that step were abandoned), a non-finite force (the
+// run diverged), or a geometric precondition that failed on the device.
+int status_error(hlbm* h, unsigned bits) {
+    if (!bits) return HLBM_OK;
+    if (bits & HLBM_ST_SYNC_TIMEOUT)
+        return fail(h, HLBM_ETIMEOUT, "status 0x%x: an FV tile waited too long for its neighbours; the FV "
+                    "sub-steps of that step were abandoned (hlbm_clear_status or hlbm_load to go on)", bits);
+    if (bits & HLBM_ST_NONFINITE)
+        return fail(h, HLBM_EUNSTABLE, "status 0x%x: the force became NaN/Inf: the run diverged", bits);
+    return fail(h, HLBM_EGEOM, "status 0x%x: a geometric precondition failed on the device", bits);
+}
+
+// Before hlbm_step queues work: the bits already seen on the host, and the
+// copy queued at the end of the previous hlbm_step call if it has arrived
+// (never waiting for it).
+int check_fault(hlbm* h) {
+    if (!h->fault && h->st_pending && cudaEventQuery(h->st_event) == cudaSuccess) {
+        h->fault |= *(volatile unsigned*)h->st_host;
+        h->st_pending = false;
+    }
+    cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error here
+    return status_error(h, h->fault);
+}
+
+// After hlbm_step queued its work: a copy of the status word that the next
+// call can look at without waiting.
+void queue_status_copy(hlbm* h) {
+    if (!h->st_host) {
+        if (cudaHostAlloc((void**)&h->st_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->st_event, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (h->st_host) cudaFreeHost(h->st_host);
+            h->st_host = nullptr;
+            return;
+        }
+    }
+    if (cudaMemcpyAsync(h->st_host, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+        cudaEventRecord(h->st_event, h->stream) == cudaSuccess)
+        h->st_pending = true;
+    else
+        cudaGetLastError();
 }
 
 }  // namespace
@@ -1292,8 +1356,11 @@ int load_impl(hlbm* h, const char* path) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d.progress, prog.data(), prog.size() * sizeof(unsigned long long),
                             cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.abort_flag, 0, sizeof(unsigned), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "checkpoint state");
+    h->fault = c.status;
+    h->st_pending = false;
     bind(h, d);
     return HLBM_OK;
 }
@@ -1596,7 +1663,74 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
 
 int hlbm_step(hlbm_t* h, int64_t nsteps) {
     if (!h || nsteps < 0) return HLBM_EINVAL;
-    return h->dtype != HLBM_F64 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
+    int rc = check_fault(h);
+    if (rc != HLBM_OK) return rc;
+    rc = h->dtype != HLBM_F64 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
+    if (nsteps > 0) queue_status_copy(h);
+    return rc;
+}
+
+int hlbm_clear_status(hlbm_t* h) {
+    if (!h) return HLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "clear status");
+    const int n_tiles = h->dtype != HLBM_F64 ? h->df.n_tiles : h->dd.n_tiles;
+    unsigned long long* prog = h->dtype != HLBM_F64 ? h->df.progress : h->dd.progress;
+    unsigned* abort_flag = h->dtype != HLBM_F64 ? h->df.abort_flag : h->dd.abort_flag;
+    // the FV kernels count sub-steps from t * n_sub (an abandoned step left
+    // the counters anywhere in its range)
+    std::vector<unsigned long long> p0(n_tiles, (unsigned long long)h->t * (unsigned long long)h->patch.n_sub);
+    e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(abort_flag, 0, sizeof(unsigned), h->stream);
+    if (e == cudaSuccess && n_tiles)
+        e = cudaMemcpyAsync(prog, p0.data(), p0.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "clear status");
+    h->fault = 0;
+    h->st_pending = false;
+    return HLBM_OK;
+}
+
+int hlbm_inject_fault(hlbm_t* h, int32_t kind, int64_t arg) {
+    if (!h) return HLBM_EINVAL;
+    if (kind == HLBM_FAULT_STALL_TILE) {
+        const int n_tiles = h->dtype != HLBM_F64 ? h->df.n_tiles : h->dd.n_tiles;
+        if (arg < 0 || arg >= n_tiles) return fail(h, HLBM_EINVAL, "no FV tile %lld", (long long)arg);
+        h->inject_stall_tile = (int)arg;
+        h->inject_spin_limit = 1L << 12;
+        return HLBM_OK;
+    }
+    if (kind == HLBM_FAULT_NAN_LATTICE) {
+        const int nx = h->grid.nx, ny = h->grid.ny;
+        if (arg < 0 || arg >= (int64_t)nx * ny) return fail(h, HLBM_EINVAL, "no lattice node %lld", (long long)arg);
+        const int64_t pitch = h->dtype != HLBM_F64 ? h->df.pitch : h->dd.pitch;
+        const int64_t plane = h->dtype != HLBM_F64 ? h->df.plane : h->dd.plane;
+        const int64_t x = arg % nx, y = arg / nx;
+        // a quiet NaN in the storage type of the populations read next
+        size_t es;
+        unsigned char nan[8];
+        if (h->dtype == HLBM_F64) {
+            const uint64_t v = 0x7ff8000000000000ull;
+            es = 8;
+            std::memcpy(nan, &v, 8);
+        } else if (h->dtype == HLBM_F32) {
+            const uint32_t v = 0x7fc00000u;
+            es = 4;
+            std::memcpy(nan, &v, 4);
+        } else {
+            const uint16_t v = h->dtype == HLBM_F16 ? 0x7e00u : 0x7fc0u;
+            es = 2;
+            std::memcpy(nan, &v, 2);
+        }
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < 9 && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync((unsigned char*)h->fbuf[h->fi] + es * (size_t)(i * plane + y * pitch + x), nan, es,
+                                cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        return cuda_check(h, e, "NaN injection");
+    }
+    return fail(h, HLBM_EINVAL, "unknown fault kind %d", (int)kind);
 }
 
 int hlbm_status(hlbm_t* h, uint32_t* bits) {
@@ -1621,8 +1755,7 @@ int hlbm_force(hlbm_t* h, int64_t first, int64_t count, double* fx, double* fy) 
     unsigned st;
     int rc = sync_status(h, &st);
     if (rc != HLBM_OK) return rc;
-    if (st & HLBM_ST_NONFINITE) return fail(h, HLBM_EUNSTABLE, "the force became NaN/Inf: the run diverged");
-    return HLBM_OK;
+    return status_error(h, st);
 }
 
 namespace {
@@ -1653,8 +1786,7 @@ int theta_window(hlbm* h, int64_t t0, int64_t t1, double* re, double* im, double
     unsigned st;
     int rc = sync_status(h, &st);
     if (rc != HLBM_OK) return rc;
-    if (st & HLBM_ST_NONFINITE) return fail(h, HLBM_EUNSTABLE, "the force became NaN/Inf: the run diverged");
-    return HLBM_OK;
+    return status_error(h, st);
 }
 }  // namespace
 
@@ -2002,17 +2134,34 @@ static void sweep_join(hlbm_sweep* w, cudaStream_t to) {
     cudaStreamWaitEvent(to, w->ev_main, 0);
 }
 
+// an instance with status bits the host has seen refuses to be stepped, as
+// in hlbm_step
+static int sweep_check(hlbm_sweep* w) {
+    for (size_t i = 0; i < w->inst.size(); ++i) {
+        int rc = check_fault(w->inst[i]);
+        if (rc != HLBM_OK) {
+            w->err = "instance " + std::to_string(i) + ": " + w->inst[i]->err;
+            return rc;
+        }
+    }
+    return HLBM_OK;
+}
+
 int hlbm_sweep_step(hlbm_sweep_t* w, int64_t nsteps) {
     if (!w || nsteps < 0) return HLBM_EINVAL;
+    int rc = sweep_check(w);
+    if (rc != HLBM_OK) return rc;
     sweep_fork(w, w->main);
-    int rc = HLBM_OK;
     for (int64_t k = 0; k < nsteps && rc == HLBM_OK; ++k) rc = sweep_one_step(w, false);
     sweep_join(w, w->main);
+    if (nsteps > 0)
+        for (hlbm* h : w->inst) queue_status_copy(h);
     return rc;
 }
 
 int hlbm_sweep_tune(hlbm_sweep_t* w, int32_t trial_steps, int32_t* tile_nodes) {
     if (!w || trial_steps < 1) return HLBM_EINVAL;
+    if (int rc = sweep_check(w); rc != HLBM_OK) return rc;
     // the tuner times every solver's own launch: no packs
     for (cudaEvent_t e : w->ev_pack)
         if (e) cudaEventDestroy(e);
@@ -2052,6 +2201,7 @@ int hlbm_sweep_tune(hlbm_sweep_t* w, int32_t trial_steps, int32_t* tile_nodes) {
 
 int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms) {
     if (!w || nsteps < 1 || !fv_ms) return HLBM_EINVAL;
+    if (int rc = sweep_check(w); rc != HLBM_OK) return rc;
     std::fill(w->fv_ms.begin(), w->fv_ms.end(), 0.0);
     sweep_fork(w, w->main);
     int rc = HLBM_OK;
@@ -2191,6 +2341,8 @@ void hlbm_destroy(hlbm_t* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->st_event) cudaEventDestroy(h->st_event);
+    if (h->st_host) cudaFreeHost(h->st_host);
     for (void* b : std::vector<void*>(h->blocks)) dev_free(h, b);
     delete h;
 }

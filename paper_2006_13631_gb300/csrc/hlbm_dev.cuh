@@ -31,6 +31,11 @@ __host__ __device__ __forceinline__ constexpr T w_of(int i) {
 
 enum : int8_t { CLS_DISC = 0, CLS_INTERP = 1, CLS_UNUSED = 2 };
 
+// Polls of a neighbour tile's progress counter before an FV wait gives up
+// (with the kernels' short sleeps between polls: well under a second), sets
+// HLBM_ST_SYNC_TIMEOUT and the abort flag, and returns.
+constexpr long kSpinLimit = 1L << 23;
+
 // patch node record: f'[9], q[6], pad
 constexpr int kRec = 16;
 
@@ -129,6 +134,8 @@ struct Dev {
     const int32_t* tile_nb;
     unsigned long long* progress;
     unsigned* abort_flag;
+    long spin_limit;   // polls of a neighbour's counter before the wait gives up
+    int stall_tile;    // fault injection: this tile never releases its counter (-1: none)
     // shared-memory tiles: halo node lists, ELL matrices with tile-local
     // columns (own nodes first, then halo), and the nodes other tiles read
     int ell_width;            // entries per row (rows padded)

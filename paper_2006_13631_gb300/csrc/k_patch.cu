@@ -436,7 +436,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 constexpr int kFvThreads = 256;
-constexpr long kMaxSpins = 1L << 23;  // with 128 ns sleeps: about a second
 
 // Lamina velocity at the end of sub-step m, t + (m+1)/n (the wall nodes'
 // Dirichlet value, eq. 182); INDUCED motion interpolates v(t) -> v(t+1).
@@ -484,7 +483,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_steps(Dev<T> d, StepArgs a, c
                         ok = false;
                         break;
                     }
-                    if (++spins > kMaxSpins) {
+                    if (++spins > d.spin_limit) {
                         atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
                         atomicExch(d.abort_flag, 1u);
                         ok = false;
@@ -505,7 +504,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_steps(Dev<T> d, StepArgs a, c
         wall_velocity(d, a, m, U, V);
         for (int P = p0 + threadIdx.x; P < p1; P += blockDim.x) fv_node(d, in, out, P, m, U, V);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && tile != d.stall_tile) {
             __threadfence();
             st_release(d.progress + tile, base + m + 1);
         }
@@ -828,7 +827,7 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
                             ok = false;
                             break;
                         }
-                        if (++spins > kMaxSpins) {
+                        if (++spins > d.spin_limit) {
                             atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
                             atomicExch(d.abort_flag, 1u);
                             ok = false;
@@ -883,7 +882,7 @@ __global__ void __launch_bounds__(kSmemThreads<T>, 1) k_fv_tiles(Dev<T> d, StepA
             }
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && tile != d.stall_tile) {
             __threadfence();
             st_release(d.progress + tile, base + m + 1);
         }
@@ -1197,7 +1196,7 @@ __device__ __forceinline__ void fv_tmem_body(const Dev<T>& d, const StepArgs& a,
                             ok = false;
                             break;
                         }
-                        if (++spins > kMaxSpins) {
+                        if (++spins > d.spin_limit) {
                             atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
                             atomicExch(d.abort_flag, 1u);
                             ok = false;
@@ -1233,7 +1232,7 @@ __device__ __forceinline__ void fv_tmem_body(const Dev<T>& d, const StepArgs& a,
                              p0);
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && tile != d.stall_tile) {
             __threadfence();
             st_release(d.progress + tile, base + m + 1);
         }

@@ -204,6 +204,14 @@ def hlbm_status(h) -> int:
     return v.value
 
 
+def hlbm_clear_status(h):
+    _check(N.load().hlbm_clear_status(h), h)
+
+
+def hlbm_inject_fault(h, kind: int, arg: int):
+    _check(N.load().hlbm_inject_fault(h, int(kind), int(arg)), h)
+
+
 def hlbm_profile(h, enable: bool):
     _check(N.load().hlbm_profile(h, 1 if enable else 0), h)
 

@@ -338,6 +338,55 @@ def test_sine_fit_recovers_phasor():
     assert rms < 1e-12
 
 
+def test_force_on_a_body_at_rest_in_a_linear_pressure_field_is_archimedes():
+    """R4 against Archimedes' principle.  A body at rest in fluid at rest
+    whose density, hence pressure p = c_s^2 (rho - rho0), varies linearly
+    carries the force -grad p times its area (the divergence theorem: the
+    integral of -p n over the closed surface).  The patch is filled from such
+    a lattice state by the type-1 rule of Sec. 4 (bilinear interpolation is
+    exact for linear fields; f^neq = 0), so the force at t = 0 is the pressure
+    term of R4 integrated by the trapezoid rule over the wall segments, which
+    is exact for a linear p on straight segments.  A missing or mis-scaled
+    pressure term, a wrong normal orientation or length, or a factor in the
+    segment sum changes the result."""
+    L, T = 12.0, 6.0
+    for gx, gy in ((0.0, 1e-3), (2e-4, -5e-4)):
+        w = inputs.Workload("archimedes", 64, 56, L, T, 31.3, 27.6, 0.8, 20, inputs.MOTION_STATIC,
+                            delta_f=1.8, bc_x=inputs.BC_PERIODIC, bc_y=inputs.BC_PERIODIC,
+                            mesh_args=dict(n_L=24, n_T=12, n_layers=8, h1=0.3, d_out=3.6))
+        Y, X = np.mgrid[0:w.ny, 0:w.nx].astype(np.float64)
+        rho = 1.0 + gx * (X - w.xc) + gy * (Y - w.yc)
+        o = oracle.Oracle(w, rho_init=rho.ravel())
+        fx, fy = o.force()
+        area = L * T  # the wall nodes trace the rectangle itself (layer 0)
+        assert fx[0] == pytest.approx(-CS2 * gx * area, rel=1e-10, abs=1e-15)
+        assert fy[0] == pytest.approx(-CS2 * gy * area, rel=1e-10, abs=1e-15)
+
+
+def test_theta_normalisation_gives_one_for_the_potential_flow_added_mass():
+    """eq. force_phasor against the textbook added mass of a flat plate.  In
+    potential flow a plate of chord L moving normal to itself carries the
+    added mass rho pi (L/2)^2 per unit depth (the mass of fluid in the
+    circumscribed circle), so F = -m_a y'' and Theta = 1: the normalisation
+    (pi/4) rho w^2 L^2 A is built so that Re Theta -> 1 (Sec. 2.1: Gamma ->
+    1.02 for large beta).  A linear damping force -c y' adds
+    Im Theta = -c / ((pi/4) rho w L^2) < 0: damping has a negative imaginary
+    part, as Gamma of eq. hydro_gamma.  A wrong power of w or L, a missing
+    pi/4 or A, or the opposite phase convention fails."""
+    for rho0, L, A, om in ((1.0, 20.0, 0.8, 2 * math.pi / 24), (1.02, 64.0, 3.2, 0.00625),
+                           (0.97, 128.0, 20.4, 1.227e-3)):
+        t = np.arange(int(5 * 2 * math.pi / om) + 2, dtype=np.float64)
+        y, ydot, yddot = A * np.sin(om * t), A * om * np.cos(om * t), -A * om * om * np.sin(om * t)
+        m_a = rho0 * math.pi * (0.5 * L) ** 2
+        th, rms = oracle.theta(-m_a * yddot, rho0, om, L, A)
+        assert th.real == pytest.approx(1.0, abs=1e-9) and abs(th.imag) < 1e-9 and rms < 1e-9
+        c = 0.3 * m_a * om  # a damping of the size of the added-mass force
+        th, _ = oracle.theta(-m_a * yddot - c * ydot, rho0, om, L, A)
+        assert th.real == pytest.approx(1.0, abs=1e-9)
+        assert th.imag == pytest.approx(-0.3 * m_a / (0.25 * math.pi * rho0 * L * L), rel=1e-9)
+        assert th.imag < 0
+
+
 def test_hybrid_disk_patch_reproduces_lbgk_shear_wave():
     """A body-free disk patch inside a periodic LBGK lattice must carry a
     decaying shear wave exactly as the plain LBGK does (same viscosity,
