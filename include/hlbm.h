@@ -143,7 +143,8 @@ typedef struct {
  * (interpolated at interpolation nodes, the patch state elsewhere).
  * fv_kernel picks the kernel of the FV sub-steps, HLBM_FV_*: AUTO takes the
  * first that applies of TMEM (rows of at most 7 off-diagonal entries,
- * outer_fv = 0), SMEM and GLOBAL; the others are for testing and
+ * outer_fv = 0), SMEM and GLOBAL; DEEP (same rows) is chosen explicitly;
+ * the others are for testing and
  * hlbm_create fails with HLBM_EINVAL when the one asked for cannot run the
  * patch.  All give the same results bit for bit. */
 typedef struct {
@@ -165,6 +166,8 @@ typedef struct {
 #define HLBM_FV_GLOBAL 1 /* records in global memory, any tile size          */
 #define HLBM_FV_SMEM 2   /* tiles in shared memory, records updated in place */
 #define HLBM_FV_TMEM 3   /* rows in tensor memory, records double-buffered   */
+#define HLBM_FV_DEEP 4   /* as TMEM with ghost layers: one exchange between   */
+                         /* tiles every K sub-steps (hlbm_set_fv_depth)       */
 
 /* Lamina motion.  HARMONIC: A, omega; UNIFORM: vx, vy.  INDUCED (the paper's
  * outlook towards fluid-structure interaction, Sec. 7): a rigid lamina on a
@@ -302,8 +305,22 @@ typedef struct {
     int32_t n_levels;       /* coarser lattice levels                     */
     int64_t n_coarse;       /* nodes of all coarser levels                */
     double coarse_updates;  /* their node updates per step, sum N_k / 2^k */
+    int32_t fv_depth;       /* HLBM_FV_DEEP: sub-steps between exchanges (else 1) */
+    int32_t fv_slots;       /* HLBM_FV_DEEP: most slots (own and ghost nodes) of a tile */
 } hlbm_info_t;
 int hlbm_info(hlbm_t* h, hlbm_info_t* info);
+
+/* Exchange interval of the HLBM_FV_DEEP kernel.  The method's FV sub-steps
+ * (Sec. 3, eq. ulbe) are unchanged; this sets how the GPU's tiles share
+ * their boundary data.  Each FV tile keeps `depth` layers of ghost
+ * nodes around its own nodes and recomputes them, so that tiles exchange
+ * records once every `depth` sub-steps instead of every sub-step; deeper
+ * layers cost redundant work and shared memory.  The tiles are rebuilt
+ * with the largest interval up to `depth` (1 .. HLBM_FV_MAX_DEPTH) that
+ * fits on the device (default 3); the results do not change, bit for bit.
+ * Synchronises the stream.  HLBM_EINVAL for another depth. */
+#define HLBM_FV_MAX_DEPTH 4
+int hlbm_set_fv_depth(hlbm_t* h, int32_t depth);
 
 /* Per-phase device time, measured with CUDA events recorded on the
  * solver's stream around each phase of hlbm_step while profiling is on.

@@ -21,16 +21,21 @@ DISC, INTERP, UNUSED = 0, 1, 2
 MAX_LEVELS = 4
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (serial, -ffp-contract=off)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+_LIB_OMP = os.path.join(_HERE, "_build", "libhlbm_oracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (-ffp-contract=off): serial, or with
+    OpenMP over the node loops (the CPU baseline; the same results)."""
+    out = _LIB_OMP if openmp else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hlbm_oracle.h"))):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] +
+                              (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class _Params(C.Structure):
@@ -56,13 +61,28 @@ class _Params(C.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
 def lib():
+    """The serial oracle (what the tests use)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
+        _lib = _declare(C.CDLL(build()))
+    return _lib
+
+
+def lib_omp():
+    """The same source built with OpenMP over its node loops (CPU baseline);
+    the threads follow OMP_NUM_THREADS, else every host core."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _declare(C.CDLL(build(openmp=True)))
+    return _lib_omp
+
+
+def _declare(L):
+    if True:
         P = C.c_void_p
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int32)
@@ -98,7 +118,7 @@ def lib():
         L.orc_fv_periodic.argtypes = [C.c_int, dp, C.c_int, ip, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int, C.c_int, dp]
         L.orc_lbgk.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp]
-    return _lib
+    return L
 
 
 def _dp(a):
@@ -209,8 +229,10 @@ def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
 class Oracle:
     """Serial FP64 MG-HLBM run for one workload (see ``inputs.Workload``)."""
 
-    def __init__(self, w, mesh=None, rho_init=None, u_init=None, level_u_init=None, level_rho_init=None):
+    def __init__(self, w, mesh=None, rho_init=None, u_init=None, level_u_init=None, level_rho_init=None,
+                 openmp=False):
         self.w = w
+        self._L = lib_omp() if openmp else lib()
         self.mesh = mesh if mesh is not None else w.mesh()
         rho = rho_init if rho_init is not None else w.rho_init()
         self._keep = [np.ascontiguousarray(rho, dtype=np.float64),
@@ -250,107 +272,107 @@ class Oracle:
             if level_rho_init is not None and level_rho_init[k] is not None:
                 self._keep.append(np.ascontiguousarray(level_rho_init[k], dtype=np.float64))
                 p.lv_rho[k] = _dp(self._keep[-1])
-        self._h = lib().orc_create(C.byref(p))
+        self._h = self._L.orc_create(C.byref(p))
         self.n = self.mesh.n_nodes
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     def step(self, nsteps=1):
-        return lib().orc_step(self._h, nsteps)
+        return self._L.orc_step(self._h, nsteps)
 
     @property
     def status(self):
-        return lib().orc_status(self._h)
+        return self._L.orc_status(self._h)
 
     @property
     def time(self):
-        return lib().orc_time(self._h)
+        return self._L.orc_time(self._h)
 
     def struct_f(self):
         out = np.empty((9, self.w.ny, self.w.nx))
-        lib().orc_struct_f(self._h, _dp(out))
+        self._L.orc_struct_f(self._h, _dp(out))
         return out
 
     def struct_macro(self):
         r, ux, uy = (np.empty((self.w.ny, self.w.nx)) for _ in range(3))
-        lib().orc_struct_macro(self._h, _dp(r), _dp(ux), _dp(uy))
+        self._L.orc_struct_macro(self._h, _dp(r), _dp(ux), _dp(uy))
         return r, ux, uy
 
     def level_macro(self, k=1):
         """rho, ux, uy of coarser level k (1..len(w.levels)) at its current time (R12)."""
         nx, ny = self.w.levels[k - 1][:2]
         r, ux, uy = (np.empty((ny, nx)) for _ in range(3))
-        lib().orc_level_macro(self._h, int(k), _dp(r), _dp(ux), _dp(uy))
+        self._L.orc_level_macro(self._h, int(k), _dp(r), _dp(ux), _dp(uy))
         return r, ux, uy
 
     def struct_class(self):
         out = np.empty((self.w.ny, self.w.nx), dtype=np.int8)
-        lib().orc_struct_class(self._h, out.ctypes.data_as(C.POINTER(C.c_int8)))
+        self._L.orc_struct_class(self._h, out.ctypes.data_as(C.POINTER(C.c_int8)))
         return out
 
     def classify_at(self, t):
         out = np.empty((self.w.ny, self.w.nx), dtype=np.int8)
-        lib().orc_classify_at(self._h, t, out.ctypes.data_as(C.POINTER(C.c_int8)))
+        self._L.orc_classify_at(self._h, t, out.ctypes.data_as(C.POINTER(C.c_int8)))
         return out
 
     def relocate_at(self, t):
         ty, d = np.empty(self.n, np.int32), np.empty(self.n, np.int32)
-        lib().orc_relocate_at(self._h, t, _ip(ty), _ip(d))
+        self._L.orc_relocate_at(self._h, t, _ip(ty), _ip(d))
         return ty, d
 
     def patch_f(self):
         out = np.empty((self.n, 9))
-        lib().orc_patch_f(self._h, _dp(out))
+        self._L.orc_patch_f(self._h, _dp(out))
         return out
 
     def patch_macro(self):
         r, ux, uy = (np.empty(self.n) for _ in range(3))
-        lib().orc_patch_macro(self._h, _dp(r), _dp(ux), _dp(uy))
+        self._L.orc_patch_macro(self._h, _dp(r), _dp(ux), _dp(uy))
         return r, ux, uy
 
     def refill_record(self):
         t, d = np.empty(self.n, np.int32), np.empty(self.n, np.int32)
-        lib().orc_refill_record(self._h, _ip(t), _ip(d))
+        self._L.orc_refill_record(self._h, _ip(t), _ip(d))
         return t, d
 
     def force(self):
         n = self.time + 1
         fx, fy = np.empty(n), np.empty(n)
-        lib().orc_force(self._h, _dp(fx), _dp(fy))
+        self._L.orc_force(self._h, _dp(fx), _dp(fy))
         return fx, fy
 
     def motion(self):
         """(y, v) of the lamina at integer times 0..t."""
         n = self.time + 1
         y, v = np.empty(n), np.empty(n)
-        lib().orc_motion_history(self._h, n, _dp(y), _dp(v))
+        self._L.orc_motion_history(self._h, n, _dp(y), _dp(v))
         return y, v
 
     def gamma(self, discard=1.0, fit=3.0):
         re, im, r = C.c_double(), C.c_double(), C.c_double()
-        rc = lib().orc_gamma(self._h, discard, fit, C.byref(re), C.byref(im), C.byref(r))
+        rc = self._L.orc_gamma(self._h, discard, fit, C.byref(re), C.byref(im), C.byref(r))
         if rc != 0:
             raise ValueError(f"orc_gamma failed ({rc})")
         return re.value, im.value, r.value
 
     def locate(self, qx, qy):
         lam = np.zeros(3)
-        k = lib().orc_locate(self._h, qx, qy, _dp(lam))
+        k = self._L.orc_locate(self._h, qx, qy, _dp(lam))
         return k, lam
 
     def fv_coeffs(self):
-        nnz = lib().orc_fv_nnz(self._h)
+        nnz = self._L.orc_fv_nnz(self._h)
         rp = np.empty(self.n + 1, np.int32)
         col = np.empty(nnz, np.int32)
         gx, gy, cc = np.empty(nnz), np.empty(nnz), np.empty(nnz)
         vol = np.empty(self.n)
-        lib().orc_fv_coeffs(self._h, _ip(rp), _ip(col), _dp(gx), _dp(gy), _dp(cc), _dp(vol))
+        self._L.orc_fv_coeffs(self._h, _ip(rp), _ip(col), _dp(gx), _dp(gy), _dp(cc), _dp(vol))
         return rp, col, gx, gy, cc, vol
 
     @property
     def n_wall_segments(self):
-        return lib().orc_n_wall_segments(self._h)
+        return self._L.orc_n_wall_segments(self._h)

@@ -845,6 +845,7 @@ static void post_from_patch(orc_t* o, int x, int y, double cx, double cy, double
     double lam[3];
     int k = locate(o, qx, qy, lam);
     if (k < 0) {
+#pragma omp atomic
         o->status |= ORC_ERR_FILL_NOT_LOCATED;
         orc_feq(o->p.rho0, 0.0, 0.0, post);
         return;
@@ -870,6 +871,9 @@ static void structured_step(orc_t* o, double cx, double cy) {
     int64_t N = o->N;
     const double* f = o->fs[o->cur];
     double* fn = o->fs[1 - o->cur];
+    /* every node's update reads only the previous state: the loops may run
+     * in parallel (OpenMP build of the CPU baseline), with the same results */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int64_t s = (int64_t)y * nx + x;
@@ -879,7 +883,10 @@ static void structured_step(orc_t* o, double cx, double cy) {
             if (is_ring(o, x, y)) {
                 for (int i = 0; i < 9; ++i) post[i] = f[i * N + s]; /* R12: the ring holds its ghost */
             } else if (c == ORC_INTERP || o->cls_prev[s] != ORC_DISC) {
-                if (c == ORC_DISC && o->cls_prev[s] == ORC_UNUSED) o->status |= ORC_ERR_UNUSED_TO_DISC;
+                if (c == ORC_DISC && o->cls_prev[s] == ORC_UNUSED) {
+#pragma omp atomic
+                    o->status |= ORC_ERR_UNUSED_TO_DISC;
+                }
                 post_from_patch(o, x, y, cx, cy, post);
             } else {
                 double fl[9];
@@ -889,6 +896,7 @@ static void structured_step(orc_t* o, double cx, double cy) {
             for (int i = 0; i < 9; ++i) o->fpost[i * N + s] = post[i];
         }
     int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int64_t s = (int64_t)y * nx + x;
@@ -961,12 +969,14 @@ static void fv_substeps(orc_t* o, int64_t t) {
         }
         const double* fin = o->fu[o->ucur];
         double* fout = o->fu[1 - o->ucur];
+#pragma omp parallel for schedule(static)
         for (int P = 0; P < nn; ++P) {
             double r, ux, uy;
             moments(fin + 9 * P, &r, &ux, &uy);
             orc_feq(r, ux, uy, o->feq_u + 9 * P);
         }
         /* interpolation (outer) nodes: structured state, linear in time (R2) */
+#pragma omp parallel for schedule(static)
         for (int P = 0; P < nn; ++P) {
             if (o->kind[P] != ORC_KIND_OUTER) continue;
             double st[12];
@@ -974,6 +984,7 @@ static void fv_substeps(orc_t* o, int64_t t) {
             for (int j = 0; j < 12; ++j) st[j] = (1.0 - theta) * s0[j] + theta * s1[j];
             f_from_struct_state(o, st, o->dstar + 9 * P);
         }
+#pragma omp parallel for schedule(static)
         for (int P = 0; P < nn; ++P) {
             if (o->kind[P] == ORC_KIND_OUTER) {
                 if (o->p.outer_fv)

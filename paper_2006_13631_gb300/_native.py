@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhlbm.so")
 HLBM_OK, HLBM_EINVAL, HLBM_ECUDA, HLBM_EUNSTABLE, HLBM_EGEOM, HLBM_ENOMEM, HLBM_EIO = 0, -1, -2, -3, -4, -5, -6
 HLBM_ETIMEOUT = -7
 HLBM_FAULT_STALL_TILE, HLBM_FAULT_NAN_LATTICE = 1, 2
-HLBM_FV_AUTO, HLBM_FV_GLOBAL, HLBM_FV_SMEM, HLBM_FV_TMEM = 0, 1, 2, 3
+HLBM_FV_AUTO, HLBM_FV_GLOBAL, HLBM_FV_SMEM, HLBM_FV_TMEM, HLBM_FV_DEEP = 0, 1, 2, 3, 4
 HLBM_BC_WALL, HLBM_BC_OUTFLOW, HLBM_BC_PERIODIC = 0, 1, 2
 HLBM_F64, HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2, 3
 HLBM_NODE_INTERIOR, HLBM_NODE_OUTER, HLBM_NODE_WALL = 0, 1, 2
@@ -57,7 +57,8 @@ class hlbm_info_t(C.Structure):
                 ("n_wall_segments", C.c_int32), ("box_w", C.c_int32), ("box_h", C.c_int32),
                 ("launches_per_step", C.c_int32), ("dtype", C.c_int32), ("fv_kernel", C.c_int32),
                 ("n_tiles", C.c_int32), ("y", C.c_double), ("vy", C.c_double), ("n_levels", C.c_int32),
-                ("n_coarse", C.c_int64), ("coarse_updates", C.c_double)]
+                ("n_coarse", C.c_int64), ("coarse_updates", C.c_double), ("fv_depth", C.c_int32),
+                ("fv_slots", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -80,6 +81,7 @@ SIGNATURES = {
     "hlbm_info": (C.c_int, [C.c_void_p, C.POINTER(hlbm_info_t)]),
     "hlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "hlbm_clear_status": (C.c_int, [C.c_void_p]),
+    "hlbm_set_fv_depth": (C.c_int, [C.c_void_p, C.c_int32]),
     "hlbm_inject_fault": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "hlbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hlbm_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),

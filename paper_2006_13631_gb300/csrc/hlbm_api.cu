@@ -47,6 +47,7 @@ struct hlbm {
     std::vector<void*> tile_blocks;  // device tables of the current FV tiling
     bool use_smem = false;      // a tile kernel (else the global-memory kernel)
     int fv_kind = HLBM_FV_GLOBAL;  // HLBM_FV_* in use
+    int fv_depth = 3;              // deep tiles: sub-steps between exchanges asked for (the largest that fits up to it)
     double mxmin = 0, mxmax = 0, mymin = 0, mymax = 0;
     int nnz = 0, nseg = 0;
 
@@ -405,14 +406,18 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
         d.spin_limit = h->inject_spin_limit;
         h->inject_stall_tile = -1;
     }
-    cudaError_t fe = h->fv_kind == HLBM_FV_TMEM   ? launch_fv_tmem<T>(d, ps.a, s)
+    cudaError_t fe = h->fv_kind == HLBM_FV_DEEP   ? launch_fv_deep<T>(d, ps.a, s)
+                     : h->fv_kind == HLBM_FV_TMEM ? launch_fv_tmem<T>(d, ps.a, s)
                      : h->fv_kind == HLBM_FV_SMEM ? launch_fv_smem<T>(d, ps.a, s)
                                                   : launch_fv_persistent<T>(d, ps.a, s);
     d.stall_tile = -1;
     d.spin_limit = kSpinLimit;
     if (ev1) cudaEventRecord(ev1, s);
     if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
-    if (d.n_sub & 1) h->ui = 1 - h->ui;
+    // the state after the last sub-step is in the record buffer of the last
+    // exchange: fu_out when the number of exchanges is odd
+    const int n_exch = h->fv_kind == HLBM_FV_DEEP ? (d.n_sub + d.deep_k - 1) / d.deep_k : d.n_sub;
+    if (n_exch & 1) h->ui = 1 - h->ui;
     bind(h, d);
     phase_end(h, HLBM_PHASE_FV, ev, 2, s);
     return HLBM_OK;
@@ -466,6 +471,129 @@ int step_impl(hlbm* h, int64_t nsteps) {
     return HLBM_OK;
 }
 
+// Deep-tile tables (k_fv_deep) for the tiles [tile_start[k], tile_start[k+1])
+// with K layers of ghost nodes.  Layer 0 is the tile's own nodes; layer j
+// the nodes the updates of layer j-1 read (row columns; outer nodes read
+// nothing) that are in no earlier layer.  Slots: own nodes whose updates read
+// only own nodes (n_a), the other own nodes, then layers 1 .. K, each group
+// in the caller's node order (on meshes built layer by layer consecutive
+// slots then run along a layer, which spreads a warp's gathers over the
+// shared-memory banks).  Sub-step s of a block computes the own nodes and
+// layers 1 .. K-1-s.  The tiles a tile waits for are the owners of its
+// ghosts and the tiles that hold its nodes as ghosts (symmetric, so that no
+// tile can overwrite an exchange buffer a neighbour still reads).  Returns
+// false when a tile's computed slots exceed comp_cap.
+struct DeepTables {
+    int K = 0, slot_cap = 0, ocap = 0;
+    std::vector<int32_t> ptr, cnt, gid, optr, rptr, row_gid, lcol, nb_ptr, nb;
+    std::vector<int8_t> send;
+    std::vector<uint16_t> oslot;
+};
+
+bool build_deep_tables(const hlbm* h, const std::vector<int32_t>& tile_start, const std::vector<int32_t>& owner,
+                       int K, int comp_cap, DeepTables& D) {
+    const int n = h->patch.n_nodes, n_tiles = (int)tile_start.size() - 1;
+    D = DeepTables{};
+    D.K = K;
+    D.ptr.assign(n_tiles + 1, 0);
+    D.optr.assign(n_tiles + 1, 0);
+    D.rptr.assign(n_tiles + 1, 0);
+    D.cnt.assign((size_t)kDeepCnt * n_tiles, 0);
+    std::vector<int32_t> loc(n, -1);
+    std::vector<int8_t> held(n, 0);  // a node some other tile holds as a ghost
+    std::vector<std::vector<int32_t>> nbs(n_tiles);
+    auto by_caller = [&](int32_t a, int32_t b) { return h->perm[a] < h->perm[b]; };
+    auto reads = [&](int q, auto&& fn) {
+        if (h->kind[q] == HLBM_NODE_OUTER) return;
+        for (int e = h->row_ptr[q] + 1; e < h->row_ptr[q + 1]; ++e) fn(h->col[e]);
+    };
+    for (int k = 0; k < n_tiles; ++k) {
+        const int p0 = tile_start[k], p1 = tile_start[k + 1];
+        std::vector<int32_t> A, B;
+        for (int q = p0; q < p1; ++q) {
+            bool inside = true;
+            reads(q, [&](int c) { inside = inside && c >= p0 && c < p1; });
+            (inside ? A : B).push_back(q);
+        }
+        std::sort(A.begin(), A.end(), by_caller);
+        std::sort(B.begin(), B.end(), by_caller);
+        std::vector<int32_t> order = A;
+        order.insert(order.end(), B.begin(), B.end());
+        for (size_t i = 0; i < order.size(); ++i) loc[order[i]] = (int32_t)i;
+        std::vector<int> layer_size;
+        std::vector<int32_t> prev = order;
+        for (int j = 1; j <= K; ++j) {
+            std::vector<int32_t> lay;
+            for (int32_t q : prev)
+                reads(q, [&](int c) {
+                    if (loc[c] < 0) {
+                        loc[c] = -2;
+                        lay.push_back(c);
+                    }
+                });
+            std::sort(lay.begin(), lay.end(), by_caller);
+            for (int32_t c : lay) {
+                loc[c] = (int32_t)order.size();
+                order.push_back(c);
+                held[c] = 1;
+                nbs[k].push_back(owner[c]);
+            }
+            layer_size.push_back((int)lay.size());
+            prev = lay;
+        }
+        const int n_own = p1 - p0, n_slot = (int)order.size();
+        int32_t* c = D.cnt.data() + (size_t)kDeepCnt * k;
+        c[0] = (int32_t)A.size();
+        c[1] = n_own;
+        c[2] = n_slot;
+        for (int st = 0; st < K; ++st) {
+            int cs = n_own;
+            for (int j = 1; j <= K - 1 - st; ++j) cs += layer_size[j - 1];
+            c[3 + st] = cs;
+        }
+        const int n_comp = c[3];
+        if (n_comp > comp_cap) return false;
+        // computed slots: row images (columns as local slots; outer nodes
+        // read none of theirs), outer slots for the staged feed
+        for (int x = 0; x < n_comp; ++x) {
+            const int q = order[x];
+            D.row_gid.push_back(q);
+            for (int j = 0; j < kTmemMaxEntries; ++j) {
+                const int e = h->row_ptr[q] + 1 + j;
+                int lc = x;
+                if (e < h->row_ptr[q + 1] && h->kind[q] != HLBM_NODE_OUTER) lc = loc[h->col[e]];
+                D.lcol.push_back(lc);
+            }
+            if (h->kind[q] == HLBM_NODE_OUTER) D.oslot.push_back((uint16_t)x);
+        }
+        D.gid.insert(D.gid.end(), order.begin(), order.end());
+        D.ptr[k + 1] = (int32_t)D.gid.size();
+        D.rptr[k + 1] = (int32_t)D.row_gid.size();
+        D.optr[k + 1] = (int32_t)D.oslot.size();
+        D.slot_cap = std::max(D.slot_cap, n_slot);
+        D.ocap = std::max(D.ocap, D.optr[k + 1] - D.optr[k]);
+        for (int32_t q : order) loc[q] = -1;
+    }
+    D.send.assign(D.gid.size(), 0);
+    for (int k = 0; k < n_tiles; ++k)
+        for (int x = 0; x < tile_start[k + 1] - tile_start[k]; ++x) D.send[D.ptr[k] + x] = held[D.gid[D.ptr[k] + x]];
+    // symmetric neighbour sets
+    std::vector<std::vector<int32_t>> sym(n_tiles);
+    for (int k = 0; k < n_tiles; ++k)
+        for (int32_t o : nbs[k]) {
+            sym[k].push_back(o);
+            sym[o].push_back(k);
+        }
+    D.nb_ptr.assign(n_tiles + 1, 0);
+    for (int k = 0; k < n_tiles; ++k) {
+        std::sort(sym[k].begin(), sym[k].end());
+        sym[k].erase(std::unique(sym[k].begin(), sym[k].end()), sym[k].end());
+        D.nb.insert(D.nb.end(), sym[k].begin(), sym[k].end());
+        D.nb_ptr[k + 1] = (int32_t)D.nb.size();
+    }
+    return true;
+}
+
 // FV tiles: equal ranges of the Morton-ordered nodes.  The shared-memory
 // kernel runs one block per tile, all co-resident; when a tile and its halo
 // do not fit in shared memory the global-memory kernel runs instead, with
@@ -475,7 +603,7 @@ int step_impl(hlbm* h, int64_t nsteps) {
 // tile-local columns, node orders and send flags; previous tables are
 // released.  Needs the FV matrices (d.coef).
 template <typename T>
-int build_tiles(hlbm* h, int n_tiles_req) {
+int build_tiles(hlbm* h, int n_tiles_req, bool tmem_only = false) {
     Dev<T>& d = dev_of<T>(h);
     cudaStream_t s = h->stream;
     const int n = h->patch.n_nodes;
@@ -530,16 +658,28 @@ int build_tiles(hlbm* h, int n_tiles_req) {
         return cap;
     };
     const int ocap0 = outer_cap();
-    const int want = h->patch.fv_kernel;  // HLBM_FV_* (0: the fastest that applies)
+    // HLBM_FV_* (0: the fastest that applies); a sweep pack needs the tensor-memory kernel
+    const int want = tmem_only ? HLBM_FV_TMEM : h->patch.fv_kernel;
     const bool tiles_ok = tile_cap <= fv_tile_max<T>() && tile_cap + halo_cap < 65536;
+    // deep tiles: the deepest exchange interval up to fv_depth that fits
+    DeepTables deep;
+    bool deep_ok = false;
+    if (want == HLBM_FV_DEEP && max_row - 1 <= 7 && h->patch.outer_fv == 0) {
+        for (int K = std::min(h->fv_depth, kDeepMaxK); K >= 1 && !deep_ok; --K) {
+            if (!build_deep_tables(h, tile_start, owner, K, fv_deep_tmem_slots<T>(), deep)) continue;
+            deep_ok = deep.slot_cap < 65536 &&
+                      fv_deep_tile_capacity<T>(fv_deep_smem_bytes<T>(deep.slot_cap, h->patch.n_sub,
+                                                                       std::max(deep.ocap, 1))) >= n_tiles;
+        }
+    }
     const size_t smem = fv_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), std::max(max_row - 1, 0),
                                          h->patch.n_sub, ocap0);
     const size_t tsmem = fv_tmem_smem_bytes<T>(tile_cap, std::max(halo_cap, 1), h->patch.n_sub, ocap0);
-    const bool tmem_ok = tiles_ok && max_row - 1 <= 7 && h->patch.outer_fv == 0 &&
+    const bool tmem_ok = !deep_ok && tiles_ok && max_row - 1 <= 7 && h->patch.outer_fv == 0 &&
                          (want == HLBM_FV_AUTO || want == HLBM_FV_TMEM) && fv_tmem_tile_capacity<T>(tsmem) >= n_tiles;
-    const bool smem_ok = !tmem_ok && tiles_ok && (want == HLBM_FV_AUTO || want == HLBM_FV_SMEM) &&
+    const bool smem_ok = !deep_ok && !tmem_ok && tiles_ok && (want == HLBM_FV_AUTO || want == HLBM_FV_SMEM) &&
                          fv_smem_tile_capacity<T>(smem) >= n_tiles;
-    h->fv_kind = tmem_ok ? HLBM_FV_TMEM : smem_ok ? HLBM_FV_SMEM : HLBM_FV_GLOBAL;
+    h->fv_kind = deep_ok ? HLBM_FV_DEEP : tmem_ok ? HLBM_FV_TMEM : smem_ok ? HLBM_FV_SMEM : HLBM_FV_GLOBAL;
     h->use_smem = h->fv_kind != HLBM_FV_GLOBAL;
     if (want != HLBM_FV_AUTO && want != h->fv_kind)
         return fail(h, HLBM_EINVAL, "FV kernel %d cannot run this patch (tiles of %d nodes, rows of %d entries)", want,
@@ -563,6 +703,35 @@ int build_tiles(hlbm* h, int n_tiles_req) {
     h->n_tiles = n_tiles;
     d.n_tiles = n_tiles;
     d.tile_start = (int32_t*)track(upload(h, tile_start.data(), tile_start.size(), &rc));
+    if (h->fv_kind == HLBM_FV_DEEP) {
+        // the deep kernel waits for the symmetric neighbour sets of its K-deep ghost layers
+        tile_nb_ptr = deep.nb_ptr;
+        tile_nb = deep.nb;
+        if (tile_nb.empty()) tile_nb.push_back(0);
+        d.deep_k = deep.K;
+        d.deep_slot_cap = deep.slot_cap;
+        d.deep_ocap = std::max(deep.ocap, 1);
+        if (deep.oslot.empty()) deep.oslot.push_back(0);
+        d.deep_ptr = (int32_t*)track(upload(h, deep.ptr.data(), deep.ptr.size(), &rc));
+        d.deep_cnt = (int32_t*)track(upload(h, deep.cnt.data(), deep.cnt.size(), &rc));
+        d.deep_gid = (int32_t*)track(upload(h, deep.gid.data(), deep.gid.size(), &rc));
+        d.deep_send = (int8_t*)track(upload(h, deep.send.data(), deep.send.size(), &rc));
+        d.deep_optr = (int32_t*)track(upload(h, deep.optr.data(), deep.optr.size(), &rc));
+        d.deep_oslot = (uint16_t*)track(upload(h, deep.oslot.data(), deep.oslot.size(), &rc));
+        d.deep_rptr = (int32_t*)track(upload(h, deep.rptr.data(), deep.rptr.size(), &rc));
+        const int64_t nrow = (int64_t)deep.row_gid.size();
+        uint32_t* rows = (uint32_t*)track(dev_alloc(h, std::max<int64_t>(nrow, 1) * fv_deep_row_words<T>() * 4));
+        int32_t* d_rgid = upload(h, deep.row_gid.data(), deep.row_gid.size(), &rc);
+        int32_t* d_lcol = upload(h, deep.lcol.data(), deep.lcol.size(), &rc);
+        if (rc != HLBM_OK) return rc;
+        if (!rows || !d_rgid || !d_lcol) return fail(h, HLBM_ENOMEM, "device allocation failed");
+        d.deep_rows = rows;
+        launch_build_deep_rows<T>(d, d_rgid, d_lcol, nrow, rows, s);
+        cudaError_t e3 = cudaStreamSynchronize(s);
+        dev_free(h, d_rgid);
+        dev_free(h, d_lcol);
+        if (e3 != cudaSuccess) return cuda_check(h, e3, "deep tile rows");
+    }
     d.tile_nb_ptr = (int32_t*)track(upload(h, tile_nb_ptr.data(), tile_nb_ptr.size(), &rc));
     d.tile_nb = (int32_t*)track(upload(h, tile_nb.data(), tile_nb.size(), &rc));
     // the FV kernel counts sub-steps from t * n_sub (t: the solver's step), so a
@@ -1430,8 +1599,8 @@ int inst_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t e0, cudaEvent_
 int inst_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
     return h->dtype != HLBM_F64 ? step_finish<float>(h, s, ps) : step_finish<double>(h, s, ps);
 }
-int inst_retile(hlbm* h, int tiles) {
-    return h->dtype != HLBM_F64 ? build_tiles<float>(h, tiles) : build_tiles<double>(h, tiles);
+int inst_retile(hlbm* h, int tiles, bool tmem_only = false) {
+    return h->dtype != HLBM_F64 ? build_tiles<float>(h, tiles, tmem_only) : build_tiles<double>(h, tiles, tmem_only);
 }
 
 // The FV sub-steps of pack p's instances in one cooperative launch of the
@@ -1571,7 +1740,7 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
         rc = fail(h, HLBM_EINVAL, "unknown motion kind %d", motion->kind);
     else if ((p.lumped != 0 && p.lumped != 1) || (p.outer_fv != 0 && p.outer_fv != 1))
         rc = fail(h, HLBM_EINVAL, "lumped = %d and outer_fv = %d must be 0 or 1", p.lumped, p.outer_fv);
-    else if (p.fv_kernel < HLBM_FV_AUTO || p.fv_kernel > HLBM_FV_TMEM)
+    else if (p.fv_kernel < HLBM_FV_AUTO || p.fv_kernel > HLBM_FV_DEEP)
         rc = fail(h, HLBM_EINVAL, "unknown FV kernel %d", p.fv_kernel);
     else if (!(p.delta_f > 1.5))
         rc = fail(h, HLBM_EINVAL, "delta_f = %g must exceed 1.5 (interpolation nodes outside the body)",
@@ -1668,6 +1837,14 @@ int hlbm_step(hlbm_t* h, int64_t nsteps) {
     rc = h->dtype != HLBM_F64 ? step_impl<float>(h, nsteps) : step_impl<double>(h, nsteps);
     if (nsteps > 0) queue_status_copy(h);
     return rc;
+}
+
+int hlbm_set_fv_depth(hlbm_t* h, int32_t depth) {
+    if (!h) return HLBM_EINVAL;
+    if (depth < 1 || depth > HLBM_FV_MAX_DEPTH || depth > kDeepMaxK)
+        return fail(h, HLBM_EINVAL, "FV exchange interval %d is not in 1 .. %d", (int)depth, HLBM_FV_MAX_DEPTH);
+    h->fv_depth = depth;
+    return h->dtype != HLBM_F64 ? build_tiles<float>(h, 0) : build_tiles<double>(h, 0);
 }
 
 int hlbm_clear_status(hlbm_t* h) {
@@ -2037,6 +2214,12 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info) {
     }
     info->fv_kernel = h->fv_kind;
     info->n_tiles = h->n_tiles;
+    info->fv_depth = 1;
+    info->fv_slots = 0;
+    if (h->fv_kind == HLBM_FV_DEEP) {
+        info->fv_depth = h->dtype != HLBM_F64 ? h->df.deep_k : h->dd.deep_k;
+        info->fv_slots = h->dtype != HLBM_F64 ? h->df.deep_slot_cap : h->dd.deep_slot_cap;
+    }
     if (h->motion.kind == HLBM_MOTION_INDUCED) {
         info->y = h->Yi;
         info->vy = h->Vi;
@@ -2277,7 +2460,7 @@ int hlbm_sweep_pack(hlbm_sweep_t* w, int32_t enable, int32_t* n_packs) {
             }
             bool ok = tsum <= sms;
             for (size_t q = 0; q < g.size() && ok && rc == HLBM_OK; ++q) {
-                rc = inst_retile(w->inst[g[q]], tiles[q]);
+                rc = inst_retile(w->inst[g[q]], tiles[q], true);
                 ok = rc == HLBM_OK && w->inst[g[q]]->fv_kind == HLBM_FV_TMEM && w->inst[g[q]]->n_tiles == tiles[q];
             }
             if (rc != HLBM_OK) {

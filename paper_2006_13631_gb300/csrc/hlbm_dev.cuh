@@ -136,6 +136,20 @@ struct Dev {
     unsigned* abort_flag;
     long spin_limit;   // polls of a neighbour's counter before the wait gives up
     int stall_tile;    // fault injection: this tile never releases its counter (-1: none)
+    // deep tiles (HLBM_FV_DEEP): each tile holds its own nodes and deep_k
+    // layers of ghost nodes as local slots and exchanges records with its
+    // neighbour tiles once every deep_k sub-steps (see k_fv_deep)
+    int deep_k;
+    int deep_slot_cap;          // most slots of a tile (own nodes and every ghost layer)
+    int deep_ocap;              // most outer nodes among a tile's slots
+    const int32_t* deep_ptr;    // [n_tiles + 1]: first slot of each tile in the slot arrays
+    const int32_t* deep_cnt;    // [n_tiles][kDeepCnt]: n_a, n_own, n_slot, then the slots computed at block sub-step s
+    const int32_t* deep_gid;    // per slot: node id
+    const int8_t* deep_send;    // per slot: an own node that other tiles hold as a ghost
+    const int32_t* deep_optr;   // [n_tiles + 1]: the tile's outer slots in deep_oslot
+    const uint16_t* deep_oslot;
+    const int32_t* deep_rptr;   // [n_tiles + 1]: first computed slot of each tile in deep_rows
+    const uint32_t* deep_rows;  // per computed slot: its FV row as stored in tensor memory
     // shared-memory tiles: halo node lists, ELL matrices with tile-local
     // columns (own nodes first, then halo), and the nodes other tiles read
     int ell_width;            // entries per row (rows padded)
@@ -417,6 +431,19 @@ template <typename T> void launch_build_ell(const Coef<T>* coef, const int32_t* 
                                             int64_t count, cudaStream_t s);
 template <typename T> int fv_smem_tile_capacity(size_t smem);
 template <typename T> cudaError_t launch_fv_smem(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+// deep tiles (temporal blocking): rows with at most 7 off-diagonal entries, Dirichlet outer nodes
+constexpr int kTmemMaxEntries = 7;  // off-diagonal entries a row may have in the TMEM and deep kernels
+constexpr int kDeepMaxK = 4;  // most sub-steps between exchanges
+constexpr int kDeepCnt = 3 + kDeepMaxK;
+template <typename T> int fv_deep_tmem_slots();          // computed slots a tile may have
+template <typename T> int fv_deep_row_words();           // words of one row image
+template <typename T> size_t fv_deep_smem_bytes(int slot_cap, int n_sub, int ocap);
+template <typename T> int fv_deep_tile_capacity(size_t smem);
+template <typename T> cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+// row images of the computed slots from the CSR matrices: slot i takes row
+// gid[i] with its off-diagonal entries' columns mapped to local slots lcol[i * 7 + j]
+template <typename T> void launch_build_deep_rows(const Dev<T>& d, const int32_t* gid, const int32_t* lcol,
+                                                  int64_t count, uint32_t* rows, cudaStream_t s);
 // tensor-memory FV kernel: rows with at most 7 off-diagonal entries, Dirichlet outer nodes
 template <typename T> size_t fv_tmem_smem_bytes(int tile_cap, int halo_cap, int n_sub, int ocap);
 template <typename T> int fv_tmem_tile_capacity(size_t smem);

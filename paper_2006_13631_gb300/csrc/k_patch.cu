@@ -909,7 +909,6 @@ template <typename T>
 constexpr int kTmemSlotWords = sizeof(T) == 4 ? 32 : 64;
 template <typename T>
 constexpr int kTmemCols = kSlots<T> * kTmemSlotWords<T>;
-constexpr int kTmemMaxEntries = 7;  // off-diagonal entries a row may have in this kernel
 static_assert(1024 / 32 / 4 * kTmemCols<float> == 512, "TMEM columns (FP32)");
 static_assert(512 / 32 / 4 * kTmemCols<double> <= 512, "TMEM columns (FP64)");
 
@@ -1314,6 +1313,455 @@ cudaError_t launch_fv_tmem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
                                        s);
 }
 
+// ---------------------------------------------------------------------------
+// Deep tiles: the FV sub-steps with one exchange between tiles every K
+// sub-steps (temporal blocking).  A tile holds, as local "slots", its own
+// nodes and K layers of ghost nodes around them: layer j holds the nodes
+// that the updates of layer j-1 read and that are not in earlier layers
+// (outer nodes read nothing).  Sub-step s of a block of K recomputes the
+// own nodes and ghost layers 1 .. K-1-s from the tile's own data, so the
+// tile needs its neighbours' records only once per block: the own nodes
+// other tiles hold as ghosts are written to the global record buffer at the
+// end of a block, the tile releases its progress counter, and at the start
+// of the next block each tile fetches its ghost layers after acquiring its
+// neighbour tiles' counters.  Meanwhile the threads update the own nodes
+// whose rows read only own nodes (slots [0, n_a)); then one block barrier
+// per sub-step.  The arithmetic of a node is that of the other FV kernels
+// (fv_acc_*, same entry order), so the results are the same bit for bit.
+//
+// Slots: own nodes (those reading only own nodes first), then the ghost
+// layers in order.  Records of all slots are double-buffered in shared
+// memory; the FV rows of the computed slots live in tensor memory, one row
+// image per slot (header cP, ne, then per off-diagonal entry gx, gy, C and
+// the local slot of the column; FP64 values take two words).  Slot x is
+// updated by thread x % kDeepThreads, which reads its row image from its
+// own TMEM lane.
+constexpr int kDeepThreads = 512;
+template <typename T>
+constexpr int kDeepSlotWords = sizeof(T) == 4 ? 32 : 64;  // TMEM columns of one slot
+template <typename T>
+constexpr int kDeepGroups = 128 * (512 / kDeepSlotWords<T>) / kDeepThreads;  // slots per thread
+template <typename T>
+constexpr int kDeepHalf = kDeepSlotWords<T> / 2;  // words per tcgen05.ld of a row
+template <typename T>
+constexpr int kDeepEntryWords = sizeof(T) == 4 ? 4 : 8;
+static_assert(kDeepGroups<float> == 4 && kDeepGroups<double> == 2, "TMEM slots per thread");
+static_assert(1 + kTmemMaxEntries <= 8, "row image: header and 7 entries");
+
+template <typename T>
+int fv_deep_tmem_slots() {
+    return kDeepGroups<T> * kDeepThreads;
+}
+template <typename T>
+int fv_deep_row_words() {
+    return kDeepSlotWords<T>;
+}
+
+struct DeepSmem {
+    size_t buf0, buf1, uv, osnap, gid, kind, send, omap, total;
+};
+
+template <typename T>
+__host__ __device__ inline DeepSmem deep_smem_layout(int cap, int n_sub, int ocap) {
+    auto up = [](size_t x) { return (x + 15) / 16 * 16; };
+    DeepSmem L;
+    size_t o = 0;
+    L.buf0 = o;
+    o = up(o + sizeof(T) * kSR * (size_t)cap);
+    L.buf1 = o;
+    o = up(o + sizeof(T) * kSR * (size_t)cap);
+    L.uv = o;
+    o = up(o + sizeof(T) * 2 * (size_t)n_sub);
+    L.osnap = o;
+    o = up(o + sizeof(T) * kSnap * (size_t)ocap);
+    L.gid = o;
+    o = up(o + sizeof(int32_t) * (size_t)cap);
+    L.kind = o;
+    o = up(o + (size_t)cap);
+    L.send = o;
+    o = up(o + (size_t)cap);
+    L.omap = o;
+    o = up(o + sizeof(int16_t) * (size_t)cap);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+size_t fv_deep_smem_bytes(int slot_cap, int n_sub, int ocap) {
+    return deep_smem_layout<T>(slot_cap, n_sub, ocap).total;
+}
+
+// 16 or 32 words of this thread's TMEM lane, complete on return
+template <int N>
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, uint32_t (&v)[N]) {
+    if constexpr (N == 16) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr)
+            : "memory");
+    } else {
+        static_assert(N == 32, "x16 or x32");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+    }
+}
+
+// entry (gx, gy, C, column) at word w of a row image half
+template <typename T, int N>
+__device__ __forceinline__ void deep_entry(const uint32_t (&v)[N], int w, T& gx, T& gy, T& c, int& col) {
+    if constexpr (sizeof(T) == 4) {
+        gx = __uint_as_float(v[w]);
+        gy = __uint_as_float(v[w + 1]);
+        c = __uint_as_float(v[w + 2]);
+        col = (int)v[w + 3];
+    } else {
+        gx = from_words<T>(v[w], v[w + 1]);
+        gy = from_words<T>(v[w + 2], v[w + 3]);
+        c = from_words<T>(v[w + 4], v[w + 5]);
+        col = (int)v[w + 6];
+    }
+}
+
+// The update of slot x (warp-uniform call: lanes with valid = false take
+// part in the TMEM loads only), written into the next record buffer and,
+// when out is set, into the global record of its node.  Both halves of the
+// row image are loaded by every lane of the warp at points where the warp
+// is converged (tcgen05.ld is .sync.aligned); only the arithmetic between
+// them is predicated.
+template <typename T>
+__device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* sm, const DeepSmem& L, const T* cur,
+                                          T* nxt, uint32_t tslot, bool valid, int x, int m, T* gout, bool out) {
+    constexpr int H = kDeepHalf<T>, EW = kDeepEntryWords<T>;
+    constexpr int E0 = H / EW - 1;  // entries in the first half (after the header)
+    uint32_t v[H];
+    tmem_ldn<H>(tslot, v);
+    const int8_t kind = valid ? reinterpret_cast<const int8_t*>(sm + L.kind)[x] : (int8_t)HLBM_NODE_OUTER;
+    const T cP = sizeof(T) == 4 ? from_words<T>(v[0], 0) : from_words<T>(v[0], v[1]);
+    const int ne = kind != HLBM_NODE_OUTER ? (int)v[sizeof(T) == 4 ? 1 : 2] : 0;
+    FvAcc<T> acc;
+    fv_acc_init(acc);
+#pragma unroll
+    for (int j = 0; j < E0; ++j) {
+        if (j < ne) {
+            T gx, gy, c;
+            int col;
+            deep_entry<T, H>(v, EW * (j + 1), gx, gy, c, col);
+            T f[9], z[3];
+            read_rec12(cur + (size_t)kSR * col, f, z);
+            fv_acc_entry(acc, gx, gy, c, f, z);
+        }
+    }
+    __syncwarp();
+    tmem_ldn<H>(tslot + H, v);  // entries E0 .. 6
+#pragma unroll
+    for (int j = E0; j < kTmemMaxEntries; ++j) {
+        if (j < ne) {
+            T gx, gy, c;
+            int col;
+            deep_entry<T, H>(v, EW * (j - E0), gx, gy, c, col);
+            T f[9], z[3];
+            read_rec12(cur + (size_t)kSR * col, f, z);
+            fv_acc_entry(acc, gx, gy, c, f, z);
+        }
+    }
+    if (!valid) return;
+    T fn[9];
+    if (kind == HLBM_NODE_OUTER) {
+        const int q = reinterpret_cast<const int16_t*>(sm + L.omap)[x];
+        fv_outer_from(d, reinterpret_cast<const T*>(sm + L.osnap) + kSnap * q, 1, m, fn);
+    } else {
+        T fP[9], zP[3];
+        read_rec12(cur + (size_t)kSR * x, fP, zP);
+        fv_acc_finish(d, acc, cP, fP, zP, fn);
+        if (kind == HLBM_NODE_WALL) {
+            const T* uv = reinterpret_cast<const T*>(sm + L.uv);
+            fv_wall(d, uv[m], uv[d.n_sub + m], fn);
+        }
+    }
+    T z[3];
+    z_of(fn, d.rho0, z);
+    T* o = nxt + (size_t)kSR * x;
+    st4(o, fn[0], fn[1], fn[2], fn[3]);
+    st4(o + 4, fn[4], fn[5], fn[6], fn[7]);
+    st4(o + 8, fn[8], z[0], z[1], z[2]);
+    if (out) {
+        T* rec = gout + (int64_t)kRec * reinterpret_cast<const int32_t*>(sm + L.gid)[x];
+        st4(rec, fn[0], fn[1], fn[2], fn[3]);
+        st4(rec + 4, fn[4], fn[5], fn[6], fn[7]);
+        st4(rec + 8, fn[8], z[0], z[1], z[2]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDeepThreads, 1) k_fv_deep(Dev<T> d, StepArgs a, T* g0, T* g1) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int abort_sh;
+    __shared__ uint32_t tmem_base_sh;
+    constexpr int NT = kDeepThreads, G = kDeepGroups<T>, SW = kDeepSlotWords<T>;
+    const int tile = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+    const int s0 = d.deep_ptr[tile];
+    const int32_t* cnt = d.deep_cnt + kDeepCnt * tile;
+    const int n_a = cnt[0], n_own = cnt[1], n_slot = cnt[2];
+    const int K = d.deep_k;
+    const DeepSmem L = deep_smem_layout<T>(d.deep_slot_cap, d.n_sub, d.deep_ocap);
+    T* buf0 = reinterpret_cast<T*>(sm + L.buf0);
+    T* buf1 = reinterpret_cast<T*>(sm + L.buf1);
+    T* uv = reinterpret_cast<T*>(sm + L.uv);
+    int32_t* gid = reinterpret_cast<int32_t*>(sm + L.gid);
+    int8_t* kd = reinterpret_cast<int8_t*>(sm + L.kind);
+    int8_t* sd = reinterpret_cast<int8_t*>(sm + L.send);
+    int16_t* om = reinterpret_cast<int16_t*>(sm + L.omap);
+    // ---- tensor memory: all 512 columns; warp w reads lanes 32 (w % 4) ..
+    // and, for its slot group j, the columns SW (j NT / 128 + w / 4) ..
+    if (warp == 0) tmem_alloc_512(&tmem_base_sh);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tbase = tmem_base_sh;
+    auto tslot_of = [&](int j) {
+        return tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(SW * (j * (NT / 128) + (warp >> 2)));
+    };
+    // ---- set-up: wall velocity per sub-step, slot tables, records of every
+    // slot at sub-step 0, the outer nodes' feed, the row images
+    for (int m = tid; m < d.n_sub; m += NT) wall_velocity(d, a, m, uv[m], uv[d.n_sub + m]);
+    for (int x = tid; x < n_slot; x += NT) {
+        const int g = d.deep_gid[s0 + x];
+        gid[x] = g;
+        kd[x] = d.kind[g];
+        sd[x] = d.deep_send[s0 + x];
+        om[x] = -1;
+    }
+    __syncthreads();
+    for (int x = tid; x < 3 * n_slot; x += NT) {
+        const int sl = x / 3, c = x - 3 * sl;
+        const Vec4<T> v = ld4(g0 + (int64_t)kRec * gid[sl] + 4 * c);
+        st4(buf0 + (size_t)kSR * sl + 4 * c, v.x, v.y, v.z, v.w);
+    }
+    {
+        const int o0 = d.deep_optr[tile], on = d.deep_optr[tile + 1] - o0;
+        T* osn = reinterpret_cast<T*>(sm + L.osnap);
+        for (int q = tid; q < on; q += NT) om[d.deep_oslot[o0 + q]] = (int16_t)q;
+        const int64_t no = d.n_outer;
+        for (int x = tid; x < kSnap * on; x += NT) {
+            const int q = x / kSnap, j = x - kSnap * q;
+            osn[x] = d.snap[j * no + d.outer_of[gid[d.deep_oslot[o0 + q]]]];
+        }
+        // row images of the computed slots (lanes without one store zeros)
+        const int n_comp = cnt[3];
+        const uint4* rows = reinterpret_cast<const uint4*>(d.deep_rows) + (int64_t)(SW / 4) * d.deep_rptr[tile];
+#pragma unroll 1
+        for (int j = 0; j < G; ++j) {
+            const int x = j * NT + tid;
+            const bool have = x < n_comp;
+            const uint32_t ts = tslot_of(j);
+#pragma unroll 1
+            for (int w4 = 0; w4 < SW / 4; ++w4) {
+                uint4 u = make_uint4(0u, 0u, 0u, 0u);
+                if (have) u = rows[(int64_t)(SW / 4) * x + w4];
+                tmem_st4(ts + 4 * w4, u.x, u.y, u.z, u.w);
+            }
+        }
+        tmem_wait_st();
+    }
+    if (tid == 0) abort_sh = 0;
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned long long base = (unsigned long long)a.t * (unsigned long long)d.n_sub;
+    const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
+    int m = 0;
+    bool aborted = false;
+    for (int b = 0; m < d.n_sub && !aborted; ++b) {
+        const int kb = min(K, d.n_sub - m);
+        const bool final_block = (m + kb == d.n_sub);
+        T* gout = (b & 1) ? g0 : g1;  // the state at the end of block b is exchange b + 1
+        for (int s = 0; s < kb; ++s, ++m) {
+            T* cur = (m & 1) ? buf1 : buf0;
+            T* nxt = (m & 1) ? buf0 : buf1;
+            const bool last = (s == kb - 1);
+            const int cs = cnt[3 + s];
+            int lo = 0;
+            if (s == 0 && b > 0) {
+                // own nodes that read only own nodes, while warp 0 waits for
+                // the neighbour tiles' exchange b and copies the ghost layers
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const int x = j * NT + tid;
+                    const bool v = x < n_a;
+                    if (__any_sync(0xffffffffu, v))
+                        deep_node(d, sm, L, cur, nxt, tslot_of(j), v, x, m, gout, false);
+                }
+                if (warp == 0) {
+                    bool ok = true;
+                    for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
+                        const unsigned long long* pc = d.progress + d.tile_nb[e];
+                        long spins = 0;
+                        while (ld_acquire(pc) < base + m) {
+                            if (*(volatile unsigned*)d.abort_flag) {
+                                ok = false;
+                                break;
+                            }
+                            if (++spins > d.spin_limit) {
+                                atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
+                                atomicExch(d.abort_flag, 1u);
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                    }
+                    __syncwarp();
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (ok) {
+                        const T* gin = (b & 1) ? g1 : g0;
+                        constexpr int kChunks = kSR * (int)sizeof(T) / 16;
+                        for (int x = tid; x < kChunks * (n_slot - n_own); x += 32) {
+                            const int hs = x / kChunks, c = x - kChunks * hs;
+                            const int sl = n_own + hs;
+                            cp_async16(reinterpret_cast<unsigned char*>(cur + (size_t)kSR * sl) + 16 * c,
+                                       reinterpret_cast<const unsigned char*>(gin + (int64_t)kRec * gid[sl]) + 16 * c);
+                        }
+                    }
+                    cp_async_wait_all();
+                    if (tid == 0 && !ok) abort_sh = 1;
+                }
+                __syncthreads();
+                if (abort_sh) {
+                    aborted = true;
+                    break;
+                }
+                // a block of one sub-step ends here: the records of those nodes go
+                // to the exchange buffer only now, after the neighbours' counters
+                // were acquired (a neighbour may still have been reading that
+                // buffer's previous contents, two exchanges back, before)
+                if (last) {
+                    for (int x = tid; x < n_a; x += NT) {
+                        if (!final_block && !sd[x]) continue;
+                        const T* r = nxt + (size_t)kSR * x;
+                        T* rec = gout + (int64_t)kRec * gid[x];
+                        const Vec4<T> a0 = ld4(r), a1 = ld4(r + 4), a2 = ld4(r + 8);
+                        st4(rec, a0.x, a0.y, a0.z, a0.w);
+                        st4(rec + 4, a1.x, a1.y, a1.z, a1.w);
+                        st4(rec + 8, a2.x, a2.y, a2.z, a2.w);
+                    }
+                }
+                lo = n_a;
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int x = j * NT + tid;
+                const bool v = x >= lo && x < cs;
+                if (__any_sync(0xffffffffu, v))
+                    deep_node(d, sm, L, cur, nxt, tslot_of(j), v, x, m, gout,
+                              last && x < n_own && (final_block || sd[x]));
+            }
+            __syncthreads();
+        }
+        if (!aborted && !final_block && tid == 0 && tile != d.stall_tile) {
+            __threadfence();
+            st_release(d.progress + tile, base + m);
+        }
+    }
+    // ---- release TMEM (also after an abort: every warp is past its last tcgen05.ld)
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 0) tmem_dealloc_512(tbase);
+}
+
+template <typename T>
+int fv_deep_tile_capacity(size_t smem) {
+    if (smem == 0) return 0;
+    int dev = 0, sms = 0, per = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, (const void*)k_fv_deep<T>) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int limit = maxsm - (int)fa.sharedSizeBytes;
+    if (smem > (size_t)limit) return 0;
+    if (cudaFuncSetAttribute((const void*)k_fv_deep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    // each block allocates all 512 TMEM columns: only one block per SM
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_fv_deep<T>, kDeepThreads, smem);
+    return per == 1 ? sms : 0;
+}
+
+template <typename T>
+cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
+    Dev<T> dd = d;
+    StepArgs aa = a;
+    T* b0 = (T*)d.fu_in;
+    T* b1 = d.fu_out;
+    void* args[] = {&dd, &aa, &b0, &b1};
+    const size_t smem = fv_deep_smem_bytes<T>(d.deep_slot_cap, d.n_sub, d.deep_ocap);
+    return cudaLaunchCooperativeKernel((const void*)k_fv_deep<T>, dim3(d.n_tiles), dim3(kDeepThreads), args, smem, s);
+}
+
+// Row image of computed slot i: header (C_PP, entry count), then the
+// off-diagonal entries of row gid[i] in row order with their local columns.
+template <typename T>
+__global__ void k_build_deep_rows(Dev<T> d, const int32_t* gid, const int32_t* lcol, int64_t count,
+                                  uint32_t* rows) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    constexpr int SW = kDeepSlotWords<T>, EW = kDeepEntryWords<T>;
+    uint32_t* r = rows + (int64_t)SW * i;
+    for (int w = 0; w < SW; ++w) r[w] = 0u;
+    const int P = gid[i];
+    const int r0 = d.row_ptr[P], ne = d.row_ptr[P + 1] - r0 - 1;
+    const T cP = d.coef[r0].c;
+    r[0] = lo_word(cP);
+    if constexpr (sizeof(T) == 4) {
+        r[1] = (uint32_t)ne;
+    } else {
+        r[1] = hi_word(cP);
+        r[2] = (uint32_t)ne;
+    }
+    for (int j = 0; j < ne && j < kTmemMaxEntries; ++j) {
+        const Coef<T> c = d.coef[r0 + 1 + j];
+        uint32_t* e = r + EW * (j + 1);
+        e[0] = lo_word(c.gx);
+        if constexpr (sizeof(T) == 4) {
+            e[1] = lo_word(c.gy);
+            e[2] = lo_word(c.c);
+            e[3] = (uint32_t)lcol[(int64_t)kTmemMaxEntries * i + j];
+        } else {
+            e[1] = hi_word(c.gx);
+            e[2] = lo_word(c.gy);
+            e[3] = hi_word(c.gy);
+            e[4] = lo_word(c.c);
+            e[5] = hi_word(c.c);
+            e[6] = (uint32_t)lcol[(int64_t)kTmemMaxEntries * i + j];
+        }
+    }
+}
+
+template <typename T>
+void launch_build_deep_rows(const Dev<T>& d, const int32_t* gid, const int32_t* lcol, int64_t count, uint32_t* rows,
+                            cudaStream_t s) {
+    if (count > 0) k_build_deep_rows<T><<<(unsigned)((count + 127) / 128), 128, 0, s>>>(d, gid, lcol, count, rows);
+}
+
 // ELL copy of the FV matrices for the shared-memory kernel: entry i takes
 // CSR entry src[i] with tile-local column col[i] (src -1: padding, zero)
 template <typename T>
@@ -1541,6 +1989,13 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
     template int fv_tmem_tile_capacity<T>(size_t);                                                            \
     template cudaError_t launch_fv_tmem<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
     template cudaError_t launch_fv_tmem_pack<T>(const FvPack<T>&, int, size_t, cudaStream_t);                 \
+    template int fv_deep_tmem_slots<T>();                                                                     \
+    template int fv_deep_row_words<T>();                                                                      \
+    template size_t fv_deep_smem_bytes<T>(int, int, int);                                                     \
+    template int fv_deep_tile_capacity<T>(size_t);                                                            \
+    template cudaError_t launch_fv_deep<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
+    template void launch_build_deep_rows<T>(const Dev<T>&, const int32_t*, const int32_t*, int64_t, uint32_t*, \
+                                            cudaStream_t);                                                    \
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \
     template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);
 HLBM_INST(float)

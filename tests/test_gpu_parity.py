@@ -229,28 +229,50 @@ def test_zero_disturbance_with_full_outer_node_update():
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_fv_kernels_agree_bit_for_bit(dtype):
-    """The three FV kernels (global-memory records, shared-memory tiles updated
-    in place, tensor-memory rows with double-buffered records) run the same
-    per-node arithmetic in the same order, so their fields agree exactly."""
-    from paper_2006_13631_gb300 import Solver
+    """The FV kernels (global-memory records, shared-memory tiles updated in
+    place, tensor-memory rows with double-buffered records, and deep tiles
+    that exchange with their neighbours every K sub-steps and recompute K
+    ghost layers in between) run the same per-node arithmetic in the same
+    order, so their fields agree exactly, whatever K.  n = 24 and 27
+    sub-steps give even and odd numbers of exchanges per step and a short
+    last block."""
+    from paper_2006_13631_gb300 import Solver, hlbm_set_fv_depth
 
     w = inputs.workload("lamina-small-" + dtype)
     mesh, rho = w.mesh(), w.rho_init()
-    got = {}
-    for kern in (1, 2, 3):
-        w.fv_kernel = kern
+    for n_sub in (24, 27):
+        w.n_sub = n_sub
+        got = {}
+        for kern in (1, 2, 3, 4):
+            w.fv_kernel = kern
+            s = Solver(w, mesh=mesh, rho_init=rho)
+            assert s.info()["fv_kernel"] == kern
+            s.step(40)
+            assert s.status == 0
+            got[kern] = tuple(s.fields()) + (s.patch_f(), s.force()[1])
+            s.close()
+        w.fv_kernel = 0
         s = Solver(w, mesh=mesh, rho_init=rho)
-        assert s.info()["fv_kernel"] == kern
-        s.step(40)
-        assert s.status == 0
-        got[kern] = tuple(s.fields()) + (s.patch_f(), s.force()[1])
+        info = s.info()
+        assert info["fv_kernel"] == 3  # the tensor-memory kernel is the default where it applies
         s.close()
-    w.fv_kernel = 0
-    s = Solver(w, mesh=mesh, rho_init=rho)
-    assert s.info()["fv_kernel"] == 3  # the tensor-memory kernel is the default where it applies
-    for kern in (2, 3):
-        for a, b in zip(got[1], got[kern]):
-            assert np.array_equal(a, b), kern
+        for kern in (2, 3, 4):
+            for a, b in zip(got[1], got[kern]):
+                assert np.array_equal(a, b), (n_sub, kern)
+        # every exchange interval, changed between steps (the tiles are rebuilt)
+        w.fv_kernel = 4
+        s = Solver(w, mesh=mesh, rho_init=rho)
+        for depth in (1, 2, 4, 3, 2, 1, 4, 3):
+            hlbm_set_fv_depth(s.h, depth)
+            # the largest interval up to the one asked for that fits (FP64 records
+            # take twice the shared memory)
+            got_depth = s.info()["fv_depth"]
+            assert got_depth == depth or (dtype == "f64" and 1 <= got_depth < depth)
+            s.step(5)
+        assert s.status == 0
+        for a, b in zip(got[1], tuple(s.fields()) + (s.patch_f(), s.force()[1])):
+            assert np.array_equal(a, b), (n_sub, "depths")
+        s.close()
 
 
 def _induced(dtype):
