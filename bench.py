@@ -116,7 +116,8 @@ def run_reference(args):
     w = inputs.workload(args.workload)
     mesh = w.mesh()
     rho = w.rho_init()
-    o = oracle.Oracle(w, mesh=mesh, rho_init=rho)
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(w, mesh=mesh, rho_init=rho, openmp=True)
     warm = min(args.warmup, 1)
     o.step(warm)
     # bounded sample: as many of the K requested steps as fit in ~60 s of CPU work
@@ -133,31 +134,56 @@ def run_reference(args):
     units = (n_disc + mesh.n_nodes) * steps
     value = units / secs / 1e6
     sample = (f"{steps} of {args.steps} requested lattice steps of {w.name} after {warm} warm-up, "
-              f"serial FP64 oracle (one host thread)")
+              f"FP64 oracle with OpenMP over its node loops on {cores} host threads")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "lattice": f"{w.nx}x{w.ny}", "patch_nodes": mesh.n_nodes,
                        "n_sub": w.n_sub},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(workload):
+    """The oracle timed on the host: its OpenMP build on every host core
+    (the same source with its node loops in parallel; identical results),
+    two lattice steps of the workload from the initial state."""
     import inputs
     import oracle
 
+    cores = os.cpu_count() or 1
     w = inputs.workload(workload)
     mesh = w.mesh()
-    o = oracle.Oracle(w, mesh=mesh)
+    o = oracle.Oracle(w, mesh=mesh, openmp=True)
     t0 = time.perf_counter()
     o.step(2)
     secs = time.perf_counter() - t0
     n_disc = int((o.struct_class() == oracle.DISC).sum())
-    return {"value": (n_disc + mesh.n_nodes) * 2 / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"2 lattice steps of {w.name} from the initial state, serial FP64 oracle"}
+    return {"value": (n_disc + mesh.n_nodes) * 2 / secs / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
+            "sample": f"2 lattice steps of {w.name} from the initial state, FP64 oracle with OpenMP over its node "
+                      f"loops on {cores} host threads"}
 
 
 # the source sections whose arithmetic and memory access define each
@@ -167,6 +193,10 @@ _KERNEL_SOURCES = {
                         "// ------------------------------------------------------------- readback"),
                        ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
                         "// ---------------------------------------------------------------- layout")],
+    "fv_deep": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
+                 "// ------------------------------------------------------------- force"),
+                ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
+                 "// ---------------------------------------------------------------- layout")],
     "fv_tmem": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
                  "// ------------------------------------------------------------- force"),
                 ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
@@ -202,10 +232,30 @@ def kernel_traffic(kernel, workload):
         return None
 
 
-# FP32 peak of plain (non-tensor) arithmetic: 152 SMs x 128 FP32 lanes x
-# 2 FLOP per FMA x 2.07 GHz maximum SM clock
-FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_ALU_TFLOPS = FP32_ALU_TFLOPS / 64
+def alu_peak_tflops(dtype, device=0):
+    """Peak of plain (non-tensor) arithmetic from the device's SM count and
+    its maximum SM clock (nvidia-smi clocks.max.sm, else the CUDA attribute):
+    SMs x 128 FP32 lanes x 2 FLOP per FMA x clock; FP64 at 1/64 of it on
+    this part.  Returns (TFLOP/s, how it was derived)."""
+    import torch
+
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={device}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except Exception:
+        mhz = None
+    if not mhz:
+        try:
+            mhz = torch.cuda.clock_rate(device)
+        except Exception:
+            mhz = 2070.0
+    fp32 = sms * 128 * 2 * mhz * 1e6 / 1e12
+    peak = fp32 if dtype == "f32" else fp32 / 64
+    return peak, f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz" + ("" if dtype == "f32" else " / 64")
 # algorithmic FLOP of one FV sub-step per CSR entry (row P, column k): for each
 # of the 9 directions a multiply-add of the streaming term S_ik f_k and one of
 # the collision term C_Pk (f - f^eq)_k
@@ -294,39 +344,61 @@ def run_ours(args):
     nnz = info["nnz"]
     fv_flop = FV_FLOP_PER_ENTRY * nnz * w.n_sub  # per launch (one lattice step)
     fv_tflops = fv_flop / (fv_ms / args.steps / 1e3) / 1e12 if fv_ms else None
-    alu_peak = FP32_ALU_TFLOPS if w.dtype == "f32" else FP64_ALU_TFLOPS
-    fv_kernel = {1: "k_fv_steps", 2: "k_fv_tiles", 3: "k_fv_tmem"}.get(info["fv_kernel"], "?")
+    alu_peak, alu_src = alu_peak_tflops(w.dtype, local)
+    fv_kernel = {1: "k_fv_steps", 2: "k_fv_tiles", 3: "k_fv_tmem", 4: "k_fv_deep"}.get(info["fv_kernel"], "?")
+    prof_key = {"k_fv_tmem": "fv_tmem", "k_fv_deep": "fv_deep"}.get(fv_kernel)
     roof = {"bound": "alu", "kernel": fv_kernel, "achieved": fv_tflops, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": fv_tflops / alu_peak if fv_tflops else None,
-            "traffic": kernel_traffic("fv_tmem", w.name) if fv_kernel == "k_fv_tmem" else None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+            "traffic": kernel_traffic(prof_key, w.name) if prof_key else None,
+            "peak_source": alu_src, "fv_depth": info.get("fv_depth"),
             "flop_per_launch": fv_flop, "ms_per_launch": fv_ms / args.steps, "dominant_phase": dom,
             "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases}}
     roof_stream = {"bound": "hbm", "kernel": "k_stream_collide", "achieved": stream_gbs, "peak": peak, "unit": "GB/s",
                    "frac": stream_gbs / peak if stream_gbs else None,
                    "traffic": kernel_traffic("stream_collide", w.name), "peak_source": peak_kind,
                    "bytes_per_launch": stream_bytes, "ms_per_launch": st_ms / args.steps if st_n else None}
+    # the whole step against HBM: algorithmic bytes per lattice step of the
+    # structured lattice (9 populations read + 9 written per discretization
+    # node), the patch (its records and FV rows read once per step, ~112 B
+    # per node at FP32) and relocation / donors / feed (~100 B per node),
+    # over the device time of a step
+    step_bytes = 18 * bytes_per * n_disc + (112 + 100) * (bytes_per // 4) * n_u
+    step_gbs = step_bytes / (ms / args.steps / 1e3) / 1e9
+    roof_step = {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s", "frac": step_gbs / peak,
+                 "bytes_per_step": step_bytes, "ms_per_step": ms / args.steps, "peak_source": peak_kind,
+                 "bytes_model": "18 x bytes per population x lattice discretization nodes + (112 + 100) B x patch "
+                                "nodes (FP32; doubled at FP64)"}
     launches = sum(v[1] for v in phases.values())
 
-    # end to end through the public API from host buffers
+    # end to end through the public API from host buffers: creation from
+    # pinned host arrays (timed on its own), then as many steps as the
+    # device-timed run, each with the host call and a force read-back to the
+    # host, wall-clock over the steps
     e2e = None
     if not args.no_e2e:
-        k_e2e = args.steps  # the device-timed run's step count, creation included
+        k_e2e = args.steps
         rho_pinned = torch.from_numpy(rho).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             s2 = Solver(w, mesh=mesh, rho_init=rho_pinned.numpy(), stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             for k in range(k_e2e):
                 H.hlbm_step(s2.h, 1)
                 H.hlbm_force(s2.h, k + 1, 1)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
             s2.close()
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
+        create_s, secs = t1 - t0, t2 - t1
         h2d = rho.nbytes + mesh.xy.nbytes + mesh.tri.nbytes + mesh.kind.nbytes
         e2e = {"value": world * (n_disc + n_u) * k_e2e / secs / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": h2d / k_e2e, "d2h_bytes_per_step": 16,
-               "note": f"{k_e2e} steps incl. creation from host arrays and a force read-back every step"}
+               "create_s": create_s,
+               "value_with_create": world * (n_disc + n_u) * k_e2e / (secs + create_s) / 1e6,
+               "note": f"{k_e2e} steps through hlbm_step(1) + hlbm_force (a 16-byte read-back) each, wall clock; "
+                       "creation from pinned host arrays timed apart (create_s); h2d counts the creation inputs "
+                       "spread over the steps"}
     s.close()
     # the same workload with the lattice populations stored as FP16 / BF16
     # deviations (FP32 arithmetic), each against the FP32 path above
@@ -401,7 +473,8 @@ def run_ours(args):
                        "lattice_disc_nodes": n_disc, "n_sub": w.n_sub, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (two lattice buffers of %.0f MB)"
                              % (9 * bytes_per * (w.nx * w.ny + sum(a * b for a, b, _, _ in w.levels)) / 1e6)},
-            "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "cpu_baseline": cpu, "e2e": e2e,
+            "mlups_subiter": mlups_subiter, "roofline": roof, "roofline_stream": roof_stream, "roofline_step": roof_step,
+            "cpu_baseline": cpu, "e2e": e2e,
             "reduced_storage": reduced or None, "variants": variants or None, "refined": refined, "sweep": sweep,
             "gradient": gradient,
             "gpu_launches": launches, "clocks": clocks, "status": status, "force_finite": finite}

@@ -142,9 +142,8 @@ typedef struct {
  * truncated control volume, with the starred values of the paper
  * (interpolated at interpolation nodes, the patch state elsewhere).
  * fv_kernel picks the kernel of the FV sub-steps, HLBM_FV_*: AUTO takes the
- * first that applies of TMEM (rows of at most 7 off-diagonal entries,
- * outer_fv = 0), SMEM and GLOBAL; DEEP (same rows) is chosen explicitly;
- * the others are for testing and
+ * first that applies of DEEP and TMEM (rows of at most 7 off-diagonal
+ * entries, outer_fv = 0), SMEM and GLOBAL; the others are for testing and
  * hlbm_create fails with HLBM_EINVAL when the one asked for cannot run the
  * patch.  All give the same results bit for bit. */
 typedef struct {
@@ -317,7 +316,7 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info);
  * records once every `depth` sub-steps instead of every sub-step; deeper
  * layers cost redundant work and shared memory.  The tiles are rebuilt
  * with the largest interval up to `depth` (1 .. HLBM_FV_MAX_DEPTH) that
- * fits on the device (default 3); the results do not change, bit for bit.
+ * fits on the device (default 2); the results do not change, bit for bit.
  * Synchronises the stream.  HLBM_EINVAL for another depth. */
 #define HLBM_FV_MAX_DEPTH 4
 int hlbm_set_fv_depth(hlbm_t* h, int32_t depth);

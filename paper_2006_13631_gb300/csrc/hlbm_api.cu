@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "hlbm_dev.cuh"
+#include "partition.h"
 
 using namespace hk;
 
@@ -42,12 +43,13 @@ struct hlbm {
     std::vector<int32_t> tri;
     std::vector<int8_t> kind;
     std::vector<int32_t> row_ptr, col, outer;
-    std::vector<int32_t> perm;  // internal node -> caller's node (Morton order)
+    std::vector<int32_t> perm;  // internal node -> caller's node (partition order, see create_impl)
+    std::vector<int32_t> part_start;  // the parts of that order (the default FV tiles)
     int n_tiles = 0;
     std::vector<void*> tile_blocks;  // device tables of the current FV tiling
     bool use_smem = false;      // a tile kernel (else the global-memory kernel)
     int fv_kind = HLBM_FV_GLOBAL;  // HLBM_FV_* in use
-    int fv_depth = 3;              // deep tiles: sub-steps between exchanges asked for (the largest that fits up to it)
+    int fv_depth = 2;              // deep tiles: sub-steps between exchanges asked for (the largest that fits up to it)
     double mxmin = 0, mxmax = 0, mymin = 0, mymax = 0;
     int nnz = 0, nseg = 0;
 
@@ -526,7 +528,7 @@ bool build_deep_tables(const hlbm* h, const std::vector<int32_t>& tile_start, co
             std::vector<int32_t> lay;
             for (int32_t q : prev)
                 reads(q, [&](int c) {
-                    if (loc[c] < 0) {
+                    if (loc[c] == -1) {  // not in the tile's slots yet, nor in this layer (-2)
                         loc[c] = -2;
                         lay.push_back(c);
                     }
@@ -617,7 +619,10 @@ int build_tiles(hlbm* h, int n_tiles_req, bool tmem_only = false) {
     int tile_cap = 0, halo_cap = 0;
     auto make_tiles = [&](int nt_) {
         tile_start.assign(nt_ + 1, 0);
-        for (int k = 0; k <= nt_; ++k) tile_start[k] = (int32_t)((int64_t)k * n / nt_);
+        if ((int)h->part_start.size() == nt_ + 1)
+            tile_start = h->part_start;  // the parts of the node order
+        else
+            for (int k = 0; k <= nt_; ++k) tile_start[k] = (int32_t)((int64_t)k * n / nt_);
         for (int k = 0; k < nt_; ++k)
             for (int q = tile_start[k]; q < tile_start[k + 1]; ++q) owner[q] = k;
         tile_nb_ptr.assign(nt_ + 1, 0);
@@ -664,7 +669,7 @@ int build_tiles(hlbm* h, int n_tiles_req, bool tmem_only = false) {
     // deep tiles: the deepest exchange interval up to fv_depth that fits
     DeepTables deep;
     bool deep_ok = false;
-    if (want == HLBM_FV_DEEP && max_row - 1 <= 7 && h->patch.outer_fv == 0) {
+    if ((want == HLBM_FV_AUTO || want == HLBM_FV_DEEP) && max_row - 1 <= 7 && h->patch.outer_fv == 0) {
         for (int K = std::min(h->fv_depth, kDeepMaxK); K >= 1 && !deep_ok; --K) {
             if (!build_deep_tables(h, tile_start, owner, K, fv_deep_tmem_slots<T>(), deep)) continue;
             deep_ok = deep.slot_cap < 65536 &&
@@ -866,9 +871,16 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     d.n = n;
     d.ntri = nt;
 
-    // --- renumber the nodes along a Morton curve of their positions so that
-    // contiguous node ranges (the FV tiles) are compact; triangles keep the
-    // caller's order (donor ties resolve to the lowest triangle index)
+    // --- renumber the nodes so that the default FV tiles (equal parts, one
+    // per SM) are compact in graph distance, which sets the size of their
+    // halos and ghost layers: recursive bisection of the mesh graph into
+    // that many parts, each node set split (in proportion to its parts) by
+    // the difference of its BFS distances from two far-apart nodes, so the
+    // cut runs across the set's longest extent and follows the mesh around
+    // the lamina (nodes on the two faces of the thin lamina are close in
+    // space but not in the graph); within a part, Morton order of the
+    // positions.  Triangles keep the caller's order (donor ties resolve to
+    // the lowest triangle index).
     {
         double hq = 0.0;
         for (int k = 0; k < nt; ++k) {
@@ -879,20 +891,22 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         hq = std::sqrt(hq / std::max(n, 1));
         double span = std::max(h->mxmax - h->mxmin, h->mymax - h->mymin);
         if (span / hq > 65000.0) hq = span / 65000.0;
-        std::vector<std::pair<uint64_t, int32_t>> key(n);
+        std::vector<uint64_t> mkey(n);
         for (int i = 0; i < n; ++i) {
             uint32_t ix = (uint32_t)((h->xy[2 * i] - h->mxmin) / hq), iy = (uint32_t)((h->xy[2 * i + 1] - h->mymin) / hq);
             uint64_t k = 0;
             for (int b = 0; b < 16; ++b) k |= (uint64_t)((ix >> b) & 1u) << (2 * b) | (uint64_t)((iy >> b) & 1u) << (2 * b + 1);
-            key[i] = {k, i};
+            mkey[i] = k;
         }
-        std::sort(key.begin(), key.end());
-        h->perm.resize(n);
+        int devi = 0, sms = 1;
+        cudaGetDevice(&devi);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devi);
+        const int parts = std::max(1, std::min(sms, (n + 63) / 64));
+        std::vector<int32_t> order;
+        partition_order(n, h->tri.data(), nt, mkey.data(), parts, order, h->part_start);
+        h->perm.assign(order.begin(), order.end());
         std::vector<int32_t> inv(n);
-        for (int p = 0; p < n; ++p) {
-            h->perm[p] = key[p].second;
-            inv[key[p].second] = p;
-        }
+        for (int p = 0; p < n; ++p) inv[h->perm[p]] = p;
         std::vector<double> xy2(2 * (size_t)n);
         std::vector<int8_t> kind2(n);
         for (int p = 0; p < n; ++p) {

@@ -1335,22 +1335,25 @@ cudaError_t launch_fv_tmem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 // image per slot (header cP, ne, then per off-diagonal entry gx, gy, C and
 // the local slot of the column; FP64 values take two words).  Slot x is
 // updated by thread x % kDeepThreads, which reads its row image from its
-// own TMEM lane.
-constexpr int kDeepThreads = 512;
+// own TMEM lane: FP32 runs 1024 threads of two slots and loads a row entry
+// by entry (64 registers), FP64 512 threads of two slots that load a row in
+// two halves.
+template <typename T>
+constexpr int kDeepThreads = sizeof(T) == 4 ? 1024 : 512;
 template <typename T>
 constexpr int kDeepSlotWords = sizeof(T) == 4 ? 32 : 64;  // TMEM columns of one slot
 template <typename T>
-constexpr int kDeepGroups = 128 * (512 / kDeepSlotWords<T>) / kDeepThreads;  // slots per thread
+constexpr int kDeepGroups = 128 * (512 / kDeepSlotWords<T>) / kDeepThreads<T>;  // slots per thread
 template <typename T>
 constexpr int kDeepHalf = kDeepSlotWords<T> / 2;  // words per tcgen05.ld of a row
 template <typename T>
 constexpr int kDeepEntryWords = sizeof(T) == 4 ? 4 : 8;
-static_assert(kDeepGroups<float> == 4 && kDeepGroups<double> == 2, "TMEM slots per thread");
+static_assert(kDeepGroups<float> == 2 && kDeepGroups<double> == 2, "TMEM slots per thread");
 static_assert(1 + kTmemMaxEntries <= 8, "row image: header and 7 entries");
 
 template <typename T>
 int fv_deep_tmem_slots() {
-    return kDeepGroups<T> * kDeepThreads;
+    return kDeepGroups<T> * kDeepThreads<T>;
 }
 template <typename T>
 int fv_deep_row_words() {
@@ -1444,37 +1447,59 @@ __device__ __forceinline__ void deep_entry(const uint32_t (&v)[N], int w, T& gx,
 template <typename T>
 __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* sm, const DeepSmem& L, const T* cur,
                                           T* nxt, uint32_t tslot, bool valid, int x, int m, T* gout, bool out) {
-    constexpr int H = kDeepHalf<T>, EW = kDeepEntryWords<T>;
-    constexpr int E0 = H / EW - 1;  // entries in the first half (after the header)
-    uint32_t v[H];
-    tmem_ldn<H>(tslot, v);
+    constexpr int EW = kDeepEntryWords<T>;
     const int8_t kind = valid ? reinterpret_cast<const int8_t*>(sm + L.kind)[x] : (int8_t)HLBM_NODE_OUTER;
-    const T cP = sizeof(T) == 4 ? from_words<T>(v[0], 0) : from_words<T>(v[0], v[1]);
-    const int ne = kind != HLBM_NODE_OUTER ? (int)v[sizeof(T) == 4 ? 1 : 2] : 0;
     FvAcc<T> acc;
     fv_acc_init(acc);
+    T cP;
+    if constexpr (sizeof(T) == 4) {
+        // header, then the entries one by one up to the warp's longest row
+        uint32_t hdr[4];
+        tmem_ld4(tslot, hdr);
+        cP = __uint_as_float(hdr[0]);
+        const int ne = kind != HLBM_NODE_OUTER ? (int)hdr[1] : 0;
+        const int nem = (int)__reduce_max_sync(0xffffffffu, (unsigned)ne);
 #pragma unroll
-    for (int j = 0; j < E0; ++j) {
-        if (j < ne) {
-            T gx, gy, c;
-            int col;
-            deep_entry<T, H>(v, EW * (j + 1), gx, gy, c, col);
-            T f[9], z[3];
-            read_rec12(cur + (size_t)kSR * col, f, z);
-            fv_acc_entry(acc, gx, gy, c, f, z);
+        for (int j = 0; j < kTmemMaxEntries; ++j) {
+            if (j >= nem) break;
+            uint32_t e[4];
+            tmem_ld4(tslot + EW * (j + 1), e);
+            if (j < ne) {
+                T f[9], z[3];
+                read_rec12(cur + (size_t)kSR * (int)e[3], f, z);
+                fv_acc_entry(acc, __uint_as_float(e[0]), __uint_as_float(e[1]), __uint_as_float(e[2]), f, z);
+            }
         }
-    }
-    __syncwarp();
-    tmem_ldn<H>(tslot + H, v);  // entries E0 .. 6
+    } else {
+        constexpr int H = kDeepHalf<T>;
+        constexpr int E0 = H / EW - 1;  // entries in the first half (after the header)
+        uint32_t v[H];
+        tmem_ldn<H>(tslot, v);
+        cP = from_words<T>(v[0], v[1]);
+        const int ne = kind != HLBM_NODE_OUTER ? (int)v[2] : 0;
 #pragma unroll
-    for (int j = E0; j < kTmemMaxEntries; ++j) {
-        if (j < ne) {
-            T gx, gy, c;
-            int col;
-            deep_entry<T, H>(v, EW * (j - E0), gx, gy, c, col);
-            T f[9], z[3];
-            read_rec12(cur + (size_t)kSR * col, f, z);
-            fv_acc_entry(acc, gx, gy, c, f, z);
+        for (int j = 0; j < E0; ++j) {
+            if (j < ne) {
+                T gx, gy, c;
+                int col;
+                deep_entry<T, H>(v, EW * (j + 1), gx, gy, c, col);
+                T f[9], z[3];
+                read_rec12(cur + (size_t)kSR * col, f, z);
+                fv_acc_entry(acc, gx, gy, c, f, z);
+            }
+        }
+        __syncwarp();
+        tmem_ldn<H>(tslot + H, v);  // entries E0 .. 6
+#pragma unroll
+        for (int j = E0; j < kTmemMaxEntries; ++j) {
+            if (j < ne) {
+                T gx, gy, c;
+                int col;
+                deep_entry<T, H>(v, EW * (j - E0), gx, gy, c, col);
+                T f[9], z[3];
+                read_rec12(cur + (size_t)kSR * col, f, z);
+                fv_acc_entry(acc, gx, gy, c, f, z);
+            }
         }
     }
     if (!valid) return;
@@ -1506,11 +1531,11 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kDeepThreads, 1) k_fv_deep(Dev<T> d, StepArgs a, T* g0, T* g1) {
+__global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepArgs a, T* g0, T* g1) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int abort_sh;
     __shared__ uint32_t tmem_base_sh;
-    constexpr int NT = kDeepThreads, G = kDeepGroups<T>, SW = kDeepSlotWords<T>;
+    constexpr int NT = kDeepThreads<T>, G = kDeepGroups<T>, SW = kDeepSlotWords<T>;
     const int tile = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
     const int s0 = d.deep_ptr[tile];
     const int32_t* cnt = d.deep_cnt + kDeepCnt * tile;
@@ -1702,7 +1727,7 @@ int fv_deep_tile_capacity(size_t smem) {
         return 0;
     }
     // each block allocates all 512 TMEM columns: only one block per SM
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_fv_deep<T>, kDeepThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_fv_deep<T>, kDeepThreads<T>, smem);
     return per == 1 ? sms : 0;
 }
 
@@ -1714,7 +1739,8 @@ cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
     T* b1 = d.fu_out;
     void* args[] = {&dd, &aa, &b0, &b1};
     const size_t smem = fv_deep_smem_bytes<T>(d.deep_slot_cap, d.n_sub, d.deep_ocap);
-    return cudaLaunchCooperativeKernel((const void*)k_fv_deep<T>, dim3(d.n_tiles), dim3(kDeepThreads), args, smem, s);
+    return cudaLaunchCooperativeKernel((const void*)k_fv_deep<T>, dim3(d.n_tiles), dim3(kDeepThreads<T>), args, smem,
+                                       s);
 }
 
 // Row image of computed slot i: header (C_PP, entry count), then the

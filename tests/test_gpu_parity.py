@@ -254,7 +254,7 @@ def test_fv_kernels_agree_bit_for_bit(dtype):
         w.fv_kernel = 0
         s = Solver(w, mesh=mesh, rho_init=rho)
         info = s.info()
-        assert info["fv_kernel"] == 3  # the tensor-memory kernel is the default where it applies
+        assert info["fv_kernel"] == 4 and info["fv_depth"] == 2  # the deep kernel is the default where it applies
         s.close()
         for kern in (2, 3, 4):
             for a, b in zip(got[1], got[kern]):
