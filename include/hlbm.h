@@ -391,6 +391,34 @@ int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, doub
                         const hlbm_motion_t* motion, int64_t nsteps, double discard_periods, double fit_periods,
                         double rel_step, void* cuda_stream, double* theta, double* grad, double* sweep_ms);
 
+/* Gradient of the hydrodynamic function by the adjoint (reverse mode) of the
+ * discrete hybrid step.  A solver is created from the inputs (as
+ * hlbm_create), stepped nsteps with its dynamic state checkpointed in
+ * device memory every checkpoint_every steps, and Theta is fitted over the
+ * steps [ceil(discard_periods T), floor((discard_periods + fit_periods) T)],
+ * T = 2 pi / omega (Sec. 2.1, eq. force_phasor).  For the objective
+ * L = w_re Re Theta + w_im Im Theta, the reverse sweep then visits the
+ * segments between checkpoints from the last to the first: each is stepped
+ * again from its checkpoint keeping what every step's reverse needs, and
+ * the steps are reversed one by one -- force, the n FV sub-steps of eq. ulbe
+ * (recomputed), the outer-node feed (eq. postcollision2_u), stream-collide
+ * (eq. LBE), the eq. postcollision2_s fill and the refill of Sec. 4 -- with
+ * every decision of the forward step held fixed (node classes, refill types,
+ * donor cells and triangles; Theta is smooth in the parameters between
+ * them).  theta[2] receives (Re, Im) Theta, grad[3] dL/dA, dL/domega,
+ * dL/dtau_s (A and omega through the positions y(t) = A sin(w t), the wall
+ * velocity and the fit; tau_s through 1/tau_s, 1/tau_u, and the interface
+ * factors 2 (tau_s - 1)/(2 tau_s - 1) and 1 - 1/(2 tau_s)).  fwd_ms and bwd_ms
+ * (may be NULL) receive the device time of the checkpointed forward run and
+ * of the reverse sweep.  HARMONIC motion, one lattice level, outer_fv = 0,
+ * FP64 or FP32 populations (adjoints in FP64).  Device memory: one lattice
+ * copy per checkpoint and per step of a segment, released before the call
+ * returns.  Errors as for hlbm_create (message: hlbm_last_error(NULL)). */
+int hlbm_theta_adjoint(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s, const hlbm_motion_t* motion,
+                       int64_t nsteps, double discard_periods, double fit_periods, double w_re, double w_im,
+                       int32_t checkpoint_every, void* cuda_stream, double* theta, double* grad, double* fwd_ms,
+                       double* bwd_ms);
+
 /* Least-squares fit F(t) = a sin(w t) + b cos(w t) over t = t0..t1 of the
  * samples F(t) = samples[t * stride] (DEVICE memory, caller-owned, at least
  * t1 * stride + 1 doubles), the fit hlbm_gamma performs, for callers that

@@ -211,6 +211,58 @@ def theta_fd_gradient(w, nsteps, discard=1.0, fit=3.0, rel_step=1e-4, mesh=None,
     return th[0], grad
 
 
+def theta_tangent(w, nsteps, discard=1.0, fit=3.0, rel_step=1e-6, mesh=None, rho_init=None):
+    """The FP64 tangent of Theta in (A, omega, tau_s) along the oracle's branch
+    of decisions: for each parameter, two oracle runs at -/+ rel_step of its
+    value, stepped in lockstep, must take the same decisions at every step
+    (lattice node classes and refill types; a donor triangle may differ only
+    where the moved node lies on an edge shared by both, where the
+    interpolated value is the same); Theta of each is fitted
+    over the base window as in theta_fd_gradient, and the central quotient is
+    then the derivative of the map the method is smooth on between decisions,
+    to O(rel_step^2) (at 1e-6 relative the truncation and FP64 rounding are
+    both far below 1e-6 of the result).  Raises ValueError when a decision
+    differs, naming the parameter and step.  Returns (grad [3] complex, the
+    number of node-steps whose donor triangles differed at such ties)."""
+    import copy
+
+    mesh = mesh if mesh is not None else w.mesh()
+    rho = rho_init if rho_init is not None else w.rho_init()
+    base = (w.A, w.omega, w.tau_s)
+    Tp = 2.0 * math.pi / w.omega
+    t0, t1 = int(math.ceil(discard * Tp)), int(math.floor((discard + fit) * Tp))
+    grad = []
+    ties = 0
+    for k, name in enumerate(("A", "omega", "tau_s")):
+        h = rel_step * abs(base[k])
+        runs = []
+        for sgn in (-1.0, 1.0):
+            v = copy.copy(w)
+            setattr(v, name, base[k] + sgn * h)
+            runs.append((v, Oracle(v, mesh=mesh, rho_init=rho)))
+        for t in range(nsteps):
+            for _, o in runs:
+                o.step(1)
+            (_, om), (_, op) = runs
+            if not np.array_equal(om.struct_class(), op.struct_class()):
+                raise ValueError(f"{name}: node classes differ at step {t + 1}")
+            tm, dm = om.refill_record()
+            tp, dp = op.refill_record()
+            if not np.array_equal(tm, tp):
+                raise ValueError(f"{name}: refill types differ at step {t + 1}")
+            # a node moved onto an edge may take either triangle: the linear
+            # interpolants agree there, so the value does not jump
+            ties += int((dm != dp).sum())
+        th = []
+        for v, o in runs:
+            _, fy = o.force()
+            a, b, _ = sine_fit(fy, t0, t1, v.omega)
+            N = 0.25 * math.pi * v.rho0 * v.omega ** 2 * v.L ** 2 * v.A
+            th.append(complex(a / N, b / N))
+        grad.append((th[1] - th[0]) / (2.0 * h))
+    return np.array(grad), ties
+
+
 def theta_semi_analytic(beta, eps):
     """eq. hydro_tot with eq. hydro_gamma and eq. hydro_delta (Sec. 2.1):
     Theta = 1.02 + 2.45 beta^-1/2 - i (2.49 beta^-1/2 + 0.879 beta^3/4 eps^2)."""

@@ -98,6 +98,8 @@ SIGNATURES = {
     "hlbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "hlbm_theta_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_double,
                                       C.c_double, C.c_double, C.c_void_p, _dp, _dp, _dp]),
+    "hlbm_theta_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_double,
+                                     C.c_double, C.c_double, C.c_double, C.c_int32, C.c_void_p, _dp, _dp, _dp, _dp]),
     "hlbm_last_error": (C.c_char_p, [C.c_void_p]),
     "hlbm_destroy": (None, [C.c_void_p]),
 }

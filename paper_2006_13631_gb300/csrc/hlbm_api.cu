@@ -1702,6 +1702,392 @@ int sweep_one_step(hlbm_sweep* w, bool time_fv) {
 
 }  // namespace
 
+// ---- adjoint of the hybrid step (reverse mode, decisions held fixed) -----
+namespace {
+
+// A solver's dynamic state at a step boundary, in device memory.
+struct AdjCkpt {
+    void* lat = nullptr;  // fbuf[fi]
+    void* sbox = nullptr; // sbox[si]
+    int8_t* cls = nullptr;
+    void* fu = nullptr;   // fu[ui]
+    int64_t t = 0;
+    double Xprev = 0, Yprev = 0;
+    int pbx0 = 0, pby0 = 0, ci = 0, si = 0, ui = 0, fi = 0;
+};
+
+// What the reverse of one step needs from its forward pass.
+template <typename T>
+struct AdjRec {
+    StepArgs a{};
+    T* P0 = nullptr;   // patch before the refill
+    T* Pm = nullptr;   // after it
+    T* lat = nullptr;  // lattice populations the stream-collide read (after the eq. 178 fill)
+    T* sbo = nullptr;  // window state at t (previous window)
+    T* sbn = nullptr;  // at t+1
+    int8_t* clp = nullptr;
+    int8_t* clc = nullptr;
+    int32_t* rt = nullptr;
+    int32_t* rd = nullptr;
+    T* snap = nullptr;
+};
+
+template <typename T>
+size_t adj_sizes(hlbm* h, size_t* lat, size_t* box, size_t* fu, size_t* cls) {
+    Dev<T>& d = dev_of<T>(h);
+    *lat = 9 * (size_t)d.plane * sizeof(T);
+    *box = 9 * (size_t)d.bplane * sizeof(T);
+    *fu = (size_t)kRec * d.n * sizeof(T);
+    *cls = (size_t)d.bplane;
+    return *lat;
+}
+
+template <typename T>
+int adj_snapshot(hlbm* h, AdjCkpt& c, bool restore) {
+    size_t lat, box, fu, cls;
+    adj_sizes<T>(h, &lat, &box, &fu, &cls);
+    cudaStream_t s = h->stream;
+    if (restore) {
+        h->t = c.t;
+        h->Xprev = c.Xprev;
+        h->Yprev = c.Yprev;
+        h->pbx0 = c.pbx0;
+        h->pby0 = c.pby0;
+        h->ci = c.ci;
+        h->si = c.si;
+        h->ui = c.ui;
+        h->fi = c.fi;
+    }
+    auto cp = [&](void* dst, const void* src, size_t n) { return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s); };
+    cudaError_t e;
+    if (restore) {
+        e = cp(h->fbuf[h->fi], c.lat, lat);
+        if (e == cudaSuccess) e = cp(h->sbox[h->si], c.sbox, box);
+        if (e == cudaSuccess) e = cp(h->cls[h->ci], c.cls, cls);
+        if (e == cudaSuccess) e = cp(h->fu[h->ui], c.fu, fu);
+        // the FV kernels count sub-steps from t * n_sub
+        Dev<T>& d = dev_of<T>(h);
+        std::vector<unsigned long long> prog(d.n_tiles, (unsigned long long)h->t * (unsigned long long)d.n_sub);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d.progress, prog.data(), prog.size() * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        bind(h, d);
+    } else {
+        c.t = h->t;
+        c.Xprev = h->Xprev;
+        c.Yprev = h->Yprev;
+        c.pbx0 = h->pbx0;
+        c.pby0 = h->pby0;
+        c.ci = h->ci;
+        c.si = h->si;
+        c.ui = h->ui;
+        c.fi = h->fi;
+        e = cp(c.lat, h->fbuf[h->fi], lat);
+        if (e == cudaSuccess) e = cp(c.sbox, h->sbox[h->si], box);
+        if (e == cudaSuccess) e = cp(c.cls, h->cls[h->ci], cls);
+        if (e == cudaSuccess) e = cp(c.fu, h->fu[h->ui], fu);
+    }
+    return cuda_check(h, e, "adjoint checkpoint");
+}
+
+// one forward step that keeps what its reverse needs
+template <typename T>
+int adj_forward_step(hlbm* h, AdjRec<T>& R) {
+    cudaStream_t s = h->stream;
+    Dev<T>& d = dev_of<T>(h);
+    size_t lat, box, fu, cls;
+    adj_sizes<T>(h, &lat, &box, &fu, &cls);
+    auto cp = [&](void* dst, const void* src, size_t n) { cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s); };
+    cp(R.P0, h->fu[h->ui], fu);
+    cp(R.sbo, h->sbox[h->si], box);
+    cp(R.clp, h->cls[h->ci], cls);
+    PendingStep ps{};
+    int rc = step_lattice<T>(h, s, ps);
+    if (rc != HLBM_OK) return rc;
+    R.a = ps.a;
+    cp(R.Pm, h->fu[h->ui], fu);
+    cp(R.lat, h->fbuf[h->fi], lat);
+    cp(R.sbn, h->sbox[1 - h->si], box);
+    cp(R.clc, h->cls[ps.ncls], cls);
+    cp(R.rt, d.rtype, (size_t)d.n * sizeof(int32_t));
+    cp(R.rd, d.rdonor, (size_t)d.n * sizeof(int32_t));
+    cp(R.snap, d.snap, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
+    rc = step_fv<T>(h, s, ps);
+    if (rc == HLBM_OK) rc = step_finish<T>(h, s, ps);
+    return rc;
+}
+
+// adjoint buffers: adjoints in the population type, parameter sums in FP64
+template <typename T>
+struct AdjBufs {
+    T *lfA, *lfB, *lSo, *lSn, *lPn, *lPm, *lP0, *psi, *x0, *x1, *lsnap;
+    double *par, *lY, *lV;
+    int32_t* tpos;
+};
+
+// reverse of step R.a.t; B.lPn holds the adjoint of the patch at t+1 on entry
+// and of the patch at t on exit, B.lfB / lfA and lSn / lSo likewise
+template <typename T>
+int adj_reverse_step(hlbm* h, const AdjRec<T>& R, AdjBufs<T>& B, T* sub, double lamF) {
+    cudaStream_t s = h->stream;
+    Dev<T> dd = dev_of<T>(h);
+    const int n = dd.n, ns = dd.n_sub;
+    const size_t rec = (size_t)kRec * n;
+    // the FV sub-steps again, every state kept
+    dd.snap = R.snap;
+    cudaMemcpyAsync(sub, R.Pm, rec * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    for (int m = 0; m < ns; ++m) launch_adj_fv_fwd<T>(dd, R.a, sub + m * rec, sub + (m + 1) * rec, m, s);
+    // force at t+1
+    if (lamF != 0.0) {
+        dd.fu_in = sub + ns * rec;
+        launch_adj_force<T>(dd, lamF, B.lPn, s);
+    }
+    // FV sub-steps, last to first
+    cudaMemsetAsync(B.lsnap, 0, (size_t)24 * std::max(dd.n_outer, 1) * sizeof(T), s);
+    const T* lnext = B.lPn;
+    for (int m = ns - 1; m >= 0; --m) {
+        T* lcur = (m & 1) ? B.x1 : B.x0;
+        launch_adj_fv_rev<T>(dd, R.a, sub + m * rec, m, lnext, B.psi, B.tpos, lcur, B.lsnap, B.par, B.lV, s);
+        lnext = lcur;
+    }
+    cudaMemcpyAsync(B.lPm, lnext, (size_t)9 * n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    // feed, stream-collide, eq. 178 fill, refill
+    dd.sbox_old = R.sbo;
+    dd.sbox_new = R.sbn;
+    dd.cls_prev = R.clp;
+    dd.cls_cur = R.clc;
+    cudaMemsetAsync(B.lSo, 0, (size_t)9 * dd.bplane * sizeof(T), s);
+    launch_adj_feed<T>(dd, R.a, B.lsnap, B.lSo, B.lSn, B.lY, s);
+    cudaMemsetAsync(B.lfA, 0, (size_t)9 * dd.plane * sizeof(T), s);
+    dd.fA = R.lat;
+    launch_adj_stream<T>(dd, R.a, B.lfB, B.lSn, B.lfA, B.par, s);
+    dd.fu_in = R.Pm;
+    launch_adj_fill<T>(dd, R.a, B.lfA, B.lPm, B.par, B.lY, s);
+    cudaMemsetAsync(B.lP0, 0, (size_t)9 * n * sizeof(T), s);
+    if (R.a.t > 0) {
+        dd.fu_in = R.P0;
+        dd.rtype = R.rt;
+        dd.rdonor = R.rd;
+        launch_adj_refill<T>(dd, R.a, B.lPm, B.lP0, B.lSo, B.par, B.lY, s);
+    }
+    std::swap(B.lPn, B.lP0);
+    std::swap(B.lfB, B.lfA);
+    std::swap(B.lSn, B.lSo);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HLBM_OK : cuda_check(h, e, "adjoint launch");
+}
+
+// The whole adjoint: forward with checkpoints, Theta, then segments of
+// `every` steps recomputed and reversed, last to first.
+template <typename T>
+int adjoint_impl(hlbm* h, int64_t nsteps, double discard, double fit, double w_re, double w_im, int every,
+                 double* theta, double* grad, double* fwd_ms, double* bwd_ms) {
+    const double PI = 3.14159265358979323846;
+    cudaStream_t s = h->stream;
+    Dev<T>& d = dev_of<T>(h);
+    const hlbm_motion_t& mo = h->motion;
+    const int n = d.n, ns = d.n_sub;
+    size_t lat, box, fu, cls;
+    adj_sizes<T>(h, &lat, &box, &fu, &cls);
+    // transposed row positions: row k's entry of column P -> row P's entry of column k
+    std::vector<int32_t> tpos(h->nnz, -1);
+    for (int k = 0; k < n; ++k)
+        for (int e = h->row_ptr[k] + 1; e < h->row_ptr[k + 1]; ++e) {
+            const int P = h->col[e];
+            for (int q = h->row_ptr[P] + 1; q < h->row_ptr[P + 1]; ++q)
+                if (h->col[q] == k) tpos[e] = q;
+            if (tpos[e] < 0) return fail(h, HLBM_EGEOM, "FV rows are not symmetric (node %d, %d)", k, P);
+        }
+    std::vector<void*> mine;
+    auto alloc = [&](size_t bytes) {
+        void* p = dev_alloc(h, bytes);
+        if (p) mine.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(s);
+        for (void* p : mine) dev_free(h, p);
+        mine.clear();
+    };
+    int rc = HLBM_OK;
+    const int64_t nseg = (nsteps + every - 1) / every;
+    std::vector<AdjCkpt> ck(nseg);
+    for (auto& c : ck) {
+        c.lat = alloc(lat);
+        c.sbox = alloc(box);
+        c.cls = (int8_t*)alloc(cls);
+        c.fu = alloc(fu);
+        if (!c.lat || !c.sbox || !c.cls || !c.fu) rc = fail(h, HLBM_ENOMEM, "adjoint checkpoints");
+    }
+    const size_t snapb = (size_t)24 * std::max(d.n_outer, 1) * sizeof(T);
+    std::vector<AdjRec<T>> recs(every);
+    for (auto& r : recs) {
+        r.P0 = (T*)alloc(fu);
+        r.Pm = (T*)alloc(fu);
+        r.lat = (T*)alloc(lat);
+        r.sbo = (T*)alloc(box);
+        r.sbn = (T*)alloc(box);
+        r.clp = (int8_t*)alloc(cls);
+        r.clc = (int8_t*)alloc(cls);
+        r.rt = (int32_t*)alloc((size_t)n * 4);
+        r.rd = (int32_t*)alloc((size_t)n * 4);
+        r.snap = (T*)alloc(snapb);
+        if (!r.P0 || !r.Pm || !r.lat || !r.sbo || !r.sbn || !r.clp || !r.clc || !r.rt || !r.rd || !r.snap)
+            rc = fail(h, HLBM_ENOMEM, "adjoint step records");
+    }
+    AdjBufs<T> B{};
+    const size_t z = sizeof(T);
+    B.lfA = (T*)alloc(9 * (size_t)d.plane * z);
+    B.lfB = (T*)alloc(9 * (size_t)d.plane * z);
+    B.lSo = (T*)alloc(9 * (size_t)d.bplane * z);
+    B.lSn = (T*)alloc(9 * (size_t)d.bplane * z);
+    B.lPn = (T*)alloc(9 * (size_t)n * z);
+    B.lPm = (T*)alloc(9 * (size_t)n * z);
+    B.lP0 = (T*)alloc(9 * (size_t)n * z);
+    B.psi = (T*)alloc(9 * (size_t)n * z);
+    B.x0 = (T*)alloc(9 * (size_t)n * z);
+    B.x1 = (T*)alloc(9 * (size_t)n * z);
+    B.lsnap = (T*)alloc(24 * (size_t)std::max(d.n_outer, 1) * z);
+    B.par = (double*)alloc(8 * 8);
+    B.lY = (double*)alloc((size_t)(nsteps + 2) * 8);
+    B.lV = (double*)alloc((size_t)(nsteps + 1) * ns * 8);
+    B.tpos = (int32_t*)alloc((size_t)std::max(h->nnz, 1) * 4);
+    T* sub = (T*)alloc((size_t)(ns + 1) * fu);
+    if (!B.lfA || !B.lfB || !B.lSo || !B.lSn || !B.lPn || !B.lPm || !B.lP0 || !B.psi || !B.x0 || !B.x1 ||
+        !B.lsnap || !B.par || !B.lY || !B.lV || !B.tpos || !sub)
+        rc = fail(h, HLBM_ENOMEM, "adjoint buffers");
+    if (rc != HLBM_OK) {
+        release();
+        return rc;
+    }
+    cudaMemcpyAsync(B.tpos, tpos.data(), tpos.size() * 4, cudaMemcpyHostToDevice, s);
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    // ---- forward, checkpoints every `every` steps
+    cudaEventRecord(e0, s);
+    for (int64_t t = 0; t < nsteps && rc == HLBM_OK; ++t) {
+        if (t % every == 0) rc = adj_snapshot<T>(h, ck[t / every], false);
+        if (rc == HLBM_OK) rc = step_impl<T>(h, 1);
+    }
+    cudaEventRecord(e1, s);
+    // ---- Theta and the adjoint of the force history (the fit, Sec. 2.1)
+    const double Tp = 2.0 * PI / mo.omega;
+    const int64_t t0 = (int64_t)std::ceil(discard * Tp), t1 = (int64_t)std::floor((discard + fit) * Tp);
+    if (rc == HLBM_OK && (t1 > nsteps || t1 <= t0 || t0 < 0))
+        rc = fail(h, HLBM_EINVAL, "fit window [%lld, %lld] is not inside the %lld steps", (long long)t0,
+                  (long long)t1, (long long)nsteps);
+    std::vector<double> F(2 * (size_t)(nsteps + 1));
+    if (rc == HLBM_OK) {
+        cudaError_t e = cudaMemcpyAsync(F.data(), h->force, F.size() * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_check(h, e, "force history");
+    }
+    if (rc == HLBM_OK) {
+        unsigned st = 0;
+        rc = sync_status(h, &st);
+        if (rc == HLBM_OK) rc = status_error(h, st);
+    }
+    std::vector<double> lamF(nsteps + 1, 0.0);
+    double gA = 0, gW = 0, gT = 0;
+    if (rc == HLBM_OK) {
+        const double om = mo.omega, A = mo.A;
+        const double N = 0.25 * PI * h->grid.rho0 * om * om * h->patch.lamina_L * h->patch.lamina_L * A;
+        double M00 = 0, M01 = 0, M11 = 0, r0 = 0, r1 = 0;
+        double dM00 = 0, dM01 = 0, dM11 = 0, dr0 = 0, dr1 = 0;  // d/domega
+        for (int64_t t = t0; t <= t1; ++t) {
+            const double sn = std::sin(om * t), cs = std::cos(om * t), Fy = F[2 * t + 1], tt = (double)t;
+            M00 += sn * sn;
+            M01 += sn * cs;
+            M11 += cs * cs;
+            r0 += Fy * sn;
+            r1 += Fy * cs;
+            dM00 += 2 * sn * cs * tt;
+            dM01 += (cs * cs - sn * sn) * tt;
+            dM11 += -2 * sn * cs * tt;
+            dr0 += Fy * cs * tt;
+            dr1 += -Fy * sn * tt;
+        }
+        const double det = M00 * M11 - M01 * M01;
+        const double a = (r0 * M11 - r1 * M01) / det, b = (r1 * M00 - r0 * M01) / det;
+        theta[0] = a / N;
+        theta[1] = b / N;
+        const double J = w_re * theta[0] + w_im * theta[1];
+        // y = M^{-1} v, v = (w_re, w_im) / N
+        const double v0 = w_re / N, v1 = w_im / N;
+        const double y0 = (v0 * M11 - v1 * M01) / det, y1 = (v1 * M00 - v0 * M01) / det;
+        for (int64_t t = t0; t <= t1; ++t) lamF[t] = y0 * std::sin(om * t) + y1 * std::cos(om * t);
+        // explicit terms: the basis and N in omega, N in A
+        gW = y0 * dr0 + y1 * dr1 - (y0 * (dM00 * a + dM01 * b) + y1 * (dM01 * a + dM11 * b)) - J * 2.0 / om;
+        gA = -J / A;
+    }
+    // ---- reverse sweep by segments
+    cudaEventRecord(e2, s);
+    if (rc == HLBM_OK) {
+        cudaMemsetAsync(B.par, 0, 64, s);
+        cudaMemsetAsync(B.lY, 0, (size_t)(nsteps + 2) * 8, s);
+        cudaMemsetAsync(B.lV, 0, (size_t)(nsteps + 1) * ns * 8, s);
+        cudaMemsetAsync(B.lPn, 0, 9 * (size_t)n * sizeof(T), s);
+        cudaMemsetAsync(B.lfB, 0, 9 * (size_t)d.plane * sizeof(T), s);
+        cudaMemsetAsync(B.lSn, 0, 9 * (size_t)d.bplane * sizeof(T), s);
+    }
+    for (int64_t g = nseg - 1; g >= 0 && rc == HLBM_OK; --g) {
+        rc = adj_snapshot<T>(h, ck[g], true);
+        const int64_t ta = g * every, tb = std::min<int64_t>(nsteps, ta + every);
+        for (int64_t t = ta; t < tb && rc == HLBM_OK; ++t) rc = adj_forward_step<T>(h, recs[t - ta]);
+        for (int64_t t = tb - 1; t >= ta && rc == HLBM_OK; --t)
+            rc = adj_reverse_step<T>(h, recs[t - ta], B, sub, lamF[t + 1]);
+    }
+    cudaEvent_t e3;
+    cudaEventCreate(&e3);
+    cudaEventRecord(e3, s);
+    if (rc == HLBM_OK) {
+        double par[4];
+        std::vector<double> lY(nsteps + 2), lV((size_t)(nsteps + 1) * ns);
+        cudaError_t e = cudaMemcpyAsync(par, B.par, sizeof par, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lY.data(), B.lY, lY.size() * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lV.data(), B.lV, lV.size() * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_check(h, e, "adjoint read-back");
+        if (rc == HLBM_OK) {
+            const double om = mo.omega, A = mo.A, ts = h->tau_s;
+            for (int64_t t = 0; t <= nsteps; ++t) {
+                gA += lY[t] * std::sin(om * t);
+                gW += lY[t] * A * t * std::cos(om * t);
+            }
+            for (int64_t t = 0; t < nsteps; ++t)
+                for (int m = 0; m < ns; ++m) {
+                    const double tau = (double)t + double(m + 1) / double(ns), ph = om * tau;
+                    const double lv = lV[(size_t)t * ns + m];
+                    gA += lv * om * std::cos(ph);
+                    gW += lv * (A * std::cos(ph) - A * om * tau * std::sin(ph));
+                }
+            // tau_s enters as 1/tau_s (BGK), 1/tau_u = 1/(tau_s - 1/2), the eq. 178
+            // factor 2 (tau_s - 1)/(2 tau_s - 1) and 1 - 1/(2 tau_s)
+            gT = par[0] * (-1.0 / (ts * ts)) + par[1] * (-1.0 / ((ts - 0.5) * (ts - 0.5))) +
+                 par[2] * (2.0 / ((2 * ts - 1) * (2 * ts - 1))) + par[3] * (0.5 / (ts * ts));
+            grad[0] = gA;
+            grad[1] = gW;
+            grad[2] = gT;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (fwd_ms) *fwd_ms = ms;
+            cudaEventElapsedTime(&ms, e2, e3);
+            if (bwd_ms) *bwd_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
+    release();
+    return rc;
+}
+
+}  // namespace
+
 extern "C" {
 
 int hlbm_set_allocator(hlbm_alloc_fn alloc, hlbm_free_fn release, void* ctx) {
@@ -2070,6 +2456,32 @@ int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, doub
     if (w) hlbm_sweep_destroy(w);
     for (hlbm* h : inst)
         if (h) hlbm_destroy(h);
+    return rc;
+}
+
+int hlbm_theta_adjoint(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s, const hlbm_motion_t* motion,
+                       int64_t nsteps, double discard_periods, double fit_periods, double w_re, double w_im,
+                       int32_t checkpoint_every, void* cuda_stream, double* theta, double* grad, double* fwd_ms,
+                       double* bwd_ms) {
+    std::string& err = g_create_err;
+    if (!grid || !patch || !motion || !theta || !grad || nsteps < 1 || checkpoint_every < 1) {
+        err = "hlbm_theta_adjoint: invalid argument";
+        return HLBM_EINVAL;
+    }
+    if (motion->kind != HLBM_MOTION_HARMONIC || !(motion->omega > 0) || motion->A == 0.0 || grid->n_levels != 0 ||
+        patch->outer_fv != 0 || (grid->dtype != HLBM_F64 && grid->dtype != HLBM_F32)) {
+        err = "hlbm_theta_adjoint: needs HARMONIC motion, one lattice level, outer_fv = 0 and FP64 or FP32";
+        return HLBM_EINVAL;
+    }
+    hlbm_t* h = nullptr;
+    int rc = hlbm_create(grid, patch, tau_s, motion, cuda_stream, &h);
+    if (rc != HLBM_OK) return rc;
+    rc = h->dtype == HLBM_F64 ? adjoint_impl<double>(h, nsteps, discard_periods, fit_periods, w_re, w_im,
+                                                     checkpoint_every, theta, grad, fwd_ms, bwd_ms)
+                              : adjoint_impl<float>(h, nsteps, discard_periods, fit_periods, w_re, w_im,
+                                                    checkpoint_every, theta, grad, fwd_ms, bwd_ms);
+    if (rc != HLBM_OK) err = "hlbm_theta_adjoint: " + h->err;
+    hlbm_destroy(h);
     return rc;
 }
 

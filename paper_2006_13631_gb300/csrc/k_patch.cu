@@ -1998,6 +1998,662 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
     k_gamma_resid<<<1, 512, 0, s>>>(force, t0, t1, omega, a, b, out);
 }
 
+// ------------------------------------------------------------ adjoint
+// Reverse mode of one lattice step, with every decision of the forward step
+// held fixed (node classes, refill types, donor cells and triangles: the map
+// is smooth in the states and parameters between decisions).  All adjoints
+// are FP64.  Notation: for a deviation set f (f_i = f'_i), rho = rho0 + dr,
+// u = j / rho; the equilibrium's derivatives are
+//   d feq_i / d dr |_u = A_i = w_i (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u^2),
+//   d feq_i / d u      = B_i = w_i rho (3 c_i + 9 (c.u) c_i - 3 u),
+// so that d feq_i / d f_j = A_i + B_i . (c_j - u) / rho, and the transpose
+// product is (J^T l)_j = a + b . (c_j - u) / rho with a = sum_i l_i A_i,
+// b = sum_i l_i B_i.
+template <typename R>
+__device__ __forceinline__ void feq_ab(int i, R rho, R ux, R uy, R& A, R& Bx, R& By) {
+    const R w = w_of<R>(i), cx = R(cx_of(i)), cy = R(cy_of(i));
+    const R cu = cx * ux + cy * uy, usq = ux * ux + uy * uy;
+    A = w * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+    Bx = w * rho * (R(3) * cx + R(9) * cu * cx - R(3) * ux);
+    By = w * rho * (R(3) * cy + R(9) * cu * cy - R(3) * uy);
+}
+
+template <typename R>
+__device__ __forceinline__ void mom_d(const R (&f)[9], R rho0, R& dr, R& rho, R& ux, R& uy) {
+    R r = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        r += f[i];
+        jx += R(cx_of(i)) * f[i];
+        jy += R(cy_of(i)) * f[i];
+    }
+    dr = r;
+    rho = rho0 + r;
+    ux = jx / rho;
+    uy = jy / rho;
+}
+
+template <typename R>
+__device__ __forceinline__ R feq_d(int i, R dr, R rho, R ux, R uy) {
+    const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy, usq = ux * ux + uy * uy;
+    return w_of<R>(i) * (dr + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+}
+
+// out += scale * J_feq(f)^T lam, J at the moments (dr, rho, u) of f
+template <typename R>
+__device__ __forceinline__ void jfeqT_add(R rho, R ux, R uy, const R (&lam)[9], R scale, R (&out)[9]) {
+    R a = 0, bx = 0, by = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        R A, Bx, By;
+        feq_ab(i, rho, ux, uy, A, Bx, By);
+        a += lam[i] * A;
+        bx += lam[i] * Bx;
+        by += lam[i] * By;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) out[j] += scale * (a + (bx * (R(cx_of(j)) - ux) + by * (R(cy_of(j)) - uy)) / rho);
+}
+
+// the interpolated state s(f) = (dr, ux, uy, f^neq[9]) of a deviation set
+template <typename R>
+__device__ __forceinline__ void state_d(const R (&f)[9], R rho0, R (&st)[12]) {
+    R dr, rho, ux, uy;
+    mom_d(f, rho0, dr, rho, ux, uy);
+    st[0] = dr;
+    st[1] = ux;
+    st[2] = uy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st[3 + i] = f[i] - feq_d(i, dr, rho, ux, uy);
+}
+
+// out += scale * (d s / d f)^T ls
+template <typename R>
+__device__ __forceinline__ void stateT_add(const R (&f)[9], R rho0, const R (&ls)[12], R scale, R (&out)[9]) {
+    R dr, rho, ux, uy;
+    mom_d(f, rho0, dr, rho, ux, uy);
+    R ln[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        ln[j] = ls[3 + j];
+        out[j] += scale * (ls[0] + (ls[1] * (R(cx_of(j)) - ux) + ls[2] * (R(cy_of(j)) - uy)) / rho + ls[3 + j]);
+    }
+    jfeqT_add(rho, ux, uy, ln, -scale, out);
+}
+
+// f = f^eq(st) + k f^neq(st) (eq. continuity_stresses with k = 1 - 1/(2 tau_s),
+// eq. postcollision2_s with k = 2 (tau_s - 1)/(2 tau_s - 1)): ls = (d f / d st)^T lf,
+// lk += d f / d k . lf
+template <typename R>
+__device__ __forceinline__ void ffsT(const R (&st)[12], R rho0, R k, const R (&lf)[9], R (&ls)[12], double& lk) {
+    const R rho = rho0 + st[0];
+    R a = 0, bx = 0, by = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        R A, Bx, By;
+        feq_ab(i, rho, st[1], st[2], A, Bx, By);
+        a += lf[i] * A;
+        bx += lf[i] * Bx;
+        by += lf[i] * By;
+        ls[3 + i] = k * lf[i];
+        lk += lf[i] * st[3 + i];
+    }
+    ls[0] = a;
+    ls[1] = bx;
+    ls[2] = by;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_d(const T* p, T (&f)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = p[i];
+}
+
+// sum over the warp, one atomic per warp (every lane of the warp must call)
+__device__ __forceinline__ void warp_atomic_add(double* dst, double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+}
+
+template <typename R>
+__device__ __forceinline__ void atomic_add9(R* dst, const R (&v)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        if (v[i] != R(0)) atomicAdd(dst + i, v[i]);
+}
+
+// the window node of lattice cell corner q (0..3) for the bilinear stencil
+// at (wx, wy), its weight and the weight's derivative in wy; false when the
+// corner is outside the window (the forward skipped it)
+template <typename T>
+__device__ __forceinline__ bool bilinear_corner(const Dev<T>& d, int ox, int oy, double wx, double wy, int q,
+                                                int64_t& b, double& w, double& dwy) {
+    const double fx0 = floor(wx), fy0 = floor(wy);
+    const int ix = (int)fx0, iy = (int)fy0;
+    const double ax = __dsub_rn(wx, fx0), ay = __dsub_rn(wy, fy0);
+    const double wxq = (q & 1) ? ax : 1.0 - ax, wyq = (q >> 1) ? ay : 1.0 - ay;
+    w = wxq * wyq;
+    dwy = (q >> 1) ? wxq : -wxq;
+    const int bx = ix + (q & 1) - ox, by = iy + (q >> 1) - oy;
+    if ((unsigned)bx >= (unsigned)d.bw || (unsigned)by >= (unsigned)d.bh) return false;
+    b = (int64_t)by * d.bw + bx;
+    return true;
+}
+
+// derivatives of the barycentric coordinates of triangle k in q_y
+__device__ __forceinline__ void bary_dqy(const double* g, double (&dl)[3]) {  // FP64 geometry
+    const double x1 = g[2], x2 = g[4], det = g[6];
+    dl[1] = -x2 / det;
+    dl[2] = x1 / det;
+    dl[0] = -dl[1] - dl[2];
+}
+
+// Adjoint of F_y at t+1 (lamF = dJ/dF_y(t+1)) into the patch state that the
+// force was computed from (d.fu_in): sigma_xy = -sum f^neq c_x c_y,
+// sigma_yy = -dr/3 - sum f^neq c_y^2, F_y = sum_seg (sigma_xy n_x + sigma_yy n_y)
+// at the mean of its two nodes.
+template <typename T>
+__global__ void k_adj_force(Dev<T> d, double lamF, T* lP) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.nseg) return;
+    const T nx = T(d.seg_n[2 * k]), ny = T(d.seg_n[2 * k + 1]);
+    const T lxy = 0.5 * nx * lamF, lyy = 0.5 * ny * lamF;
+    for (int e = 0; e < 2; ++e) {
+        const int P = e == 0 ? d.seg_a[k] : d.seg_b[k];
+        T f[9], dr, rho, ux, uy;
+        load_d(d.fu_in + (int64_t)kRec * P, f);
+        mom_d(f, T(d.rho0), dr, rho, ux, uy);
+        T ln[9], out[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            ln[i] = -(lxy * cx_of(i) * cy_of(i) + lyy * cy_of(i) * cy_of(i));
+            out[i] = -lyy / 3.0 + ln[i];
+        }
+        jfeqT_add(rho, ux, uy, ln, T(-1), out);
+        atomic_add9(lP + 9 * (int64_t)P, out);
+    }
+}
+
+// one FV sub-step of every node (the arithmetic of the FV kernels), keeping
+// the state of each sub-step for the reverse sweep
+template <typename T>
+__global__ void k_adj_fv_fwd(Dev<T> d, StepArgs a, const T* in, T* out, int m) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= d.n) return;
+    T U, V;
+    wall_velocity(d, a, m, U, V);
+    fv_node(d, in, out, P, m, U, V);
+}
+
+// The FV update of a regular node P from state `in` in FP64: the updated
+// populations fv and the collision sums Cf_i - ceq_i (eq. ulbe).
+template <typename T>
+__device__ __forceinline__ void fv_update_d(const Dev<T>& d, const T* in, int P, T (&fv)[9], T (&cneq)[9]) {
+    const T rho0 = T(d.rho0);
+    T S[9], Cf[9], Z[3] = {0, 0, 0}, gpx = 0, gpy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) S[i] = Cf[i] = 0.0;
+    const int r0 = d.row_ptr[P], r1 = d.row_ptr[P + 1];
+    for (int e = r0 + 1; e < r1; ++e) {
+        const Coef<T> c = d.coef[e];
+        T f[9], zz[3];
+        load_d(in + (int64_t)kRec * c.col, f);
+        T dr, rho, ux, uy;
+        mom_d(f, rho0, dr, rho, ux, uy);
+        zz[0] = ux * ux * rho;
+        zz[1] = ux * uy * rho;
+        zz[2] = uy * uy * rho;
+        const T gx = T(c.gx), gy = T(c.gy), cc = T(c.c);
+        gpx -= gx;
+        gpy -= gy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            S[i] += (cx_of(i) * gx + cy_of(i) * gy) * f[i];
+            Cf[i] += cc * f[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Z[j] += cc * zz[j];
+    }
+    T fP[9];
+    load_d(in + (int64_t)kRec * P, fP);
+    {
+        T dr, rho, ux, uy;
+        mom_d(fP, rho0, dr, rho, ux, uy);
+        const T cc = T(d.coef[r0].c);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            S[i] += (cx_of(i) * gpx + cy_of(i) * gpy) * fP[i];
+            Cf[i] += cc * fP[i];
+        }
+        Z[0] += cc * ux * ux * rho;
+        Z[1] += cc * ux * uy * rho;
+        Z[2] += cc * uy * uy * rho;
+    }
+    // sum_k C (f^eq_k) from the linear parts Cf and the quadratic ones Z
+    T dr = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        dr += Cf[i];
+        jx += cx_of(i) * Cf[i];
+        jy += cy_of(i) * Cf[i];
+    }
+    const T q0 = dr - 1.5 * (Z[0] + Z[2]);
+    const T inv = T(d.inv_tau_u), dt = T(d.dt_u);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T cx = cx_of(i), cy = cy_of(i);
+        const T ceq = w_of<T>(i) * (q0 + 3.0 * (cx * jx + cy * jy) +
+                                              4.5 * (cx * cx * Z[0] + 2.0 * cx * cy * Z[1] + cy * cy * Z[2]));
+        cneq[i] = Cf[i] - ceq;
+        fv[i] = fP[i] + dt * (S[i] - inv * cneq[i]);
+    }
+}
+
+// Reverse of sub-step m, first pass: psi_P, the adjoint of node P's FV
+// update (through the wall rule at wall nodes), the outer nodes' feed
+// adjoint, and the parameter terms (1/tau_u, kneq, wall velocity).
+template <typename T>
+__global__ void k_adj_fv_psi(Dev<T> d, StepArgs a, const T* in, int m, const T* lnext, T* psi,
+                             T* lsnap, double* par, double* lV) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    T l_inv = 0, l_v = 0;
+    double l_kneq = 0.0;
+    if (P < d.n) {
+        const int8_t kind = d.kind[P];
+        T lam[9], ps[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lam[i] = lnext[9 * (int64_t)P + i];
+        if (kind == HLBM_NODE_OUTER) {
+            const int64_t no = d.n_outer;
+            const int o = d.outer_of[P];
+            const T th = T(m + 1) / T(d.n_sub);
+            T st[12], ls[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j)
+                st[j] = (1.0 - th) * T(d.snap[j * no + o]) + th * T(d.snap[(12 + j) * no + o]);
+            ffsT(st, T(d.rho0), T(d.kneq), lam, ls, l_kneq);
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                lsnap[j * no + o] += (1.0 - th) * ls[j];
+                lsnap[(12 + j) * no + o] += th * ls[j];
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) ps[i] = 0.0;
+        } else {
+            T fv[9], cneq[9];
+            fv_update_d(d, in, P, fv, cneq);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) ps[i] = lam[i];
+            if (kind == HLBM_NODE_WALL) {
+                // g(f) = f + f^eq(rho, U) - f^eq(rho, u(f))
+                T Ut, Vt;
+                wall_velocity(d, a, m, Ut, Vt);
+                const T U = T(Ut), V = T(Vt);
+                T dr, rho, ux, uy;
+                mom_d(fv, T(d.rho0), dr, rho, ux, uy);
+                T aU = 0.0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    T A, Bx, By;
+                    feq_ab(i, rho, U, V, A, Bx, By);
+                    aU += lam[i] * A;
+                    l_v += lam[i] * By;
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) ps[i] += aU;
+                jfeqT_add(rho, ux, uy, lam, T(-1), ps);
+            }
+            const T dt = T(d.dt_u);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) l_inv -= dt * ps[i] * cneq[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) psi[9 * (int64_t)P + i] = ps[i];
+    }
+    warp_atomic_add(par + 1, l_inv);
+    warp_atomic_add(par + 3, l_kneq);
+    warp_atomic_add(lV + (int64_t)a.t * d.n_sub + m, l_v);
+}
+
+// Reverse of sub-step m, second pass: the adjoint of node k's state before
+// the sub-step, gathered from the rows that read it (k itself and its
+// neighbours; tpos gives row P's entry of column k).
+template <typename T>
+__global__ void k_adj_fv_gather(Dev<T> d, const T* in, const T* psi, const int32_t* tpos, T* lcur) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const T dt = T(d.dt_u), inv = T(d.inv_tau_u);
+    T out[9], Lc[9];
+    const bool regular = d.kind[k] != HLBM_NODE_OUTER;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        out[i] = regular ? psi[9 * (int64_t)k + i] : 0.0;
+        Lc[i] = 0.0;
+    }
+    const int r0 = d.row_ptr[k], r1 = d.row_ptr[k + 1];
+    for (int e = r0; e < r1; ++e) {
+        const int P = e == r0 ? k : d.coef[e].col;
+        if (d.kind[P] == HLBM_NODE_OUTER) continue;
+        T gx, gy, cc;
+        if (P == k) {
+            gx = gy = 0.0;
+            for (int q = r0 + 1; q < r1; ++q) {
+                gx -= T(d.coef[q].gx);
+                gy -= T(d.coef[q].gy);
+            }
+            cc = T(d.coef[r0].c);
+        } else {
+            const Coef<T> c = d.coef[tpos[e]];
+            gx = T(c.gx);
+            gy = T(c.gy);
+            cc = T(c.c);
+        }
+        const T* pp = psi + 9 * (int64_t)P;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            out[j] += dt * ((cx_of(j) * gx + cy_of(j) * gy) - inv * cc) * pp[j];
+            Lc[j] += cc * pp[j];
+        }
+    }
+    T f[9], dr, rho, ux, uy;
+    load_d(in + (int64_t)kRec * k, f);
+    mom_d(f, T(d.rho0), dr, rho, ux, uy);
+    jfeqT_add(rho, ux, uy, Lc, dt * inv, out);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) lcur[9 * (int64_t)k + j] = out[j];
+}
+
+// Reverse of the outer nodes' feed: snap[0] bilinear from the window state
+// at t (previous window), snap[1] from the one at t+1; positions at y(t).
+template <typename T>
+__global__ void k_adj_feed(Dev<T> d, StepArgs a, const T* lsnap, T* lSo, T* lSn, double* lY) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    double gy = 0.0;
+    if (o < d.n_outer) {
+        const int P = d.outer[o];
+        const double wx = __dadd_rn(a.cx, d.xy[2 * P]), wy = __dadd_rn(a.cy, d.xy[2 * P + 1]);
+        const int64_t no = d.n_outer;
+        for (int side = 0; side < 2; ++side) {
+            const T* box = side == 0 ? d.sbox_old : (const T*)d.sbox_new;
+            const int ox = side == 0 ? a.pbx0 : a.bx0, oy = side == 0 ? a.pby0 : a.by0;
+            T* lS = side == 0 ? lSo : lSn;
+            T ls[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) ls[j] = lsnap[(12 * side + j) * no + o];
+            for (int q = 0; q < 4; ++q) {
+                int64_t b;
+                double w, dw;
+                if (!bilinear_corner(d, ox, oy, wx, wy, q, b, w, dw)) continue;
+                T f[9], st[12], out[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    f[i] = T(box[i * d.bplane + b]);
+                    out[i] = 0.0;
+                }
+                state_d(f, T(d.rho0), st);
+                stateT_add(f, T(d.rho0), ls, T(w), out);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (out[i] != 0.0) atomicAdd(lS + i * d.bplane + b, out[i]);
+                T dot = 0.0;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) dot += ls[j] * st[j];
+                gy += dw * double(dot);
+            }
+        }
+    }
+    warp_atomic_add(lY + a.t, gy);
+}
+
+// source element of population i pulled by node (x, y) (the boundary rules
+// of the stream-collide: bounce-back walls, zero-gradient outflow, periodic)
+template <typename T>
+__device__ __forceinline__ int64_t pull_src(const Dev<T>& d, int x, int y, int i) {
+    int sx = x - cx_of(i), sy = y - cy_of(i);
+    if (sx < 0 || sx >= d.nx) {
+        if (d.bc_x == HLBM_BC_PERIODIC)
+            sx = (sx + d.nx) % d.nx;
+        else if (d.bc_x == HLBM_BC_WALL)
+            return opp_of(i) * d.plane + (int64_t)y * d.pitch + x;
+        else
+            sx = x;
+    }
+    if (sy < 0 || sy >= d.ny) {
+        if (d.bc_y == HLBM_BC_PERIODIC)
+            sy = (sy + d.ny) % d.ny;
+        else if (d.bc_y == HLBM_BC_WALL)
+            return opp_of(i) * d.plane + (int64_t)y * d.pitch + x;
+        else
+            sy = y;
+    }
+    return i * d.plane + (int64_t)sy * d.pitch + sx;
+}
+
+// Reverse of the stream-collide (pull, BGK with 1/tau_s) at every node it
+// wrote (discretization nodes), plus the window state it wrote (lSn).
+template <typename T>
+__global__ void k_adj_stream(Dev<T> d, StepArgs a, const T* lfB, const T* lSn, T* lfA, double* par) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    T l_om = 0;
+    bool active = x < d.nx;
+    int64_t b = -1;
+    if (active) {
+        const unsigned rx = (unsigned)(x - a.bx0), ry = (unsigned)(y - a.by0);
+        if (rx < (unsigned)d.bw && ry < (unsigned)d.bh) {
+            b = (int64_t)ry * d.bw + rx;
+            active = d.cls_cur[b] == CLS_DISC;
+        }
+    }
+    if (active) {
+        const T* A = d.fA;
+        T f[9];
+        int64_t src[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            src[i] = pull_src(d, x, y, i);
+            f[i] = T(A[src[i]]);
+        }
+        T dr, rho, ux, uy;
+        mom_d(f, T(d.rho0), dr, rho, ux, uy);
+        const T om = 1.0 / T(d.tau_s);
+        const int64_t s = (int64_t)y * d.pitch + x;
+        T lam[9], mu[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            lam[i] = lfB[i * d.plane + s];
+            mu[i] = (1.0 - om) * lam[i];
+            l_om -= lam[i] * (f[i] - feq_d(i, dr, rho, ux, uy));
+        }
+        jfeqT_add(rho, ux, uy, lam, om, mu);
+        if (b >= 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) mu[i] += lSn[i * d.bplane + b];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if (mu[i] != 0.0) atomicAdd(lfA + src[i], mu[i]);
+    }
+    warp_atomic_add(par + 0, l_om);
+}
+
+// Reverse of the eq. postcollision2_s fill: the adjoint of the populations
+// it wrote goes to the patch state it interpolated (and is consumed).
+template <typename T>
+__global__ void k_adj_fill(Dev<T> d, StepArgs a, T* lfA, T* lP, double* par, double* lY) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double l_k = 0.0, gy = 0.0;
+    bool fill = false;
+    int x = 0, y = 0;
+    if (b < d.bplane) {
+        const int8_t c = d.cls_cur[b];
+        x = a.bx0 + (int)(b % d.bw);
+        y = a.by0 + (int)(b / d.bw);
+        if (c == CLS_INTERP) {
+            fill = true;
+        } else if (c == CLS_DISC && !a.first) {
+            const unsigned px = (unsigned)(x - a.pbx0), py = (unsigned)(y - a.pby0);
+            const int8_t prev = (px < (unsigned)d.bw && py < (unsigned)d.bh) ? d.cls_prev[(int64_t)py * d.bw + px]
+                                                                             : (int8_t)CLS_DISC;
+            fill = prev != CLS_DISC;
+        }
+    }
+    if (fill) {
+        const int64_t s = (int64_t)y * d.pitch + x;
+        T lp[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            lp[i] = lfA[i * d.plane + s];
+            lfA[i * d.plane + s] = 0.0;
+        }
+        double lam[3];
+        const double qx = __dsub_rn((double)x, a.cx), qy = __dsub_rn((double)y, a.cy);
+        const int k = locate_dev(d, qx, qy, lam);
+        if (k >= 0) {
+            const T rho0 = T(d.rho0);
+            T fv[3][9], sv[3][12], st[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) st[j] = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                load_d(d.fu_in + (int64_t)kRec * d.tri[3 * k + q], fv[q]);
+                state_d(fv[q], rho0, sv[q]);
+#pragma unroll
+                for (int j = 0; j < 12; ++j) st[j] += T(lam[q]) * sv[q][j];
+            }
+            T ls[12];
+            ffsT(st, rho0, T(d.k178), lp, ls, l_k);
+            double dl[3];
+            bary_dqy(d.trigeo + 8 * (int64_t)k, dl);
+            for (int q = 0; q < 3; ++q) {
+                T out[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) out[i] = 0.0;
+                stateT_add(fv[q], rho0, ls, T(lam[q]), out);
+                atomic_add9(lP + 9 * (int64_t)d.tri[3 * k + q], out);
+                T dot = 0.0;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) dot += ls[j] * sv[q][j];
+                gy -= dl[q] * double(dot);  // q_y = y - c_y
+            }
+        }
+    }
+    warp_atomic_add(par + 2, l_k);
+    warp_atomic_add(lY + a.t, gy);
+}
+
+// Reverse of the refill of Sec. 4 (types 1, 2, 3 and wall nodes) from the
+// adjoint lPm of the refilled state into the state before it (lP0) and the
+// window state at t (lSo).
+template <typename T>
+__global__ void k_adj_refill(Dev<T> d, StepArgs a, const T* lPm, T* lP0, T* lSo, double* par,
+                             double* lY) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    double l_k = 0.0, gy = 0.0, gdy = 0.0;
+    if (P < d.n) {
+        T lam[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lam[i] = lPm[9 * (int64_t)P + i];
+        const int type = d.rtype[P];
+        const T rho0 = T(d.rho0);
+        if (type == 0 || type == 2) {
+            atomic_add9(lP0 + 9 * (int64_t)P, lam);
+        } else if (type == 3) {
+            const int k = d.rdonor[P];
+            const double qx = __dadd_rn(d.xy[2 * P], a.dX), qy = __dadd_rn(d.xy[2 * P + 1], a.dY);
+            double l0, l1, l2, dl[3];
+            bary_rn(d.trigeo + 8 * (int64_t)k, qx, qy, l0, l1, l2);
+            bary_dqy(d.trigeo + 8 * (int64_t)k, dl);
+            const T lb[3] = {T(l0), T(l1), T(l2)};
+            for (int q = 0; q < 3; ++q) {
+                const int v = d.tri[3 * k + q];
+                T out[9], f[9];
+                load_d(d.fu_in + (int64_t)kRec * v, f);
+                T dot = 0.0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    out[i] = lb[q] * lam[i];
+                    dot += lam[i] * f[i];
+                }
+                atomic_add9(lP0 + 9 * (int64_t)v, out);
+                gdy += dl[q] * double(dot);
+            }
+        } else if (type == 1) {
+            const double wx = __dadd_rn(a.cx, d.xy[2 * P]), wy = __dadd_rn(a.cy, d.xy[2 * P + 1]);
+            T st[12], fq[4][9], sq[4][12];
+            double wq[4], dwq[4];
+            int64_t bq[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) st[j] = 0.0;
+            for (int q = 0; q < 4; ++q) {
+                ok[q] = bilinear_corner(d, a.pbx0, a.pby0, wx, wy, q, bq[q], wq[q], dwq[q]);
+                if (!ok[q]) continue;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fq[q][i] = T(d.sbox_old[i * d.bplane + bq[q]]);
+                state_d(fq[q], rho0, sq[q]);
+#pragma unroll
+                for (int j = 0; j < 12; ++j) st[j] += T(wq[q]) * sq[q][j];
+            }
+            T ls[12];
+            ffsT(st, rho0, T(d.kneq), lam, ls, l_k);
+            for (int q = 0; q < 4; ++q) {
+                if (!ok[q]) continue;
+                T out[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) out[i] = 0.0;
+                stateT_add(fq[q], rho0, ls, T(wq[q]), out);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (out[i] != 0.0) atomicAdd(lSo + i * d.bplane + bq[q], out[i]);
+                T dot = 0.0;
+#pragma unroll
+                for (int j = 0; j < 12; ++j) dot += ls[j] * sq[q][j];
+                gy += dwq[q] * double(dot);
+            }
+        }
+    }
+    warp_atomic_add(par + 3, l_k);
+    warp_atomic_add(lY + a.t, gy + gdy);
+    warp_atomic_add(lY + a.t - 1, -gdy);
+}
+
+template <typename T>
+void launch_adj_force(const Dev<T>& d, double lamF, T* lP, cudaStream_t s) {
+    if (d.nseg > 0) k_adj_force<T><<<(d.nseg + 127) / 128, 128, 0, s>>>(d, lamF, lP);
+}
+template <typename T>
+void launch_adj_fv_fwd(const Dev<T>& d, const StepArgs& a, const T* in, T* out, int m, cudaStream_t s) {
+    k_adj_fv_fwd<T><<<(d.n + 63) / 64, 64, 0, s>>>(d, a, in, out, m);
+}
+template <typename T>
+void launch_adj_fv_rev(const Dev<T>& d, const StepArgs& a, const T* in, int m, const T* lnext, T* psi,
+                       const int32_t* tpos, T* lcur, T* lsnap, double* par, double* lV, cudaStream_t s) {
+    // the patch is small next to the GPU: 64-thread blocks spread it over more SMs
+    k_adj_fv_psi<T><<<(d.n + 63) / 64, 64, 0, s>>>(d, a, in, m, lnext, psi, lsnap, par, lV);
+    k_adj_fv_gather<T><<<(d.n + 63) / 64, 64, 0, s>>>(d, in, psi, tpos, lcur);
+}
+template <typename T>
+void launch_adj_feed(const Dev<T>& d, const StepArgs& a, const T* lsnap, T* lSo, T* lSn, double* lY,
+                     cudaStream_t s) {
+    if (d.n_outer) k_adj_feed<T><<<(d.n_outer + 127) / 128, 128, 0, s>>>(d, a, lsnap, lSo, lSn, lY);
+}
+template <typename T>
+void launch_adj_stream(const Dev<T>& d, const StepArgs& a, const T* lfB, const T* lSn, T* lfA,
+                       double* par, cudaStream_t s) {
+    dim3 grid((d.nx + 127) / 128, d.ny);
+    k_adj_stream<T><<<grid, 128, 0, s>>>(d, a, lfB, lSn, lfA, par);
+}
+template <typename T>
+void launch_adj_fill(const Dev<T>& d, const StepArgs& a, T* lfA, T* lP, double* par, double* lY,
+                     cudaStream_t s) {
+    k_adj_fill<T><<<(unsigned)((d.bplane + 127) / 128), 128, 0, s>>>(d, a, lfA, lP, par, lY);
+}
+template <typename T>
+void launch_adj_refill(const Dev<T>& d, const StepArgs& a, const T* lPm, T* lP0, T* lSo, double* par,
+                       double* lY, cudaStream_t s) {
+    k_adj_refill<T><<<(d.n + 127) / 128, 128, 0, s>>>(d, a, lPm, lP0, lSo, par, lY);
+}
+
 #define HLBM_INST(T)                                                                                        \
     template void launch_fv_coeffs<T>(const Dev<T>&, int, Coef<T>*, cudaStream_t);                          \
     template void launch_patch_init<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                         \
@@ -2023,7 +2679,17 @@ void launch_gamma_resid(const double* force, int64_t t0, int64_t t1, double omeg
     template void launch_build_deep_rows<T>(const Dev<T>&, const int32_t*, const int32_t*, int64_t, uint32_t*, \
                                             cudaStream_t);                                                    \
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \
-    template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);
+    template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);    \
+    template void launch_adj_force<T>(const Dev<T>&, double, T*, cudaStream_t);                               \
+    template void launch_adj_fv_fwd<T>(const Dev<T>&, const StepArgs&, const T*, T*, int, cudaStream_t);      \
+    template void launch_adj_fv_rev<T>(const Dev<T>&, const StepArgs&, const T*, int, const T*, T*,            \
+                                       const int32_t*, T*, T*, double*, double*, cudaStream_t);               \
+    template void launch_adj_feed<T>(const Dev<T>&, const StepArgs&, const T*, T*, T*, double*, cudaStream_t); \
+    template void launch_adj_stream<T>(const Dev<T>&, const StepArgs&, const T*, const T*, T*, double*,        \
+                                       cudaStream_t);                                                         \
+    template void launch_adj_fill<T>(const Dev<T>&, const StepArgs&, T*, T*, double*, double*, cudaStream_t);  \
+    template void launch_adj_refill<T>(const Dev<T>&, const StepArgs&, const T*, T*, T*, double*, double*,     \
+                                       cudaStream_t);
 HLBM_INST(float)
 HLBM_INST(double)
 

@@ -137,6 +137,71 @@ def hlbm_theta_gradient(grid: dict, patch: dict, tau_s: float, motion: dict, nst
     return complex(th[0], th[1]), gr[0::2] + 1j * gr[1::2], float(ms[0])
 
 
+def hlbm_theta_adjoint(grid: dict, patch: dict, tau_s: float, motion: dict, nsteps: int, discard=1.0, fit=3.0,
+                       w_re=1.0, w_im=0.0, checkpoint_every=256, cuda_stream: int = 0):
+    """Theta and the gradient of L = w_re Re Theta + w_im Im Theta in
+    (A, omega, tau_s) by the adjoint of the discrete step.  Returns
+    (theta complex, grad [3] real, forward ms, reverse ms)."""
+    g, p, m, keep = _structs(grid, patch, motion)
+    th, gr, fw, bw = np.zeros(2), np.zeros(3), np.zeros(1), np.zeros(1)
+    _check(N.load().hlbm_theta_adjoint(C.byref(g), C.byref(p), float(tau_s), C.byref(m), int(nsteps), float(discard),
+                                       float(fit), float(w_re), float(w_im), int(checkpoint_every),
+                                       C.c_void_p(cuda_stream or None), _dp(th), _dp(gr), _dp(fw), _dp(bw)))
+    return complex(th[0], th[1]), gr.copy(), float(fw[0]), float(bw[0])
+
+
+def theta_function(w, nsteps: int, discard=1.0, fit=3.0, checkpoint_every=256, mesh=None, rho_init=None,
+                   cuda_stream: int = 0):
+    """A differentiable Theta(A, omega, tau_s) of workload w (HARMONIC motion):
+    returns f(params) -> tensor (Re, Im), params a float64 tensor (A, omega,
+    tau_s) with requires_grad.  The forward pass steps one solver and fits
+    Theta (Sec. 2.1); the backward pass runs the adjoint of the discrete step
+    (hlbm_theta_adjoint) with the incoming gradient as the weights of Re and
+    Im.  Everything runs in the CUDA library; torch only carries the values."""
+    import torch
+
+    mesh = mesh if mesh is not None else w.mesh()
+    rho_init = rho_init if rho_init is not None else w.rho_init()
+
+    def inputs_at(params):
+        A, om, tau = (float(x) for x in params)
+        ww = type(w)(**{k: getattr(w, k) for k in w.__dataclass_fields__})
+        ww.A, ww.omega, ww.tau_s = A, om, tau
+        grid, patch, motion = workload_inputs(ww, mesh, rho_init)
+        return grid, patch, motion, tau
+
+    class _Theta(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params):
+            grid, patch, motion, tau = inputs_at(params.detach().cpu())
+            h = hlbm_create(grid, patch, tau, motion, cuda_stream)
+            try:
+                hlbm_step(h, nsteps)
+                re, im, _ = hlbm_gamma_window(h, motion["omega"], discard, fit)
+            finally:
+                hlbm_destroy(h)
+            ctx.save_for_backward(params)
+            return torch.tensor([re, im], dtype=torch.float64, device=params.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (params,) = ctx.saved_tensors
+            grid, patch, motion, tau = inputs_at(params.detach().cpu())
+            go = grad_out.detach().cpu().double()
+            _, gr, _, _ = hlbm_theta_adjoint(grid, patch, tau, motion, nsteps, discard, fit, float(go[0]),
+                                             float(go[1]), checkpoint_every, cuda_stream)
+            return torch.tensor(gr, dtype=torch.float64, device=params.device)
+
+    return _Theta.apply
+
+
+def hlbm_gamma_window(h, omega: float, discard: float, fit: float):
+    """Theta over [discard, discard + fit] periods of the solver's force history."""
+    re, im, rms = C.c_double(), C.c_double(), C.c_double()
+    _check(N.load().hlbm_gamma(h, float(discard), float(fit), C.byref(re), C.byref(im), C.byref(rms)), h)
+    return re.value, im.value, rms.value
+
+
 def hlbm_step(h, nsteps: int):
     _check(N.load().hlbm_step(h, int(nsteps)), h)
 
