@@ -1722,6 +1722,7 @@ struct AdjRec {
     StepArgs a{};
     T* P0 = nullptr;   // patch before the refill
     T* Pm = nullptr;   // after it
+    T* Pnext = nullptr; // after the FV sub-steps (the patch at t+1)
     T* lat = nullptr;  // lattice populations the stream-collide read (after the eq. 178 fill)
     T* sbo = nullptr;  // window state at t (previous window)
     T* sbn = nullptr;  // at t+1
@@ -1815,6 +1816,7 @@ int adj_forward_step(hlbm* h, AdjRec<T>& R) {
     cp(R.snap, d.snap, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
     rc = step_fv<T>(h, s, ps);
     if (rc == HLBM_OK) rc = step_finish<T>(h, s, ps);
+    cp(R.Pnext, h->fu[h->ui], fu);
     return rc;
 }
 
@@ -1834,24 +1836,17 @@ int adj_reverse_step(hlbm* h, const AdjRec<T>& R, AdjBufs<T>& B, T* sub, double 
     Dev<T> dd = dev_of<T>(h);
     const int n = dd.n, ns = dd.n_sub;
     const size_t rec = (size_t)kRec * n;
-    // the FV sub-steps again, every state kept
+    // the FV sub-steps again (every state kept) and their reverse, one launch;
+    // the force at t+1 first, from the state after the last sub-step
     dd.snap = R.snap;
     cudaMemcpyAsync(sub, R.Pm, rec * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    for (int m = 0; m < ns; ++m) launch_adj_fv_fwd<T>(dd, R.a, sub + m * rec, sub + (m + 1) * rec, m, s);
-    // force at t+1
-    if (lamF != 0.0) {
-        dd.fu_in = sub + ns * rec;
+    cudaMemsetAsync(B.lsnap, 0, (size_t)24 * std::max(dd.n_outer, 1) * sizeof(T), s);
+    if (lamF != 0.0) {  // the force at t+1, from the patch after the sub-steps
+        dd.fu_in = R.Pnext;
         launch_adj_force<T>(dd, lamF, B.lPn, s);
     }
-    // FV sub-steps, last to first
-    cudaMemsetAsync(B.lsnap, 0, (size_t)24 * std::max(dd.n_outer, 1) * sizeof(T), s);
-    const T* lnext = B.lPn;
-    for (int m = ns - 1; m >= 0; --m) {
-        T* lcur = (m & 1) ? B.x1 : B.x0;
-        launch_adj_fv_rev<T>(dd, R.a, sub + m * rec, m, lnext, B.psi, B.tpos, lcur, B.lsnap, B.par, B.lV, s);
-        lnext = lcur;
-    }
-    cudaMemcpyAsync(B.lPm, lnext, (size_t)9 * n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    cudaError_t fe = launch_adj_fv<T>(dd, R.a, sub, B.lPn, B.x0, B.x1, B.psi, B.tpos, B.lsnap, B.par, B.lV, B.lPm, s);
+    if (fe != cudaSuccess) return cuda_check(h, fe, "adjoint FV launch");
     // feed, stream-collide, eq. 178 fill, refill
     dd.sbox_old = R.sbo;
     dd.sbox_new = R.sbn;
@@ -1925,6 +1920,7 @@ int adjoint_impl(hlbm* h, int64_t nsteps, double discard, double fit, double w_r
     for (auto& r : recs) {
         r.P0 = (T*)alloc(fu);
         r.Pm = (T*)alloc(fu);
+        r.Pnext = (T*)alloc(fu);
         r.lat = (T*)alloc(lat);
         r.sbo = (T*)alloc(box);
         r.sbn = (T*)alloc(box);
@@ -1933,7 +1929,7 @@ int adjoint_impl(hlbm* h, int64_t nsteps, double discard, double fit, double w_r
         r.rt = (int32_t*)alloc((size_t)n * 4);
         r.rd = (int32_t*)alloc((size_t)n * 4);
         r.snap = (T*)alloc(snapb);
-        if (!r.P0 || !r.Pm || !r.lat || !r.sbo || !r.sbn || !r.clp || !r.clc || !r.rt || !r.rd || !r.snap)
+        if (!r.P0 || !r.Pm || !r.Pnext || !r.lat || !r.sbo || !r.sbn || !r.clp || !r.clc || !r.rt || !r.rd || !r.snap)
             rc = fail(h, HLBM_ENOMEM, "adjoint step records");
     }
     AdjBufs<T> B{};

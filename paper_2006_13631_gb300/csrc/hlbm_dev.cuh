@@ -468,11 +468,9 @@ void launch_gamma_sums(const double* force, int64_t t0, int64_t t1, double omega
 // adjoint of one lattice step (decisions held fixed); adjoints in the
 // population type T, parameter sums (par, lY, lV) in FP64
 template <typename T> void launch_adj_force(const Dev<T>& d, double lamF, T* lP, cudaStream_t s);
-template <typename T> void launch_adj_fv_fwd(const Dev<T>& d, const StepArgs& a, const T* in, T* out, int m,
-                                             cudaStream_t s);
-template <typename T> void launch_adj_fv_rev(const Dev<T>& d, const StepArgs& a, const T* in, int m, const T* lnext,
-                                             T* psi, const int32_t* tpos, T* lcur, T* lsnap, double* par, double* lV,
-                                             cudaStream_t s);
+template <typename T> cudaError_t launch_adj_fv(const Dev<T>& d, const StepArgs& a, T* sub, const T* lPn, T* x0,
+                                                T* x1, T* psi, const int32_t* tpos, T* lsnap, double* par,
+                                                double* lV, T* lPm, cudaStream_t s);
 template <typename T> void launch_adj_feed(const Dev<T>& d, const StepArgs& a, const T* lsnap, T* lSo, T* lSn,
                                            double* lY, cudaStream_t s);
 template <typename T> void launch_adj_stream(const Dev<T>& d, const StepArgs& a, const T* lfB, const T* lSn, T* lfA,

@@ -5,6 +5,8 @@
 //
 // Patch state: one record of kRec values per node, f'[0..8] (deviation from
 // w_i rho0) followed by the quadratic equilibrium terms z[0..2] (z_of).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "hlbm_dev.cuh"
@@ -2175,18 +2177,7 @@ __global__ void k_adj_force(Dev<T> d, double lamF, T* lP) {
     }
 }
 
-// one FV sub-step of every node (the arithmetic of the FV kernels), keeping
-// the state of each sub-step for the reverse sweep
-template <typename T>
-__global__ void k_adj_fv_fwd(Dev<T> d, StepArgs a, const T* in, T* out, int m) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= d.n) return;
-    T U, V;
-    wall_velocity(d, a, m, U, V);
-    fv_node(d, in, out, P, m, U, V);
-}
-
-// The FV update of a regular node P from state `in` in FP64: the updated
+// The FV update of a regular node P from state `in`: the updated
 // populations fv and the collision sums Cf_i - ceq_i (eq. ulbe).
 template <typename T>
 __device__ __forceinline__ void fv_update_d(const Dev<T>& d, const T* in, int P, T (&fv)[9], T (&cneq)[9]) {
@@ -2250,86 +2241,76 @@ __device__ __forceinline__ void fv_update_d(const Dev<T>& d, const T* in, int P,
     }
 }
 
-// Reverse of sub-step m, first pass: psi_P, the adjoint of node P's FV
-// update (through the wall rule at wall nodes), the outer nodes' feed
-// adjoint, and the parameter terms (1/tau_u, kneq, wall velocity).
+// Reverse of sub-step m, first pass at node P: psi_P, the adjoint of its
+// FV update (through the wall rule at wall nodes), the outer nodes' feed
+// adjoint, and the parameter terms (1/tau_u, kneq, wall velocity) added to
+// the caller's sums.
 template <typename T>
-__global__ void k_adj_fv_psi(Dev<T> d, StepArgs a, const T* in, int m, const T* lnext, T* psi,
-                             T* lsnap, double* par, double* lV) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    T l_inv = 0, l_v = 0;
-    double l_kneq = 0.0;
-    if (P < d.n) {
-        const int8_t kind = d.kind[P];
-        T lam[9], ps[9];
+__device__ __forceinline__ void adj_psi_node(const Dev<T>& d, const StepArgs& a, const T* in, int m, const T* lnext,
+                                             T* psi, T* lsnap, int P, T& l_inv, double& l_kneq, T& l_v) {
+    const int8_t kind = d.kind[P];
+    T lam[9], ps[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) lam[i] = lnext[9 * (int64_t)P + i];
-        if (kind == HLBM_NODE_OUTER) {
-            const int64_t no = d.n_outer;
-            const int o = d.outer_of[P];
-            const T th = T(m + 1) / T(d.n_sub);
-            T st[12], ls[12];
+    for (int i = 0; i < 9; ++i) lam[i] = lnext[9 * (int64_t)P + i];
+    if (kind == HLBM_NODE_OUTER) {
+        const int64_t no = d.n_outer;
+        const int o = d.outer_of[P];
+        const T th = T(m + 1) / T(d.n_sub);
+        T st[12], ls[12];
 #pragma unroll
-            for (int j = 0; j < 12; ++j)
-                st[j] = (1.0 - th) * T(d.snap[j * no + o]) + th * T(d.snap[(12 + j) * no + o]);
-            ffsT(st, T(d.rho0), T(d.kneq), lam, ls, l_kneq);
+        for (int j = 0; j < 12; ++j) st[j] = (T(1) - th) * T(d.snap[j * no + o]) + th * T(d.snap[(12 + j) * no + o]);
+        ffsT(st, T(d.rho0), T(d.kneq), lam, ls, l_kneq);
 #pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                lsnap[j * no + o] += (1.0 - th) * ls[j];
-                lsnap[(12 + j) * no + o] += th * ls[j];
-            }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) ps[i] = 0.0;
-        } else {
-            T fv[9], cneq[9];
-            fv_update_d(d, in, P, fv, cneq);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) ps[i] = lam[i];
-            if (kind == HLBM_NODE_WALL) {
-                // g(f) = f + f^eq(rho, U) - f^eq(rho, u(f))
-                T Ut, Vt;
-                wall_velocity(d, a, m, Ut, Vt);
-                const T U = T(Ut), V = T(Vt);
-                T dr, rho, ux, uy;
-                mom_d(fv, T(d.rho0), dr, rho, ux, uy);
-                T aU = 0.0;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    T A, Bx, By;
-                    feq_ab(i, rho, U, V, A, Bx, By);
-                    aU += lam[i] * A;
-                    l_v += lam[i] * By;
-                }
-#pragma unroll
-                for (int i = 0; i < 9; ++i) ps[i] += aU;
-                jfeqT_add(rho, ux, uy, lam, T(-1), ps);
-            }
-            const T dt = T(d.dt_u);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) l_inv -= dt * ps[i] * cneq[i];
+        for (int j = 0; j < 12; ++j) {
+            lsnap[j * no + o] += (T(1) - th) * ls[j];
+            lsnap[(12 + j) * no + o] += th * ls[j];
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) psi[9 * (int64_t)P + i] = ps[i];
+        for (int i = 0; i < 9; ++i) ps[i] = T(0);
+    } else {
+        T fv[9], cneq[9];
+        fv_update_d(d, in, P, fv, cneq);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ps[i] = lam[i];
+        if (kind == HLBM_NODE_WALL) {
+            // g(f) = f + f^eq(rho, U) - f^eq(rho, u(f))
+            T U, V;
+            wall_velocity(d, a, m, U, V);
+            T dr, rho, ux, uy;
+            mom_d(fv, T(d.rho0), dr, rho, ux, uy);
+            T aU = T(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                T A, Bx, By;
+                feq_ab(i, rho, U, V, A, Bx, By);
+                aU += lam[i] * A;
+                l_v += lam[i] * By;
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) ps[i] += aU;
+            jfeqT_add(rho, ux, uy, lam, T(-1), ps);
+        }
+        const T dt = T(d.dt_u);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) l_inv -= dt * ps[i] * cneq[i];
     }
-    warp_atomic_add(par + 1, l_inv);
-    warp_atomic_add(par + 3, l_kneq);
-    warp_atomic_add(lV + (int64_t)a.t * d.n_sub + m, l_v);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) psi[9 * (int64_t)P + i] = ps[i];
 }
 
-// Reverse of sub-step m, second pass: the adjoint of node k's state before
-// the sub-step, gathered from the rows that read it (k itself and its
+// Reverse of sub-step m, second pass at node k: the adjoint of its state
+// before the sub-step, gathered from the rows that read it (k itself and its
 // neighbours; tpos gives row P's entry of column k).
 template <typename T>
-__global__ void k_adj_fv_gather(Dev<T> d, const T* in, const T* psi, const int32_t* tpos, T* lcur) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
+__device__ __forceinline__ void adj_gather_node(const Dev<T>& d, const T* in, const T* psi, const int32_t* tpos,
+                                                T* lcur, int k) {
     const T dt = T(d.dt_u), inv = T(d.inv_tau_u);
     T out[9], Lc[9];
     const bool regular = d.kind[k] != HLBM_NODE_OUTER;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        out[i] = regular ? psi[9 * (int64_t)k + i] : 0.0;
-        Lc[i] = 0.0;
+        out[i] = regular ? psi[9 * (int64_t)k + i] : T(0);
+        Lc[i] = T(0);
     }
     const int r0 = d.row_ptr[k], r1 = d.row_ptr[k + 1];
     for (int e = r0; e < r1; ++e) {
@@ -2337,22 +2318,22 @@ __global__ void k_adj_fv_gather(Dev<T> d, const T* in, const T* psi, const int32
         if (d.kind[P] == HLBM_NODE_OUTER) continue;
         T gx, gy, cc;
         if (P == k) {
-            gx = gy = 0.0;
+            gx = gy = T(0);
             for (int q = r0 + 1; q < r1; ++q) {
-                gx -= T(d.coef[q].gx);
-                gy -= T(d.coef[q].gy);
+                gx -= d.coef[q].gx;
+                gy -= d.coef[q].gy;
             }
-            cc = T(d.coef[r0].c);
+            cc = d.coef[r0].c;
         } else {
             const Coef<T> c = d.coef[tpos[e]];
-            gx = T(c.gx);
-            gy = T(c.gy);
-            cc = T(c.c);
+            gx = c.gx;
+            gy = c.gy;
+            cc = c.c;
         }
         const T* pp = psi + 9 * (int64_t)P;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            out[j] += dt * ((cx_of(j) * gx + cy_of(j) * gy) - inv * cc) * pp[j];
+            out[j] += dt * ((T(cx_of(j)) * gx + T(cy_of(j)) * gy) - inv * cc) * pp[j];
             Lc[j] += cc * pp[j];
         }
     }
@@ -2362,6 +2343,48 @@ __global__ void k_adj_fv_gather(Dev<T> d, const T* in, const T* psi, const int32
     jfeqT_add(rho, ux, uy, Lc, dt * inv, out);
 #pragma unroll
     for (int j = 0; j < 9; ++j) lcur[9 * (int64_t)k + j] = out[j];
+}
+
+// The FV part of one step's reverse in one cooperative launch: the n
+// sub-steps forward again from sub[0] (every state kept in sub), then their
+// reverse from lPn (the adjoint of the patch after them) to lPm (before
+// them), with grid-wide barriers between the passes.  Every thread runs the
+// same number of node iterations, so the warp sums stay convergent.
+template <typename T>
+__global__ void __launch_bounds__(128) k_adj_fv_all(Dev<T> d, StepArgs a, T* sub, const T* lPn, T* x0, T* x1,
+                                                    T* psi, const int32_t* tpos, T* lsnap, double* par, double* lV,
+                                                    T* lPm) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const int n = d.n, ns = d.n_sub;
+    const int nth = gridDim.x * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rec = (int64_t)kRec * n;
+    for (int m = 0; m < ns; ++m) {
+        T U, V;
+        wall_velocity(d, a, m, U, V);
+        for (int P = gtid; P < n; P += nth) fv_node(d, sub + m * rec, sub + (m + 1) * rec, P, m, U, V);
+        grid.sync();
+    }
+    T l_inv = T(0);
+    double l_kneq = 0.0;
+    const T* lnext = lPn;
+    for (int m = ns - 1; m >= 0; --m) {
+        const T* in = sub + m * rec;
+        T l_v = T(0);
+        for (int base = 0; base < n; base += nth) {
+            const int P = base + gtid;
+            if (P < n) adj_psi_node(d, a, in, m, lnext, psi, lsnap, P, l_inv, l_kneq, l_v);
+        }
+        warp_atomic_add(lV + (int64_t)a.t * ns + m, double(l_v));
+        grid.sync();
+        T* lcur = (m & 1) ? x1 : x0;
+        for (int k = gtid; k < n; k += nth) adj_gather_node(d, in, psi, tpos, lcur, k);
+        grid.sync();
+        lnext = lcur;
+    }
+    for (int64_t i = gtid; i < 9 * (int64_t)n; i += nth) lPm[i] = lnext[i];
+    warp_atomic_add(par + 1, double(l_inv));
+    warp_atomic_add(par + 3, l_kneq);
 }
 
 // Reverse of the outer nodes' feed: snap[0] bilinear from the window state
@@ -2622,15 +2645,17 @@ void launch_adj_force(const Dev<T>& d, double lamF, T* lP, cudaStream_t s) {
     if (d.nseg > 0) k_adj_force<T><<<(d.nseg + 127) / 128, 128, 0, s>>>(d, lamF, lP);
 }
 template <typename T>
-void launch_adj_fv_fwd(const Dev<T>& d, const StepArgs& a, const T* in, T* out, int m, cudaStream_t s) {
-    k_adj_fv_fwd<T><<<(d.n + 63) / 64, 64, 0, s>>>(d, a, in, out, m);
-}
-template <typename T>
-void launch_adj_fv_rev(const Dev<T>& d, const StepArgs& a, const T* in, int m, const T* lnext, T* psi,
-                       const int32_t* tpos, T* lcur, T* lsnap, double* par, double* lV, cudaStream_t s) {
-    // the patch is small next to the GPU: 64-thread blocks spread it over more SMs
-    k_adj_fv_psi<T><<<(d.n + 63) / 64, 64, 0, s>>>(d, a, in, m, lnext, psi, lsnap, par, lV);
-    k_adj_fv_gather<T><<<(d.n + 63) / 64, 64, 0, s>>>(d, in, psi, tpos, lcur);
+cudaError_t launch_adj_fv(const Dev<T>& d, const StepArgs& a, T* sub, const T* lPn, T* x0, T* x1, T* psi,
+                          const int32_t* tpos, T* lsnap, double* par, double* lV, T* lPm, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_adj_fv_all<T>, 128, 0);
+    const int blocks = std::max(1, std::min((d.n + 127) / 128, std::max(per, 1) * sms));
+    Dev<T> dd = d;
+    StepArgs aa = a;
+    void* args[] = {&dd, &aa, &sub, &lPn, &x0, &x1, &psi, &tpos, &lsnap, &par, &lV, &lPm};
+    return cudaLaunchCooperativeKernel((const void*)k_adj_fv_all<T>, dim3(blocks), dim3(128), args, 0, s);
 }
 template <typename T>
 void launch_adj_feed(const Dev<T>& d, const StepArgs& a, const T* lsnap, T* lSo, T* lSn, double* lY,
@@ -2681,9 +2706,8 @@ void launch_adj_refill(const Dev<T>& d, const StepArgs& a, const T* lPm, T* lP0,
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \
     template void launch_patch_macro<T>(const Dev<T>&, double*, double*, double*, double*, cudaStream_t);    \
     template void launch_adj_force<T>(const Dev<T>&, double, T*, cudaStream_t);                               \
-    template void launch_adj_fv_fwd<T>(const Dev<T>&, const StepArgs&, const T*, T*, int, cudaStream_t);      \
-    template void launch_adj_fv_rev<T>(const Dev<T>&, const StepArgs&, const T*, int, const T*, T*,            \
-                                       const int32_t*, T*, T*, double*, double*, cudaStream_t);               \
+    template cudaError_t launch_adj_fv<T>(const Dev<T>&, const StepArgs&, T*, const T*, T*, T*, T*,            \
+                                          const int32_t*, T*, double*, double*, T*, cudaStream_t);            \
     template void launch_adj_feed<T>(const Dev<T>&, const StepArgs&, const T*, T*, T*, double*, cudaStream_t); \
     template void launch_adj_stream<T>(const Dev<T>&, const StepArgs&, const T*, const T*, T*, double*,        \
                                        cudaStream_t);                                                         \
