@@ -365,7 +365,9 @@ int hlbm_sweep_fv_time(hlbm_sweep_t* w, int64_t nsteps, double* fv_ms);
  * each lattice step runs their FV sub-steps in one cooperative launch of the
  * tensor-memory kernel (each solver keeps its own tables, counters and
  * buffers).  Solvers with outer_fv = 1 or a forced fv_kernel stay alone.
- * enable = 0 undoes it (default tiling).  n_packs (may be NULL) receives
+ * A group whose tiles the tensor-memory kernel cannot hold even with more,
+ * smaller tiles stays unpacked.  enable = 0 undoes it (the tuner's tiling,
+ * or the default one before hlbm_sweep_tune).  n_packs (may be NULL) receives
  * the number of packs.  Results do not change: a node's arithmetic does not
  * depend on its tile or launch.  hlbm_sweep_tune after this call undoes it. */
 int hlbm_sweep_pack(hlbm_sweep_t* w, int32_t enable, int32_t* n_packs);

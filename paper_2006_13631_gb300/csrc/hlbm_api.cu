@@ -1617,6 +1617,12 @@ int inst_retile(hlbm* h, int tiles, bool tmem_only = false) {
     return h->dtype != HLBM_F64 ? build_tiles<float>(h, tiles, tmem_only) : build_tiles<double>(h, tiles, tmem_only);
 }
 
+// the tile count of solver i for the tuner's pick (0, the default, before tuning)
+int tuned_tiles(const hlbm_sweep* w, int i) {
+    const int c = w->tile_nodes[i];
+    return c > 0 ? (w->inst[i]->patch.n_nodes + c - 1) / c : 0;
+}
+
 // The FV sub-steps of pack p's instances in one cooperative launch of the
 // tensor-memory kernel on the sweep's FV stream.
 template <typename T>
@@ -2882,15 +2888,33 @@ int hlbm_sweep_pack(hlbm_sweep_t* w, int32_t enable, int32_t* n_packs) {
             }
             bool ok = tsum <= sms;
             for (size_t q = 0; q < g.size() && ok && rc == HLBM_OK; ++q) {
-                rc = inst_retile(w->inst[g[q]], tiles[q], true);
-                ok = rc == HLBM_OK && w->inst[g[q]]->fv_kind == HLBM_FV_TMEM && w->inst[g[q]]->n_tiles == tiles[q];
+                hlbm* h = w->inst[g[q]];
+                // tiles the tensor-memory kernel cannot hold (its shared
+                // memory grows with the tile and its halo) are made smaller,
+                // a quarter more tiles at a time, while the SMs last
+                for (;;) {
+                    rc = inst_retile(h, tiles[q], true);
+                    if (rc != HLBM_EINVAL) break;
+                    const int more = std::max(1, tiles[q] / 4);
+                    if (tsum + more > sms || tiles[q] + more > std::max(1, h->patch.n_nodes / 64)) break;
+                    tiles[q] += more;
+                    tsum += more;
+                }
+                if (rc == HLBM_EINVAL) {
+                    rc = HLBM_OK;
+                    ok = false;
+                    break;
+                }
+                ok = rc == HLBM_OK && h->fv_kind == HLBM_FV_TMEM && h->n_tiles == tiles[q];
             }
             if (rc != HLBM_OK) {
                 w->err = "packing: " + w->inst[g[0]]->err;
                 break;
             }
             if (!ok) {
-                for (int i : g) rc = rc == HLBM_OK ? inst_retile(w->inst[i], 0) : rc;
+                // this group stays unpacked, each solver with its own tiling
+                for (int i : g) rc = rc == HLBM_OK ? inst_retile(w->inst[i], tuned_tiles(w, i)) : rc;
+                if (rc != HLBM_OK) w->err = "packing: " + w->inst[g[0]]->err;
                 continue;
             }
             cudaEvent_t e = nullptr;
@@ -2903,7 +2927,7 @@ int hlbm_sweep_pack(hlbm_sweep_t* w, int32_t enable, int32_t* n_packs) {
             w->packs.push_back(g);
         }
     } else {
-        for (int i = 0; i < n && rc == HLBM_OK; ++i) rc = inst_retile(w->inst[i], 0);
+        for (int i = 0; i < n && rc == HLBM_OK; ++i) rc = inst_retile(w->inst[i], tuned_tiles(w, i));
     }
     if (n_packs) *n_packs = (int32_t)w->packs.size();
     return rc;

@@ -269,64 +269,81 @@ void launch_feed(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 // ----------------------------------------------------------- FV steps
 // n explicit steps of eq. ulbe on interior and wall nodes,
 //   f_P += dt_u sum_k [ (c_i . g_Pk) f_k - (C_Pk / tau_u) (f_k - f_k^eq) ],
-// evaluated as dt_u [ c_ix Gx_i + c_iy Gy_i - (Cf_i - f^eq_i(Q)) / tau_u ]
-// with Gx_i = sum_k gx_Pk f'_k,i, Cf_i = sum_k C_Pk f'_k,i, Q = sum_k C_Pk q_k
-// (the deviations drop out of the streaming sum because sum_k g_Pk = 0).
+// evaluated as dt_u [ S_i - (Cf_i - f^eq_i(Q)) / tau_u ]
+// with S_i = sum_{k != P} (c_i . g_Pk) (f'_k,i - f'_P,i),
+// Cf_i = sum_k C_Pk f'_k,i, Q = sum_k C_Pk q_k (the deviations drop out of
+// the streaming sum because sum_k g_Pk = 0).
 // Wall nodes then take the lamina velocity: f += f^eq(rho, U) - f^eq(rho, u).
 // Outer nodes take the lattice state, linear in time at theta = (m+1)/n:
 //   f = f^eq(rho, u) + (1 - 1/(2 tau_s)) f^neq   (eq. postcollision2_u).
 // The FV update of one node (eq. ulbe), shared by both FV kernels so that
 // the result of a node does not depend on the kernel or the tiling: the
-// off-diagonal entries k != P in row order, then the pivot with
-// g_PP = -sum_k g_Pk (exact zero row sum).
+// off-diagonal entries k != P in row order, then the pivot.  With the
+// exact zero row sum g_PP = -sum_k g_Pk the streaming sums are written
+// S_i = sum_{k != P} (c_i . g_Pk) (f_k,i - f_P,i): the same number in exact
+// arithmetic, but the differences are small next to f_k, so that in FP32 the
+// products no longer round at the scale of |g| |f| (|g| ~ 1/h, h down to 0.1
+// at the wall).  c_i . g_Pk is gx, gy, gx + gy or gx - gy up to its sign.
 template <typename T>
 struct FvAcc {
-    T Gx[9], Gy[9], Cf[9], Z[3];
-    T gpx, gpy;
+    T S[9], Cf[9], Z[3];  // S[0] stays 0 (c_0 = 0)
 };
 
 template <typename T>
 __device__ __forceinline__ void fv_acc_init(FvAcc<T>& a) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) a.Gx[i] = a.Gy[i] = a.Cf[i] = T(0);
+    for (int i = 0; i < 9; ++i) a.S[i] = a.Cf[i] = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) a.Z[j] = T(0);
-    a.gpx = a.gpy = T(0);
 }
 
+// entry (g_Pk, C_Pk) of row P with the neighbour's state f, z; fP is the
+// pivot's state
 template <typename T>
-__device__ __forceinline__ void fv_acc_entry(FvAcc<T>& a, T gx, T gy, T c, const T (&f)[9], const T (&z)[3]) {
-    a.gpx -= gx;
-    a.gpy -= gy;
+__device__ __forceinline__ void fv_acc_entry(FvAcc<T>& a, T gx, T gy, T c, const T (&f)[9], const T (&z)[3],
+                                             const T (&fP)[9]) {
+    const T gp = gx + gy, gm = gx - gy;
+    a.S[1] += gx * (f[1] - fP[1]);
+    a.S[2] += gy * (f[2] - fP[2]);
+    a.S[3] -= gx * (f[3] - fP[3]);
+    a.S[4] -= gy * (f[4] - fP[4]);
+    a.S[5] += gp * (f[5] - fP[5]);
+    a.S[6] -= gm * (f[6] - fP[6]);
+    a.S[7] -= gp * (f[7] - fP[7]);
+    a.S[8] += gm * (f[8] - fP[8]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if (cx_of(i) != 0) a.Gx[i] += gx * f[i];
-        if (cy_of(i) != 0) a.Gy[i] += gy * f[i];
-        a.Cf[i] += c * f[i];
-    }
+    for (int i = 0; i < 9; ++i) a.Cf[i] += c * f[i];
 #pragma unroll
     for (int k = 0; k < 3; ++k) a.Z[k] += c * z[k];
 }
 
+// The update of eq. ulbe from the sums.  The collision sums Cf_i - ceq_i
+// carry no mass and no momentum in exact arithmetic (ceq is built from the
+// moments of Cf); their rounding residues m0 = sum_i n_i, m = sum_i c_i n_i
+// are removed by subtracting w_i (m0 + 3 c_i.m), which leaves exact values
+// unchanged and stops the residues from acting, sub-step after sub-step, as
+// spurious sources of mass and momentum.
 template <typename T>
 __device__ __forceinline__ void fv_acc_finish(const Dev<T>& d, FvAcc<T>& a, T cP, const T (&fP)[9], const T (&zP)[3],
                                               T (&fn)[9]) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if (cx_of(i) != 0) a.Gx[i] += a.gpx * fP[i];
-        if (cy_of(i) != 0) a.Gy[i] += a.gpy * fP[i];
-        a.Cf[i] += cP * fP[i];
-    }
+    for (int i = 0; i < 9; ++i) a.Cf[i] += cP * fP[i];
 #pragma unroll
     for (int k = 0; k < 3; ++k) a.Z[k] += cP * zP[k];
     T ceq[9];
     ceq_of(a.Cf, a.Z, ceq);
+    T nq[9], m0 = T(0), mx = T(0), my = T(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        T s = -(a.Cf[i] - ceq[i]) * d.inv_tau_u;
-        if (cx_of(i) != 0) s += T(cx_of(i)) * a.Gx[i];
-        if (cy_of(i) != 0) s += T(cy_of(i)) * a.Gy[i];
-        fn[i] = fP[i] + d.dt_u * s;
+        nq[i] = a.Cf[i] - ceq[i];
+        m0 += nq[i];
+        mx += T(cx_of(i)) * nq[i];
+        my += T(cy_of(i)) * nq[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        nq[i] -= w_of<T>(i) * (m0 + T(3) * (T(cx_of(i)) * mx + T(cy_of(i)) * my));
+        fn[i] = fP[i] + d.dt_u * (a.S[i] - nq[i] * d.inv_tau_u);
     }
 }
 
@@ -382,7 +399,7 @@ __device__ __forceinline__ void fv_node(const Dev<T>& d, const T* __restrict__ i
 #pragma unroll
                     for (int j = 0; j < 3; ++j) z[j] = rec[9 + j];
                 }
-                fv_acc_entry(acc, c.gx, c.gy, c.c, f, z);
+                fv_acc_entry(acc, c.gx, c.gy, c.c, f, z, fn);
             }
             T fP[9], zP[3];
 #pragma unroll
@@ -393,6 +410,12 @@ __device__ __forceinline__ void fv_node(const Dev<T>& d, const T* __restrict__ i
         store_rec(out + (int64_t)kRec * P, fn, d.rho0);
         return;
     }
+    T fP[9], zP[3];
+    const T* own = in + (int64_t)kRec * P;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fP[i] = own[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) zP[j] = own[9 + j];
     FvAcc<T> acc;
     fv_acc_init(acc);
     const int r0 = d.row_ptr[P], r1 = d.row_ptr[P + 1];
@@ -404,14 +427,8 @@ __device__ __forceinline__ void fv_node(const Dev<T>& d, const T* __restrict__ i
         for (int i = 0; i < 9; ++i) f[i] = rec[i];
 #pragma unroll
         for (int j = 0; j < 3; ++j) z[j] = rec[9 + j];
-        fv_acc_entry(acc, c.gx, c.gy, c.c, f, z);
+        fv_acc_entry(acc, c.gx, c.gy, c.c, f, z, fP);
     }
-    T fP[9], zP[3];
-    const T* own = in + (int64_t)kRec * P;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fP[i] = own[i];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) zP[j] = own[9 + j];
     fv_acc_finish(d, acc, d.coef[r0].c, fP, zP, fn);
     if (kind == HLBM_NODE_WALL) fv_wall(d, U, V, fn);
     store_rec(out + (int64_t)kRec * P, fn, d.rho0);
@@ -643,6 +660,20 @@ __device__ __forceinline__ void read_rec12(const T* r, T (&f)[9], T (&z)[3]) {
     f[8] = c.x, z[0] = c.y, z[1] = c.z, z[2] = c.w;
 }
 
+// f'[0..8] of a record, and its z terms on their own (the pivot of a row is
+// read before its entries for the gradient differences, its z only at the end)
+template <typename T>
+__device__ __forceinline__ void read_rec9(const T* r, T (&f)[9]) {
+    const Vec4<T> a = ld4(r), b = ld4(r + 4);
+    f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w;
+    f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+    f[8] = r[8];
+}
+template <typename T>
+__device__ __forceinline__ void read_z3(const T* r, T (&z)[3]) {
+    z[0] = r[9], z[1] = r[10], z[2] = r[11];
+}
+
 template <typename T>
 __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned char* sm, const TileSmem& L, int r,
                                              T (&fn)[9]) {
@@ -651,6 +682,8 @@ __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned cha
     const T* halo = reinterpret_cast<const T*>(sm + L.halo) - (size_t)kSR * cap;
     const T* ec = reinterpret_cast<const T*>(sm + L.ecoef);
     const uint16_t* ecol = reinterpret_cast<const uint16_t*>(sm + L.ecol);
+    T fP[9], zP[3];
+    read_rec9(own + (size_t)kSR * r, fP);
     FvAcc<T> acc;
     fv_acc_init(acc);
     const int ne = reinterpret_cast<const uint8_t*>(sm + L.cnt)[r];  // off-diagonal entries of the row
@@ -659,10 +692,9 @@ __device__ __forceinline__ void fv_node_tile(const Dev<T>& d, const unsigned cha
         const int col = ecol[e];
         T f[9], z[3];
         read_rec12((col < cap ? own : halo) + (size_t)kSR * col, f, z);
-        fv_acc_entry(acc, ec[e], ec[(roff + j) * cap + r], ec[(2 * roff + j) * cap + r], f, z);
+        fv_acc_entry(acc, ec[e], ec[(roff + j) * cap + r], ec[(2 * roff + j) * cap + r], f, z, fP);
     }
-    T fP[9], zP[3];
-    read_rec12(own + (size_t)kSR * r, fP, zP);
+    read_z3(own + (size_t)kSR * r, zP);
     fv_acc_finish(d, acc, reinterpret_cast<const T*>(sm + L.cpp)[r], fP, zP, fn);
 }
 
@@ -705,7 +737,7 @@ __device__ __noinline__ void fv_outer_sums_tile(const Dev<T>& d, const unsigned 
                 read_rec12(halo + (size_t)kSR * (col - cap), f, z);
             }
         }
-        fv_acc_entry(acc, ec[e], ec[(roff + j) * cap + r], ec[(2 * roff + j) * cap + r], f, z);
+        fv_acc_entry(acc, ec[e], ec[(roff + j) * cap + r], ec[(2 * roff + j) * cap + r], f, z, fn);
     }
     T fP[9], zP[3];
 #pragma unroll
@@ -1044,6 +1076,8 @@ __device__ __forceinline__ void fv_tmem_node(const Dev<T>& d, const unsigned cha
     const int ne = (valid && kind != HLBM_NODE_OUTER) ? (int)hdr[2] : 0;
     const int nem = __reduce_max_sync(0xffffffffu, (unsigned)ne);
     T fn[9];
+    T fP[9] = {};
+    if (valid && kind != HLBM_NODE_OUTER) read_rec9(cur + (size_t)kSR * r, fP);
     FvAcc<T> acc;
     fv_acc_init(acc);
     const T* halo = reinterpret_cast<const T*>(sm + L.halo) - (size_t)kSR * cap;
@@ -1056,7 +1090,7 @@ __device__ __forceinline__ void fv_tmem_node(const Dev<T>& d, const unsigned cha
         if (j < ne) {
             T f[9], z[3];
             read_rec12((col < cap ? cur : halo) + (size_t)kSR * col, f, z);
-            fv_acc_entry(acc, gx, gy, c, f, z);
+            fv_acc_entry(acc, gx, gy, c, f, z, fP);
         }
     }
     if (!valid) return;
@@ -1064,8 +1098,8 @@ __device__ __forceinline__ void fv_tmem_node(const Dev<T>& d, const unsigned cha
         const int q = reinterpret_cast<const int16_t*>(sm + L.omap)[r];
         fv_outer_from(d, reinterpret_cast<const T*>(sm + L.osnap) + kSnap * q, 1, m, fn);
     } else {
-        T fP[9], zP[3];
-        read_rec12(cur + (size_t)kSR * r, fP, zP);
+        T zP[3];
+        read_z3(cur + (size_t)kSR * r, zP);
         fv_acc_finish(d, acc, cP, fP, zP, fn);
         if (kind == HLBM_NODE_WALL) {
             const T* uv = reinterpret_cast<const T*>(sm + L.uv);
@@ -1451,6 +1485,8 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
                                           T* nxt, uint32_t tslot, bool valid, int x, int m, T* gout, bool out) {
     constexpr int EW = kDeepEntryWords<T>;
     const int8_t kind = valid ? reinterpret_cast<const int8_t*>(sm + L.kind)[x] : (int8_t)HLBM_NODE_OUTER;
+    T fP[9] = {};
+    if (valid && kind != HLBM_NODE_OUTER) read_rec9(cur + (size_t)kSR * x, fP);
     FvAcc<T> acc;
     fv_acc_init(acc);
     T cP;
@@ -1469,7 +1505,7 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
             if (j < ne) {
                 T f[9], z[3];
                 read_rec12(cur + (size_t)kSR * (int)e[3], f, z);
-                fv_acc_entry(acc, __uint_as_float(e[0]), __uint_as_float(e[1]), __uint_as_float(e[2]), f, z);
+                fv_acc_entry(acc, __uint_as_float(e[0]), __uint_as_float(e[1]), __uint_as_float(e[2]), f, z, fP);
             }
         }
     } else {
@@ -1487,7 +1523,7 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
                 deep_entry<T, H>(v, EW * (j + 1), gx, gy, c, col);
                 T f[9], z[3];
                 read_rec12(cur + (size_t)kSR * col, f, z);
-                fv_acc_entry(acc, gx, gy, c, f, z);
+                fv_acc_entry(acc, gx, gy, c, f, z, fP);
             }
         }
         __syncwarp();
@@ -1500,7 +1536,7 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
                 deep_entry<T, H>(v, EW * (j - E0), gx, gy, c, col);
                 T f[9], z[3];
                 read_rec12(cur + (size_t)kSR * col, f, z);
-                fv_acc_entry(acc, gx, gy, c, f, z);
+                fv_acc_entry(acc, gx, gy, c, f, z, fP);
             }
         }
     }
@@ -1510,8 +1546,8 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
         const int q = reinterpret_cast<const int16_t*>(sm + L.omap)[x];
         fv_outer_from(d, reinterpret_cast<const T*>(sm + L.osnap) + kSnap * q, 1, m, fn);
     } else {
-        T fP[9], zP[3];
-        read_rec12(cur + (size_t)kSR * x, fP, zP);
+        T zP[3];
+        read_z3(cur + (size_t)kSR * x, zP);
         fv_acc_finish(d, acc, cP, fP, zP, fn);
         if (kind == HLBM_NODE_WALL) {
             const T* uv = reinterpret_cast<const T*>(sm + L.uv);

@@ -127,6 +127,40 @@ def test_sweep_smallest_study_instance_matches_oracle():
     sw.close()
 
 
+def test_pack_of_the_largest_study_patches_runs_and_changes_nothing():
+    """The study's L = 64 instances (about 100k-node patches) after the
+    tuner: their groups either pack with tiles the tensor-memory kernel can
+    hold or stay unpacked with the tuned tiles; packing never fails and the
+    results equal those of the same solvers stepped one by one."""
+    from paper_2006_13631_gb300 import Solver, Sweep
+
+    ws = [w for w in inputs.sweep_workloads() if w.L == 64.0][:4]
+    assert len(ws) == 4
+    meshes = [w.mesh() for w in ws]
+    alone = [Solver(w, mesh=m) for w, m in zip(ws, meshes)]
+    batch = [Solver(w, mesh=m) for w, m in zip(ws, meshes)]
+    sw = Sweep(batch)
+    sw.tune(trial_steps=1)
+    for s in alone:
+        s.step(4)  # the tuner's four trial steps
+    n_packs = sw.pack()
+    assert 0 <= n_packs <= 2
+    sw.step(3)
+    for s in alone:
+        s.step(3)
+    torch.cuda.synchronize()
+    for a, b in zip(alone, batch):
+        assert a.status == 0 and b.status == 0
+        _same(_state(a), _state(b))
+    assert sw.pack(False) == 0
+    sw.step(1)
+    for s in alone:
+        s.step(1)
+    for a, b in zip(alone, batch):
+        _same(_state(a), _state(b))
+    sw.close()
+
+
 def test_sweep_rejects_bad_arguments():
     from paper_2006_13631_gb300 import HLBMError, Sweep
 
