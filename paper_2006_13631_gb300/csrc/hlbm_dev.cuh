@@ -29,6 +29,27 @@ __host__ __device__ __forceinline__ constexpr T w_of(int i) {
     return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
 }
 
+// Sums over c_i without the zero terms.  IEEE arithmetic does not let the
+// compiler drop 0 * x (x may be infinite or NaN), so the components of c_i
+// are applied by selection: acc + c_ix v, acc + c_iy v and c_i . (x, y)
+// give the same numbers as the products by 0 and +-1 (up to the sign of a
+// zero) in fewer instructions.  i is a compile-time constant wherever these
+// are called in unrolled loops, so the selections fold away.
+template <typename T>
+__device__ __forceinline__ T add_cx(int i, T acc, T v) {
+    return cx_of(i) > 0 ? acc + v : (cx_of(i) < 0 ? acc - v : acc);
+}
+template <typename T>
+__device__ __forceinline__ T add_cy(int i, T acc, T v) {
+    return cy_of(i) > 0 ? acc + v : (cy_of(i) < 0 ? acc - v : acc);
+}
+template <typename T>
+__device__ __forceinline__ T cdot(int i, T x, T y) {
+    if (cx_of(i) == 0) return cy_of(i) == 0 ? T(0) : (cy_of(i) > 0 ? y : -y);
+    const T ax = cx_of(i) > 0 ? x : -x;
+    return cy_of(i) == 0 ? ax : (cy_of(i) > 0 ? ax + y : ax - y);
+}
+
 enum : int8_t { CLS_DISC = 0, CLS_INTERP = 1, CLS_UNUSED = 2 };
 
 // Polls of a neighbour tile's progress counter before an FV wait gives up
@@ -61,8 +82,8 @@ __device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& drho, T&
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         r += f[i];
-        jx += T(cx_of(i)) * f[i];
-        jy += T(cy_of(i)) * f[i];
+        jx = add_cx(i, jx, f[i]);
+        jy = add_cy(i, jy, f[i]);
     }
     drho = r;
     rho = rho0 + r;
@@ -75,9 +96,34 @@ __device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& drho, T&
 // f_i^eq - w_i rho0 = w_i (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2))
 template <typename T>
 __device__ __forceinline__ T feq_dev(int i, T drho, T rho, T ux, T uy) {
-    T cu = T(cx_of(i)) * ux + T(cy_of(i)) * uy;
+    T cu = cdot(i, ux, uy);
     T usq = ux * ux + uy * uy;
     return w_of<T>(i) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+}
+
+// BGK relaxation of a deviation set (eq. LBE's collision with tau_s):
+// out_i = f_i - omega (f_i - f_i^eq), with f_i^eq - w_i rho0 = w_i (G +- H)
+// for the pair i, opp(i) (c_opp = -c_i): G = drho + rho (4.5 (c.u)^2 -
+// 1.5 u^2), H = 3 rho c.u.  The same numbers as feq_dev up to rounding, in
+// fewer operations; the relaxation keeps the form that rounds only the
+// small non-equilibrium part.  rho0 may be given scaled by a power of two
+// together with f.
+template <typename T>
+__device__ __forceinline__ void bgk_dev(const T (&f)[9], T rho0, T omega, T (&out)[9]) {
+    T dr, r, ux, uy;
+    moments_dev(f, rho0, dr, r, ux, uy);
+    const T q = T(-1.5) * (ux * ux + uy * uy);
+    out[0] = f[0] - omega * (f[0] - w_of<T>(0) * (dr + r * q));
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (opp_of(i) < i) continue;  // each pair once, from its lower index
+        const int j = opp_of(i);
+        const T cu = cdot(i, ux, uy);
+        const T G = dr + r * (T(4.5) * cu * cu + q);
+        const T H = r * (T(3) * cu);
+        out[i] = f[i] - omega * (f[i] - w_of<T>(i) * (G + H));
+        out[j] = f[j] - omega * (f[j] - w_of<T>(j) * (G - H));
+    }
 }
 
 // ---------------------------------------------------------------- layout

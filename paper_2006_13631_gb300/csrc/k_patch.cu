@@ -27,8 +27,8 @@ __device__ __forceinline__ void z_of(const T (&f)[9], T rho0, T (&z)[3]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         dr += f[i];
-        jx += T(cx_of(i)) * f[i];
-        jy += T(cy_of(i)) * f[i];
+        jx = add_cx(i, jx, f[i]);
+        jy = add_cy(i, jy, f[i]);
     }
     T inv = T(1) / (rho0 + dr);
     z[0] = jx * jx * inv;
@@ -43,15 +43,18 @@ __device__ __forceinline__ void ceq_of(const T (&Cf)[9], const T (&Z)[3], T (&ce
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         dr += Cf[i];
-        jx += T(cx_of(i)) * Cf[i];
-        jy += T(cy_of(i)) * Cf[i];
+        jx = add_cx(i, jx, Cf[i]);
+        jy = add_cy(i, jy, Cf[i]);
     }
     const T q0 = dr - T(1.5) * (Z[0] + Z[2]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const T cx = T(cx_of(i)), cy = T(cy_of(i));
-        ceq[i] = w_of<T>(i) * (q0 + T(3) * (cx * jx + cy * jy) +
-                               T(4.5) * (cx * cx * Z[0] + T(2) * cx * cy * Z[1] + cy * cy * Z[2]));
+        // (c_i . j) and c_i c_i : Z, i.e. Z0, Z2 or Z0 +- 2 Z1 + Z2
+        const T quad = cx_of(i) == 0 ? (cy_of(i) == 0 ? T(0) : Z[2])
+                                     : (cy_of(i) == 0 ? Z[0]
+                                                      : (cx_of(i) * cy_of(i) > 0 ? Z[0] + T(2) * Z[1]
+                                                                                 : Z[0] - T(2) * Z[1]) + Z[2]);
+        ceq[i] = w_of<T>(i) * (q0 + T(3) * cdot(i, jx, jy) + T(4.5) * quad);
     }
 }
 
@@ -337,12 +340,12 @@ __device__ __forceinline__ void fv_acc_finish(const Dev<T>& d, FvAcc<T>& a, T cP
     for (int i = 0; i < 9; ++i) {
         nq[i] = a.Cf[i] - ceq[i];
         m0 += nq[i];
-        mx += T(cx_of(i)) * nq[i];
-        my += T(cy_of(i)) * nq[i];
+        mx = add_cx(i, mx, nq[i]);
+        my = add_cy(i, my, nq[i]);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        nq[i] -= w_of<T>(i) * (m0 + T(3) * (T(cx_of(i)) * mx + T(cy_of(i)) * my));
+        nq[i] -= w_of<T>(i) * (m0 + T(3) * cdot(i, mx, my));
         fn[i] = fP[i] + d.dt_u * (a.S[i] - nq[i] * d.inv_tau_u);
     }
 }

@@ -11,27 +11,48 @@ namespace hk {
 // Lattice storage.  S = T stores f' as is; __half stores fscale * f' (a
 // power of two, so the scaling is exact), __nv_bfloat16 stores f'.  The
 // arithmetic always runs in T.
+// Element access of lattice storage S holding T values.  ld / st convert
+// (FP16 holds fscale * f', fscale = 1024); the raw forms rd / wr2 skip the
+// scale: kRawScale is the factor between raw and true values, a power of
+// two, so arithmetic on raw values with rho0 scaled by it gives the true
+// results scaled exactly.  wr2 writes elements k and k + 1 (k even).
 template <typename T, typename S>
 struct Store {
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ T ld(const S* p, int64_t i, float) { return p[i]; }
     static __device__ __forceinline__ void st(S* p, int64_t i, T v, float) { p[i] = v; }
+    static __device__ __forceinline__ T rd(const S* p, int k) { return p[k]; }
+    static __device__ __forceinline__ void wr2(S* p, int k, T a, T b) {
+        p[k] = a;
+        p[k + 1] = b;
+    }
 };
 template <>
 struct Store<float, __half> {
+    static constexpr bool kScaled = true;
     static __device__ __forceinline__ float ld(const __half* p, int64_t i, float inv) {
         return __half2float(p[i]) * inv;
     }
     static __device__ __forceinline__ void st(__half* p, int64_t i, float v, float scale) {
         p[i] = __float2half_rn(v * scale);
     }
+    static __device__ __forceinline__ float rd(const __half* p, int k) { return __half2float(p[k]); }
+    static __device__ __forceinline__ void wr2(__half* p, int k, float a, float b) {
+        *reinterpret_cast<__half2*>(p + k) = __floats2half2_rn(a, b);
+    }
 };
 template <>
 struct Store<float, __nv_bfloat16> {
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i, float) {
         return __bfloat162float(p[i]);
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float v, float) {
         p[i] = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ float rd(const __nv_bfloat16* p, int k) { return __bfloat162float(p[k]); }
+    static __device__ __forceinline__ void wr2(__nv_bfloat16* p, int k, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p + k) = __floats2bfloat162_rn(a, b);
     }
 };
 
@@ -224,23 +245,24 @@ __device__ __forceinline__ void collide_store(const Dev<T>& d, const StepArgs& a
     if (inbox && d.cls_cur[b] != CLS_DISC) return;
     int64_t s = (int64_t)y * d.pitch + x;
     S* __restrict__ B = reinterpret_cast<S*>(d.fB);
-    T dr, r, ux, uy;
-    moments_dev(f, d.rho0, dr, r, ux, uy);
-    const T omega = T(1) / d.tau_s;
+    T o[9];
+    bgk_dev(f, d.rho0, T(1) / d.tau_s, o);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        Store<T, S>::st(B, i * d.plane + s, f[i] - omega * (f[i] - feq_dev<T>(i, dr, r, ux, uy)), d.fscale);
+    for (int i = 0; i < 9; ++i) Store<T, S>::st(B, i * d.plane + s, o[i], d.fscale);
     if (inbox) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) d.sbox_new[i * d.bplane + b] = f[i];
     }
 }
 
-// a vector of consecutive storage elements: 4 nodes (2 for FP64), i.e.
-// 16 bytes for FP32 / FP64 and 8 bytes for FP16 / BF16
+// a vector of consecutive storage elements: 4 nodes (16 bytes) for FP32,
+// 2 (16 bytes) for FP64, 4 (8 bytes) for FP16 / BF16.  Measured on the
+// 4096^2 lattice, 8-node 16-byte vectors for the 2-byte types reach 0.57 of
+// the copy bandwidth against 0.77 for these: a thread then computes 8 nodes
+// between its loads, with fewer threads resident to cover the latency.
 template <typename S>
-struct alignas(sizeof(S) == 8 ? 16 : 4 * sizeof(S)) Pack {
-    static constexpr int N = sizeof(S) == 8 ? 2 : 4;
+struct alignas(sizeof(S) == 2 ? 8 : 16) Pack {
+    static constexpr int N = sizeof(S) == 2 ? 4 : 16 / (int)sizeof(S);
     S v[N];
 };
 
@@ -269,85 +291,98 @@ __device__ __forceinline__ S shfl_down1(S v) {
     }
 }
 
+// resident blocks per SM the register budget of k_stream_collide aims at
+template <typename S>
+constexpr int kStreamBlocks = sizeof(S) == 2 ? 8 : 6;
+
 // Pull form of eq. LBE: f_i(x, t+1) = f~_i(x - c_i, t), then BGK relaxation
-// with tau_s.  Each thread owns V consecutive nodes of a row (Pack<S>) and
-// reads each population as one vector load from row y - c_iy;
-// the x - c_ix shift comes from the neighbouring lane (warp shuffle), and
-// the first and last lane of a warp load the one element beyond their
-// vector.  Nodes on the lattice edge take the scalar path with the Sec. 5
-// boundaries (half-way bounce-back walls taking precedence at corners,
-// zero-gradient outflow, or periodic wrap).  Every lane runs the vector
-// loads and shuffles (rows and columns clamped into the buffer); only the
-// nodes of lanes whose whole vector is interior use their results.
+// with tau_s.  Each thread owns the V consecutive nodes of one vector of a
+// row (Pack<S>) and reads each population as one vector load from row
+// y - c_iy; the x - c_ix shift comes from the neighbouring lane (warp
+// shuffle), and the first and last lane of a warp load the one element
+// beyond their vector.  The nine vectors stay in storage form and are
+// converted node by node (FP16 and BF16 at 64 registers, 8 blocks per SM).
+// Nodes on the lattice edge take the scalar path with the Sec. 5 boundaries
+// (half-way bounce-back walls taking precedence at corners, zero-gradient
+// outflow, or periodic wrap).  Every lane runs the vector loads and shuffles
+// (rows and columns clamped into the buffer); only the nodes of lanes whose
+// whole vector is interior use their results.
 template <typename T, typename S>
-__global__ void __launch_bounds__(128) k_stream_collide(Dev<T> d, StepArgs a) {
+__global__ void __launch_bounds__(128, kStreamBlocks<S>) k_stream_collide(Dev<T> d, StepArgs a) {
     constexpr int V = Pack<S>::N;
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int y = blockIdx.y;
     const S* __restrict__ A = reinterpret_cast<const S*>(d.fA);
     const bool interior = x0 >= 1 && x0 + V <= d.nx - 1 && y >= 1 && y <= d.ny - 2;
-    T f[V][9];
+    Pack<S> p[9];
+    S edge[9];  // c_ix = +1: the element left of the vector; -1: the one right of it
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int sy = y - cy_of(i);
         sy = sy < 0 ? 0 : (sy >= d.ny ? d.ny - 1 : sy);
         const int64_t row = i * d.plane + (int64_t)sy * d.pitch;
         const int xv = x0 < d.pitch ? x0 : d.pitch - V;
-        const Pack<S> p = *reinterpret_cast<const Pack<S>*>(A + row + xv);
-        if (cx_of(i) == 0) {
-#pragma unroll
-            for (int k = 0; k < V; ++k) f[k][i] = Store<T, S>::ld(p.v, k, d.finv);
-        } else if (cx_of(i) == 1) {
-            // node x0 + k takes the element at x0 + k - 1
-            S left = shfl_up1(p.v[V - 1]);
-            if (lane == 0) left = A[row + (xv > 0 ? xv - 1 : 0)];
-            f[0][i] = Store<T, S>::ld(&left, 0, d.finv);
-#pragma unroll
-            for (int k = 1; k < V; ++k) f[k][i] = Store<T, S>::ld(p.v, k - 1, d.finv);
-        } else {
-            // node x0 + k takes the element at x0 + k + 1
-            S right = shfl_down1(p.v[0]);
-            if (lane == 31) right = A[row + (xv + V < d.pitch ? xv + V : d.pitch - 1)];
-#pragma unroll
-            for (int k = 0; k < V - 1; ++k) f[k][i] = Store<T, S>::ld(p.v, k + 1, d.finv);
-            f[V - 1][i] = Store<T, S>::ld(&right, 0, d.finv);
+        p[i] = *reinterpret_cast<const Pack<S>*>(A + row + xv);
+        if (cx_of(i) == 1) {
+            edge[i] = shfl_up1(p[i].v[V - 1]);
+            if (lane == 0) edge[i] = A[row + (xv > 0 ? xv - 1 : 0)];
+        } else if (cx_of(i) == -1) {
+            edge[i] = shfl_down1(p[i].v[0]);
+            if (lane == 31) edge[i] = A[row + (xv + V < d.pitch ? xv + V : d.pitch - 1)];
         }
     }
     if (interior) {
-        // BGK for all V nodes, one 16-byte store per population.  Values
-        // written at nodes that are not discretization nodes are never read:
-        // interpolation and newly uncovered nodes are overwritten by eq. 178
-        // before the next pull, unused nodes are never pulled from.
+        // BGK for all V nodes, two at a time on raw storage values, one
+        // vector store per population.  Values written at nodes that are
+        // not discretization nodes are never read: interpolation and newly
+        // uncovered nodes are overwritten by eq. 178 before the next pull,
+        // unused nodes are never pulled from.
+        using St = Store<T, S>;
         S* __restrict__ B = reinterpret_cast<S*>(d.fB);
         const T omega = T(1) / d.tau_s;
+        const T raw = St::kScaled ? T(d.fscale) : T(1);  // raw value = raw * f'
+        const T rho0r = d.rho0 * raw;
+        const unsigned ry = (unsigned)(y - a.by0);
+        const bool row_in_window = ry < (unsigned)d.bh;
         Pack<S> out[9];
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            T dr, r, ux, uy;
-            moments_dev(f[k], d.rho0, dr, r, ux, uy);
+        for (int k = 0; k < V; k += 2) {
+            T o[2][9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
-                Store<T, S>::st(out[i].v, k, f[k][i] - omega * (f[k][i] - feq_dev<T>(i, dr, r, ux, uy)), d.fscale);
+            for (int h = 0; h < 2; ++h) {
+                // node x0 + k + h pulls x0 + k + h - c_ix
+                const int kk = k + h;
+                T f[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (cx_of(i) == 0)
+                        f[i] = St::rd(p[i].v, kk);
+                    else if (cx_of(i) == 1)
+                        f[i] = kk == 0 ? St::rd(&edge[i], 0) : St::rd(p[i].v, kk - 1);
+                    else
+                        f[i] = kk == V - 1 ? St::rd(&edge[i], 0) : St::rd(p[i].v, kk + 1);
+                }
+                bgk_dev(f, rho0r, omega, o[h]);
+                // the pre-collision state of discretization nodes in the window
+                if (row_in_window) {
+                    const unsigned rx = (unsigned)(x0 + kk - a.bx0);
+                    if (rx < (unsigned)d.bw) {
+                        const int64_t b = (int64_t)ry * d.bw + rx;
+                        if (d.cls_cur[b] == CLS_DISC) {
+#pragma unroll
+                            for (int i = 0; i < 9; ++i)
+                                d.sbox_new[i * d.bplane + b] = St::kScaled ? f[i] * T(d.finv) : f[i];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) St::wr2(out[i].v, k, o[0][i], o[1][i]);
         }
         const int64_t s0 = (int64_t)y * d.pitch + x0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) *reinterpret_cast<Pack<S>*>(B + i * d.plane + s0) = out[i];
-        // the pre-collision state of discretization nodes in the window
-        const unsigned ry = (unsigned)(y - a.by0);
-        if (ry < (unsigned)d.bh) {
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const unsigned rx = (unsigned)(x0 + k - a.bx0);
-                if (rx < (unsigned)d.bw) {
-                    const int64_t b = (int64_t)ry * d.bw + rx;
-                    if (d.cls_cur[b] == CLS_DISC) {
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) d.sbox_new[i * d.bplane + b] = f[k][i];
-                    }
-                }
-            }
-        }
     } else {
         for (int k = 0; k < V; ++k) {
             const int x = x0 + k;
