@@ -325,6 +325,22 @@ def run_ours(args):
         status = s.status
         _, fy = s.force()
         finite = bool(np.isfinite(fy).all())
+        # the same solver with the lattice-patch overlap off (each step's
+        # stream-collide whole, before its FV launch): the two kernels timed
+        # apart, for their own rooflines
+        k_iso = max(10, min(args.steps, 100))
+        H.hlbm_set_overlap(s.h, False)
+        s.step(2)
+        torch.cuda.synchronize()
+        s.profile(True)
+        ev0.record(stream)
+        s.step(k_iso)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_iso = ev0.elapsed_time(ev1)
+        phases_iso = s.profile_read()
+        s.profile(False)
+        H.hlbm_set_overlap(s.h, True)
     ms, units = combine_ranks(ms, float((n_disc + n_u) * args.steps), dist, "cuda")
     value = units / (ms / 1e3) / 1e6
     _, units_sub = combine_ranks(ms, float((n_disc + w.n_sub * n_u) * args.steps), dist, "cuda")
@@ -335,15 +351,18 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     bytes_per = 4 if w.dtype == "f32" else 8
     dom = max(phases, key=lambda p: phases[p][0])
-    st_ms, st_n = phases["stream"]
     stream_bytes = 18 * bytes_per * n_disc  # 9 populations read + 9 written per discretization node
     # per step: one launch on a single level; with nested levels the phase
     # also holds the coarser levels' launches and the coupling launches
-    stream_gbs = stream_bytes / (st_ms / args.steps / 1e3) / 1e9 if st_n else None
+    st_ms, st_n = phases_iso["stream"]
+    stream_gbs = stream_bytes / (st_ms / k_iso / 1e3) / 1e9 if st_n else None
     fv_ms, _ = phases["fv"]
+    fv_iso_ms, _ = phases_iso["fv"]
+    overlapped = phases["stream"][0] < 0.5 * st_ms * args.steps / k_iso  # the far lattice ran in the FV launch
     nnz = info["nnz"]
     fv_flop = FV_FLOP_PER_ENTRY * nnz * w.n_sub  # per launch (one lattice step)
     fv_tflops = fv_flop / (fv_ms / args.steps / 1e3) / 1e12 if fv_ms else None
+    fv_iso_tflops = fv_flop / (fv_iso_ms / k_iso / 1e3) / 1e12 if fv_iso_ms else None
     alu_peak, alu_src = alu_peak_tflops(w.dtype, local)
     fv_kernel = {1: "k_fv_steps", 2: "k_fv_tiles", 3: "k_fv_tmem", 4: "k_fv_deep"}.get(info["fv_kernel"], "?")
     prof_key = {"k_fv_tmem": "fv_tmem", "k_fv_deep": "fv_deep"}.get(fv_kernel)
@@ -352,11 +371,16 @@ def run_ours(args):
             "traffic": kernel_traffic(prof_key, w.name) if prof_key else None,
             "peak_source": alu_src, "fv_depth": info.get("fv_depth"),
             "flop_per_launch": fv_flop, "ms_per_launch": fv_ms / args.steps, "dominant_phase": dom,
-            "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases}}
+            "with_next_step_far_lattice": overlapped,
+            "isolated": {"ms_per_launch": fv_iso_ms / k_iso, "achieved": fv_iso_tflops,
+                         "frac": fv_iso_tflops / alu_peak if fv_iso_tflops else None},
+            "phase_ms_per_step": {p: phases[p][0] / args.steps for p in phases},
+            "phase_ms_per_step_overlap_off": {p: phases_iso[p][0] / k_iso for p in phases_iso}}
     roof_stream = {"bound": "hbm", "kernel": "k_stream_collide", "achieved": stream_gbs, "peak": peak, "unit": "GB/s",
                    "frac": stream_gbs / peak if stream_gbs else None,
                    "traffic": kernel_traffic("stream_collide", w.name), "peak_source": peak_kind,
-                   "bytes_per_launch": stream_bytes, "ms_per_launch": st_ms / args.steps if st_n else None}
+                   "bytes_per_launch": stream_bytes, "ms_per_launch": st_ms / k_iso if st_n else None,
+                   "timed": "whole-lattice launches of the overlap-off run"}
     # the whole step against HBM: algorithmic bytes per lattice step of the
     # structured lattice (9 populations read + 9 written per discretization
     # node), the patch (its records and FV rows read once per step, ~112 B
@@ -367,7 +391,9 @@ def run_ours(args):
     roof_step = {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s", "frac": step_gbs / peak,
                  "bytes_per_step": step_bytes, "ms_per_step": ms / args.steps, "peak_source": peak_kind,
                  "bytes_model": "18 x bytes per population x lattice discretization nodes + (112 + 100) B x patch "
-                                "nodes (FP32; doubled at FP64)"}
+                                "nodes (FP32; doubled at FP64)",
+                 "overlap_off": {"ms_per_step": ms_iso / k_iso,
+                                 "frac": step_bytes / (ms_iso / k_iso / 1e3) / 1e9 / peak}}
     launches = sum(v[1] for v in phases.values())
 
     # end to end through the public API from host buffers: creation from

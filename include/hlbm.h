@@ -321,6 +321,18 @@ int hlbm_info(hlbm_t* h, hlbm_info_t* info);
 #define HLBM_FV_MAX_DEPTH 4
 int hlbm_set_fv_depth(hlbm_t* h, int32_t depth);
 
+/* Overlap of the lattice and the patch (enable = 1, the default): with an
+ * FP32 lattice, the deep-tile FV kernel, one lattice level and a prescribed
+ * motion, the FV launch of step t also runs step t+1's stream-collide of
+ * every lattice node outside step t+1's window and the nodes pulling from it
+ * (the only nodes that step t+1's relocation, classification and eq. 178
+ * feed change), on warps of its own; step t+1's stream-collide then covers
+ * that rectangle alone.  The results are the same bits either way.  Across
+ * hlbm_step calls the precomputed part is kept (hlbm_load, hlbm_clear_status
+ * and an injected lattice fault drop it).  enable = 0 runs each step's
+ * stream-collide whole, before its FV launch. */
+int hlbm_set_overlap(hlbm_t* h, int32_t enable);
+
 /* Per-phase device time, measured with CUDA events recorded on the
  * solver's stream around each phase of hlbm_step while profiling is on.
  * hlbm_profile(h, 1) starts recording and clears the totals; (h, 0) stops.

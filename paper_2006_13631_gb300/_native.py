@@ -82,6 +82,7 @@ SIGNATURES = {
     "hlbm_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "hlbm_clear_status": (C.c_int, [C.c_void_p]),
     "hlbm_set_fv_depth": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hlbm_set_overlap": (C.c_int, [C.c_void_p, C.c_int32]),
     "hlbm_inject_fault": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "hlbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hlbm_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),

@@ -84,6 +84,14 @@ struct hlbm {
     // with this tile never releasing its counter and this spin limit
     int inject_stall_tile = -1;
     long inject_spin_limit = 0;
+    // the next step's stream-collide away from the patch, run by the spare
+    // warps of the FP32 deep-tile FV kernel (FarArgs): far_ready when the
+    // current post-collision buffer's successor already holds it outside
+    // far_rect, which the next stream-collide then covers alone
+    int overlap = 1;
+    unsigned* far_next = nullptr;
+    bool far_ready = false;
+    int far_rect[4] = {0, 0, 0, 0};
 
     int64_t t = 0;
     double Xprev = 0, Yprev = 0;
@@ -184,6 +192,17 @@ double rect_dist(double x, double y, double a, double b) {
 void window_origin(const hlbm* h, double cx, double cy, int* bx0, int* by0) {
     *bx0 = (int)std::floor(cx + h->mxmin) - kWindowMargin;
     *by0 = (int)std::floor(cy + h->mymin) - kWindowMargin;
+}
+
+// The lattice nodes a step with its window at (bx0, by0) has to stream
+// after its relocation, classification and eq. 178 feed: the window (the
+// only nodes those touch) and the nodes pulling from it, with the columns
+// widened to multiples of 4 (vector boundaries).  r = {x0, y0, x1, y1}.
+void near_rect(int nx, int ny, int bw, int bh, int bx0, int by0, int r[4]) {
+    r[0] = std::max(0, ((bx0 - 1) / 4) * 4);
+    r[1] = std::max(0, by0 - 1);
+    r[2] = std::min(nx, ((bx0 + bw + 1 + 3) / 4) * 4);
+    r[3] = std::min(ny, by0 + bh + 1);
 }
 
 template <typename T>
@@ -383,7 +402,13 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
             level_step<T>(h, k, s);
             ++nl;
         }
-    launch_stream_collide<T>(d, a, s);
+    int nr[4];
+    near_rect(d.nx, d.ny, d.bw, d.bh, a.bx0, a.by0, nr);
+    if (h->far_ready && std::equal(nr, nr + 4, h->far_rect))
+        launch_stream_collide_rect<T>(d, a, nr[0], nr[1], nr[2], nr[3], s);
+    else
+        launch_stream_collide<T>(d, a, s);
+    h->far_ready = false;
     // restrictions (finest first) and the rings of the levels that just stepped
     for (int k = 0; k < (int)h->lv.size(); ++k)
         nl += level_couple<T>(h, k, t + 1, d.fB, a.bx0, a.by0, false, s) ? 1 : 0;
@@ -397,10 +422,42 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
     return HLBM_OK;
 }
 
+// FarArgs of the next step's stream-collide outside its near rectangle, when
+// the spare warps of the FV kernel can run it: FP32 lattice, deep-tile FV,
+// one lattice level, a prescribed motion (the next window is known)
 template <typename T>
-int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+bool far_args(hlbm* h, const PendingStep& ps, FarArgs<T>& far) {
     Dev<T>& d = dev_of<T>(h);
-    // 5b. n FV sub-steps (eq. ulbe, eq. postcollision2_u)
+    if (!h->overlap || sizeof(T) != 4 || h->dtype != HLBM_F32 || h->fv_kind != HLBM_FV_DEEP || !h->lv.empty() ||
+        h->motion.kind == HLBM_MOTION_INDUCED)
+        return false;
+    double X, Y;
+    motion_pos(h->motion, ps.a.t + 1, &X, &Y);
+    int bx0, by0;
+    window_origin(h, h->patch.x_c + X, h->patch.y_c + Y, &bx0, &by0);
+    if (bx0 < 1 || by0 < 1 || bx0 + d.bw > d.nx - 1 || by0 + d.bh > d.ny - 1) return false;
+    near_rect(d.nx, d.ny, d.bw, d.bh, bx0, by0, h->far_rect);
+    far.src = d.fB;  // the post-collision state at t+1 this step's stream-collide wrote
+    far.dst = d.fA;
+    far.ex0 = h->far_rect[0];
+    far.ey0 = h->far_rect[1];
+    far.ex1 = h->far_rect[2];
+    far.ey1 = h->far_rect[3];
+    far.n_seg = (d.nx + 63) / 64;
+    far.n_chunks = d.ny * far.n_seg;
+    far.next = h->far_next;
+    return true;
+}
+
+template <typename T>
+int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+            bool lookahead = false) {
+    Dev<T>& d = dev_of<T>(h);
+    // 5b. n FV sub-steps (eq. ulbe, eq. postcollision2_u), with the next
+    // step's far stream-collide when lookahead is asked for and possible
+    FarArgs<T> far{};
+    const bool use_far = lookahead && far_args<T>(h, ps, far);
+    if (use_far) cudaMemsetAsync(h->far_next, 0, sizeof(unsigned), s);
     int ev = phase_begin(h, s);
     if (ev0) cudaEventRecord(ev0, s);
     if (h->inject_stall_tile >= 0) {  // one launch only
@@ -408,7 +465,7 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
         d.spin_limit = h->inject_spin_limit;
         h->inject_stall_tile = -1;
     }
-    cudaError_t fe = h->fv_kind == HLBM_FV_DEEP   ? launch_fv_deep<T>(d, ps.a, s)
+    cudaError_t fe = h->fv_kind == HLBM_FV_DEEP   ? launch_fv_deep<T>(d, ps.a, use_far ? &far : nullptr, s)
                      : h->fv_kind == HLBM_FV_TMEM ? launch_fv_tmem<T>(d, ps.a, s)
                      : h->fv_kind == HLBM_FV_SMEM ? launch_fv_smem<T>(d, ps.a, s)
                                                   : launch_fv_persistent<T>(d, ps.a, s);
@@ -416,6 +473,7 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
     d.spin_limit = kSpinLimit;
     if (ev1) cudaEventRecord(ev1, s);
     if (fe != cudaSuccess) return cuda_check(h, fe, "FV sub-step launch");
+    h->far_ready = use_far;
     // the state after the last sub-step is in the record buffer of the last
     // exchange: fu_out when the number of exchanges is odd
     const int n_exch = h->fv_kind == HLBM_FV_DEEP ? (d.n_sub + d.deep_k - 1) / d.deep_k : d.n_sub;
@@ -466,9 +524,12 @@ int step_impl(hlbm* h, int64_t nsteps) {
     for (int64_t k = 0; k < nsteps; ++k) {
         PendingStep ps{};
         int rc = step_lattice<T>(h, h->stream, ps);
-        if (rc == HLBM_OK) rc = step_fv<T>(h, h->stream, ps);
+        if (rc == HLBM_OK) rc = step_fv<T>(h, h->stream, ps, nullptr, nullptr, true);
         if (rc == HLBM_OK) rc = step_finish<T>(h, h->stream, ps);
-        if (rc != HLBM_OK) return rc;
+        if (rc != HLBM_OK) {
+            h->far_ready = false;
+            return rc;
+        }
     }
     return HLBM_OK;
 }
@@ -1143,6 +1204,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     int32_t* d_tlist = upload(h, tlist.data(), tlist.size(), &rc);
     Coef<T>* coefv = (Coef<T>*)dev_alloc(h, (size_t)h->nnz * sizeof(Coef<T>));
     d.abort_flag = (unsigned*)dev_alloc(h, 16);
+    h->far_next = (unsigned*)dev_alloc(h, 16);
     d.snap = (T*)dev_alloc(h, (size_t)24 * std::max(d.n_outer, 1) * sizeof(T));
     d.rtype = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
     d.rdonor = (int32_t*)dev_alloc(h, (size_t)n * sizeof(int32_t));
@@ -1155,7 +1217,7 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     h->force = (double*)dev_alloc(h, (size_t)h->force_cap * 2 * sizeof(double));
     if (rc != HLBM_OK) return rc;
     if (!coefv || !d.snap || !d.rtype || !d.rdonor || !h->status || !h->scratch || !h->force || !d.fcontrib ||
-        !d.abort_flag)
+        !d.abort_flag || !h->far_next)
         return fail(h, HLBM_ENOMEM, "device allocation failed");
     d.coef = coefv;
     d.spin_limit = kSpinLimit;
@@ -2268,6 +2330,13 @@ int hlbm_clear_status(hlbm_t* h) {
     if (e != cudaSuccess) return cuda_check(h, e, "clear status");
     h->fault = 0;
     h->st_pending = false;
+    h->far_ready = false;  // the next stream-collide covers the whole lattice
+    return HLBM_OK;
+}
+
+int hlbm_set_overlap(hlbm_t* h, int32_t enable) {
+    if (!h) return HLBM_EINVAL;
+    h->overlap = enable ? 1 : 0;
     return HLBM_OK;
 }
 
@@ -2281,6 +2350,7 @@ int hlbm_inject_fault(hlbm_t* h, int32_t kind, int64_t arg) {
         return HLBM_OK;
     }
     if (kind == HLBM_FAULT_NAN_LATTICE) {
+        h->far_ready = false;  // the next stream-collide must read the planted value everywhere
         const int nx = h->grid.nx, ny = h->grid.ny;
         if (arg < 0 || arg >= (int64_t)nx * ny) return fail(h, HLBM_EINVAL, "no lattice node %lld", (long long)arg);
         const int64_t pitch = h->dtype != HLBM_F64 ? h->df.pitch : h->dd.pitch;
@@ -2961,6 +3031,7 @@ int hlbm_save(hlbm_t* h, const char* path) {
 
 int hlbm_load(hlbm_t* h, const char* path) {
     if (!h || !path) return HLBM_EINVAL;
+    h->far_ready = false;
     return h->dtype != HLBM_F64 ? load_impl<float>(h, path) : load_impl<double>(h, path);
 }
 

@@ -6,6 +6,8 @@
 // triangles and cells) are taken in FP64 with explicitly rounded operations
 // (__dadd_rn, __dmul_rn, ...) so that they never depend on FMA contraction.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +31,19 @@ __host__ __device__ __forceinline__ constexpr T w_of(int i) {
     return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
 }
 
+// Explicitly rounded operations: the compiler contracts a * b + c into a
+// fused multiply-add at its discretion, and its choice may differ between
+// kernels that inline the same helper; these leave it none, so that a
+// helper gives the same bits in every kernel that calls it.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Sums over c_i without the zero terms.  IEEE arithmetic does not let the
 // compiler drop 0 * x (x may be infinite or NaN), so the components of c_i
 // are applied by selection: acc + c_ix v, acc + c_iy v and c_i . (x, y)
@@ -37,17 +52,17 @@ __host__ __device__ __forceinline__ constexpr T w_of(int i) {
 // are called in unrolled loops, so the selections fold away.
 template <typename T>
 __device__ __forceinline__ T add_cx(int i, T acc, T v) {
-    return cx_of(i) > 0 ? acc + v : (cx_of(i) < 0 ? acc - v : acc);
+    return cx_of(i) > 0 ? add_rn(acc, v) : (cx_of(i) < 0 ? sub_rn(acc, v) : acc);
 }
 template <typename T>
 __device__ __forceinline__ T add_cy(int i, T acc, T v) {
-    return cy_of(i) > 0 ? acc + v : (cy_of(i) < 0 ? acc - v : acc);
+    return cy_of(i) > 0 ? add_rn(acc, v) : (cy_of(i) < 0 ? sub_rn(acc, v) : acc);
 }
 template <typename T>
 __device__ __forceinline__ T cdot(int i, T x, T y) {
     if (cx_of(i) == 0) return cy_of(i) == 0 ? T(0) : (cy_of(i) > 0 ? y : -y);
     const T ax = cx_of(i) > 0 ? x : -x;
-    return cy_of(i) == 0 ? ax : (cy_of(i) > 0 ? ax + y : ax - y);
+    return cy_of(i) == 0 ? ax : (cy_of(i) > 0 ? add_rn(ax, y) : sub_rn(ax, y));
 }
 
 enum : int8_t { CLS_DISC = 0, CLS_INTERP = 1, CLS_UNUSED = 2 };
@@ -81,15 +96,15 @@ __device__ __forceinline__ void moments_dev(const T (&f)[9], T rho0, T& drho, T&
     T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        r += f[i];
+        r = add_rn(r, f[i]);
         jx = add_cx(i, jx, f[i]);
         jy = add_cy(i, jy, f[i]);
     }
     drho = r;
-    rho = rho0 + r;
+    rho = add_rn(rho0, r);
     T inv = T(1) / rho;
-    ux = jx * inv;
-    uy = jy * inv;
+    ux = mul_rn(jx, inv);
+    uy = mul_rn(jy, inv);
 }
 
 // Eq. local_eq minus w_i rho0:
@@ -107,22 +122,23 @@ __device__ __forceinline__ T feq_dev(int i, T drho, T rho, T ux, T uy) {
 // 1.5 u^2), H = 3 rho c.u.  The same numbers as feq_dev up to rounding, in
 // fewer operations; the relaxation keeps the form that rounds only the
 // small non-equilibrium part.  rho0 may be given scaled by a power of two
-// together with f.
+// together with f.  Explicitly rounded: the lattice is collided by more
+// than one kernel, which must agree bit for bit.
 template <typename T>
 __device__ __forceinline__ void bgk_dev(const T (&f)[9], T rho0, T omega, T (&out)[9]) {
     T dr, r, ux, uy;
     moments_dev(f, rho0, dr, r, ux, uy);
-    const T q = T(-1.5) * (ux * ux + uy * uy);
-    out[0] = f[0] - omega * (f[0] - w_of<T>(0) * (dr + r * q));
+    const T q = mul_rn(T(-1.5), fma_rn(ux, ux, mul_rn(uy, uy)));
+    out[0] = fma_rn(-omega, sub_rn(f[0], mul_rn(w_of<T>(0), fma_rn(r, q, dr))), f[0]);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         if (opp_of(i) < i) continue;  // each pair once, from its lower index
         const int j = opp_of(i);
         const T cu = cdot(i, ux, uy);
-        const T G = dr + r * (T(4.5) * cu * cu + q);
-        const T H = r * (T(3) * cu);
-        out[i] = f[i] - omega * (f[i] - w_of<T>(i) * (G + H));
-        out[j] = f[j] - omega * (f[j] - w_of<T>(j) * (G - H));
+        const T G = fma_rn(r, fma_rn(mul_rn(T(4.5), cu), cu, q), dr);
+        const T H = mul_rn(r, mul_rn(T(3), cu));
+        out[i] = fma_rn(-omega, sub_rn(f[i], mul_rn(w_of<T>(i), add_rn(G, H))), f[i]);
+        out[j] = fma_rn(-omega, sub_rn(f[j], mul_rn(w_of<T>(j), sub_rn(G, H))), f[j]);
     }
 }
 
@@ -135,6 +151,22 @@ struct StepArgs {
     int pbx0, pby0; // window of the previous step (previous class and state)
     int first;      // 1 at t == 0
     double v0, v1;  // INDUCED motion: lamina velocity at t and t+1
+};
+
+// The next lattice step's stream-collide outside a rectangle, run by the
+// spare warps of the FV kernel while the FV sub-steps of this step run:
+// the nodes outside [ex0, ex1) x [ey0, ey1) (the next step's window with the
+// pull margin; ex0, ex1 multiples of 4) pull from src (the post-collision
+// state at t+1, written by this step's stream-collide) and write dst, in
+// chunks of 64 consecutive nodes of a row taken from the counter *next.
+template <typename T>
+struct FarArgs {
+    const T* src;
+    T* dst;
+    int ex0, ey0, ex1, ey1;
+    int n_seg;      // chunks per row
+    int n_chunks;   // 0: no lattice work
+    unsigned* next; // zero at the launch
 };
 
 template <typename T>
@@ -230,6 +262,77 @@ struct Dev {
     int motion;
     double A, omega, vx, vy;
 };
+
+// ---------------------------------------------------------------- lattice storage
+// Element access of lattice storage S holding T values.  ld / st convert
+// (FP16 holds fscale * f', fscale = 1024); the raw forms rd / wr2 skip the
+// scale: kRawScale is the factor between raw and true values, a power of
+// two, so arithmetic on raw values with rho0 scaled by it gives the true
+// results scaled exactly.  wr2 writes elements k and k + 1 (k even).
+template <typename T, typename S>
+struct Store {
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ T ld(const S* p, int64_t i, float) { return p[i]; }
+    static __device__ __forceinline__ void st(S* p, int64_t i, T v, float) { p[i] = v; }
+    static __device__ __forceinline__ T rd(const S* p, int k) { return p[k]; }
+    static __device__ __forceinline__ void wr2(S* p, int k, T a, T b) {
+        p[k] = a;
+        p[k + 1] = b;
+    }
+};
+template <>
+struct Store<float, __half> {
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float ld(const __half* p, int64_t i, float inv) {
+        return __half2float(p[i]) * inv;
+    }
+    static __device__ __forceinline__ void st(__half* p, int64_t i, float v, float scale) {
+        p[i] = __float2half_rn(v * scale);
+    }
+    static __device__ __forceinline__ float rd(const __half* p, int k) { return __half2float(p[k]); }
+    static __device__ __forceinline__ void wr2(__half* p, int k, float a, float b) {
+        *reinterpret_cast<__half2*>(p + k) = __floats2half2_rn(a, b);
+    }
+};
+template <>
+struct Store<float, __nv_bfloat16> {
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i, float) {
+        return __bfloat162float(p[i]);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float v, float) {
+        p[i] = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ float rd(const __nv_bfloat16* p, int k) { return __bfloat162float(p[k]); }
+    static __device__ __forceinline__ void wr2(__nv_bfloat16* p, int k, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p + k) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// Pull of population i at lattice node (x, y) from buffer A with the Sec. 5
+// boundaries: half-way bounce-back walls (taking precedence at corners),
+// zero-gradient outflow, or periodic wrap.
+template <typename T, typename S>
+__device__ __forceinline__ T pull_edge(const Dev<T>& d, const S* A, int x, int y, int i) {
+    int sx = x - cx_of(i), sy = y - cy_of(i);
+    if (sx < 0 || sx >= d.nx) {
+        if (d.bc_x == HLBM_BC_PERIODIC)
+            sx = (sx + d.nx) % d.nx;
+        else if (d.bc_x == HLBM_BC_WALL)
+            return Store<T, S>::ld(A, opp_of(i) * d.plane + (int64_t)y * d.pitch + x, d.finv);
+        else
+            sx = x;
+    }
+    if (sy < 0 || sy >= d.ny) {
+        if (d.bc_y == HLBM_BC_PERIODIC)
+            sy = (sy + d.ny) % d.ny;
+        else if (d.bc_y == HLBM_BC_WALL)
+            return Store<T, S>::ld(A, opp_of(i) * d.plane + (int64_t)y * d.pitch + x, d.finv);
+        else
+            sy = y;
+    }
+    return Store<T, S>::ld(A, i * d.plane + (int64_t)sy * d.pitch + sx, d.finv);
+}
 
 // ---------------------------------------------------------------- geometry
 // Barycentric coordinates of q in triangle k (precomputed ax ay x1 y1 x2 y2 det).
@@ -450,6 +553,8 @@ template <typename T> void launch_init_box(const Dev<T>& d, int bx0, int by0, co
 template <typename T> void launch_classify(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_fill(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T> void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T>
+void launch_stream_collide_rect(const Dev<T>& d, const StepArgs& a, int x0, int y0, int x1, int y1, cudaStream_t s);
 template <typename T> void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                                cudaStream_t s);
 // One coupling launch: the fine ring (into ring_dst) from coarse buffer c0
@@ -485,7 +590,8 @@ template <typename T> int fv_deep_tmem_slots();          // computed slots a til
 template <typename T> int fv_deep_row_words();           // words of one row image
 template <typename T> size_t fv_deep_smem_bytes(int slot_cap, int n_sub, int ocap);
 template <typename T> int fv_deep_tile_capacity(size_t smem);
-template <typename T> cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, const FarArgs<T>* far, cudaStream_t s);
 // row images of the computed slots from the CSR matrices: slot i takes row
 // gid[i] with its off-diagonal entries' columns mapped to local slots lcol[i * 7 + j]
 template <typename T> void launch_build_deep_rows(const Dev<T>& d, const int32_t* gid, const int32_t* lcol,

@@ -1374,25 +1374,34 @@ cudaError_t launch_fv_tmem(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 // image per slot (header cP, ne, then per off-diagonal entry gx, gy, C and
 // the local slot of the column; FP64 values take two words).  Slot x is
 // updated by thread x % kDeepThreads, which reads its row image from its
-// own TMEM lane: FP32 runs 1024 threads of two slots and loads a row entry
-// by entry (64 registers), FP64 512 threads of two slots that load a row in
-// two halves.
+// own TMEM lane: FP32 runs 768 FV threads of two slots and loads a row
+// entry by entry (64 registers), FP64 512 threads of two slots that load a
+// row in two halves.  The FP32 block has 256 more threads (8 warps) that run
+// the next lattice step's stream-collide away from the patch (FarArgs)
+// while the FV warps step the patch: the FV work is latency-bound and the
+// lattice work bandwidth-bound, so they share the SM.  On the 4096^2
+// workload 768 FV threads of exactly two slots each also beat 1024 of one
+// or two (0.416 against 0.423 ms per step).
 template <typename T>
-constexpr int kDeepThreads = sizeof(T) == 4 ? 1024 : 512;
+constexpr int kDeepThreads = sizeof(T) == 4 ? 1024 : 512;  // block size
+template <typename T>
+constexpr int kDeepFv = sizeof(T) == 4 ? 768 : 512;  // FV threads: warps 0 .. kDeepFv / 32 - 1
 template <typename T>
 constexpr int kDeepSlotWords = sizeof(T) == 4 ? 32 : 64;  // TMEM columns of one slot
 template <typename T>
-constexpr int kDeepGroups = 128 * (512 / kDeepSlotWords<T>) / kDeepThreads<T>;  // slots per thread
+constexpr int kDeepGroups = 2;  // slots per FV thread
 template <typename T>
 constexpr int kDeepHalf = kDeepSlotWords<T> / 2;  // words per tcgen05.ld of a row
 template <typename T>
 constexpr int kDeepEntryWords = sizeof(T) == 4 ? 4 : 8;
-static_assert(kDeepGroups<float> == 2 && kDeepGroups<double> == 2, "TMEM slots per thread");
+static_assert(kDeepSlotWords<float> * (kDeepGroups<float> * kDeepFv<float> / 128) <= 512 &&
+                  kDeepSlotWords<double> * (kDeepGroups<double> * kDeepFv<double> / 128) <= 512,
+              "row images of all slots within the 512 TMEM columns");
 static_assert(1 + kTmemMaxEntries <= 8, "row image: header and 7 entries");
 
 template <typename T>
 int fv_deep_tmem_slots() {
-    return kDeepGroups<T> * kDeepThreads<T>;
+    return kDeepGroups<T> * kDeepFv<T>;
 }
 template <typename T>
 int fv_deep_row_words() {
@@ -1571,12 +1580,80 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
     }
 }
 
+// One chunk of the next lattice step's stream-collide (FarArgs, FP32
+// storage) on the lattice warps: row y = c / n_seg, nodes [64 seg,
+// 64 seg + 64), two per lane.  The pull and BGK arithmetic of a node is that
+// of k_stream_collide (the same pulled values through bgk_dev; edge nodes
+// through pull_edge), so the results are the same bits.  Every lane of the
+// warp takes part in the loads and shuffles; only lanes whose nodes lie
+// outside the rectangle store.  (Staging the rows in shared memory with
+// cp.async, two chunks per warp, measured slower: the FV tile leaves about
+// 50 KB of shared memory, too little to keep more loads in flight.)
+__device__ __forceinline__ void far_chunk(const Dev<float>& d, const FarArgs<float>& far, int c, int lane) {
+    const int y = c / far.n_seg, seg = c - y * far.n_seg;
+    const int x0 = 64 * seg + 2 * lane;
+    const bool rows_out = y < far.ey0 || y >= far.ey1;
+    if (!rows_out && 64 * seg >= far.ex0 && 64 * seg + 64 <= far.ex1) return;  // the whole chunk inside
+    const bool mine = x0 < d.nx && (rows_out || x0 < far.ex0 || x0 >= far.ex1);
+    const bool interior = x0 >= 1 && x0 + 2 <= d.nx - 1 && y >= 1 && y <= d.ny - 2;
+    const float* __restrict__ A = far.src;
+    float* __restrict__ B = far.dst;
+    const float omega = 1.0f / d.tau_s;
+    float2 p[9];
+    float edge[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sy = y - cy_of(i);
+        sy = sy < 0 ? 0 : (sy >= d.ny ? d.ny - 1 : sy);
+        const int64_t row = i * d.plane + (int64_t)sy * d.pitch;
+        const int xv = x0 < d.pitch ? x0 : d.pitch - 2;
+        p[i] = *reinterpret_cast<const float2*>(A + row + xv);
+        if (cx_of(i) == 1) {
+            edge[i] = __shfl_up_sync(0xffffffffu, p[i].y, 1);
+            if (lane == 0) edge[i] = A[row + (xv > 0 ? xv - 1 : 0)];
+        } else if (cx_of(i) == -1) {
+            edge[i] = __shfl_down_sync(0xffffffffu, p[i].x, 1);
+            if (lane == 31) edge[i] = A[row + (xv + 2 < d.pitch ? xv + 2 : d.pitch - 1)];
+        }
+    }
+    if (!mine) return;
+    if (interior) {
+        float f[9], o0[9], o1[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = cx_of(i) == 0 ? p[i].x : (cx_of(i) == 1 ? edge[i] : p[i].y);
+        bgk_dev(f, d.rho0, omega, o0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = cx_of(i) == 0 ? p[i].y : (cx_of(i) == 1 ? p[i].x : edge[i]);
+        bgk_dev(f, d.rho0, omega, o1);
+        const int64_t s0 = (int64_t)y * d.pitch + x0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(B + i * d.plane + s0) = make_float2(o0[i], o1[i]);
+    } else {
+        for (int k = 0; k < 2; ++k) {
+            const int x = x0 + k;
+            if (x >= d.nx) break;
+            float g[9], o[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = pull_edge<float, float>(d, A, x, y, i);
+            bgk_dev(g, d.rho0, omega, o);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) B[i * d.plane + (int64_t)y * d.pitch + x] = o[i];
+        }
+    }
+}
+
+// the FV warps' barrier (named barrier 1; the lattice warps never join it)
+template <int N>
+__device__ __forceinline__ void fv_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepArgs a, T* g0, T* g1) {
+__global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepArgs a, T* g0, T* g1, FarArgs<T> far) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int abort_sh;
     __shared__ uint32_t tmem_base_sh;
-    constexpr int NT = kDeepThreads<T>, G = kDeepGroups<T>, SW = kDeepSlotWords<T>;
+    constexpr int NT = kDeepFv<T>, BT = kDeepThreads<T>, G = kDeepGroups<T>, SW = kDeepSlotWords<T>;
     const int tile = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
     const int s0 = d.deep_ptr[tile];
     const int32_t* cnt = d.deep_cnt + kDeepCnt * tile;
@@ -1602,8 +1679,8 @@ __global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepAr
     };
     // ---- set-up: wall velocity per sub-step, slot tables, records of every
     // slot at sub-step 0, the outer nodes' feed, the row images
-    for (int m = tid; m < d.n_sub; m += NT) wall_velocity(d, a, m, uv[m], uv[d.n_sub + m]);
-    for (int x = tid; x < n_slot; x += NT) {
+    for (int m = tid; m < d.n_sub; m += BT) wall_velocity(d, a, m, uv[m], uv[d.n_sub + m]);
+    for (int x = tid; x < n_slot; x += BT) {
         const int g = d.deep_gid[s0 + x];
         gid[x] = g;
         kd[x] = d.kind[g];
@@ -1611,7 +1688,7 @@ __global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepAr
         om[x] = -1;
     }
     __syncthreads();
-    for (int x = tid; x < 3 * n_slot; x += NT) {
+    for (int x = tid; x < 3 * n_slot; x += BT) {
         const int sl = x / 3, c = x - 3 * sl;
         const Vec4<T> v = ld4(g0 + (int64_t)kRec * gid[sl] + 4 * c);
         st4(buf0 + (size_t)kSR * sl + 4 * c, v.x, v.y, v.z, v.w);
@@ -1619,17 +1696,18 @@ __global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepAr
     {
         const int o0 = d.deep_optr[tile], on = d.deep_optr[tile + 1] - o0;
         T* osn = reinterpret_cast<T*>(sm + L.osnap);
-        for (int q = tid; q < on; q += NT) om[d.deep_oslot[o0 + q]] = (int16_t)q;
+        for (int q = tid; q < on; q += BT) om[d.deep_oslot[o0 + q]] = (int16_t)q;
         const int64_t no = d.n_outer;
-        for (int x = tid; x < kSnap * on; x += NT) {
+        for (int x = tid; x < kSnap * on; x += BT) {
             const int q = x / kSnap, j = x - kSnap * q;
             osn[x] = d.snap[j * no + d.outer_of[gid[d.deep_oslot[o0 + q]]]];
         }
-        // row images of the computed slots (lanes without one store zeros)
+        // row images of the computed slots (lanes without one store zeros;
+        // FV warps only)
         const int n_comp = cnt[3];
         const uint4* rows = reinterpret_cast<const uint4*>(d.deep_rows) + (int64_t)(SW / 4) * d.deep_rptr[tile];
 #pragma unroll 1
-        for (int j = 0; j < G; ++j) {
+        for (int j = 0; j < G && tid < NT; ++j) {
             const int x = j * NT + tid;
             const bool have = x < n_comp;
             const uint32_t ts = tslot_of(j);
@@ -1647,98 +1725,110 @@ __global__ void __launch_bounds__(kDeepThreads<T>, 1) k_fv_deep(Dev<T> d, StepAr
     __syncthreads();
     tmem_fence_after();
     const unsigned long long base = (unsigned long long)a.t * (unsigned long long)d.n_sub;
-    const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
-    int m = 0;
-    bool aborted = false;
-    for (int b = 0; m < d.n_sub && !aborted; ++b) {
-        const int kb = min(K, d.n_sub - m);
-        const bool final_block = (m + kb == d.n_sub);
-        T* gout = (b & 1) ? g0 : g1;  // the state at the end of block b is exchange b + 1
-        for (int s = 0; s < kb; ++s, ++m) {
-            T* cur = (m & 1) ? buf1 : buf0;
-            T* nxt = (m & 1) ? buf0 : buf1;
-            const bool last = (s == kb - 1);
-            const int cs = cnt[3 + s];
-            int lo = 0;
-            if (s == 0 && b > 0) {
-                // own nodes that read only own nodes, while warp 0 waits for
-                // the neighbour tiles' exchange b and copies the ghost layers
-#pragma unroll
+    if (tid < NT) {
+        const int nb0 = d.tile_nb_ptr[tile], nb1 = d.tile_nb_ptr[tile + 1];
+        int m = 0;
+        bool aborted = false;
+        for (int b = 0; m < d.n_sub && !aborted; ++b) {
+            const int kb = min(K, d.n_sub - m);
+            const bool final_block = (m + kb == d.n_sub);
+            T* gout = (b & 1) ? g0 : g1;  // the state at the end of block b is exchange b + 1
+            for (int s = 0; s < kb; ++s, ++m) {
+                T* cur = (m & 1) ? buf1 : buf0;
+                T* nxt = (m & 1) ? buf0 : buf1;
+                const bool last = (s == kb - 1);
+                const int cs = cnt[3 + s];
+                int lo = 0;
+                if (s == 0 && b > 0) {
+                    // own nodes that read only own nodes, while warp 0 waits for
+                    // the neighbour tiles' exchange b and copies the ghost layers
+    #pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        const int x = j * NT + tid;
+                        const bool v = x < n_a;
+                        if (__any_sync(0xffffffffu, v))
+                            deep_node(d, sm, L, cur, nxt, tslot_of(j), v, x, m, gout, false);
+                    }
+                    if (warp == 0) {
+                        bool ok = true;
+                        for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
+                            const unsigned long long* pc = d.progress + d.tile_nb[e];
+                            long spins = 0;
+                            while (ld_acquire(pc) < base + m) {
+                                if (*(volatile unsigned*)d.abort_flag) {
+                                    ok = false;
+                                    break;
+                                }
+                                if (++spins > d.spin_limit) {
+                                    atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
+                                    atomicExch(d.abort_flag, 1u);
+                                    ok = false;
+                                    break;
+                                }
+                                __nanosleep(32);
+                            }
+                        }
+                        __syncwarp();
+                        ok = __all_sync(0xffffffffu, ok);
+                        if (ok) {
+                            const T* gin = (b & 1) ? g1 : g0;
+                            constexpr int kChunks = kSR * (int)sizeof(T) / 16;
+                            for (int x = tid; x < kChunks * (n_slot - n_own); x += 32) {
+                                const int hs = x / kChunks, c = x - kChunks * hs;
+                                const int sl = n_own + hs;
+                                cp_async16(reinterpret_cast<unsigned char*>(cur + (size_t)kSR * sl) + 16 * c,
+                                           reinterpret_cast<const unsigned char*>(gin + (int64_t)kRec * gid[sl]) + 16 * c);
+                            }
+                        }
+                        cp_async_wait_all();
+                        if (tid == 0 && !ok) abort_sh = 1;
+                    }
+                    fv_bar<NT>();
+                    if (abort_sh) {
+                        aborted = true;
+                        break;
+                    }
+                    // a block of one sub-step ends here: the records of those nodes go
+                    // to the exchange buffer only now, after the neighbours' counters
+                    // were acquired (a neighbour may still have been reading that
+                    // buffer's previous contents, two exchanges back, before)
+                    if (last) {
+                        for (int x = tid; x < n_a; x += NT) {
+                            if (!final_block && !sd[x]) continue;
+                            const T* r = nxt + (size_t)kSR * x;
+                            T* rec = gout + (int64_t)kRec * gid[x];
+                            const Vec4<T> a0 = ld4(r), a1 = ld4(r + 4), a2 = ld4(r + 8);
+                            st4(rec, a0.x, a0.y, a0.z, a0.w);
+                            st4(rec + 4, a1.x, a1.y, a1.z, a1.w);
+                            st4(rec + 8, a2.x, a2.y, a2.z, a2.w);
+                        }
+                    }
+                    lo = n_a;
+                }
+    #pragma unroll
                 for (int j = 0; j < G; ++j) {
                     const int x = j * NT + tid;
-                    const bool v = x < n_a;
+                    const bool v = x >= lo && x < cs;
                     if (__any_sync(0xffffffffu, v))
-                        deep_node(d, sm, L, cur, nxt, tslot_of(j), v, x, m, gout, false);
+                        deep_node(d, sm, L, cur, nxt, tslot_of(j), v, x, m, gout,
+                                  last && x < n_own && (final_block || sd[x]));
                 }
-                if (warp == 0) {
-                    bool ok = true;
-                    for (int e = nb0 + tid; e < nb1 && ok; e += 32) {
-                        const unsigned long long* pc = d.progress + d.tile_nb[e];
-                        long spins = 0;
-                        while (ld_acquire(pc) < base + m) {
-                            if (*(volatile unsigned*)d.abort_flag) {
-                                ok = false;
-                                break;
-                            }
-                            if (++spins > d.spin_limit) {
-                                atomicOr(d.status, HLBM_ST_SYNC_TIMEOUT);
-                                atomicExch(d.abort_flag, 1u);
-                                ok = false;
-                                break;
-                            }
-                            __nanosleep(32);
-                        }
-                    }
-                    __syncwarp();
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (ok) {
-                        const T* gin = (b & 1) ? g1 : g0;
-                        constexpr int kChunks = kSR * (int)sizeof(T) / 16;
-                        for (int x = tid; x < kChunks * (n_slot - n_own); x += 32) {
-                            const int hs = x / kChunks, c = x - kChunks * hs;
-                            const int sl = n_own + hs;
-                            cp_async16(reinterpret_cast<unsigned char*>(cur + (size_t)kSR * sl) + 16 * c,
-                                       reinterpret_cast<const unsigned char*>(gin + (int64_t)kRec * gid[sl]) + 16 * c);
-                        }
-                    }
-                    cp_async_wait_all();
-                    if (tid == 0 && !ok) abort_sh = 1;
-                }
-                __syncthreads();
-                if (abort_sh) {
-                    aborted = true;
-                    break;
-                }
-                // a block of one sub-step ends here: the records of those nodes go
-                // to the exchange buffer only now, after the neighbours' counters
-                // were acquired (a neighbour may still have been reading that
-                // buffer's previous contents, two exchanges back, before)
-                if (last) {
-                    for (int x = tid; x < n_a; x += NT) {
-                        if (!final_block && !sd[x]) continue;
-                        const T* r = nxt + (size_t)kSR * x;
-                        T* rec = gout + (int64_t)kRec * gid[x];
-                        const Vec4<T> a0 = ld4(r), a1 = ld4(r + 4), a2 = ld4(r + 8);
-                        st4(rec, a0.x, a0.y, a0.z, a0.w);
-                        st4(rec + 4, a1.x, a1.y, a1.z, a1.w);
-                        st4(rec + 8, a2.x, a2.y, a2.z, a2.w);
-                    }
-                }
-                lo = n_a;
+                fv_bar<NT>();
             }
-#pragma unroll
-            for (int j = 0; j < G; ++j) {
-                const int x = j * NT + tid;
-                const bool v = x >= lo && x < cs;
-                if (__any_sync(0xffffffffu, v))
-                    deep_node(d, sm, L, cur, nxt, tslot_of(j), v, x, m, gout,
-                              last && x < n_own && (final_block || sd[x]));
+            if (!aborted && !final_block && tid == 0 && tile != d.stall_tile) {
+                __threadfence();
+                st_release(d.progress + tile, base + m);
             }
-            __syncthreads();
         }
-        if (!aborted && !final_block && tid == 0 && tile != d.stall_tile) {
-            __threadfence();
-            st_release(d.progress + tile, base + m);
+    } else if constexpr (sizeof(T) == 4) {
+        // lattice warps: chunks of the next step's stream-collide until none is left
+        const int lane = tid & 31;
+        for (; far.n_chunks > 0;) {
+            int c = 0;
+            if (lane == 0) c = (int)atomicAdd(far.next, 1u);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= far.n_chunks) break;
+            far_chunk(d, far, c, lane);
         }
     }
     // ---- release TMEM (also after an abort: every warp is past its last tcgen05.ld)
@@ -1773,12 +1863,14 @@ int fv_deep_tile_capacity(size_t smem) {
 }
 
 template <typename T>
-cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
+cudaError_t launch_fv_deep(const Dev<T>& d, const StepArgs& a, const FarArgs<T>* far, cudaStream_t s) {
     Dev<T> dd = d;
     StepArgs aa = a;
     T* b0 = (T*)d.fu_in;
     T* b1 = d.fu_out;
-    void* args[] = {&dd, &aa, &b0, &b1};
+    FarArgs<T> fa{};
+    if (far && sizeof(T) == 4) fa = *far;
+    void* args[] = {&dd, &aa, &b0, &b1, &fa};
     const size_t smem = fv_deep_smem_bytes<T>(d.deep_slot_cap, d.n_sub, d.deep_ocap);
     return cudaLaunchCooperativeKernel((const void*)k_fv_deep<T>, dim3(d.n_tiles), dim3(kDeepThreads<T>), args, smem,
                                        s);
@@ -2739,7 +2831,7 @@ void launch_adj_refill(const Dev<T>& d, const StepArgs& a, const T* lPm, T* lP0,
     template int fv_deep_row_words<T>();                                                                      \
     template size_t fv_deep_smem_bytes<T>(int, int, int);                                                     \
     template int fv_deep_tile_capacity<T>(size_t);                                                            \
-    template cudaError_t launch_fv_deep<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                     \
+    template cudaError_t launch_fv_deep<T>(const Dev<T>&, const StepArgs&, const FarArgs<T>*, cudaStream_t);  \
     template void launch_build_deep_rows<T>(const Dev<T>&, const int32_t*, const int32_t*, int64_t, uint32_t*, \
                                             cudaStream_t);                                                    \
     template void launch_force<T>(const Dev<T>&, int64_t, cudaStream_t);                                      \

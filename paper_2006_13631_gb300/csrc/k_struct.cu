@@ -11,51 +11,6 @@ namespace hk {
 // Lattice storage.  S = T stores f' as is; __half stores fscale * f' (a
 // power of two, so the scaling is exact), __nv_bfloat16 stores f'.  The
 // arithmetic always runs in T.
-// Element access of lattice storage S holding T values.  ld / st convert
-// (FP16 holds fscale * f', fscale = 1024); the raw forms rd / wr2 skip the
-// scale: kRawScale is the factor between raw and true values, a power of
-// two, so arithmetic on raw values with rho0 scaled by it gives the true
-// results scaled exactly.  wr2 writes elements k and k + 1 (k even).
-template <typename T, typename S>
-struct Store {
-    static constexpr bool kScaled = false;
-    static __device__ __forceinline__ T ld(const S* p, int64_t i, float) { return p[i]; }
-    static __device__ __forceinline__ void st(S* p, int64_t i, T v, float) { p[i] = v; }
-    static __device__ __forceinline__ T rd(const S* p, int k) { return p[k]; }
-    static __device__ __forceinline__ void wr2(S* p, int k, T a, T b) {
-        p[k] = a;
-        p[k + 1] = b;
-    }
-};
-template <>
-struct Store<float, __half> {
-    static constexpr bool kScaled = true;
-    static __device__ __forceinline__ float ld(const __half* p, int64_t i, float inv) {
-        return __half2float(p[i]) * inv;
-    }
-    static __device__ __forceinline__ void st(__half* p, int64_t i, float v, float scale) {
-        p[i] = __float2half_rn(v * scale);
-    }
-    static __device__ __forceinline__ float rd(const __half* p, int k) { return __half2float(p[k]); }
-    static __device__ __forceinline__ void wr2(__half* p, int k, float a, float b) {
-        *reinterpret_cast<__half2*>(p + k) = __floats2half2_rn(a, b);
-    }
-};
-template <>
-struct Store<float, __nv_bfloat16> {
-    static constexpr bool kScaled = false;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i, float) {
-        return __bfloat162float(p[i]);
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float v, float) {
-        p[i] = __float2bfloat16_rn(v);
-    }
-    static __device__ __forceinline__ float rd(const __nv_bfloat16* p, int k) { return __bfloat162float(p[k]); }
-    static __device__ __forceinline__ void wr2(__nv_bfloat16* p, int k, float a, float b) {
-        *reinterpret_cast<__nv_bfloat162*>(p + k) = __floats2bfloat162_rn(a, b);
-    }
-};
-
 // call f.template operator()<S>() with the lattice storage type of d
 template <typename T, typename F>
 void with_store(const Dev<T>& d, F&& f) {
@@ -212,30 +167,7 @@ void launch_fill(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
 
 // ------------------------------------------------------ stream-collide
 // Pull form of eq. LBE: f_i(x, t+1) = f~_i(x - c_i, t), then BGK relaxation
-// with tau_s.  Boundaries (Sec. 5): half-way bounce-back walls (taking
-// precedence at corners), zero-gradient outflow, or periodic wrap.
-template <typename T, typename S>
-__device__ __forceinline__ T pull_edge(const Dev<T>& d, const S* A, int x, int y, int i) {
-    int sx = x - cx_of(i), sy = y - cy_of(i);
-    if (sx < 0 || sx >= d.nx) {
-        if (d.bc_x == HLBM_BC_PERIODIC)
-            sx = (sx + d.nx) % d.nx;
-        else if (d.bc_x == HLBM_BC_WALL)
-            return Store<T, S>::ld(A, opp_of(i) * d.plane + (int64_t)y * d.pitch + x, d.finv);
-        else
-            sx = x;
-    }
-    if (sy < 0 || sy >= d.ny) {
-        if (d.bc_y == HLBM_BC_PERIODIC)
-            sy = (sy + d.ny) % d.ny;
-        else if (d.bc_y == HLBM_BC_WALL)
-            return Store<T, S>::ld(A, opp_of(i) * d.plane + (int64_t)y * d.pitch + x, d.finv);
-        else
-            sy = y;
-    }
-    return Store<T, S>::ld(A, i * d.plane + (int64_t)sy * d.pitch + sx, d.finv);
-}
-
+// with tau_s (pull_edge: the Sec. 5 boundaries).
 // One lattice node: pull (or take the given pulled values), BGK, store.
 template <typename T, typename S>
 __device__ __forceinline__ void collide_store(const Dev<T>& d, const StepArgs& a, int x, int y, T (&f)[9]) {
@@ -306,15 +238,17 @@ constexpr int kStreamBlocks = sizeof(S) == 2 ? 8 : 6;
 // (half-way bounce-back walls taking precedence at corners, zero-gradient
 // outflow, or periodic wrap).  Every lane runs the vector loads and shuffles
 // (rows and columns clamped into the buffer); only the nodes of lanes whose
-// whole vector is interior use their results.
+// whole vector is interior use their results.  The launch covers the
+// columns [rx0, rx1) of the rows ry0 + blockIdx.y (rx0 a multiple of V).
 template <typename T, typename S>
-__global__ void __launch_bounds__(128, kStreamBlocks<S>) k_stream_collide(Dev<T> d, StepArgs a) {
+__global__ void __launch_bounds__(128, kStreamBlocks<S>)
+    k_stream_collide(Dev<T> d, StepArgs a, int rx0, int ry0, int rx1) {
     constexpr int V = Pack<S>::N;
     const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int y = blockIdx.y;
+    const int x0 = rx0 + (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const int y = ry0 + blockIdx.y;
     const S* __restrict__ A = reinterpret_cast<const S*>(d.fA);
-    const bool interior = x0 >= 1 && x0 + V <= d.nx - 1 && y >= 1 && y <= d.ny - 2;
+    const bool interior = x0 >= 1 && x0 + V <= d.nx - 1 && x0 + V <= rx1 && y >= 1 && y <= d.ny - 2;
     Pack<S> p[9];
     S edge[9];  // c_ix = +1: the element left of the vector; -1: the one right of it
 #pragma unroll
@@ -386,7 +320,7 @@ __global__ void __launch_bounds__(128, kStreamBlocks<S>) k_stream_collide(Dev<T>
     } else {
         for (int k = 0; k < V; ++k) {
             const int x = x0 + k;
-            if (x >= d.nx) break;
+            if (x >= d.nx || x >= rx1) break;
             T g[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) g[i] = pull_edge<T, S>(d, A, x, y, i);
@@ -397,11 +331,18 @@ __global__ void __launch_bounds__(128, kStreamBlocks<S>) k_stream_collide(Dev<T>
 
 template <typename T>
 void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
+    launch_stream_collide_rect(d, a, 0, 0, d.nx, d.ny, s);
+}
+
+// the nodes of [x0, x1) x [y0, y1) (x0 a multiple of 4)
+template <typename T>
+void launch_stream_collide_rect(const Dev<T>& d, const StepArgs& a, int x0, int y0, int x1, int y1, cudaStream_t s) {
+    if (x1 <= x0 || y1 <= y0) return;
     with_store(d, [&]<typename S>() {
         constexpr int V = Pack<S>::N;
-        const int threads_x = (d.nx + V - 1) / V;
-        dim3 grid((threads_x + 127) / 128, d.ny);
-        k_stream_collide<T, S><<<grid, 128, 0, s>>>(d, a);
+        const int threads_x = (x1 - x0 + V - 1) / V;
+        dim3 grid((threads_x + 127) / 128, y1 - y0);
+        k_stream_collide<T, S><<<grid, 128, 0, s>>>(d, a, x0, y0, x1);
     });
 }
 
@@ -570,6 +511,7 @@ void launch_couple(const Dev<T>& d, const Refine& r, const Couple& c, cudaStream
     template void launch_classify<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                      \
     template void launch_fill<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                          \
     template void launch_stream_collide<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                \
+    template void launch_stream_collide_rect<T>(const Dev<T>&, const StepArgs&, int, int, int, int, cudaStream_t); \
     template void launch_struct_macro<T>(const Dev<T>&, double*, double*, double*, cudaStream_t);        \
     template void launch_couple<T>(const Dev<T>&, const Refine&, const Couple&, cudaStream_t);
 HLBM_INST(float)

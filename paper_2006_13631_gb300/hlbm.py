@@ -273,6 +273,10 @@ def hlbm_set_fv_depth(h, depth: int):
     _check(N.load().hlbm_set_fv_depth(h, int(depth)), h)
 
 
+def hlbm_set_overlap(h, enable: bool = True):
+    _check(N.load().hlbm_set_overlap(h, int(bool(enable))), h)
+
+
 def hlbm_clear_status(h):
     _check(N.load().hlbm_clear_status(h), h)
 

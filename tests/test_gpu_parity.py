@@ -375,3 +375,44 @@ def test_parity_induced_motion(dtype, steps, tol_u, tol_rho, tol_y):
     assert abs(info["y"] - y[-1]) < tol_y * abs(w.y0) and abs(info["vy"] - v[-1]) < tol_y * abs(w.y0)
     assert abs(y[-1] - w.y0) > 0.1  # it moved
     assert s.status == 0 and o.status == 0
+
+
+def _exact_state(s):
+    rs, uxs, uys, ru, uxu, uyu = s.fields()
+    tg, dg = s.refill_record()
+    fx, fy = s.force()
+    return dict(rs=rs, uxs=uxs, uys=uys, ru=ru, uxu=uxu, uyu=uyu, cls=s.struct_class(), tg=tg, dg=dg, fx=fx, fy=fy)
+
+
+def test_overlap_of_the_far_lattice_changes_no_bit(tmp_path):
+    """The next step's stream-collide away from the patch, run inside the FV
+    launch (hlbm_set_overlap, on by default), gives the bits of the plain
+    order: over a harmonic motion whose window moves, across single-step
+    calls, and on through a checkpoint written while the precomputed part is
+    pending."""
+    from paper_2006_13631_gb300 import Solver, hlbm_set_overlap
+
+    w = inputs.workload("lamina-small-f32")
+    mesh, rho = w.mesh(), w.rho_init()
+    on = Solver(w, mesh=mesh, rho_init=rho)
+    off = Solver(w, mesh=mesh, rho_init=rho)
+    hlbm_set_overlap(off.h, False)
+    assert on.info()["fv_kernel"] == 4
+    for k in (5, 1, 1, 3, 1, 9):
+        on.step(k)
+    off.step(20)
+    a, b = _exact_state(on), _exact_state(off)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    # a checkpoint taken now (the far part of step 20 is pending in `on`)
+    path = str(tmp_path / "ck.bin")
+    on.save(path)
+    back = Solver(w, mesh=mesh, rho_init=rho)
+    back.load(path)
+    for s in (on, off, back):
+        s.step(7)
+    a, b, c = _exact_state(on), _exact_state(off), _exact_state(back)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+        assert np.array_equal(a[key], c[key]), key
+    assert on.status == 0 and off.status == 0 and back.status == 0
