@@ -192,11 +192,15 @@ _KERNEL_SOURCES = {
     "stream_collide": [("k_struct.cu", "// ------------------------------------------------------ stream-collide",
                         "// ------------------------------------------------------------- readback"),
                        ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
-                        "// ---------------------------------------------------------------- layout")],
+                        "// ---------------------------------------------------------------- layout"),
+                       ("hlbm_dev.cuh", "// ---------------------------------------------------------------- lattice storage",
+                        "// ---------------------------------------------------------------- geometry")],
     "fv_deep": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
                  "// ------------------------------------------------------------- force"),
                 ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
-                 "// ---------------------------------------------------------------- layout")],
+                 "// ---------------------------------------------------------------- layout"),
+                ("hlbm_dev.cuh", "// ---------------------------------------------------------------- lattice storage",
+                 "// ---------------------------------------------------------------- geometry")],
     "fv_tmem": [("k_patch.cu", "// ----------------------------------------------------------- FV steps",
                  "// ------------------------------------------------------------- force"),
                 ("hlbm_dev.cuh", "// ---------------------------------------------------------------- D2Q9",
