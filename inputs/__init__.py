@@ -274,7 +274,7 @@ class Workload:
     u0y: float = 0.0
     lumped: int = 0          # 1: lumped collision matrix C = identity
     outer_fv: int = 0        # 1: outer nodes take eq. 182 with its FV sums
-    fv_kernel: int = 0       # CUDA FV kernel: 0 automatic, 1 global, 2 shared-memory, 3 tensor-memory tiles
+    fv_kernel: int = 0       # CUDA FV kernel: 0 automatic, 1 global, 2 shared-memory, 3 tensor-memory, 4 deep tiles
     # INDUCED motion: m y'' + c y' + k y = F_y (per unit length), y(0) = y0, y'(0) = v0
     mass: float = 1.0
     stiffness: float = 0.0
@@ -286,6 +286,11 @@ class Workload:
     # holds level k-1's node (0, 0) at its node (ox, oy); every level inside
     # another has odd sizes, and bc_x, bc_y belong to the coarsest
     levels: list = field(default_factory=list)
+    # absorbing layer along the outflow sides of the lattice carrying the
+    # domain boundary (the coarsest level): rows deep, strength at the
+    # boundary row; 0 rows = the plain zero-gradient outflow
+    sponge_rows: int = 0
+    sponge_sigma: float = 0.0
     mesh_args: dict = field(default_factory=dict)
 
     def mesh(self) -> PatchMesh:

@@ -57,6 +57,7 @@ class _Params(C.Structure):
         ("lv_ox", C.c_int * MAX_LEVELS), ("lv_oy", C.c_int * MAX_LEVELS),
         ("lv_rho", C.POINTER(C.c_double) * MAX_LEVELS), ("lv_ux", C.POINTER(C.c_double) * MAX_LEVELS),
         ("lv_uy", C.POINTER(C.c_double) * MAX_LEVELS),
+        ("sponge_rows", C.c_int), ("sponge_sigma", C.c_double),
     ]
 
 
@@ -117,7 +118,7 @@ def _declare(L):
                                 C.c_double, dp, dp, dp]
         L.orc_fv_periodic.argtypes = [C.c_int, dp, C.c_int, ip, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int, C.c_int, dp]
-        L.orc_lbgk.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp]
+        L.orc_lbgk.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int, dp]
     return L
 
 
@@ -271,10 +272,12 @@ def theta_semi_analytic(beta, eps):
     return 1.02 + 2.45 * beta ** -0.5 - 1j * (2.49 * beta ** -0.5 + 0.879 * beta ** 0.75 * eps ** 2)
 
 
-def lbgk(f9, bc_x, bc_y, tau_s, n_iter):
+def lbgk(f9, bc_x, bc_y, tau_s, n_iter, sponge_rows=0, sponge_sigma=0.0):
+    """n_iter collide-and-stream steps of the plain lattice (Sec. 3, eq. LBE;
+    Sec. 5 boundaries; R13's absorbing layer when sponge_rows > 0, rho0 = 1)."""
     f = np.ascontiguousarray(f9, dtype=np.float64).copy()
     _, ny, nx = f.shape
-    lib().orc_lbgk(nx, ny, bc_x, bc_y, tau_s, n_iter, _dp(f))
+    lib().orc_lbgk(nx, ny, bc_x, bc_y, tau_s, int(sponge_rows), float(sponge_sigma), n_iter, _dp(f))
     return f
 
 
@@ -308,6 +311,8 @@ class Oracle:
         p.kind = self._keep[3].ctypes.data_as(C.POINTER(C.c_int8))
         p.n_sub, p.lumped, p.motion = w.n_sub, w.lumped, w.motion
         p.outer_fv = int(getattr(w, "outer_fv", 0))
+        p.sponge_rows = int(getattr(w, "sponge_rows", 0))
+        p.sponge_sigma = float(getattr(w, "sponge_sigma", 0.0))
         p.mass, p.stiffness, p.damping = float(w.mass), float(w.stiffness), float(w.damping)
         p.y0, p.v0 = float(w.y0), float(w.v0)
         p.A, p.omega, p.vx, p.vy = w.A, w.omega, w.vx, w.vy

@@ -70,6 +70,15 @@
  *      the post-collision state of the fine node they sit on.  Levels step
  *      coarsest first, restrict finest first, and rebuild their rings on
  *      their own clocks.
+ *  R13 Non-reflecting outflow, the second reading of Sec. 5's unspecified
+ *      outflow (a flag; R5 stays the default): an absorbing layer of N rows
+ *      along each outflow side of the lattice that carries the domain
+ *      boundary.  At a node d rows from the nearest such side (d < N) the
+ *      post-collision populations relax towards the rest state,
+ *      f <- w rho0 + (1 - sigma(d)) (f - w rho0), sigma(d) = sigma_max
+ *      ((N - d)/N)^2, so that waves leaving the domain are damped before
+ *      the zero-gradient copy can reflect them.  Nodes with d >= N are not
+ *      touched.
  */
 #include "hlbm_oracle.h"
 
@@ -512,6 +521,30 @@ static void bgk_collide(const double* f, double tau, double* post) {
     for (int i = 0; i < 9; ++i) post[i] = f[i] - (f[i] - feq[i]) / tau;
 }
 
+/* R13: the factor 1 - sigma(d) of node (x, y), d its distance in rows from
+ * the nearest outflow side; 1 outside the layer */
+static double sponge_keep(int nx, int ny, int bcx, int bcy, int rows, double sigma, int x, int y) {
+    if (rows <= 0 || sigma == 0.0) return 1.0;
+    int d = rows;
+    if (bcy == ORC_BC_OUTFLOW) {
+        d = y < d ? y : d;
+        d = ny - 1 - y < d ? ny - 1 - y : d;
+    }
+    if (bcx == ORC_BC_OUTFLOW) {
+        d = x < d ? x : d;
+        d = nx - 1 - x < d ? nx - 1 - x : d;
+    }
+    if (d >= rows) return 1.0;
+    const double t = (double)(rows - d) / (double)rows;
+    return 1.0 - sigma * t * t;
+}
+
+/* R13 applied to a post-collision set (keep < 1 only inside the layer) */
+static void sponge_apply(double keep, double rho0, double* post) {
+    if (keep == 1.0) return;
+    for (int i = 0; i < 9; ++i) post[i] = W[i] * rho0 + keep * (post[i] - W[i] * rho0);
+}
+
 /* f_i(x, y, t+1) from the post-collision field (pull form of eq. LBE).
  * Sets *bad if the source node is not a computed node. */
 static double pull(int nx, int ny, int bcx, int bcy, const double* post, int64_t N, int x, int y,
@@ -640,6 +673,9 @@ static void level_step(orc_t* o, int k) {
             double f[9], q[9];
             for (int i = 0; i < 9; ++i) f[i] = pull(L->nx, L->ny, bcx, bcy, post, L->N, x, y, i, NULL, &bad);
             bgk_collide(f, tc, q);
+            if (coarsest)
+                sponge_apply(sponge_keep(L->nx, L->ny, bcx, bcy, o->p.sponge_rows, o->p.sponge_sigma, x, y),
+                             o->p.rho0, q);
             for (int i = 0; i < 9; ++i) out[i * L->N + (int64_t)y * L->nx + x] = q[i];
         }
 }
@@ -691,7 +727,8 @@ void orc_level_macro(const orc_t* o, int k, double* rho, double* ux, double* uy)
     }
 }
 
-int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int n_iter, double* f9) {
+int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int sponge_rows, double sponge_sigma, int n_iter,
+             double* f9) {
     int64_t N = (int64_t)nx * ny;
     double* post = malloc((size_t)N * 9 * sizeof(double));
     int bad = 0;
@@ -700,6 +737,9 @@ int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int n_iter, doubl
             double f[9], q[9];
             for (int i = 0; i < 9; ++i) f[i] = f9[i * N + s];
             bgk_collide(f, tau_s, q);
+            /* R13 with rho0 = 1 */
+            sponge_apply(sponge_keep(nx, ny, bc_x, bc_y, sponge_rows, sponge_sigma, (int)(s % nx), (int)(s / nx)), 1.0,
+                         q);
             for (int i = 0; i < 9; ++i) post[i * N + s] = q[i];
         }
         for (int y = 0; y < ny; ++y)
@@ -892,6 +932,9 @@ static void structured_step(orc_t* o, double cx, double cy) {
                 double fl[9];
                 for (int i = 0; i < 9; ++i) fl[i] = f[i * N + s];
                 bgk_collide(fl, o->p.tau_s, post);
+                if (o->p.n_levels == 0)
+                    sponge_apply(sponge_keep(nx, ny, o->p.bc_x, o->p.bc_y, o->p.sponge_rows, o->p.sponge_sigma, x, y),
+                                 o->p.rho0, post);
             }
             for (int i = 0; i < 9; ++i) o->fpost[i * N + s] = post[i];
         }

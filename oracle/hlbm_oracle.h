@@ -67,6 +67,11 @@ typedef struct {
     const double* lv_rho[ORC_MAX_LEVELS];
     const double* lv_ux[ORC_MAX_LEVELS];
     const double* lv_uy[ORC_MAX_LEVELS];
+    /* R13: absorbing layer next to the outflow sides of the lattice that
+     * carries the domain boundary (the coarsest level): sponge_rows > 0
+     * rows deep, strength sponge_sigma at the boundary row (0: none) */
+    int sponge_rows;
+    double sponge_sigma;
 } orc_params_t;
 
 typedef struct orc orc_t;
@@ -130,7 +135,8 @@ int orc_outer_fv(int n_nodes, const double* xy, int n_tris, const int32_t* tri, 
                  double tau_u, double dt_u, int lumped, const double* fin, const double* dstar, double* fout);
 
 /* structured LBGK alone (no patch): n_iter steps of eq. LBE on f9 [9][ny][nx] */
-int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int n_iter, double* f9);
+int orc_lbgk(int nx, int ny, int bc_x, int bc_y, double tau_s, int sponge_rows, double sponge_sigma, int n_iter,
+             double* f9);
 
 #ifdef __cplusplus
 }

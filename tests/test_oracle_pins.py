@@ -780,3 +780,46 @@ def test_levels_zero_disturbance_with_translating_lamina(levels):
         covered, fnx, fny = cov, nx, ny
     r, ux, uy = o.patch_macro()
     assert np.abs(ux - 0.02).max() < 1e-12 and np.abs(r - 1.0).max() < 1e-12
+
+
+def _plane_pulse(ny=240, nx=4, amp=1e-3, width=6.0):
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    y = np.arange(ny)
+    rho = 1.0 + amp * np.exp(-((y - ny / 2) / width) ** 2)
+    return w[:, None, None] * np.tile(rho[None, :, None], (1, 1, nx))
+
+
+def _pulse_energy(f):
+    r = f.sum(axis=0)[:, 0]
+    return float(((r - 1.0) ** 2).sum())
+
+
+def test_absorbing_layer_takes_the_reflection_of_a_plane_acoustic_pulse():
+    """R13 (the non-reflecting reading of Sec. 5's outflow) against what it is
+    for: a plane density pulse at rest splits into two sound waves that leave
+    through the outflow rows.  The plain zero-gradient copy (R5) sends part of
+    them back; 40 rows of the absorbing layer take all but a trace.  The
+    layer leaves the fluid away from it alone, and with sigma = 0 it is the
+    plain scheme bit for bit."""
+    tau = 0.52
+    f0 = _plane_pulse()
+    e0 = _pulse_energy(f0)
+    plain = oracle.lbgk(f0, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, tau, 400)
+    layer = oracle.lbgk(f0, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, tau, 400, 40, 0.1)
+    # both waves have left and come back (c_s t = 231 > 120 rows): the
+    # energy still in the domain is the reflection
+    e_plain, e_layer = _pulse_energy(plain), _pulse_energy(layer)
+    assert e_plain > 1e-2 * e0
+    assert e_layer < 1e-3 * e_plain
+    # before the waves reach the layer (40 rows, fronts at 120 -+ 29 after 50
+    # steps) the middle rows are those of the plain scheme to roundoff
+    p50 = oracle.lbgk(f0, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, tau, 50)
+    l50 = oracle.lbgk(f0, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, tau, 50, 40, 0.1)
+    assert np.abs(p50[:, 60:180] - l50[:, 60:180]).max() < 1e-15
+    # no strength: the plain scheme exactly
+    z = oracle.lbgk(f0, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, tau, 400, 40, 0.0)
+    assert np.array_equal(z, plain)
+    # the rest state stays at rest inside the layer (to the roundoff of the
+    # full-population arithmetic)
+    rest = _plane_pulse(amp=0.0)
+    assert np.abs(oracle.lbgk(rest, inputs.BC_PERIODIC, inputs.BC_OUTFLOW, tau, 30, 40, 0.1) - rest).max() < 1e-15
