@@ -125,6 +125,16 @@ typedef struct {
      * levels[0] first (see hlbm_level_t).  0 = one uniform lattice. */
     int32_t n_levels;
     const hlbm_level_t* levels;
+    /* Non-reflecting outflow (the second reading of Sec. 5's unspecified
+     * outflow; 0 rows = the zero-gradient copy alone): along each outflow
+     * side of the lattice that carries the domain boundary (the coarsest
+     * level), the post-collision populations of the sponge_rows rows next
+     * to it relax towards the rest state, f <- w rho0 + (1 - s(d)) (f -
+     * w rho0) at d rows from the side, s(d) = sponge_sigma ((N - d)/N)^2.
+     * 0 <= sponge_rows < half the lattice side it lies along,
+     * 0 <= sponge_sigma < 1. */
+    int32_t sponge_rows;
+    double sponge_sigma;
 } hlbm_grid_t;
 
 /* Body-fitted triangular patch around the lamina (Sec. 3, Sec. 4).
@@ -425,7 +435,8 @@ int hlbm_theta_gradient(const hlbm_grid_t* grid, const hlbm_patch_t* patch, doub
  * factors 2 (tau_s - 1)/(2 tau_s - 1) and 1 - 1/(2 tau_s)).  fwd_ms and bwd_ms
  * (may be NULL) receive the device time of the checkpointed forward run and
  * of the reverse sweep.  HARMONIC motion, one lattice level, outer_fv = 0,
- * FP64 or FP32 populations (adjoints in FP64).  Device memory: one lattice
+ * no absorbing layer (sponge_rows = 0), FP64 or FP32 populations (adjoints
+ * in the population type, the parameter sums in FP64).  Device memory: one lattice
  * copy per checkpoint and per step of a segment, released before the call
  * returns.  Errors as for hlbm_create (message: hlbm_last_error(NULL)). */
 int hlbm_theta_adjoint(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s, const hlbm_motion_t* motion,

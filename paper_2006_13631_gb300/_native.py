@@ -35,7 +35,8 @@ class hlbm_grid_t(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
                 ("dtype", C.c_int32), ("rho0", C.c_double), ("u0x", C.c_double), ("u0y", C.c_double),
                 ("rho_init", _dp), ("ux_init", _dp), ("uy_init", _dp),
-                ("n_levels", C.c_int32), ("levels", C.POINTER(hlbm_level_t))]
+                ("n_levels", C.c_int32), ("levels", C.POINTER(hlbm_level_t)),
+                ("sponge_rows", C.c_int32), ("sponge_sigma", C.c_double)]
 
 
 class hlbm_patch_t(C.Structure):

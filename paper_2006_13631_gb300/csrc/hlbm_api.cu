@@ -189,6 +189,15 @@ double rect_dist(double x, double y, double a, double b) {
 
 // window of lattice nodes that follows the patch: covers the mesh bounding
 // box at centre (cx, cy) widened by kWindowMargin nodes on every side
+// an absorbing layer reaching half way across the lattice it lies on (the
+// coarsest level with levels)
+bool sponge_too_deep(const hlbm_grid_t* g) {
+    const bool lv = g->n_levels > 0 && g->levels;
+    const int nx = lv ? g->levels[g->n_levels - 1].nx : g->nx, ny = lv ? g->levels[g->n_levels - 1].ny : g->ny;
+    return (g->bc_y == HLBM_BC_OUTFLOW && 2 * g->sponge_rows >= ny) ||
+           (g->bc_x == HLBM_BC_OUTFLOW && 2 * g->sponge_rows >= nx);
+}
+
 void window_origin(const hlbm* h, double cx, double cy, int* bx0, int* by0) {
     *bx0 = (int)std::floor(cx + h->mxmin) - kWindowMargin;
     *by0 = (int)std::floor(cy + h->mymin) - kWindowMargin;
@@ -241,6 +250,7 @@ void level_step(hlbm* h, int k, cudaStream_t s) {
     c.fB = (T*)L.buf[1 - L.cur];
     StepArgs ac{};
     launch_stream_collide<T>(c, ac, s);
+    launch_sponge<T>(c, s);  // the coarsest level's absorbing outflow layer, if any
 }
 
 template <typename T>
@@ -409,6 +419,7 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
     else
         launch_stream_collide<T>(d, a, s);
     h->far_ready = false;
+    nl += launch_sponge<T>(d, s);  // the absorbing outflow layer, if any, on the step's output
     // restrictions (finest first) and the rings of the levels that just stepped
     for (int k = 0; k < (int)h->lv.size(); ++k)
         nl += level_couple<T>(h, k, t + 1, d.fB, a.bx0, a.by0, false, s) ? 1 : 0;
@@ -912,6 +923,9 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
     // every finer level is rebuilt every step, whatever its pull wrote
     d.bc_x = g->n_levels ? HLBM_BC_OUTFLOW : g->bc_x;
     d.bc_y = g->n_levels ? HLBM_BC_OUTFLOW : g->bc_y;
+    // the absorbing layer belongs to the lattice carrying the domain boundary
+    d.sponge_rows = g->n_levels ? 0 : g->sponge_rows;
+    d.sponge_sigma = g->n_levels ? 0.0 : g->sponge_sigma;
     d.rho0 = T(g->rho0);
     d.tau_s = T(h->tau_s);
     d.tau_u = T(h->tau_s - 0.5);
@@ -1166,6 +1180,8 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         const bool coarsest = k == g->n_levels;
         c.bc_x = coarsest ? g->bc_x : HLBM_BC_OUTFLOW;
         c.bc_y = coarsest ? g->bc_y : HLBM_BC_OUTFLOW;
+        c.sponge_rows = coarsest ? g->sponge_rows : 0;
+        c.sponge_sigma = coarsest ? g->sponge_sigma : 0.0;
         const double tau_f = 0.5 + std::ldexp(h->tau_s - 0.5, -(k - 1)), tau_c = 0.5 + std::ldexp(h->tau_s - 0.5, -k);
         c.tau_s = T(tau_c);
         c.bw = c.bh = 0;  // no window: every node of a coarser level is computed
@@ -1283,6 +1299,13 @@ int create_impl(hlbm* h, const hlbm_grid_t* g) {
         launch_init_struct<T>(c, lr, lx, ly, g->u0x, g->u0y, s);
     }
     for (int k = 0; k < g->n_levels; ++k) level_couple<T>(h, k, 0, d.fA, a.bx0, a.by0, true, s);
+    // the initial buffers stand for the post-collision state at t = 0: the
+    // absorbing layer acts on them as on every later collision
+    {
+        Dev<T> di = g->n_levels ? ldev_of<T>(h->lv[g->n_levels - 1]) : d;
+        di.fB = di.fA;
+        launch_sponge<T>(di, s);
+    }
     h->ui = 1;  // the type-1 fill wrote the patch into fu[1]
     bind(h, d);
     launch_force<T>(d, 0, s);
@@ -1378,6 +1401,8 @@ struct CkptHeader {
     int32_t pbx0, pby0, ci, si, ui, fi;
     uint32_t status, pad;
     double mass, stiffness, damping, y0, v0;  // INDUCED motion parameters
+    int32_t sponge_rows, pad1;
+    double sponge_sigma;
     double Yi, Vi;                            // and its state at t
     int32_t n_levels, lv_cur[HLBM_MAX_LEVELS]; // nested levels and their current buffers
     int32_t lv_dim[HLBM_MAX_LEVELS][4];       // nx, ny, ox, oy of each
@@ -1406,7 +1431,7 @@ CkptHeader ckpt_header(hlbm* h) {
     Dev<T>& d = dev_of<T>(h);
     CkptHeader c{};
     std::memcpy(c.magic, kCkptMagic, 8);
-    c.version = 4;
+    c.version = 5;
     c.dtype = h->dtype;
     c.nx = d.nx;
     c.ny = d.ny;
@@ -1417,6 +1442,8 @@ CkptHeader ckpt_header(hlbm* h) {
     c.bh = d.bh;
     c.bc_x = h->grid.bc_x;
     c.bc_y = h->grid.bc_y;
+    c.sponge_rows = h->grid.sponge_rows;
+    c.sponge_sigma = h->grid.sponge_sigma;
     c.motion = h->motion.kind;
     c.lumped = h->patch.lumped;
     c.outer_fv = h->patch.outer_fv;
@@ -1516,7 +1543,7 @@ int load_impl(hlbm* h, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(h, HLBM_EIO, "cannot open %s", path);
     CkptHeader c{};
-    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 4) {
+    if (std::fread(&c, sizeof c, 1, fp) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 5) {
         std::fclose(fp);
         return fail(h, HLBM_EIO, "%s is not a solver checkpoint", path);
     }
@@ -1526,6 +1553,7 @@ int load_impl(hlbm* h, const char* path) {
                       c.bc_x == m.bc_x && c.bc_y == m.bc_y && c.motion == m.motion && c.lumped == m.lumped &&
                       c.outer_fv == m.outer_fv && c.mass == m.mass && c.stiffness == m.stiffness &&
                       c.damping == m.damping && c.y0 == m.y0 && c.v0 == m.v0 &&
+                      c.sponge_rows == m.sponge_rows && c.sponge_sigma == m.sponge_sigma &&
                       c.tau_s == m.tau_s && c.rho0 == m.rho0 && c.A == m.A && c.omega == m.omega &&
                       c.vx == m.vx && c.vy == m.vy && c.lamina_L == m.lamina_L && c.lamina_T == m.lamina_T &&
                       c.x_c == m.x_c && c.y_c == m.y_c && c.delta_f == m.delta_f && c.mesh_hash == m.mesh_hash &&
@@ -2191,6 +2219,10 @@ int hlbm_create(const hlbm_grid_t* grid, const hlbm_patch_t* patch, double tau_s
         rc = fail(h, HLBM_EINVAL, "unknown dtype %d", grid->dtype);
     else if (grid->bc_x < 0 || grid->bc_x > 2 || grid->bc_y < 0 || grid->bc_y > 2)
         rc = fail(h, HLBM_EINVAL, "unknown boundary kind");
+    else if (grid->sponge_rows < 0 || !(grid->sponge_sigma >= 0.0 && grid->sponge_sigma < 1.0) ||
+             (grid->sponge_rows > 0 && sponge_too_deep(grid)))
+        rc = fail(h, HLBM_EINVAL, "absorbing layer of %d rows at strength %g does not fit the lattice",
+                  (int)grid->sponge_rows, grid->sponge_sigma);
     else if (!(tau_s > 0.5))
         rc = fail(h, HLBM_EINVAL, "tau_s = %g must exceed 1/2", tau_s);
     else if (p.n_sub < 1 || !(1.0 / p.n_sub < 2.0 * (tau_s - 0.5)))
@@ -2541,8 +2573,9 @@ int hlbm_theta_adjoint(const hlbm_grid_t* grid, const hlbm_patch_t* patch, doubl
         return HLBM_EINVAL;
     }
     if (motion->kind != HLBM_MOTION_HARMONIC || !(motion->omega > 0) || motion->A == 0.0 || grid->n_levels != 0 ||
-        patch->outer_fv != 0 || (grid->dtype != HLBM_F64 && grid->dtype != HLBM_F32)) {
-        err = "hlbm_theta_adjoint: needs HARMONIC motion, one lattice level, outer_fv = 0 and FP64 or FP32";
+        patch->outer_fv != 0 || grid->sponge_rows != 0 || (grid->dtype != HLBM_F64 && grid->dtype != HLBM_F32)) {
+        err = "hlbm_theta_adjoint: needs HARMONIC motion, one lattice level, outer_fv = 0, no absorbing layer and "
+              "FP64 or FP32";
         return HLBM_EINVAL;
     }
     hlbm_t* h = nullptr;

@@ -175,6 +175,8 @@ struct Dev {
     int nx, ny, pitch;
     int64_t plane; // pitch * ny
     int bc_x, bc_y;
+    int sponge_rows;     // absorbing layer along this lattice's outflow sides (0: none)
+    double sponge_sigma;
     T* fA;         // post-collision populations read by this step [9][plane]
     T* fB;         // written by this step
     int store;     // lattice storage: 0 as T, HLBM_F16 or HLBM_BF16 (pointers then hold that type)
@@ -308,6 +310,22 @@ struct Store<float, __nv_bfloat16> {
         *reinterpret_cast<__nv_bfloat162*>(p + k) = __floats2bfloat162_rn(a, b);
     }
 };
+
+// The non-reflecting outflow reading of Sec. 5: the factor 1 - s(d) by which
+// the post-collision deviations of node (x, y) are damped, d its distance in
+// rows from the nearest outflow side, s(d) = sigma ((N - d)/N)^2; 1 outside
+// the layer (and on lattices without one).  Computed in FP64 in the order
+// the oracle writes it.
+template <typename T>
+__device__ __forceinline__ T sponge_keep(const Dev<T>& d, int x, int y) {
+    const int rows = d.sponge_rows;
+    int dist = rows;
+    if (d.bc_y == HLBM_BC_OUTFLOW) dist = min(dist, min(y, d.ny - 1 - y));
+    if (d.bc_x == HLBM_BC_OUTFLOW) dist = min(dist, min(x, d.nx - 1 - x));
+    if (dist >= rows) return T(1);
+    const double t = __ddiv_rn((double)(rows - dist), (double)rows);
+    return T(__dsub_rn(1.0, __dmul_rn(__dmul_rn(d.sponge_sigma, t), t)));
+}
 
 // Pull of population i at lattice node (x, y) from buffer A with the Sec. 5
 // boundaries: half-way bounce-back walls (taking precedence at corners),
@@ -555,6 +573,7 @@ template <typename T> void launch_fill(const Dev<T>& d, const StepArgs& a, cudaS
 template <typename T> void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s);
 template <typename T>
 void launch_stream_collide_rect(const Dev<T>& d, const StepArgs& a, int x0, int y0, int x1, int y1, cudaStream_t s);
+template <typename T> int launch_sponge(const Dev<T>& d, cudaStream_t s);
 template <typename T> void launch_struct_macro(const Dev<T>& d, double* rho, double* ux, double* uy,
                                                cudaStream_t s);
 // One coupling launch: the fine ring (into ring_dst) from coarse buffer c0

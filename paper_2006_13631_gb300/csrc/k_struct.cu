@@ -334,6 +334,52 @@ void launch_stream_collide(const Dev<T>& d, const StepArgs& a, cudaStream_t s) {
     launch_stream_collide_rect(d, a, 0, 0, d.nx, d.ny, s);
 }
 
+// The absorbing layer (non-reflecting outflow reading of Sec. 5) on the
+// post-collision populations stream-collide has just written to fB: the
+// nodes of [x0, x1) x [y0, y1) within sponge_rows of an outflow side are
+// damped towards the rest state (their deviations times 1 - s(d)).  Run
+// right after stream-collide, before anything reads fB, it gives the values
+// of a damping inside the collision.
+template <typename T, typename S>
+__global__ void k_sponge(Dev<T> d, int x0, int y0, int x1, int y1) {
+    const int x = x0 + blockIdx.x * blockDim.x + threadIdx.x, y = y0 + blockIdx.y;
+    if (x >= x1 || y >= y1) return;
+    const T keep = sponge_keep(d, x, y);
+    if (keep == T(1)) return;
+    S* B = reinterpret_cast<S*>(d.fB);
+    const int64_t s = (int64_t)y * d.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        Store<T, S>::st(B, i * d.plane + s, mul_rn(keep, Store<T, S>::ld(B, i * d.plane + s, d.finv)), d.fscale);
+}
+
+// the layer's rows along the y sides (whole rows), then its columns along the
+// x sides between them, so that every node is damped once; returns launches
+template <typename T>
+int launch_sponge(const Dev<T>& d, cudaStream_t s) {
+    const int N = d.sponge_rows;
+    if (N <= 0 || d.sponge_sigma == 0.0) return 0;
+    int n = 0;
+    auto rect = [&](int x0, int y0, int x1, int y1) {
+        if (x1 <= x0 || y1 <= y0) return;
+        dim3 grid((x1 - x0 + 127) / 128, y1 - y0);
+        with_store(d, [&]<typename S>() { k_sponge<T, S><<<grid, 128, 0, s>>>(d, x0, y0, x1, y1); });
+        ++n;
+    };
+    int ya = 0, yb = d.ny;
+    if (d.bc_y == HLBM_BC_OUTFLOW) {
+        rect(0, 0, d.nx, N);
+        rect(0, d.ny - N, d.nx, d.ny);
+        ya = N;
+        yb = d.ny - N;
+    }
+    if (d.bc_x == HLBM_BC_OUTFLOW) {
+        rect(0, ya, N, yb);
+        rect(d.nx - N, ya, d.nx, yb);
+    }
+    return n;
+}
+
 // the nodes of [x0, x1) x [y0, y1) (x0 a multiple of 4)
 template <typename T>
 void launch_stream_collide_rect(const Dev<T>& d, const StepArgs& a, int x0, int y0, int x1, int y1, cudaStream_t s) {
@@ -357,6 +403,16 @@ __global__ void k_struct_macro(Dev<T> d, double* rho, double* ux, double* uy) {
     T f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = Store<T, S>::ld(A, i * d.plane + s, d.finv);
+    // the buffer holds post-collision populations, whose moments are those of
+    // the state (BGK conserves them) except inside the absorbing layer, where
+    // the layer scaled the deviations by keep: undo it for the moments
+    if (d.sponge_rows > 0) {
+        const T keep = sponge_keep(d, x, y);
+        if (keep != T(1)) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = f[i] / keep;
+        }
+    }
     T dr, r, vx, vy;
     moments_dev(f, d.rho0, dr, r, vx, vy);
     int64_t g = (int64_t)y * d.nx + x;
@@ -512,6 +568,7 @@ void launch_couple(const Dev<T>& d, const Refine& r, const Couple& c, cudaStream
     template void launch_fill<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                          \
     template void launch_stream_collide<T>(const Dev<T>&, const StepArgs&, cudaStream_t);                \
     template void launch_stream_collide_rect<T>(const Dev<T>&, const StepArgs&, int, int, int, int, cudaStream_t); \
+    template int launch_sponge<T>(const Dev<T>&, cudaStream_t);                                           \
     template void launch_struct_macro<T>(const Dev<T>&, double*, double*, double*, cudaStream_t);        \
     template void launch_couple<T>(const Dev<T>&, const Refine&, const Couple&, cudaStream_t);
 HLBM_INST(float)

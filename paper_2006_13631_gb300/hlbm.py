@@ -79,6 +79,7 @@ def _structs(grid: dict, patch: dict, motion: dict):
     g.rho_init = _dp(arr(grid.get("rho_init"), np.float64))
     g.ux_init = _dp(arr(grid.get("ux_init"), np.float64))
     g.uy_init = _dp(arr(grid.get("uy_init"), np.float64))
+    g.sponge_rows, g.sponge_sigma = int(grid.get("sponge_rows", 0)), float(grid.get("sponge_sigma", 0.0))
     levels = grid.get("levels") or []
     g.n_levels = len(levels)
     if levels:
@@ -326,7 +327,8 @@ def workload_inputs(w, mesh=None, rho_init=None, u_init=None, level_u_init=None,
     mesh = mesh if mesh is not None else w.mesh()
     rho = rho_init if rho_init is not None else w.rho_init()
     grid = dict(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, dtype=w.dtype, rho0=w.rho0, u0x=w.u0x,
-                u0y=w.u0y, rho_init=rho,
+                u0y=w.u0y, rho_init=rho, sponge_rows=getattr(w, "sponge_rows", 0),
+                sponge_sigma=getattr(w, "sponge_sigma", 0.0),
                 ux_init=None if u_init is None else u_init[0], uy_init=None if u_init is None else u_init[1])
     levels = list(getattr(w, "levels", []))
     if levels:

@@ -87,6 +87,23 @@ def test_levels_parity(name, chunks, tol_u, tol_rho):
     assert info["launches_per_step"] == 8 + 2 * len(w.levels)
 
 
+def test_levels_parity_with_absorbing_layer_on_the_coarsest():
+    """The absorbing outflow layer belongs to the lattice that carries the
+    domain boundary: with three levels it acts on the coarsest only (6 of
+    its rows along each outflow side), in the oracle and in the CUDA path."""
+    w = inputs.workload("lamina-small-levels3-f64")
+    w.sponge_rows, w.sponge_sigma = 6, 0.1
+    s, o = pair(w)
+    for c in (3, 29):
+        s.step(c)
+        o.step(c)
+        assert np.array_equal(s.struct_class(), o.struct_class())
+        e = errors(s, o, len(w.levels))
+        assert all(v < 2e-9 for k, v in e.items() if k.endswith("_u")), e
+        assert all(v < 1e-12 for k, v in e.items() if k.endswith("_rho")), e
+    assert s.status == 0 and o.status == 0
+
+
 def test_levels_ring_and_restriction_are_consistent():
     """Invariants at any size: after 2^levels steps, the nodes of each level
     strictly inside the box of the level below equal the finer nodes under

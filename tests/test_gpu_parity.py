@@ -416,3 +416,31 @@ def test_overlap_of_the_far_lattice_changes_no_bit(tmp_path):
         assert np.array_equal(a[key], b[key]), key
         assert np.array_equal(a[key], c[key]), key
     assert on.status == 0 and off.status == 0 and back.status == 0
+
+
+@pytest.mark.parametrize("dtype,tol_u,tol_rho", [("f64", 2e-9, 1e-12), ("f32", 1e-5, 1e-5)])
+def test_parity_absorbing_outflow_layer(dtype, tol_u, tol_rho):
+    """The non-reflecting outflow reading (an absorbing layer of 24 rows along
+    the outflow sides y = 0 and ny - 1): the CUDA path (a layer kernel after
+    each stream-collide, with the overlap of the far lattice on) against the
+    oracle's R13 in the collision; classes and donors bit-exact.  The layer
+    must change the fields against the plain outflow."""
+    from paper_2006_13631_gb300 import Solver
+
+    w = inputs.workload("lamina-small-f32")
+    w.dtype = dtype
+    w.sponge_rows, w.sponge_sigma = 24, 0.1
+    mesh, rho = w.mesh(), w.rho_init()
+    s = Solver(w, mesh=mesh, rho_init=rho)
+    o = oracle.Oracle(w, mesh=mesh, rho_init=rho)
+    for chunk in (3, 60, 57):
+        s.step(chunk)
+        o.step(chunk)
+        compare_geometry(s, o)
+    compare_fields(s, o, tol_u, tol_rho)
+    w.sponge_rows, w.sponge_sigma = 0, 0.0
+    plain = Solver(w, mesh=mesh, rho_init=rho)
+    plain.step(120)
+    r_layer, r_plain = s.fields()[0], plain.fields()[0]
+    assert np.abs(r_layer[:24] - r_plain[:24]).max() > 1e-9
+    assert s.status == 0
