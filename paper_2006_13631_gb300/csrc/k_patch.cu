@@ -1509,15 +1509,22 @@ __device__ __forceinline__ void deep_node(const Dev<T>& d, const unsigned char* 
         cP = __uint_as_float(hdr[0]);
         const int ne = kind != HLBM_NODE_OUTER ? (int)hdr[1] : 0;
         const int nem = (int)__reduce_max_sync(0xffffffffu, (unsigned)ne);
+        // two entries per tensor-memory load (one wait for both; entry 7 of
+        // the last pair reads the next columns, which no row uses)
 #pragma unroll
-        for (int j = 0; j < kTmemMaxEntries; ++j) {
+        for (int j = 0; j < kTmemMaxEntries; j += 2) {
             if (j >= nem) break;
-            uint32_t e[4];
-            tmem_ld4(tslot + EW * (j + 1), e);
+            uint32_t e[8];
+            tmem_ld8(tslot + EW * (j + 1), e);
             if (j < ne) {
                 T f[9], z[3];
                 read_rec12(cur + (size_t)kSR * (int)e[3], f, z);
                 fv_acc_entry(acc, __uint_as_float(e[0]), __uint_as_float(e[1]), __uint_as_float(e[2]), f, z, fP);
+            }
+            if (j + 1 < ne) {
+                T f[9], z[3];
+                read_rec12(cur + (size_t)kSR * (int)e[7], f, z);
+                fv_acc_entry(acc, __uint_as_float(e[4]), __uint_as_float(e[5]), __uint_as_float(e[6]), f, z, fP);
             }
         }
     } else {
