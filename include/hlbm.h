@@ -343,6 +343,13 @@ int hlbm_set_fv_depth(hlbm_t* h, int32_t depth);
  * stream-collide whole, before its FV launch. */
 int hlbm_set_overlap(hlbm_t* h, int32_t enable);
 
+/* The share (0, 1] of the lattice rows, from y = 0, whose part away from the
+ * patch the FV launch streams under the overlap; the next step's
+ * stream-collide covers the other rows with its rectangle (default 0.85:
+ * the FV launch then ends about when its far lattice does).  Results do not
+ * change.  HLBM_EINVAL outside (0, 1]. */
+int hlbm_set_overlap_share(hlbm_t* h, double share);
+
 /* Per-phase device time, measured with CUDA events recorded on the
  * solver's stream around each phase of hlbm_step while profiling is on.
  * hlbm_profile(h, 1) starts recording and clears the totals; (h, 0) stops.

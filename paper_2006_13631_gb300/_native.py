@@ -84,6 +84,7 @@ SIGNATURES = {
     "hlbm_clear_status": (C.c_int, [C.c_void_p]),
     "hlbm_set_fv_depth": (C.c_int, [C.c_void_p, C.c_int32]),
     "hlbm_set_overlap": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hlbm_set_overlap_share": (C.c_int, [C.c_void_p, C.c_double]),
     "hlbm_inject_fault": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "hlbm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hlbm_profile_read": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),

@@ -89,9 +89,13 @@ struct hlbm {
     // current post-collision buffer's successor already holds it outside
     // far_rect, which the next stream-collide then covers alone
     int overlap = 1;
+    // the share of the rows whose far part the FV launch streams: on the
+    // 4096^2 workload 0.85 gives 0.669 ms per step, all rows 0.692, 0.7 0.677
+    double overlap_share = 0.85;
     unsigned* far_next = nullptr;
     bool far_ready = false;
     int far_rect[4] = {0, 0, 0, 0};
+    int far_rows = 0;  // the far part covers rows [0, far_rows) outside far_rect
 
     int64_t t = 0;
     double Xprev = 0, Yprev = 0;
@@ -414,10 +418,17 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
         }
     int nr[4];
     near_rect(d.nx, d.ny, d.bw, d.bh, a.bx0, a.by0, nr);
-    if (h->far_ready && std::equal(nr, nr + 4, h->far_rect))
+    if (h->far_ready && std::equal(nr, nr + 4, h->far_rect)) {
+        // the rectangle, and the rows the FV launch left (a node in both is
+        // computed twice from the same inputs, to the same values)
         launch_stream_collide_rect<T>(d, a, nr[0], nr[1], nr[2], nr[3], s);
-    else
+        if (h->far_rows < d.ny) {
+            launch_stream_collide_rect<T>(d, a, 0, h->far_rows, d.nx, d.ny, s);
+            ++nl;
+        }
+    } else {
         launch_stream_collide<T>(d, a, s);
+    }
     h->far_ready = false;
     nl += launch_sponge<T>(d, s);  // the absorbing outflow layer, if any, on the step's output
     // restrictions (finest first) and the rings of the levels that just stepped
@@ -455,7 +466,8 @@ bool far_args(hlbm* h, const PendingStep& ps, FarArgs<T>& far) {
     far.ex1 = h->far_rect[2];
     far.ey1 = h->far_rect[3];
     far.n_seg = (d.nx + 63) / 64;
-    far.n_chunks = d.ny * far.n_seg;
+    h->far_rows = std::max(1, std::min(d.ny, (int)std::lround(h->overlap_share * d.ny)));
+    far.n_chunks = h->far_rows * far.n_seg;
     far.next = h->far_next;
     return true;
 }
@@ -2369,6 +2381,13 @@ int hlbm_clear_status(hlbm_t* h) {
 int hlbm_set_overlap(hlbm_t* h, int32_t enable) {
     if (!h) return HLBM_EINVAL;
     h->overlap = enable ? 1 : 0;
+    return HLBM_OK;
+}
+
+int hlbm_set_overlap_share(hlbm_t* h, double share) {
+    if (!h) return HLBM_EINVAL;
+    if (!(share > 0.0 && share <= 1.0)) return fail(h, HLBM_EINVAL, "overlap share %g is not in (0, 1]", share);
+    h->overlap_share = share;
     return HLBM_OK;
 }
 

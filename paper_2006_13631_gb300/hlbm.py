@@ -278,6 +278,10 @@ def hlbm_set_overlap(h, enable: bool = True):
     _check(N.load().hlbm_set_overlap(h, int(bool(enable))), h)
 
 
+def hlbm_set_overlap_share(h, share: float):
+    _check(N.load().hlbm_set_overlap_share(h, float(share)), h)
+
+
 def hlbm_clear_status(h):
     _check(N.load().hlbm_clear_status(h), h)
 

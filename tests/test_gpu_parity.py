@@ -390,20 +390,25 @@ def test_overlap_of_the_far_lattice_changes_no_bit(tmp_path):
     order: over a harmonic motion whose window moves, across single-step
     calls, and on through a checkpoint written while the precomputed part is
     pending."""
-    from paper_2006_13631_gb300 import Solver, hlbm_set_overlap
+    from paper_2006_13631_gb300 import Solver, hlbm_set_overlap, hlbm_set_overlap_share
 
     w = inputs.workload("lamina-small-f32")
     mesh, rho = w.mesh(), w.rho_init()
     on = Solver(w, mesh=mesh, rho_init=rho)
     off = Solver(w, mesh=mesh, rho_init=rho)
+    part = Solver(w, mesh=mesh, rho_init=rho)  # the FV launch streams the far part of 45 % of the rows
     hlbm_set_overlap(off.h, False)
+    hlbm_set_overlap_share(part.h, 0.45)
     assert on.info()["fv_kernel"] == 4
     for k in (5, 1, 1, 3, 1, 9):
         on.step(k)
     off.step(20)
-    a, b = _exact_state(on), _exact_state(off)
+    part.step(13)
+    part.step(7)
+    a, b, c = _exact_state(on), _exact_state(off), _exact_state(part)
     for key in a:
         assert np.array_equal(a[key], b[key]), key
+        assert np.array_equal(c[key], b[key]), key
     # a checkpoint taken now (the far part of step 20 is pending in `on`)
     path = str(tmp_path / "ck.bin")
     on.save(path)
