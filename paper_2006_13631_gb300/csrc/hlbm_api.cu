@@ -96,6 +96,13 @@ struct hlbm {
     bool far_ready = false;
     int far_rect[4] = {0, 0, 0, 0};
     int far_rows = 0;  // the far part covers rows [0, far_rows) outside far_rect
+    // the force of a step runs on a side stream beside the next step's
+    // relocation, classification and eq. 178 feed (it reads only the patch
+    // after the FV sub-steps); the next FV launch, which rewrites both patch
+    // buffers, waits for it, and every hlbm_step call joins it before returning
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fv = nullptr, ev_force = nullptr;
+    bool force_pending = false;
 
     int64_t t = 0;
     double Xprev = 0, Yprev = 0;
@@ -315,6 +322,7 @@ void phase_end(hlbm* h, int phase, int i, int launches, cudaStream_t s) {
 // fold recorded event pairs into the totals (synchronises the stream)
 int phase_collect(hlbm* h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && h->side) e = cudaStreamSynchronize(h->side);
     if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
     for (auto& m : h->ev_marks) {
         float ms = 0.f;
@@ -480,6 +488,10 @@ int step_fv(hlbm* h, cudaStream_t s, PendingStep& ps, cudaEvent_t ev0 = nullptr,
     // step's far stream-collide when lookahead is asked for and possible
     FarArgs<T> far{};
     const bool use_far = lookahead && far_args<T>(h, ps, far);
+    if (h->force_pending) {  // the previous step's force still reads a patch buffer
+        cudaStreamWaitEvent(s, h->ev_force, 0);
+        h->force_pending = false;
+    }
     if (use_far) cudaMemsetAsync(h->far_next, 0, sizeof(unsigned), s);
     int ev = phase_begin(h, s);
     if (ev0) cudaEventRecord(ev0, s);
@@ -515,12 +527,22 @@ void step_fv_packed_done(hlbm* h) {
 }
 
 template <typename T>
-int step_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
+int step_finish(hlbm* h, cudaStream_t s, const PendingStep& ps, bool on_side = false) {
     Dev<T>& d = dev_of<T>(h);
-    // 6. force on the lamina at t+1
-    int ev = phase_begin(h, s);
-    launch_force<T>(d, ps.a.t + 1, s);
-    phase_end(h, HLBM_PHASE_FORCE, ev, d.nseg > 0 ? 2 : 1, s);
+    // 6. force on the lamina at t+1 (on the side stream when asked)
+    cudaStream_t fs = s;
+    if (on_side && h->side) {
+        cudaEventRecord(h->ev_fv, s);
+        cudaStreamWaitEvent(h->side, h->ev_fv, 0);
+        fs = h->side;
+    }
+    int ev = phase_begin(h, fs);
+    launch_force<T>(d, ps.a.t + 1, fs);
+    phase_end(h, HLBM_PHASE_FORCE, ev, d.nseg > 0 ? 2 : 1, fs);
+    if (fs != s) {
+        cudaEventRecord(h->ev_force, fs);
+        h->force_pending = true;
+    }
     if (h->ev_used > 4096) {
         int rc = phase_collect(h);
         if (rc != HLBM_OK) return rc;
@@ -544,17 +566,29 @@ int step_finish(hlbm* h, cudaStream_t s, const PendingStep& ps) {
 
 template <typename T>
 int step_impl(hlbm* h, int64_t nsteps) {
-    for (int64_t k = 0; k < nsteps; ++k) {
-        PendingStep ps{};
-        int rc = step_lattice<T>(h, h->stream, ps);
-        if (rc == HLBM_OK) rc = step_fv<T>(h, h->stream, ps, nullptr, nullptr, true);
-        if (rc == HLBM_OK) rc = step_finish<T>(h, h->stream, ps);
-        if (rc != HLBM_OK) {
-            h->far_ready = false;
-            return rc;
-        }
+    // the force on a side stream, except with INDUCED motion (each step reads
+    // the previous force on the host first)
+    const bool side = h->motion.kind != HLBM_MOTION_INDUCED;
+    if (side && !h->side) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_fv, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_force, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_check(h, cudaGetLastError(), "side stream");
     }
-    return HLBM_OK;
+    int rc = HLBM_OK;
+    for (int64_t k = 0; k < nsteps && rc == HLBM_OK; ++k) {
+        PendingStep ps{};
+        rc = step_lattice<T>(h, h->stream, ps);
+        if (rc == HLBM_OK) rc = step_fv<T>(h, h->stream, ps, nullptr, nullptr, true);
+        if (rc == HLBM_OK) rc = step_finish<T>(h, h->stream, ps, side);
+    }
+    // join: whatever the caller does next on the solver's stream sees the force
+    if (h->force_pending) {
+        cudaStreamWaitEvent(h->stream, h->ev_force, 0);
+        h->force_pending = false;
+    }
+    if (rc != HLBM_OK) h->far_ready = false;
+    return rc;
 }
 
 // Deep-tile tables (k_fv_deep) for the tiles [tile_start[k], tile_start[k+1])
@@ -3092,6 +3126,12 @@ const char* hlbm_last_error(const hlbm_t* h) { return h ? h->err.c_str() : g_cre
 void hlbm_destroy(hlbm_t* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->ev_fv) cudaEventDestroy(h->ev_fv);
+    if (h->ev_force) cudaEventDestroy(h->ev_force);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->st_event) cudaEventDestroy(h->st_event);
     if (h->st_host) cudaFreeHost(h->st_host);
