@@ -124,3 +124,26 @@ def test_adjoint_rejects_what_it_does_not_cover():
     motion["kind"] = inputs.MOTION_STATIC
     with pytest.raises(HLBMError):
         hlbm_theta_adjoint(grid, patch, w.tau_s, motion, STEPS, DISCARD, FIT, 1.0, 0.0, 16)
+
+
+@pytest.mark.slow
+def test_adjoint_matches_oracle_tangent_over_eight_periods():
+    """A longer window: 200 steps (8.4 periods, the fit over all but the
+    first half period).  The oracle's FP64 tangent still has one branch of
+    decisions over the whole run (its lockstep runs at -/+ 1e-6 take the same
+    classes and refill types), and the adjoint equals it in A, omega and
+    tau_s; measured to 8-10 digits."""
+    from paper_2006_13631_gb300 import hlbm_theta_adjoint, workload_inputs
+
+    w = _case()
+    mesh, rho = w.mesh(), w.rho_init()
+    steps, discard = 200, 0.5
+    fit = (steps - 1) * w.omega / (2.0 * math.pi) - discard
+    grid, patch, motion = workload_inputs(w, mesh, rho)
+    _, g_re, _, _ = hlbm_theta_adjoint(grid, patch, w.tau_s, motion, steps, discard, fit, 1.0, 0.0, 64)
+    _, g_im, _, _ = hlbm_theta_adjoint(grid, patch, w.tau_s, motion, steps, discard, fit, 0.0, 1.0, 64)
+    tangent, _ = oracle.theta_tangent(w, steps, discard, fit, mesh=mesh, rho_init=rho)
+    t_re = np.array([g.real for g in tangent])
+    t_im = np.array([g.imag for g in tangent])
+    assert np.abs(np.asarray(g_re) - t_re).max() < 1e-6 * np.abs(t_re).max()
+    assert np.abs(np.asarray(g_im) - t_im).max() < 1e-6 * np.abs(t_im).max()
