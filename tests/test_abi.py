@@ -90,3 +90,22 @@ def test_create_rejects_bad_levels_without_touching_the_gpu(lib_path):
     refused(203, [(210, 167, 52, 43), (216, 176, 53, 44)], text="odd sizes")
     refused(203, [(204, 160, 51, 40)] * 5, text="n_levels")
     refused(203, [(211, 167, 52, 43), (216, 176, 53, 44)], tau=2.5, n_sub=4, text="tau of level 2")
+
+
+def test_create_rejects_a_bad_absorbing_layer_without_touching_the_gpu(lib_path):
+    """The non-reflecting outflow's layer is checked before any device work:
+    negative depth, a strength outside [0, 1), and a layer reaching half way
+    across the lattice side it lies along are refused with HLBM_EINVAL."""
+    import inputs
+    from paper_2006_13631_gb300 import hlbm as H
+
+    w = inputs.workload("lamina-small-f32")
+    m = w.mesh()
+    patch = dict(xy=m.xy, tri=m.tri, kind=m.kind, lamina_L=w.L, lamina_T=w.T, x_c=w.xc, y_c=w.yc,
+                 delta_f=w.delta_f, n_sub=w.n_sub, lumped=0)
+    motion = dict(kind=1, A=w.A, omega=w.omega)
+    for rows, sigma in ((-1, 0.1), (10, 1.0), (10, -0.1), ((w.ny + 1) // 2, 0.1)):
+        grid = dict(nx=w.nx, ny=w.ny, dtype="f32", sponge_rows=rows, sponge_sigma=sigma)
+        with pytest.raises(H.HLBMError) as e:
+            H.hlbm_create(grid, patch, w.tau_s, motion)
+        assert e.value.code == -1 and "absorbing layer" in str(e.value), (rows, sigma)
