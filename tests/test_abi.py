@@ -109,3 +109,13 @@ def test_create_rejects_a_bad_absorbing_layer_without_touching_the_gpu(lib_path)
         with pytest.raises(H.HLBMError) as e:
             H.hlbm_create(grid, patch, w.tau_s, motion)
         assert e.value.code == -1 and "absorbing layer" in str(e.value), (rows, sigma)
+
+
+def test_study_runner_prints_its_usage_without_points():
+    """The chord-800 study runner (python -m paper_2006_13631_gb300.study)
+    needs an output file and at least one point; without them it prints its
+    usage and returns 2, touching no GPU."""
+    from paper_2006_13631_gb300 import study
+
+    assert study.main([]) == 2
+    assert study.main(["out.json"]) == 2
