@@ -101,7 +101,7 @@ struct hlbm {
     // after the FV sub-steps); the next FV launch, which rewrites both patch
     // buffers, waits for it, and every hlbm_step call joins it before returning
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fv = nullptr, ev_force = nullptr;
+    cudaEvent_t ev_fv = nullptr, ev_force = nullptr, ev_move = nullptr, ev_cls = nullptr;
     bool force_pending = false;
 
     int64_t t = 0;
@@ -406,11 +406,24 @@ int step_lattice(hlbm* h, cudaStream_t s, PendingStep& ps) {
     d.sbox_new = (T*)h->sbox[1 - h->si];
     int ev = phase_begin(h, s);
     if (t > 0) {
+        // 2. classify the lattice nodes against the moved fictitious curve: on
+        // the side stream beside the refill when the solver steps on its own
+        // stream (classification is geometry only, and the class buffer it
+        // writes was last read by the previous step's refill and feed)
+        const bool cls_side = h->side && s == h->stream;
+        if (cls_side) {
+            cudaEventRecord(h->ev_move, s);
+            cudaStreamWaitEvent(h->side, h->ev_move, 0);
+            launch_classify<T>(d, a, h->side);
+            cudaEventRecord(h->ev_cls, h->side);
+        }
         launch_refill<T>(d, a, s);
         h->ui = 1 - h->ui;
         bind(h, d);
-        // 2. classify the lattice nodes against the moved fictitious curve
-        launch_classify<T>(d, a, s);
+        if (cls_side)
+            cudaStreamWaitEvent(s, h->ev_cls, 0);
+        else
+            launch_classify<T>(d, a, s);
     }
     // 3. interpolation nodes from the patch (eq. postcollision2_s)
     launch_fill<T>(d, a, s);
@@ -572,7 +585,9 @@ int step_impl(hlbm* h, int64_t nsteps) {
     if (side && !h->side) {
         if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h->ev_fv, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->ev_force, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&h->ev_force, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_move, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_cls, cudaEventDisableTiming) != cudaSuccess)
             return cuda_check(h, cudaGetLastError(), "side stream");
     }
     int rc = HLBM_OK;
@@ -3130,8 +3145,8 @@ void hlbm_destroy(hlbm_t* h) {
         cudaStreamSynchronize(h->side);
         cudaStreamDestroy(h->side);
     }
-    if (h->ev_fv) cudaEventDestroy(h->ev_fv);
-    if (h->ev_force) cudaEventDestroy(h->ev_force);
+    for (cudaEvent_t e : {h->ev_fv, h->ev_force, h->ev_move, h->ev_cls})
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->st_event) cudaEventDestroy(h->st_event);
     if (h->st_host) cudaFreeHost(h->st_host);
